@@ -1,0 +1,61 @@
+"""Planted mistakes in the oracle (CPU only): each must be caught by a pin.
+
+A pin that cannot fail proves nothing; these tests plant plausible errors
+(a transposed leg order, an off-by-one truncation) in
+the oracle and check that the comparison against brute force notices.
+"""
+import math
+
+import numpy as np
+
+import synthetic as syn
+from oracle import exact, tn
+from oracle.blockbp import BlockBP
+from oracle.geometry import Geometry
+
+
+def _single_block_error(monkeypatch_ctx=None, chi=10 ** 4, D=2):
+    geom = Geometry.square(3, 3, 3, 3)
+    t = syn.gaussian_peps(9, 2, D, seed=12)
+    bb = BlockBP(geom, t, chi=chi)
+    zex = exact.norm(geom.lattice, t)
+    try:
+        l, z = bb.contract([(0, 0)])
+    except Exception:
+        return math.inf
+    return abs(z * math.exp(l) - zex) / abs(zex)
+
+
+def test_clean_oracle_is_exact():
+    assert _single_block_error() < 1e-12
+
+
+def test_out_leg_order_flip_is_caught(monkeypatch):
+    real_transpose = np.transpose
+    calls = {"n": 0}
+
+    def bad_transpose(a, axes=None):
+        # reverse the out-leg order of every swallowed site tensor (4 legs)
+        if axes is not None and len(axes) == 4 and a.ndim == 4:
+            calls["n"] += 1
+            axes = list(axes)
+            nin = 2
+            axes = axes[:nin] + axes[nin:][::-1]
+        return real_transpose(a, axes)
+    monkeypatch.setattr(tn.np, "transpose", bad_transpose)
+    assert _single_block_error() > 1e-6
+    assert calls["n"] > 0
+
+
+def test_truncation_off_by_one_is_caught(monkeypatch):
+    real = tn.svd_split
+
+    def bad_split(R, chi):
+        sh = R.shape
+        M = R.reshape(sh[0] * sh[1], -1)
+        U, s, Vh = np.linalg.svd(M, full_matrices=False)
+        k = max(1, min(chi, M.shape[0], M.shape[1]) - 1)    # keeps one too few
+        return U[:, :k].reshape(sh[0], sh[1], k), (s[:k, None] * Vh[:k]).reshape((k,) + sh[2:])
+    monkeypatch.setattr(tn, "svd_split", bad_split)
+    assert _single_block_error() > 1e-8
+    monkeypatch.setattr(tn, "svd_split", real)
