@@ -1,0 +1,182 @@
+/*
+ * bbp.h -- C ABI of the GB300 BlockBP message-update engine.
+ *
+ * The engine approximately contracts the double-layer network <psi|psi> of a
+ * PEPS by Block Belief Propagation (arxiv 2603.13304, Ch. 2): the lattice is
+ * cut into blocks; each block sends to every neighbouring block an MPS
+ * "message" obtained by contracting the block with all its other incoming
+ * messages (Eq. of the BlockBP update, Sec. 2.2) by a boundary-MPS sweep with
+ * truncation bond dimension chi (Sec. 1.1.3); all messages are updated
+ * synchronously until they stop changing (Alg. 1).  Local expectation values
+ * follow from a block contracted with its converged incoming messages.
+ *
+ * Conventions
+ *  - Complex numbers are interleaved (re, im) IEEE doubles ("complex128").
+ *  - Every function returns a bbp_status; on failure bbp_last_error(ctx)
+ *    (or bbp_last_error(NULL) for failures without a context) describes it.
+ *    Nothing is thrown across the ABI.
+ *  - Host buffers are owned by the caller and never retained after a call.
+ *    Device memory is owned by the context; it is taken from the allocator
+ *    installed with bbp_set_allocator (default cudaMalloc / cudaFree).
+ *  - All device work is ordered on the CUDA stream given at creation; calls
+ *    that return host values synchronise that stream.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Input layout of PEPS tensors ("site tensors"): complex128
+ * [n_sites][d][D][D][D][D], the four virtual legs in slot order:
+ *   square  (Lx x Ly sites): site r*Lx + c (row r from the top, column c);
+ *           slots (up, right, down, left).  On an open boundary the outward
+ *           leg is closed with the unit vector e_0 (only index 0 is read).
+ *   Kagome  (Lx x Ly unit cells, always periodic): unit cell u = j*Lx + i
+ *           holds sites 3u (A), 3u+1 (B = A + a1/2), 3u+2 (C = A + a2/2);
+ *           slots A: B(i,j), C(i,j), B(i-1,j), C(i,j-1)
+ *                 B: A(i,j), C(i,j), A(i+1,j), C(i+1,j-1)
+ *                 C: A(i,j), B(i,j), A(i,j+1), B(i-1,j+1).
+ * A fused (double-layer) leg index is ket * D + bra.
+ */
+#ifndef BBP_H
+#define BBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bbp_ctx bbp_ctx;
+
+typedef enum {
+  BBP_OK = 0,
+  BBP_ERR_ARG = 1,          /* invalid argument or size                         */
+  BBP_ERR_OOM = 2,          /* device allocation failed                          */
+  BBP_ERR_CUDA = 3,         /* a CUDA call failed                                */
+  BBP_ERR_TILING = 4,       /* the block partition breaks the rules of Sec. 2.2.2 */
+  BBP_ERR_NUMERIC = 5,      /* NaN/Inf or an SVD that did not converge           */
+  BBP_NOT_CONVERGED = 6,    /* max_iter reached; messages remain valid           */
+  BBP_ERR_TIMEOUT = 7,      /* a bounded device wait ran out                     */
+  BBP_ERR_STATE = 8         /* call out of order (e.g. iterate before partition) */
+} bbp_status;
+
+typedef enum { BBP_SQUARE = 0, BBP_KAGOME = 1 } bbp_lattice;
+typedef enum { BBP_FP64 = 0, BBP_TF32 = 1, BBP_BF16 = 2 } bbp_precision;
+typedef enum { BBP_BOTTOM = 0, BBP_RIGHT = 1, BBP_TOP = 2, BBP_LEFT = 3 } bbp_face;
+
+/* Device allocator used by every context created afterwards.  alloc returns
+ * NULL on failure; free releases a pointer returned by alloc.  user is passed
+ * back verbatim.  Passing NULL functions restores cudaMalloc / cudaFree. */
+typedef void* (*bbp_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*bbp_free_fn)(void* ptr, void* stream, void* user);
+void bbp_set_allocator(bbp_alloc_fn alloc, bbp_free_fn free_fn, void* user);
+
+/* Create a PEPS context (Sec. 1.1.2, PEPS; Sec. 2.1, double layer).
+ * lattice: BBP_SQUARE (periodic 0 = open, 1 = torus) or BBP_KAGOME
+ * (periodic must be 1).  d: physical dimension; D: bond dimension (<= 8).
+ * host_tensors: layout above, d * D^4 complex128 per site, copied to the
+ * device.  cuda_stream: a cudaStream_t (NULL = legacy default stream). */
+bbp_status bbp_create_peps(bbp_ctx** out, int lattice, int Lx, int Ly, int periodic, int d, int D,
+                           const double* host_tensors, void* cuda_stream);
+
+/* Cut the lattice into blocks (Sec. 2.2.2): square blocks of bx x by sites;
+ * Kagome L x L parallelograms of unit cells with bx = by = L >= 2
+ * (N_T = 3 L^2, Sec. 2.3.1).  Fails with BBP_ERR_TILING when a block would
+ * not tile the lattice or a bond would leave a face diagonally. */
+bbp_status bbp_partition_blocks(bbp_ctx* ctx, int bx, int by);
+
+/* chi: truncation bond dimension of the boundary MPS (Sec. 1.1.3), 1..64.
+ * precision: BBP_FP64 (all arithmetic complex128).  alpha must be 1
+ * (undamped update).  seed is reserved. */
+bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, uint64_t seed);
+
+/* Initial messages (Alg. 1, "random MPS"): every incoming message becomes a
+ * bond-1 MPS whose leg j carries the D x D matrix edge_mats[s][k] of the
+ * receiving site s and its slot k.  edge_mats: complex128 [n_sites][4][D][D].
+ * Messages are normalised to unit norm with <I|M> real positive. */
+bbp_status bbp_init_messages(bbp_ctx* ctx, const double* edge_mats);
+
+/* Synchronous BlockBP iterations (Alg. 1, Eq. of the BlockBP update) until the
+ * largest message change ||M_new - M_old|| (unit-norm, phase-fixed messages)
+ * is <= tol, or max_iter iterations.  iters_out / err_out (may be NULL)
+ * receive the iterations done and the last largest change.  Returns
+ * BBP_NOT_CONVERGED when max_iter was reached (messages stay valid). */
+bbp_status bbp_iterate(bbp_ctx* ctx, double tol, int max_iter, int* iters_out, double* err_out);
+
+/* <O> for a one- or two-site operator with the converged messages.
+ * ns = 1: op is d x d complex128 on site sites[0].
+ * ns = 2: op is (d*d) x (d*d) complex128 on the pair (sites[0], its
+ *   neighbour through slot sites[1]), basis index s0 * d + s1.  If the two
+ *   sites lie in different blocks the union of both blocks is contracted.
+ * The block (or union) is contracted with all its incoming messages by a
+ * sweep to its top face; <O> = Z(O) / Z(1). */
+bbp_status bbp_expect_local(bbp_ctx* ctx, const double* op, int ns, const int* sites, double* re_out,
+                            double* im_out);
+
+/* Reduced density matrix of nsites (1 or 2) sites of one block: rdm_out
+ * receives (d^n x d^n) complex128, trace 1, basis index s0 * d + s1.
+ * For nsites = 2 the sites may be any two sites of that block. */
+bbp_status bbp_block_rdm(bbp_ctx* ctx, int block, const int* sites, int nsites, double* rdm_out);
+
+/* Heisenberg energy per site, sum over all nearest-neighbour bonds of
+ * <S_i . S_j> (Eq. of the AFM Heisenberg Hamiltonian, Sec. 4.2) divided by the
+ * number of sites; d must be 2. */
+bbp_status bbp_energy_per_site(bbp_ctx* ctx, double* e_out);
+
+/* Bethe-form log-norm: sum_a log Z_a - sum_pairs log <M_a->b, M_b->a>
+ * (real part), Z_a = block a with all incoming messages. */
+bbp_status bbp_norm(bbp_ctx* ctx, double* log_norm_out);
+
+/* Copy the incoming message of (block, face) to the host.  k_out receives
+ * the number of tensors, shapes_out (capacity 3*64 ints) the (l, p, r) of each,
+ * data_out (capacity cap doubles) the tensors back to back, row-major. */
+bbp_status bbp_get_message(bbp_ctx* ctx, int block, int face, int* k_out, int* shapes_out, double* data_out,
+                           size_t cap);
+
+/* Device bytes the context would hold for the given problem (estimate). */
+size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int by, int precision);
+
+/* Number of blocks and of message updates per iteration. */
+bbp_status bbp_info(bbp_ctx* ctx, int* n_blocks, int* n_updates, int* n_sites);
+
+/* Statistics of the last bbp_iterate call: kernel launches per iteration and
+ * the algorithmic flops of one iteration (see the design doc for the flop model). */
+bbp_status bbp_stats(bbp_ctx* ctx, long long* launches_per_iter, double* flops_per_iter);
+
+const char* bbp_last_error(const bbp_ctx* ctx);
+void bbp_destroy(bbp_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * Kernel-level entry points (device pointers, for unit tests and tools).
+ * All take a cudaStream_t and return after enqueueing the work.
+ * ------------------------------------------------------------------- */
+
+/* K1, double-layer fusion (Sec. 2.1): t: device [d][D]^4; n[4]: used extent
+ * per leg (1 or D); perm[4]: output axis q is source leg perm[q]; op: device
+ * d x d or NULL; T: device output with prod n[perm[q]]^2 entries. */
+bbp_status bbp_k_fuse(const double* t, int d, int D, const int* n, const double* op, const int* perm, double* T,
+                      void* stream);
+
+/* K3, truncated SVD (Sec. 1.1.1): Z (m x n, device, row-major) = U S V^H;
+ * keep k = min(chi, m, n) largest; writes U (m x k) and Rem = S V^H (k x n).
+ * work: device scratch of bbp_k_svd_work_bytes(m, n) bytes; status: device int
+ * (0 converged, 1 sweep limit reached). */
+size_t bbp_k_svd_work_bytes(int m, int n);
+bbp_status bbp_k_svd_trunc(const double* Z, int m, int n, int chi, double* U, double* Rem, void* work, int* status,
+                           void* stream);
+
+/* Householder QR (Sec. 2.3.3 canonical moves): A (m x n, device, destroyed)
+ * = Q (m x k) R (k x n), k = min(m, n); tau: device scratch of k complex. */
+bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, void* stream);
+
+/* Host-side plan of one boundary-MPS sweep (no GPU needed): for block `block`
+ * and out face `face`, the swallow order as (kind, id) pairs: kind 0 = site
+ * (id = global site id), kind 1 = message tensor (id = face * 1024 + index),
+ * and per step the number of in- and out-legs.  out: capacity cap ints,
+ * 4 ints per step: kind, id, nin, nout.  n_steps_out receives the count. */
+bbp_status bbp_plan_debug(int lattice, int Lx, int Ly, int periodic, int bx, int by, int block, int face, int* out,
+                          int cap, int* n_steps_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBP_H */

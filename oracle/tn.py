@@ -147,6 +147,7 @@ def sweep(region: Region, out_dir: int, T: dict, msgs: dict, chi: int, trace: li
 
     # nodes: (key, kind, payload)
     nodes = []
+    node_ident = {}
     for rs in region.sites:
         legs = []
         for k in range(4):
@@ -171,6 +172,7 @@ def sweep(region: Region, out_dir: int, T: dict, msgs: dict, chi: int, trace: li
                 a_next = math.atan2(ty, tx) % (2 * math.pi)
             a_phys = _angle(lat, e.mid4, e.inner4)
             legs = [(("b", d, m), a_prev), (e.label, a_phys), (("b", d, m + 1), a_next)]
+            node_ident[id(legs)] = (e.face[1], e.index)
             nodes.append((sweep_key(out_dir, e.mid4), "msg", (tens[m], legs)))
     nodes.sort(key=lambda z: z[0])
 
@@ -255,8 +257,9 @@ def sweep(region: Region, out_dir: int, T: dict, msgs: dict, chi: int, trace: li
         new_labels = [lab[q] for q in out_idx]
         nout = len(out_idx)
         if trace is not None:
+            ident = ("site", rs.gid) if kind == "site" else ("msg",) + node_ident[id(legs)]
             trace.append((key, kind, nin, nout, S.shape[0], S.shape[-1],
-                          [X.shape[q] for q in in_idx], [X.shape[q] for q in out_idx]))
+                          [X.shape[q] for q in in_idx], [X.shape[q] for q in out_idx], ident))
         if nout == 0:
             if i > 0:
                 A[i - 1] = np.tensordot(A[i - 1], R, axes=(2, 0))

@@ -1,0 +1,275 @@
+"""ctypes binding of the BlockBP C ABI (include/bbp.h): argument marshalling only.
+
+Each ``bbp_*`` function here has the name and meaning of the C entry point;
+NumPy arrays are passed as host pointers, torch tensors (or integers) as
+device pointers.  Every non-OK status raises ``BBPError`` carrying the
+library's message.  Loading fails loudly when the library is missing: there
+is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+STATUS = {
+    0: "BBP_OK", 1: "BBP_ERR_ARG", 2: "BBP_ERR_OOM", 3: "BBP_ERR_CUDA", 4: "BBP_ERR_TILING",
+    5: "BBP_ERR_NUMERIC", 6: "BBP_NOT_CONVERGED", 7: "BBP_ERR_TIMEOUT", 8: "BBP_ERR_STATE",
+}
+SQUARE, KAGOME = 0, 1
+FP64, TF32, BF16 = 0, 1, 2
+BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
+
+EXPORTS = [
+    "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
+    "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message",
+    "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
+    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_qr", "bbp_plan_debug",
+]
+
+
+class BBPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_keep = []   # ctypes callbacks kept alive
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_ALLOC = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
+_FREE = ctypes.CFUNCTYPE(None, _vp, _vp, _vp)
+
+_PROTOS = {
+    "bbp_set_allocator": (None, [_ALLOC, _FREE, _vp]),
+    "bbp_create_peps": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _i, _dp, _vp]),
+    "bbp_partition_blocks": (_i, [_vp, _i, _i]),
+    "bbp_set_options": (_i, [_vp, _i, _i, _d, ctypes.c_uint64]),
+    "bbp_init_messages": (_i, [_vp, _dp]),
+    "bbp_iterate": (_i, [_vp, _d, _i, _ip, _dp]),
+    "bbp_expect_local": (_i, [_vp, _dp, _i, _ip, _dp, _dp]),
+    "bbp_block_rdm": (_i, [_vp, _i, _ip, _i, _dp]),
+    "bbp_energy_per_site": (_i, [_vp, _dp]),
+    "bbp_norm": (_i, [_vp, _dp]),
+    "bbp_get_message": (_i, [_vp, _i, _i, _ip, _ip, _dp, ctypes.c_size_t]),
+    "bbp_footprint_bytes": (ctypes.c_size_t, [_i, _i, _i, _i, _i, _i, _i]),
+    "bbp_info": (_i, [_vp, _ip, _ip, _ip]),
+    "bbp_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _dp]),
+    "bbp_last_error": (ctypes.c_char_p, [_vp]),
+    "bbp_destroy": (None, [_vp]),
+    "bbp_k_fuse": (_i, [_vp, _i, _i, _ip, _vp, _ip, _vp, _vp]),
+    "bbp_k_svd_work_bytes": (ctypes.c_size_t, [_i, _i]),
+    "bbp_k_svd_trunc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "bbp_k_qr": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
+    "bbp_plan_debug": (_i, [_i, _i, _i, _i, _i, _i, _i, _i, _ip, _i, _ip]),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"BlockBP CUDA library not built ({LIB}); call paper_2603_13304_gb300.build.build()")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        msg = lib().bbp_last_error(ctx).decode()
+        raise BBPError(status, msg)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(_ip)
+
+
+def _devptr(x) -> int:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    import torch
+
+    def _alloc(size, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = _ALLOC(_alloc), _FREE(_free)
+    _keep.extend([a, f])
+    lib().bbp_set_allocator(a, f, None)
+
+
+def use_default_allocator():
+    lib().bbp_set_allocator(_ALLOC(0), _FREE(0), None)
+
+
+def _c128(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a.view(np.float64)
+
+
+# ------------------------------------------------------------ context calls
+
+def bbp_create_peps(lattice: int, Lx: int, Ly: int, periodic: int, d: int, D: int, tensors, stream=None):
+    t = _c128(tensors)
+    ctx = _vp()
+    _check(lib().bbp_create_peps(ctypes.byref(ctx), lattice, Lx, Ly, int(periodic), d, D, _dptr(t), _stream(stream)))
+    return ctx
+
+
+def bbp_partition_blocks(ctx, bx: int, by: int):
+    _check(lib().bbp_partition_blocks(ctx, bx, by), ctx)
+
+
+def bbp_set_options(ctx, chi: int, precision: int = FP64, alpha: float = 1.0, seed: int = 0):
+    _check(lib().bbp_set_options(ctx, chi, precision, alpha, seed), ctx)
+
+
+def bbp_init_messages(ctx, edge_mats):
+    e = _c128(edge_mats)
+    _check(lib().bbp_init_messages(ctx, _dptr(e)), ctx)
+
+
+def bbp_iterate(ctx, tol: float, max_iter: int, allow_not_converged: bool = True):
+    it = ctypes.c_int(0)
+    err = ctypes.c_double(0.0)
+    st = lib().bbp_iterate(ctx, tol, max_iter, ctypes.byref(it), ctypes.byref(err))
+    if st == 6 and allow_not_converged:
+        return it.value, err.value, False
+    _check(st, ctx)
+    return it.value, err.value, True
+
+
+def bbp_expect_local(ctx, op, sites):
+    o = _c128(op)
+    s = np.ascontiguousarray(sites, dtype=np.int32)
+    ns = len(s)   # [site] or [site, slot of the bond]
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bbp_expect_local(ctx, _dptr(o), ns, _iptr(s), ctypes.byref(re), ctypes.byref(im)), ctx)
+    return complex(re.value, im.value)
+
+
+def bbp_block_rdm(ctx, block: int, sites, d: int = 2):
+    s = np.ascontiguousarray(sites, dtype=np.int32)
+    dim = d ** len(s)
+    out = np.zeros((dim, dim), dtype=np.complex128)
+    _check(lib().bbp_block_rdm(ctx, block, _iptr(s), len(s), _dptr(out.view(np.float64))), ctx)
+    return out
+
+
+def bbp_energy_per_site(ctx) -> float:
+    e = ctypes.c_double()
+    _check(lib().bbp_energy_per_site(ctx, ctypes.byref(e)), ctx)
+    return e.value
+
+
+def bbp_norm(ctx) -> float:
+    v = ctypes.c_double()
+    _check(lib().bbp_norm(ctx, ctypes.byref(v)), ctx)
+    return v.value
+
+
+def bbp_get_message(ctx, block: int, face: int, cap: int = 1 << 22):
+    k = ctypes.c_int()
+    shapes = np.zeros(3 * 64, dtype=np.int32)
+    data = np.zeros(cap, dtype=np.float64)
+    _check(lib().bbp_get_message(ctx, block, face, ctypes.byref(k), _iptr(shapes), _dptr(data), cap), ctx)
+    out, off = [], 0
+    for q in range(k.value):
+        l, p, r = shapes[3 * q:3 * q + 3]
+        n = int(l * p * r)
+        out.append(data[off:off + 2 * n].view(np.complex128).reshape(l, p, r).copy())
+        off += 2 * n
+    return out
+
+
+def bbp_footprint_bytes(lattice, n_sites, D, chi, bx, by, precision=FP64) -> int:
+    return int(lib().bbp_footprint_bytes(lattice, n_sites, D, chi, bx, by, precision))
+
+
+def bbp_info(ctx):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().bbp_info(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), ctx)
+    return a.value, b.value, c.value
+
+
+def bbp_stats(ctx):
+    n = ctypes.c_longlong()
+    f = ctypes.c_double()
+    _check(lib().bbp_stats(ctx, ctypes.byref(n), ctypes.byref(f)), ctx)
+    return n.value, f.value
+
+
+def bbp_last_error(ctx=None) -> str:
+    return lib().bbp_last_error(ctx).decode()
+
+
+def bbp_destroy(ctx):
+    lib().bbp_destroy(ctx)
+
+
+# ------------------------------------------------------------ kernel calls
+
+def bbp_k_fuse(t, d: int, D: int, n, op, perm, T, stream=None):
+    nn = np.ascontiguousarray(n, dtype=np.int32)
+    pp = np.ascontiguousarray(perm, dtype=np.int32)
+    _check(lib().bbp_k_fuse(_devptr(t), d, D, _iptr(nn), _devptr(op), _iptr(pp), _devptr(T), _stream(stream)))
+
+
+def bbp_k_svd_work_bytes(m: int, n: int) -> int:
+    return int(lib().bbp_k_svd_work_bytes(m, n))
+
+
+def bbp_k_svd_trunc(Z, m: int, n: int, chi: int, U, Rem, work, status, stream=None):
+    _check(lib().bbp_k_svd_trunc(_devptr(Z), m, n, chi, _devptr(U), _devptr(Rem), _devptr(work), _devptr(status),
+                                 _stream(stream)))
+
+
+def bbp_k_qr(A, m: int, n: int, Q, R, tau, stream=None):
+    _check(lib().bbp_k_qr(_devptr(A), m, n, _devptr(Q), _devptr(R), _devptr(tau), _stream(stream)))
+
+
+def bbp_plan_debug(lattice, Lx, Ly, periodic, bx, by, block, face):
+    out = np.zeros(4 * 4096, dtype=np.int32)
+    n = ctypes.c_int()
+    _check(lib().bbp_plan_debug(lattice, Lx, Ly, int(periodic), bx, by, block, face, _iptr(out), out.size,
+                                ctypes.byref(n)))
+    return out[:4 * n.value].reshape(-1, 4)

@@ -1,0 +1,358 @@
+// extern "C" boundary of the BlockBP engine (contract in include/bbp.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bbp.h"
+#include "engine.h"
+#include "kernels.h"
+
+struct bbp_ctx {
+  bbp::Engine eng;
+};
+
+namespace {
+thread_local std::string g_err;
+
+bbp_status set_err(bbp_status s, const std::string& m) {
+  g_err = m;
+  return s;
+}
+
+bbp_status from(bbp_ctx* c, int rc) {
+  if (rc != 0) g_err = c->eng.last_error;
+  return (bbp_status)rc;
+}
+
+bbp_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BBP_OK;
+  return set_err(BBP_ERR_CUDA, cudaGetErrorString(e));
+}
+
+template <typename F>
+bbp_status guarded(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return set_err(BBP_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return set_err(BBP_ERR_STATE, e.what());
+  } catch (...) {
+    return set_err(BBP_ERR_STATE, "unknown exception");
+  }
+}
+}  // namespace
+
+extern "C" {
+
+void bbp_set_allocator(bbp_alloc_fn alloc, bbp_free_fn free_fn, void* user) {
+  if (!alloc || !free_fn) bbp::set_allocator(nullptr, nullptr, nullptr);
+  else bbp::set_allocator(alloc, free_fn, user);
+}
+
+bbp_status bbp_create_peps(bbp_ctx** out, int lattice, int Lx, int Ly, int periodic, int d, int D,
+                           const double* host_tensors, void* cuda_stream) {
+  return guarded([&]() -> bbp_status {
+    if (!out) return set_err(BBP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    bbp_ctx* c = new bbp_ctx();
+    int rc = c->eng.create(lattice, Lx, Ly, periodic, d, D, host_tensors, (cudaStream_t)cuda_stream);
+    if (rc) {
+      g_err = c->eng.last_error;
+      delete c;
+      return (bbp_status)rc;
+    }
+    *out = c;
+    return BBP_OK;
+  });
+}
+
+bbp_status bbp_partition_blocks(bbp_ctx* ctx, int bx, int by) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  return guarded([&] { return from(ctx, ctx->eng.partition(bx, by)); });
+}
+
+bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, uint64_t seed) {
+  (void)seed;
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (chi < 1 || chi > 64) return set_err(BBP_ERR_ARG, "chi must be 1..64");
+  if (precision != BBP_FP64) return set_err(BBP_ERR_ARG, "this build implements precision BBP_FP64");
+  if (alpha != 1.0) return set_err(BBP_ERR_ARG, "only the undamped update (alpha = 1) is implemented");
+  if (ctx->eng.messages_ready) return set_err(BBP_ERR_STATE, "options must be set before bbp_init_messages");
+  ctx->eng.chi = chi;
+  ctx->eng.precision = precision;
+  return BBP_OK;
+}
+
+bbp_status bbp_init_messages(bbp_ctx* ctx, const double* edge_mats) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  return guarded([&] { return from(ctx, ctx->eng.init_messages(edge_mats)); });
+}
+
+bbp_status bbp_iterate(bbp_ctx* ctx, double tol, int max_iter, int* iters_out, double* err_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  return guarded([&] { return from(ctx, ctx->eng.iterate(tol, max_iter, iters_out, err_out)); });
+}
+
+bbp_status bbp_expect_local(bbp_ctx* ctx, const double* op, int ns, const int* sites, double* re_out,
+                            double* im_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!op || !sites || !re_out || !im_out) return set_err(BBP_ERR_ARG, "NULL argument");
+  if (ns != 1 && ns != 2) return set_err(BBP_ERR_ARG, "ns must be 1 or 2");
+  return guarded([&]() -> bbp_status {
+    bbp::Engine& e = ctx->eng;
+    if (!e.partitioned || !e.messages_ready) return set_err(BBP_ERR_STATE, "partition and messages are required first");
+    const int d = e.d;
+    const int n = e.geom.lat.n_sites();
+    if (sites[0] < 0 || sites[0] >= n) return set_err(BBP_ERR_ARG, "site out of range");
+    std::vector<std::array<int, 2>> coords;
+    std::array<int, 2> k1, k2;
+    if (ns == 1) {
+      int loc = -1;
+      int b = e.geom.home_block(sites[0], &loc);
+      coords = {{e.geom.blocks[b].X, e.geom.blocks[b].Y}};
+      k1 = {0, loc};
+    } else {
+      int rc = e.bond_region(sites[0], sites[1], coords, k1, k2);
+      if (rc) return from(ctx, rc);
+    }
+    // <O> = sum over the elementary operators |a><a'| (x) |b><b'| weighted by O
+    const int dim = ns == 1 ? d : d * d;
+    std::vector<std::vector<std::array<int, 2>>> C;
+    std::vector<std::vector<std::pair<std::array<int, 2>, const double*>>> O;
+    std::vector<double> elem;   // host copies of elementary d x d operators
+    std::vector<double2> w;     // weight of each contraction
+    const int nb = ns == 1 ? d * d : d * d * d * d;
+    elem.assign((size_t)(ns == 1 ? nb : 2 * nb) * d * d * 2, 0.0);
+    bbp::DBuf dev;
+    if (!dev.ensure(sizeof(double) * elem.size() + 256, e.stream)) return set_err(BBP_ERR_OOM, "allocation failed");
+    C.push_back(coords);
+    O.push_back({});
+    int slot = 0;
+    for (int a = 0; a < dim; ++a)
+      for (int ap = 0; ap < dim; ++ap) {
+        double2 wt = make_double2(op[2 * (a * dim + ap)], op[2 * (a * dim + ap) + 1]);
+        if (wt.x == 0.0 && wt.y == 0.0) continue;
+        w.push_back(wt);
+        std::vector<std::pair<std::array<int, 2>, const double*>> ops;
+        if (ns == 1) {
+          double* E = elem.data() + (size_t)slot * d * d * 2;
+          E[2 * (a * d + ap)] = 1.0;
+          ops.push_back({k1, (const double*)dev.p + (size_t)slot * d * d * 2});
+          ++slot;
+        } else {
+          int a0 = a / d, a1 = a % d, b0 = ap / d, b1 = ap % d;
+          double* E0 = elem.data() + (size_t)slot * d * d * 2;
+          double* E1 = elem.data() + (size_t)(slot + 1) * d * d * 2;
+          E0[2 * (a0 * d + b0)] = 1.0;
+          E1[2 * (a1 * d + b1)] = 1.0;
+          ops.push_back({k1, (const double*)dev.p + (size_t)slot * d * d * 2});
+          ops.push_back({k2, (const double*)dev.p + (size_t)(slot + 1) * d * d * 2});
+          slot += 2;
+        }
+        C.push_back(coords);
+        O.push_back(ops);
+      }
+    cudaError_t ce = cudaMemcpyAsync(dev.p, elem.data(), sizeof(double) * elem.size(), cudaMemcpyHostToDevice, e.stream);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    std::vector<double> ls, re, im;
+    int rc = e.contract_batch(C, O, ls, re, im);
+    if (rc) return from(ctx, rc);
+    double den = re[0] * re[0] + im[0] * im[0];
+    double sr = 0.0, si = 0.0;
+    for (size_t j = 1; j < C.size(); ++j) {
+      double sc = std::exp(ls[j] - ls[0]);
+      // ratio z_j / z_0
+      double rr = (re[j] * re[0] + im[j] * im[0]) / den * sc;
+      double ri = (im[j] * re[0] - re[j] * im[0]) / den * sc;
+      double2 wt = w[j - 1];
+      sr += wt.x * rr - wt.y * ri;
+      si += wt.x * ri + wt.y * rr;
+    }
+    *re_out = sr;
+    *im_out = si;
+    return BBP_OK;
+  });
+}
+
+bbp_status bbp_block_rdm(bbp_ctx* ctx, int block, const int* sites, int nsites, double* rdm_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!sites || !rdm_out || (nsites != 1 && nsites != 2)) return set_err(BBP_ERR_ARG, "bad arguments");
+  return guarded([&]() -> bbp_status {
+    bbp::Engine& e = ctx->eng;
+    if (!e.partitioned || !e.messages_ready) return set_err(BBP_ERR_STATE, "partition and messages are required first");
+    if (block < 0 || block >= e.geom.n_blocks()) return set_err(BBP_ERR_ARG, "block out of range");
+    const bbp::Block& b = e.geom.blocks[block];
+    std::array<int, 2> keys[2];
+    for (int q = 0; q < nsites; ++q) {
+      auto it = std::find(b.gids.begin(), b.gids.end(), sites[q]);
+      if (it == b.gids.end()) return set_err(BBP_ERR_ARG, "site not in block");
+      keys[q] = {0, (int)(it - b.gids.begin())};
+    }
+    const int d = e.d;
+    const int dim = nsites == 1 ? d : d * d;
+    std::vector<std::vector<std::array<int, 2>>> C(1 + dim * dim, std::vector<std::array<int, 2>>{{b.X, b.Y}});
+    std::vector<std::vector<std::pair<std::array<int, 2>, const double*>>> O(1 + dim * dim);
+    std::vector<double> elem((size_t)dim * dim * nsites * d * d * 2, 0.0);
+    bbp::DBuf dev;
+    if (!dev.ensure(sizeof(double) * elem.size() + 256, e.stream)) return set_err(BBP_ERR_OOM, "allocation failed");
+    for (int a = 0; a < dim; ++a)
+      for (int bb = 0; bb < dim; ++bb) {
+        const int j = a * dim + bb;
+        for (int q = 0; q < nsites; ++q) {
+          int ia = nsites == 1 ? a : (q == 0 ? a / d : a % d);
+          int ib = nsites == 1 ? bb : (q == 0 ? bb / d : bb % d);
+          double* E = elem.data() + ((size_t)j * nsites + q) * d * d * 2;
+          E[2 * (ib * d + ia)] = 1.0;   // |ib><ia| gives rho[ia, ib]
+          O[1 + j].push_back({keys[q], (const double*)dev.p + ((size_t)j * nsites + q) * d * d * 2});
+        }
+      }
+    cudaError_t ce = cudaMemcpyAsync(dev.p, elem.data(), sizeof(double) * elem.size(), cudaMemcpyHostToDevice, e.stream);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    std::vector<double> ls, re, im;
+    int rc = e.contract_batch(C, O, ls, re, im);
+    if (rc) return from(ctx, rc);
+    double den = re[0] * re[0] + im[0] * im[0];
+    std::vector<double> rho(2 * (size_t)dim * dim);
+    double tr_re = 0.0, tr_im = 0.0;
+    for (int j = 0; j < dim * dim; ++j) {
+      double sc = std::exp(ls[1 + j] - ls[0]);
+      rho[2 * j] = (re[1 + j] * re[0] + im[1 + j] * im[0]) / den * sc;
+      rho[2 * j + 1] = (im[1 + j] * re[0] - re[1 + j] * im[0]) / den * sc;
+      if (j / dim == j % dim) { tr_re += rho[2 * j]; tr_im += rho[2 * j + 1]; }
+    }
+    double tden = tr_re * tr_re + tr_im * tr_im;
+    for (int j = 0; j < dim * dim; ++j) {
+      double xr = rho[2 * j], xi = rho[2 * j + 1];
+      rdm_out[2 * j] = (xr * tr_re + xi * tr_im) / tden;
+      rdm_out[2 * j + 1] = (xi * tr_re - xr * tr_im) / tden;
+    }
+    return BBP_OK;
+  });
+}
+
+bbp_status bbp_energy_per_site(bbp_ctx* ctx, double* e_out) {
+  if (!ctx || !e_out) return set_err(BBP_ERR_ARG, "NULL argument");
+  return guarded([&] { return from(ctx, ctx->eng.energy_per_site(e_out)); });
+}
+
+bbp_status bbp_norm(bbp_ctx* ctx, double* log_norm_out) {
+  if (!ctx || !log_norm_out) return set_err(BBP_ERR_ARG, "NULL argument");
+  return guarded([&] { return from(ctx, ctx->eng.log_norm(log_norm_out)); });
+}
+
+bbp_status bbp_get_message(bbp_ctx* ctx, int block, int face, int* k_out, int* shapes_out, double* data_out,
+                           size_t cap) {
+  if (!ctx || !k_out || !shapes_out || !data_out) return set_err(BBP_ERR_ARG, "NULL argument");
+  return guarded([&] { return from(ctx, ctx->eng.get_message(block, face, k_out, shapes_out, data_out, cap)); });
+}
+
+size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int by, int precision) {
+  (void)precision;
+  const size_t z = 16;
+  const size_t blk = (size_t)bx * by * (lattice == BBP_KAGOME ? 3 : 1);
+  const size_t nblocks = blk ? (n_sites + blk - 1) / blk : 0;
+  const size_t k = lattice == BBP_KAGOME ? 2 * (size_t)bx : (size_t)std::max(bx, by);
+  const size_t D2 = (size_t)D * D;
+  const size_t msgs = nblocks * 4 * 2 * k * chi * chi * D2 * z;
+  const size_t fused = (size_t)n_sites * 4 * D2 * D2 * D2 * D2 * z;
+  const size_t seg = (size_t)chi * chi * D2 * std::max(D2, (size_t)chi) * z;
+  const size_t work = 16 * (12 * seg + 2 * seg);
+  return msgs + fused + work + (size_t)n_sites * 2 * D2 * D2 * z;
+}
+
+bbp_status bbp_info(bbp_ctx* ctx, int* n_blocks, int* n_updates, int* n_sites) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!ctx->eng.partitioned) return set_err(BBP_ERR_STATE, "bbp_partition_blocks must come first");
+  if (n_blocks) *n_blocks = ctx->eng.geom.n_blocks();
+  if (n_updates) *n_updates = (int)ctx->eng.geom.updates().size();
+  if (n_sites) *n_sites = ctx->eng.geom.lat.n_sites();
+  return BBP_OK;
+}
+
+bbp_status bbp_stats(bbp_ctx* ctx, long long* launches_per_iter, double* flops_per_iter) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (launches_per_iter) *launches_per_iter = ctx->eng.launches_per_iter;
+  if (flops_per_iter) *flops_per_iter = ctx->eng.flops_per_iter;
+  return BBP_OK;
+}
+
+const char* bbp_last_error(const bbp_ctx* ctx) {
+  (void)ctx;
+  return g_err.c_str();
+}
+
+void bbp_destroy(bbp_ctx* ctx) {
+  if (!ctx) return;
+  try {
+    if (ctx->eng.stream) cudaStreamSynchronize(ctx->eng.stream);
+    delete ctx;
+  } catch (...) {
+  }
+}
+
+// ------------------------------------------------------------ kernel level
+
+bbp_status bbp_k_fuse(const double* t, int d, int D, const int* n, const double* op, const int* perm, double* T,
+                      void* stream) {
+  if (!t || !n || !perm || !T || d < 1 || D < 1) return set_err(BBP_ERR_ARG, "bad arguments");
+  int seen = 0;
+  for (int q = 0; q < 4; ++q) {
+    if (perm[q] < 0 || perm[q] > 3 || (seen >> perm[q]) & 1) return set_err(BBP_ERR_ARG, "perm is not a permutation");
+    seen |= 1 << perm[q];
+    if (n[q] != 1 && n[q] != D) return set_err(BBP_ERR_ARG, "n[k] must be 1 or D");
+  }
+  return cuda_status(bbp::launch_fuse((const double2*)t, d, D, n, (const double2*)op, perm, (double2*)T,
+                                      (cudaStream_t)stream));
+}
+
+size_t bbp_k_svd_work_bytes(int m, int n) { return (m > 0 && n > 0) ? bbp::svd_work_bytes(m, n) : 0; }
+
+bbp_status bbp_k_svd_trunc(const double* Z, int m, int n, int chi, double* U, double* Rem, void* work, int* status,
+                           void* stream) {
+  if (!Z || !U || !Rem || !work || !status || m < 1 || n < 1 || chi < 1) return set_err(BBP_ERR_ARG, "bad arguments");
+  if (std::min(m, n) > 4096) return set_err(BBP_ERR_ARG, "matrix too large");
+  return cuda_status(bbp::launch_svd_trunc((const double2*)Z, m, n, chi, (double2*)U, (double2*)Rem, work, status,
+                                           (cudaStream_t)stream));
+}
+
+bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, void* stream) {
+  if (!A || !Q || !R || !tau || m < 1 || n < 1) return set_err(BBP_ERR_ARG, "bad arguments");
+  return cuda_status(bbp::launch_qr((double2*)A, m, n, (double2*)Q, (double2*)R, (double2*)tau, (cudaStream_t)stream));
+}
+
+bbp_status bbp_plan_debug(int lattice, int Lx, int Ly, int periodic, int bx, int by, int block, int face, int* out,
+                          int cap, int* n_steps_out) {
+  return guarded([&]() -> bbp_status {
+    if (!out || !n_steps_out) return set_err(BBP_ERR_ARG, "NULL argument");
+    bbp::Geometry g;
+    std::string err = g.build(lattice, Lx, Ly, periodic != 0, bx, by);
+    if (!err.empty()) return set_err(BBP_ERR_TILING, err);
+    if (block < 0 || block >= g.n_blocks() || face < 0 || face > 3) return set_err(BBP_ERR_ARG, "block or face out of range");
+    bbp::Region R;
+    err = bbp::build_region(g, {{g.blocks[block].X, g.blocks[block].Y}}, R);
+    if (!err.empty()) return set_err(BBP_ERR_TILING, err);
+    bbp::SweepPlan plan;
+    err = bbp::compile_sweep(g, R, face, plan);
+    if (!err.empty()) return set_err(BBP_ERR_TILING, err);
+    const int ns = (int)plan.steps.size();
+    if (4 * ns > cap) return set_err(BBP_ERR_ARG, "output buffer too small");
+    for (int s = 0; s < ns; ++s) {
+      const bbp::SweepNode& nd = plan.nodes[s];
+      out[4 * s] = nd.site ? 0 : 1;
+      out[4 * s + 1] = nd.site ? nd.gid : nd.msg_dir * 1024 + nd.msg_index;
+      out[4 * s + 2] = plan.steps[s].nin;
+      out[4 * s + 3] = plan.steps[s].nout;
+    }
+    *n_steps_out = ns;
+    return BBP_OK;
+  });
+}
+
+}  // extern "C"
