@@ -1,0 +1,317 @@
+"""Benchmark of the BlockBP message update on one GB300 (or N independent replicas).
+
+One step = one synchronous BlockBP iteration: every message update of the
+network (Alg. 1).  Workload (default): the translation-periodic Kagome
+super-cell of 6 x 2 unit cells cut into 3 parallelogram blocks of 12 sites
+(L = 2), d = 2, D = 4, chi = 32, dimer-singlet tensors plus 1e-2 complex
+Gaussian noise; 12 message updates per iteration.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "kagome-6x2-L2-D4-chi32",
+    "lattice": "kagome", "Lx": 6, "Ly": 2, "L": 2, "d": 2, "D": 4, "chi": 32,
+    "tensor_seed": 2, "noise": 1e-2, "noise_seed": 3, "message_seed": 7,
+}
+
+
+def make_inputs(w):
+    import synthetic as syn
+    nb = syn.kagome_neighbours(w["Lx"], w["Ly"])
+    t = syn.dimer_singlet_peps(nb, w["d"], w["D"], seed=w["tensor_seed"], noise=w["noise"], noise_seed=w["noise_seed"])
+    em = syn.initial_edge_matrices(len(nb), w["D"], seed=w["message_seed"])
+    return t, em
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- our engine
+
+def svd_roofline(P, torch, m=512, n=512, chi=32, reps=3):
+    """Time the dominant kernel (FP64 one-sided Jacobi truncated SVD at the
+    workload's bulk shape) with CUDA events; count its flops from the sweeps
+    and rotations it reports."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    k = min(m, n)
+    U, _ = np.linalg.qr(rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k)))
+    s = np.sort(0.9 ** np.arange(k) * (1 + 0.1 * rng.random(k)))[::-1]
+    Z = torch.from_numpy((U * s) @ V.conj().T).cuda()
+    Ud = torch.zeros(m * chi, dtype=torch.complex128, device="cuda")
+    Rd = torch.zeros(chi * n, dtype=torch.complex128, device="cuda")
+    work = torch.zeros(P.bbp_k_svd_work_bytes(m, n) // 16 + 16, dtype=torch.complex128, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    P.bbp_k_svd_trunc(Z, m, n, chi, Ud, Rd, work, st)          # warm-up
+    torch.cuda.synchronize()
+    times, flops = [], []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.bbp_k_svd_trunc(Z, m, n, chi, Ud, Rd, work, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+        sweeps, rot = P.bbp_k_svd_stats(work, m, n)
+        M, N = min(m, n), max(m, n)
+        flops.append(sweeps * (M * (M - 1) / 2) * 16.0 * N + rot * 18.0 * (N + M))
+    t = statistics.mean(times)
+    f = statistics.mean(flops)
+    return {"kernel": "k_jacobi (FP64 one-sided Jacobi SVD, 512 x 512, chi 32)", "seconds": t, "flops": f}
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import paper_2603_13304_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    P.build()
+    P.use_torch_allocator()
+    w = WORKLOAD
+    t, em = make_inputs(w)
+    stream = torch.cuda.current_stream()
+
+    def setup():
+        ctx = P.bbp_create_peps(P.KAGOME, w["Lx"], w["Ly"], 1, w["d"], w["D"], t)
+        P.bbp_partition_blocks(ctx, w["L"], w["L"])
+        P.bbp_set_options(ctx, w["chi"], P.FP64)
+        P.bbp_init_messages(ctx, em)
+        return ctx
+
+    ctx = setup()
+    _, n_updates, n_sites = P.bbp_info(ctx)
+    for _ in range(args.warmup):
+        P.bbp_iterate(ctx, 0.0, 1)
+    # L2 flush buffer (larger than the 126 MB L2), rewritten between timed steps
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            P.bbp_iterate(ctx, 0.0, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) * 1e-3
+    launches, flops_iter = P.bbp_stats(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([secs], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        secs = float(tt.item())
+    value = world * n_updates * args.steps / secs
+    energy = P.bbp_energy_per_site(ctx) if rank == 0 else None
+    P.bbp_destroy(ctx)
+
+    # end to end through the C ABI with host buffers: upload, iterate, read back
+    tp = torch.from_numpy(np.ascontiguousarray(t)).pin_memory()
+    ep = torch.from_numpy(np.ascontiguousarray(em)).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = P.bbp_create_peps(P.KAGOME, w["Lx"], w["Ly"], 1, w["d"], w["D"], tp.numpy())
+    P.bbp_partition_blocks(ctx, w["L"], w["L"])
+    P.bbp_set_options(ctx, w["chi"], P.FP64)
+    P.bbp_init_messages(ctx, ep.numpy())
+    P.bbp_iterate(ctx, 0.0, args.steps)
+    d2h = 0
+    for b in range(3):
+        for f in range(4):
+            msg = P.bbp_get_message(ctx, b, f)
+            d2h += sum(x.nbytes for x in msg)
+    torch.cuda.synchronize()
+    e2e_secs = time.perf_counter() - t0
+    P.bbp_destroy(ctx)
+    e2e = {"value": n_updates * args.steps / e2e_secs, "unit": "message updates/s",
+           "h2d_bytes_per_step": (t.nbytes + em.nbytes) / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+
+    roof = None
+    if rank == 0:
+        r = svd_roofline(P, torch)
+        achieved = r["flops"] / r["seconds"] / 1e12
+        peak = 152 * 2 * 2 * 2.07e9 / 1e12     # FP64 FMA units x clock
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": r["kernel"], "launch_s": r["seconds"]}
+    return {
+        "value": value, "secs": secs, "n_updates": n_updates, "n_sites": n_sites, "energy": energy,
+        "clocks": clk.summary(), "launches": launches, "flops_iter": flops_iter, "e2e": e2e, "roofline": roof,
+    }
+
+
+# ---------------------------------------------------------------- oracle
+
+def oracle_sample(w, n_updates_sample: int):
+    """Time the FP64 oracle on a bounded sample: the first iteration's first
+    message updates (bond-1 inputs), then the same updates with full-bond
+    inputs after one iteration.  Returns updates/s over the timed updates."""
+    from oracle.blockbp import BlockBP
+    from oracle.geometry import Geometry
+    t, em = make_inputs(w)
+    geom = Geometry.kagome(w["Lx"], w["Ly"], w["L"])
+    bb = BlockBP(geom, t, chi=w["chi"])
+    bb.init_messages(em)
+    bb.step()                                # full-bond messages
+    ups = geom.updates()[:n_updates_sample]
+    t0 = time.perf_counter()
+    for (bid, face, _) in ups:
+        bb.update_message(bid, face)
+    dt = time.perf_counter() - t0
+    return len(ups) / dt, dt
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    w = WORKLOAD
+    config = {"workload": w["workload"], "lattice": "kagome periodic super-cell 6x2 unit cells, 3 blocks of 12 sites",
+              "d": w["d"], "D": w["D"], "chi": w["chi"], "updates_per_step": 12,
+              "l2": "flushed between timed steps (256 MB write)", "tol": 0.0}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per_step = []
+        for _ in range(args.warmup):
+            oracle_sample(w, 2)
+        t_all = 0.0
+        n_all = 0
+        for _ in range(args.steps):
+            v, dt = oracle_sample(w, 2)
+            per_step.append(v)
+            t_all += dt
+            n_all += 2
+        value = n_all / t_all
+        cores = blas_threads()
+        line = {"metric": "BlockBP message updates/s", "value": value, "unit": "message updates/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic", "config": config, "impl": "reference",
+                "cpu_baseline": {"value": value, "unit": "message updates/s", "cores": cores, "kind": "oracle",
+                                 "sample": "2 message updates (full-bond inputs) of the workload per step"},
+                "e2e": {"value": value, "unit": "message updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt = oracle_sample(w, 2)
+        cpu = {"value": v, "unit": "message updates/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"2 message updates with full-bond inputs ({dt:.1f} s of CPU work)"}
+    line = {
+        "metric": "BlockBP message updates/s", "value": res["value"], "unit": "message updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * res["secs"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": config,
+        "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["launches"] * args.steps,
+        "roofline": res["roofline"], "cpu_baseline": cpu,
+        "energy_per_site": res["energy"], "absorb_tflop_per_step": res["flops_iter"] / 1e12,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

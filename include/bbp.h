@@ -102,12 +102,15 @@ bbp_status bbp_init_messages(bbp_ctx* ctx, const double* edge_mats);
 bbp_status bbp_iterate(bbp_ctx* ctx, double tol, int max_iter, int* iters_out, double* err_out);
 
 /* <O> for a one- or two-site operator with the converged messages.
- * ns = 1: op is d x d complex128 on site sites[0].
+ * ns = 1: op is d x d complex128 on site sites[0], inserted as a whole.
  * ns = 2: op is (d*d) x (d*d) complex128 on the pair (sites[0], its
- *   neighbour through slot sites[1]), basis index s0 * d + s1.  If the two
- *   sites lie in different blocks the union of both blocks is contracted.
+ *   neighbour through slot sites[1]), basis index s0 * d + s1; it is
+ *   expanded in the product basis |a0><b0| (x) |a1><b1|, one contraction per
+ *   nonzero entry.  If the two sites lie in different blocks the union of
+ *   both blocks is contracted.
  * The block (or union) is contracted with all its incoming messages by a
- * sweep to its top face; <O> = Z(O) / Z(1). */
+ * sweep to its top face; <O> = Z(O) / Z(1).  A truncated sweep is not linear
+ * in the inserted operator, so the expansion above is part of the result. */
 bbp_status bbp_expect_local(bbp_ctx* ctx, const double* op, int ns, const int* sites, double* re_out,
                             double* im_out);
 
@@ -157,11 +160,15 @@ bbp_status bbp_k_fuse(const double* t, int d, int D, const int* n, const double*
 
 /* K3, truncated SVD (Sec. 1.1.1): Z (m x n, device, row-major) = U S V^H;
  * keep k = min(chi, m, n) largest; writes U (m x k) and Rem = S V^H (k x n).
- * work: device scratch of bbp_k_svd_work_bytes(m, n) bytes; status: device int
- * (0 converged, 1 sweep limit reached). */
+ * work: device scratch of bbp_k_svd_work_bytes(m, n) bytes; status: device
+ * int, set to 1 if the sweep limit was reached (never cleared: zero it first). */
 size_t bbp_k_svd_work_bytes(int m, int n);
 bbp_status bbp_k_svd_trunc(const double* Z, int m, int n, int chi, double* U, double* Rem, void* work, int* status,
                            void* stream);
+
+/* Work counters of the last bbp_k_svd_trunc that used `work`: Jacobi sweeps
+ * and rotations applied (synchronises the stream).  Feeds the flop model. */
+bbp_status bbp_k_svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, void* stream);
 
 /* Householder QR (Sec. 2.3.3 canonical moves): A (m x n, device, destroyed)
  * = Q (m x k) R (k x n), k = min(m, n); tau: device scratch of k complex. */

@@ -122,40 +122,42 @@ bbp_status bbp_expect_local(bbp_ctx* ctx, const double* op, int ns, const int* s
       int rc = e.bond_region(sites[0], sites[1], coords, k1, k2);
       if (rc) return from(ctx, rc);
     }
-    // <O> = sum over the elementary operators |a><a'| (x) |b><b'| weighted by O
+    // ns = 1: the operator itself is inserted (one contraction).  ns = 2: the
+    // operator is expanded in the product basis |a0><b0| (x) |a1><b1|, one
+    // contraction per nonzero entry (the truncated sweep is not linear in
+    // the inserted operator, so the expansion is part of the definition).
     const int dim = ns == 1 ? d : d * d;
     std::vector<std::vector<std::array<int, 2>>> C;
     std::vector<std::vector<std::pair<std::array<int, 2>, const double*>>> O;
-    std::vector<double> elem;   // host copies of elementary d x d operators
+    std::vector<double> elem;   // host copies of the inserted d x d operators
     std::vector<double2> w;     // weight of each contraction
-    const int nb = ns == 1 ? d * d : d * d * d * d;
-    elem.assign((size_t)(ns == 1 ? nb : 2 * nb) * d * d * 2, 0.0);
+    const int nb = ns == 1 ? 1 : d * d * d * d;
+    elem.assign((size_t)2 * nb * d * d * 2, 0.0);
     bbp::DBuf dev;
     if (!dev.ensure(sizeof(double) * elem.size() + 256, e.stream)) return set_err(BBP_ERR_OOM, "allocation failed");
     C.push_back(coords);
     O.push_back({});
+    if (ns == 1) {
+      std::memcpy(elem.data(), op, sizeof(double) * 2 * d * d);
+      w.push_back(make_double2(1.0, 0.0));
+      C.push_back(coords);
+      O.push_back({{k1, (const double*)dev.p}});
+    }
     int slot = 0;
-    for (int a = 0; a < dim; ++a)
+    for (int a = 0; a < dim && ns == 2; ++a)
       for (int ap = 0; ap < dim; ++ap) {
         double2 wt = make_double2(op[2 * (a * dim + ap)], op[2 * (a * dim + ap) + 1]);
         if (wt.x == 0.0 && wt.y == 0.0) continue;
         w.push_back(wt);
         std::vector<std::pair<std::array<int, 2>, const double*>> ops;
-        if (ns == 1) {
-          double* E = elem.data() + (size_t)slot * d * d * 2;
-          E[2 * (a * d + ap)] = 1.0;
-          ops.push_back({k1, (const double*)dev.p + (size_t)slot * d * d * 2});
-          ++slot;
-        } else {
-          int a0 = a / d, a1 = a % d, b0 = ap / d, b1 = ap % d;
-          double* E0 = elem.data() + (size_t)slot * d * d * 2;
-          double* E1 = elem.data() + (size_t)(slot + 1) * d * d * 2;
-          E0[2 * (a0 * d + b0)] = 1.0;
-          E1[2 * (a1 * d + b1)] = 1.0;
-          ops.push_back({k1, (const double*)dev.p + (size_t)slot * d * d * 2});
-          ops.push_back({k2, (const double*)dev.p + (size_t)(slot + 1) * d * d * 2});
-          slot += 2;
-        }
+        int a0 = a / d, a1 = a % d, b0 = ap / d, b1 = ap % d;
+        double* E0 = elem.data() + (size_t)slot * d * d * 2;
+        double* E1 = elem.data() + (size_t)(slot + 1) * d * d * 2;
+        E0[2 * (a0 * d + b0)] = 1.0;
+        E1[2 * (a1 * d + b1)] = 1.0;
+        ops.push_back({k1, (const double*)dev.p + (size_t)slot * d * d * 2});
+        ops.push_back({k2, (const double*)dev.p + (size_t)(slot + 1) * d * d * 2});
+        slot += 2;
         C.push_back(coords);
         O.push_back(ops);
       }
@@ -320,6 +322,11 @@ bbp_status bbp_k_svd_trunc(const double* Z, int m, int n, int chi, double* U, do
   if (std::min(m, n) > 4096) return set_err(BBP_ERR_ARG, "matrix too large");
   return cuda_status(bbp::launch_svd_trunc((const double2*)Z, m, n, chi, (double2*)U, (double2*)Rem, work, status,
                                            (cudaStream_t)stream));
+}
+
+bbp_status bbp_k_svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, void* stream) {
+  if (!work || !sweeps || !rotations || m < 1 || n < 1) return set_err(BBP_ERR_ARG, "bad arguments");
+  return cuda_status(bbp::svd_stats(work, m, n, sweeps, rotations, (cudaStream_t)stream));
 }
 
 bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, void* stream) {

@@ -294,6 +294,10 @@ __device__ int rotate_pair(double2* ra, double2* rb, int N, double2* wa, double2
   gy = warp_sum(gy);
   double g = sqrt(gx * gx + gy * gy);
   if (g == 0.0 || g <= tol * sqrt(al) * sqrt(be)) return 0;
+  // rows whose norms differ by more than 1e30 do not affect each other at
+  // working precision; rotating them only churns rounding noise (and never
+  // meets the relative test once the small norm is subnormal)
+  if (fmin(al, be) <= 1e-60 * fmax(al, be)) return 0;
   double2 e = make_double2(gx / g, gy / g);
   double zeta = (be - al) / (2.0 * g);
   double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -336,14 +340,15 @@ __global__ void __launch_bounds__(256) k_jacobi(SvdWork w, int M, int N, double 
     if (lane == 0 && rot) atomicAdd(&w.counters[sweep & 1], rot);
     cl.sync();
     const int total = *(volatile int*)&w.counters[sweep & 1];
-    if (crank == 0 && threadIdx.x == 0) w.counters[(sweep + 1) & 1] = 0;
-    cl.sync();
-    if (total == 0) {
-      if (crank == 0 && threadIdx.x == 0) *status = 0;
-      return;
+    if (crank == 0 && threadIdx.x == 0) {
+      w.counters[(sweep + 1) & 1] = 0;
+      w.counters[2] = sweep + 1;        // sweeps done
+      w.counters[3] += total;           // rotations applied
     }
+    cl.sync();
+    if (total == 0) return;
   }
-  if (crank == 0 && threadIdx.x == 0) *status = 1;
+  if (crank == 0 && threadIdx.x == 0) *status = 1;   // sweep limit reached
 }
 
 __global__ void k_row_norms(SvdWork w, int M, int N) {
@@ -380,7 +385,8 @@ __global__ void k_svd_out(SvdWork w, int m, int n, int k, double2* __restrict__ 
         U[e] = cconj(w.WH[(long long)a * M + i]);
       } else {
         double s = w.sigma[a];
-        U[e] = s > 0.0 ? cscale(cconj(w.G[(long long)a * N + i]), 1.0 / s) : make_double2(0.0, 0.0);
+        double smax = w.sigma[w.idx[0]];
+        U[e] = s > 1e-30 * smax ? cscale(cconj(w.G[(long long)a * N + i]), 1.0 / s) : make_double2(0.0, 0.0);
       }
     } else {
       long long f = e - totU;
@@ -616,6 +622,18 @@ cudaError_t launch_svd_trunc(const double2* Z, int m, int n, int chi, double2* U
   k_select<<<1, 256, 0, s>>>(w, M, k);
   k_svd_out<<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(w, m, n, k, U, Rem);
   return cudaGetLastError();
+}
+
+cudaError_t svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, cudaStream_t s) {
+  const int M = m < n ? m : n, N = m < n ? n : m;
+  SvdWork w = carve(const_cast<void*>(work), M, N);
+  int c[4];
+  cudaError_t e = cudaMemcpyAsync(c, w.counters, sizeof(c), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  *sweeps = c[2];
+  *rotations = c[3];
+  return e;
 }
 
 cudaError_t launch_normalise(double2* A, long long n, double* logscale, cudaStream_t s) {

@@ -28,10 +28,13 @@ cudaError_t launch_qr(double2* A, int m, int n, double2* Q, double2* R, double2*
 // Truncated SVD by one-sided (row) Jacobi: Z (m x n) = U S V^H, keep
 // k = min(chi, m, n) triplets with the largest singular values.
 // Writes U (m x k) and Rem = S V^H (k x n).  Z is read only.
-// work must hold svd_work_bytes(m, n); status: int (0 ok, 1 no convergence).
+// work must hold svd_work_bytes(m, n); *status is set to 1 if the sweep limit
+// was reached (left untouched otherwise, so callers clear it once).
 size_t svd_work_bytes(int m, int n);
 cudaError_t launch_svd_trunc(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work,
                              int* status, cudaStream_t s);
+// Sweeps and rotations of the last launch_svd_trunc that used `work` (synchronises s).
+cudaError_t svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, cudaStream_t s);
 
 // Frobenius norm of a tensor: A /= ||A||, *logscale += log ||A|| (0 norm: logscale = -inf).
 cudaError_t launch_normalise(double2* A, long long n, double* logscale, cudaStream_t s);
