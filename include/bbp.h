@@ -166,6 +166,20 @@ size_t bbp_k_svd_work_bytes(int m, int n);
 bbp_status bbp_k_svd_trunc(const double* Z, int m, int n, int chi, double* U, double* Rem, void* work, int* status,
                            void* stream);
 
+/* Allocation-free variant of bbp_k_svd_trunc (the thesis has no counterpart;
+ * this serves callers that cannot allocate device memory when they need the
+ * SVD, e.g. inside a stream capture or an allocator-free real-time loop).
+ * Same inputs, outputs and status as bbp_k_svd_trunc, without `work`: the
+ * scratch is a fixed device array of 8 MiB + 64 KiB that every GPU loading
+ * the library holds until exit, enough for bbp_k_svd_work_bytes(m, n) up to
+ * that size (e.g. 512 x 512).  Larger sizes return BBP_ERR_ARG.  It calls no
+ * allocator.  The first call on a device looks up the array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  All calls on a device share the array: calls that overlap on the
+ * same GPU race. */
+bbp_status bbp_k_svd_trunc_noalloc(const double* Z, int m, int n, int chi, double* U, double* Rem, int* status,
+                                   void* stream);
+
 /* Work counters of the last bbp_k_svd_trunc that used `work`: Jacobi sweeps
  * and rotations applied (synchronises the stream).  Feeds the flop model. */
 bbp_status bbp_k_svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, void* stream);

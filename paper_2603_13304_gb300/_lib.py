@@ -27,7 +27,7 @@ EXPORTS = [
     "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
     "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message",
     "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
-    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_plan_debug",
+    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_plan_debug",
 ]
 
 
@@ -68,6 +68,7 @@ _PROTOS = {
     "bbp_k_fuse": (_i, [_vp, _i, _i, _ip, _vp, _ip, _vp, _vp]),
     "bbp_k_svd_work_bytes": (ctypes.c_size_t, [_i, _i]),
     "bbp_k_svd_trunc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "bbp_k_svd_trunc_noalloc": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "bbp_k_svd_stats": (_i, [_vp, _i, _i, _ip, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "bbp_k_qr": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
     "bbp_plan_debug": (_i, [_i, _i, _i, _i, _i, _i, _i, _i, _ip, _i, _ip]),
@@ -262,6 +263,11 @@ def bbp_k_svd_work_bytes(m: int, n: int) -> int:
 def bbp_k_svd_trunc(Z, m: int, n: int, chi: int, U, Rem, work, status, stream=None):
     _check(lib().bbp_k_svd_trunc(_devptr(Z), m, n, chi, _devptr(U), _devptr(Rem), _devptr(work), _devptr(status),
                                  _stream(stream)))
+
+
+def bbp_k_svd_trunc_noalloc(Z, m: int, n: int, chi: int, U, Rem, status, stream=None):
+    _check(lib().bbp_k_svd_trunc_noalloc(_devptr(Z), m, n, chi, _devptr(U), _devptr(Rem), _devptr(status),
+                                         _stream(stream)))
 
 
 def bbp_k_svd_stats(work, m: int, n: int, stream=None):

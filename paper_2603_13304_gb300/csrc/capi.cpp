@@ -324,6 +324,19 @@ bbp_status bbp_k_svd_trunc(const double* Z, int m, int n, int chi, double* U, do
                                            (cudaStream_t)stream));
 }
 
+bbp_status bbp_k_svd_trunc_noalloc(const double* Z, int m, int n, int chi, double* U, double* Rem, int* status,
+                                   void* stream) {
+  if (!Z || !U || !Rem || !status || m < 1 || n < 1 || chi < 1) return set_err(BBP_ERR_ARG, "bad arguments");
+  bool too_large = false;
+  cudaError_t e = bbp::launch_svd_trunc_noalloc((const double2*)Z, m, n, chi, (double2*)U, (double2*)Rem, status,
+                                                (cudaStream_t)stream, &too_large);
+  if (too_large)
+    return set_err(BBP_ERR_ARG, "matrix needs " + std::to_string(bbp::svd_work_bytes(m, n)) +
+                                    " bytes of SVD scratch; the allocation-free entry point holds " +
+                                    std::to_string(bbp::noalloc_scratch_bytes()));
+  return cuda_status(e);
+}
+
 bbp_status bbp_k_svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, void* stream) {
   if (!work || !sweeps || !rotations || m < 1 || n < 1) return set_err(BBP_ERR_ARG, "bad arguments");
   return cuda_status(bbp::svd_stats(work, m, n, sweeps, rotations, (cudaStream_t)stream));

@@ -71,3 +71,12 @@ cudaError_t launch_conj_transpose(const double2* src, int rows, int cols, double
 // dst = src (d0, d1, d2) with axes permuted: dst axis q is src axis perm[q]
 cudaError_t launch_permute3(const double2* src, int d0, int d1, int d2, const int perm[3], double2* dst, cudaStream_t s);
 }  // namespace bbp
+
+namespace bbp {
+// Allocation-free truncated SVD (k_noalloc.cu): scratch in a fixed device
+// array of noalloc_scratch_bytes(); *too_large is set when svd_work_bytes(m, n)
+// exceeds it (nothing is launched then).
+size_t noalloc_scratch_bytes();
+cudaError_t launch_svd_trunc_noalloc(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, int* status,
+                                     cudaStream_t s, bool* too_large);
+}  // namespace bbp
