@@ -144,11 +144,12 @@ def run_ours(args, rank, world):
     w = WORKLOAD
     t, em = make_inputs(w)
     stream = torch.cuda.current_stream()
+    prec = P.FP32 if args.precision == "fp32" else P.FP64
 
     def setup():
         ctx = P.bbp_create_peps(P.KAGOME, w["Lx"], w["Ly"], 1, w["d"], w["D"], t)
         P.bbp_partition_blocks(ctx, w["L"], w["L"])
-        P.bbp_set_options(ctx, w["chi"], P.FP64)
+        P.bbp_set_options(ctx, w["chi"], prec)
         P.bbp_init_messages(ctx, em)
         return ctx
 
@@ -164,12 +165,14 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0 = time.perf_counter()
         e0.record(stream)
         for _ in range(args.steps):
             flush.zero_()
             P.bbp_iterate(ctx, 0.0, 1)
         e1.record(stream)
         torch.cuda.synchronize()
+        host_secs = time.perf_counter() - h0
     secs = e0.elapsed_time(e1) * 1e-3
     launches, flops_iter = P.bbp_stats(ctx)
     if world > 1:
@@ -188,7 +191,7 @@ def run_ours(args, rank, world):
     t0 = time.perf_counter()
     ctx = P.bbp_create_peps(P.KAGOME, w["Lx"], w["Ly"], 1, w["d"], w["D"], tp.numpy())
     P.bbp_partition_blocks(ctx, w["L"], w["L"])
-    P.bbp_set_options(ctx, w["chi"], P.FP64)
+    P.bbp_set_options(ctx, w["chi"], prec)
     P.bbp_init_messages(ctx, ep.numpy())
     P.bbp_iterate(ctx, 0.0, args.steps)
     d2h = 0
@@ -210,7 +213,7 @@ def run_ours(args, rank, world):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": r["kernel"], "launch_s": r["seconds"]}
     return {
-        "value": value, "secs": secs, "n_updates": n_updates, "n_sites": n_sites, "energy": energy,
+        "value": value, "secs": secs, "host_secs": host_secs, "n_updates": n_updates, "n_sites": n_sites, "energy": energy,
         "clocks": clk.summary(), "launches": launches, "flops_iter": flops_iter, "e2e": e2e, "roofline": roof,
     }
 
@@ -250,6 +253,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -301,8 +305,10 @@ def main():
     line = {
         "metric": "BlockBP message updates/s", "value": res["value"], "unit": "message updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * res["secs"] / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": config,
+        "ms_per_step": 1e3 * res["secs"] / args.steps, "host_ms_per_step": 1e3 * res["host_secs"] / args.steps,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64" if args.precision == "fp32" else "c128", "data": "synthetic",
+        "config": dict(config, precision=args.precision),
         "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["launches"] * args.steps,
         "roofline": res["roofline"], "cpu_baseline": cpu,
         "energy_per_site": res["energy"], "absorb_tflop_per_step": res["flops_iter"] / 1e12,

@@ -59,7 +59,7 @@ typedef enum {
 } bbp_status;
 
 typedef enum { BBP_SQUARE = 0, BBP_KAGOME = 1 } bbp_lattice;
-typedef enum { BBP_FP64 = 0, BBP_TF32 = 1, BBP_BF16 = 2 } bbp_precision;
+typedef enum { BBP_FP64 = 0, BBP_TF32 = 1, BBP_BF16 = 2, BBP_FP32 = 3 } bbp_precision;
 typedef enum { BBP_BOTTOM = 0, BBP_RIGHT = 1, BBP_TOP = 2, BBP_LEFT = 3 } bbp_face;
 
 /* Device allocator used by every context created afterwards.  alloc returns
@@ -84,8 +84,14 @@ bbp_status bbp_create_peps(bbp_ctx** out, int lattice, int Lx, int Ly, int perio
 bbp_status bbp_partition_blocks(bbp_ctx* ctx, int bx, int by);
 
 /* chi: truncation bond dimension of the boundary MPS (Sec. 1.1.3), 1..64.
- * precision: BBP_FP64 (all arithmetic complex128).  alpha must be 1
- * (undamped update).  seed is reserved. */
+ * precision: BBP_FP64 -- every tensor complex128, exact one-sided Jacobi
+ *   truncation (the reference path, agrees with the FP64 oracle to 1e-10);
+ * BBP_FP32 -- tensors and contractions complex64; each truncation reduces a
+ *   large matrix to chi + chi/2 directions by a randomised subspace iteration
+ *   (3 power steps) before an exact one-sided Jacobi on the reduced matrix;
+ *   message norms, phases, distances and log-scales stay double.
+ * Must be called before bbp_init_messages.  alpha must be 1 (undamped
+ * update).  seed is reserved. */
 bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, uint64_t seed);
 
 /* Initial messages (Alg. 1, "random MPS"): every incoming message becomes a

@@ -20,7 +20,7 @@ STATUS = {
     5: "BBP_ERR_NUMERIC", 6: "BBP_NOT_CONVERGED", 7: "BBP_ERR_TIMEOUT", 8: "BBP_ERR_STATE",
 }
 SQUARE, KAGOME = 0, 1
-FP64, TF32, BF16 = 0, 1, 2
+FP64, TF32, BF16, FP32 = 0, 1, 2, 3
 BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
 
 EXPORTS = [

@@ -82,11 +82,13 @@ bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, u
   (void)seed;
   if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
   if (chi < 1 || chi > 64) return set_err(BBP_ERR_ARG, "chi must be 1..64");
-  if (precision != BBP_FP64) return set_err(BBP_ERR_ARG, "this build implements precision BBP_FP64");
+  if (precision != BBP_FP64 && precision != BBP_FP32)
+    return set_err(BBP_ERR_ARG, "precision must be BBP_FP64 or BBP_FP32");
   if (alpha != 1.0) return set_err(BBP_ERR_ARG, "only the undamped update (alpha = 1) is implemented");
   if (ctx->eng.messages_ready) return set_err(BBP_ERR_STATE, "options must be set before bbp_init_messages");
+  int rc = ctx->eng.set_precision(precision == BBP_FP64 ? 0 : 1);
+  if (rc) return from(ctx, rc);
   ctx->eng.chi = chi;
-  ctx->eng.precision = precision;
   return BBP_OK;
 }
 

@@ -1,6 +1,6 @@
 // BlockBP engine (see engine.h).  Every step of the message update runs in the
-// CUDA kernels of k_fp64.cu; this file only sizes buffers, follows the sweep
-// plan and enqueues launches.
+// CUDA kernels of k_core.cu; this file only sizes buffers, follows the sweep
+// plans and enqueues launches.
 #include "engine.h"
 
 #include <algorithm>
@@ -19,8 +19,25 @@ std::mutex g_alloc_mu;
 void* (*g_alloc)(size_t, void*, void*) = nullptr;
 void (*g_free)(void*, void*, void*) = nullptr;
 void* g_user = nullptr;
-const double2 kOne = {1.0, 0.0};
-const double2 kZero = {0.0, 0.0};
+
+template <typename C> C one_of();
+template <> double2 one_of<double2>() { return make_double2(1.0, 0.0); }
+template <> float2 one_of<float2>() { return make_float2(1.f, 0.f); }
+template <typename C> C zero_of();
+template <> double2 zero_of<double2>() { return make_double2(0.0, 0.0); }
+template <> float2 zero_of<float2>() { return make_float2(0.f, 0.f); }
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+// truncated SVD of one split, per element type
+cudaError_t svd_call(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work, int* status,
+                     cudaStream_t s, int) {
+  return launch_svd_trunc(Z, m, n, chi, U, Rem, work, status, s);
+}
+cudaError_t svd_call(const float2* Z, int m, int n, int chi, float2* U, float2* Rem, void* work, int* status,
+                     cudaStream_t s, int power_iters) {
+  return launch_svd_trunc(Z, m, n, chi, U, Rem, work, status, s, power_iters);
+}
 }  // namespace
 
 void set_allocator(void* (*a)(size_t, void*, void*), void (*f)(void*, void*, void*), void* user) {
@@ -65,53 +82,54 @@ int fail(Engine* e, int status, const std::string& msg) {
   return status;
 }
 
-#define CK(call)                                                                          \
-  do {                                                                                    \
-    cudaError_t _e = (call);                                                              \
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t _e = (call);                                                                          \
     if (_e != cudaSuccess) return fail(this, 3, std::string(#call) + ": " + cudaGetErrorString(_e)); \
   } while (0)
 
 // ------------------------------------------------------------ sweep work
 
-namespace {
-size_t al(size_t x) { return (x + 255) & ~size_t(255); }
-}
-
-bool SweepWork::reserve(size_t ct, size_t cs, size_t cx, size_t sb, size_t ns, size_t cd) {
-  if (ct <= cap_t && cs <= cap_seg && cx <= cap_x && sb <= svd_bytes && ns <= nslots && cd <= cap_d && arena.p) return true;
+bool SweepWork::reserve(size_t el, size_t ct, size_t cs, size_t cx, size_t sb, size_t ns, size_t cd) {
+  if (el == elem && ct <= cap_t && cs <= cap_seg && cx <= cap_x && sb <= svd_bytes && ns <= nslots && cd <= cap_d &&
+      arena.p)
+    return true;
+  if (el != elem) { cap_t = cap_seg = cap_x = svd_bytes = nslots = cap_d = 0; }
+  elem = el;
   cap_t = std::max(ct, cap_t);
   cap_seg = std::max(cs, cap_seg);
   cap_x = std::max(cx, cap_x);
   svd_bytes = std::max(sb, svd_bytes);
   nslots = std::max(ns, nslots);
   cap_d = std::max(cd, cap_d);
-  const size_t z = sizeof(double2);
+  const size_t z = elem, zd = sizeof(double2);
   size_t total = nslots * al(cap_t * z) + 4 * al(cap_seg * z) + 3 * al(cap_t * z) + al(4096 * z) + al(cap_x * z) +
                  al(svd_bytes) + 256 * 4 + al(64 * sizeof(void*) * 2) + al(64 * 3 * 2 * sizeof(int)) +
-                 al((2 * 64 * 64 + 64 * 64 * 64 + 256) * z) + 4 * al(cap_d * z);
+                 al((2 * 64 * 64 + 64 * 64 * 64 + 256) * zd) + 4 * al(cap_d * zd) + al(4096 * zd);
   if (!arena.ensure(total, stream)) return false;
   char* p = (char*)arena.p;
   slot.assign(nslots, nullptr);
-  for (size_t i = 0; i < nslots; ++i) { slot[i] = (double2*)p; p += al(cap_t * z); }
-  for (int i = 0; i < 2; ++i) { S[i] = (double2*)p; p += al(cap_seg * z); }
-  for (int i = 0; i < 2; ++i) { R[i] = (double2*)p; p += al(cap_seg * z); }
-  qrA = (double2*)p; p += al(cap_t * z);
-  qrQ = (double2*)p; p += al(cap_t * z);
-  qrR = (double2*)p; p += al(cap_t * z);
-  tau = (double2*)p; p += al(4096 * z);
-  X = (double2*)p; p += al(cap_x * z);
+  for (size_t i = 0; i < nslots; ++i) { slot[i] = p; p += al(cap_t * z); }
+  for (int i = 0; i < 2; ++i) { S[i] = p; p += al(cap_seg * z); }
+  for (int i = 0; i < 2; ++i) { R[i] = p; p += al(cap_seg * z); }
+  qrA = p; p += al(cap_t * z);
+  qrQ = p; p += al(cap_t * z);
+  qrR = p; p += al(cap_t * z);
+  tau = p; p += al(4096 * z);
+  X = p; p += al(cap_x * z);
   svd = p; p += al(svd_bytes);
   logscale = (double*)p; p += 256;
   status = (int*)p; p += 256;
   scal = (double2*)p; p += 256;
   p += 256;
-  ptrs = (double2**)p; p += al(64 * sizeof(void*) * 2);
+  ptrs = (void**)p; p += al(64 * sizeof(void*) * 2);
   ints = (int*)p; p += al(64 * 3 * 2 * sizeof(int));
-  k4 = (double2*)p; p += al((2 * 64 * 64 + 64 * 64 * 64 + 256) * z);
-  dX0 = (double2*)p; p += al(cap_d * z);
-  dX1 = (double2*)p; p += al(cap_d * z);
-  dQ = (double2*)p; p += al(cap_d * z);
-  dR = (double2*)p; p += al(cap_d * z);
+  k4 = (double2*)p; p += al((2 * 64 * 64 + 64 * 64 * 64 + 256) * zd);
+  dX0 = (double2*)p; p += al(cap_d * zd);
+  dX1 = (double2*)p; p += al(cap_d * zd);
+  dQ = (double2*)p; p += al(cap_d * zd);
+  dR = (double2*)p; p += al(cap_d * zd);
+  dtau = (double2*)p; p += al(4096 * zd);
   return true;
 }
 
@@ -125,7 +143,6 @@ Engine::~Engine() {
     if (w->stream) cudaStreamDestroy(w->stream);
     delete w;
   }
-  for (DBuf* b : op_fused) delete b;
 }
 
 SweepWork* Engine::work(size_t i) {
@@ -162,7 +179,6 @@ int Engine::create(int lattice, int Lx, int Ly, int periodic, int d_, int D_, co
 int Engine::partition(int bx, int by) {
   std::string err = geom.build(geom.lat.kind, geom.lat.Lx, geom.lat.Ly, geom.lat.periodic, bx, by);
   if (!err.empty()) return fail(this, 4, err);
-  // leg extents per site (1 on open legs)
   const int n = geom.lat.n_sites();
   site_n.assign(n, {D, D, D, D});
   for (const Block& b : geom.blocks)
@@ -174,7 +190,6 @@ int Engine::partition(int bx, int by) {
         if (geom.lat.site_id(t2, i2, j2) < 0) site_n[b.gids[q]][k] = 1;
       }
     }
-  // single-block regions and the plans of every message update
   block_regions.assign(geom.blocks.size(), Region());
   for (const Block& b : geom.blocks) {
     err = build_region(geom, {{b.X, b.Y}}, block_regions[b.id]);
@@ -187,7 +202,6 @@ int Engine::partition(int bx, int by) {
     if (!err.empty()) return fail(this, 4, "sweep plan: " + err);
     plans[{u.block, u.face}] = std::move(plan);
   }
-  // message buffers (open faces carry a fixed trivial message of dimension 1)
   msgs.clear();
   for (const Block& b : geom.blocks)
     for (int f = 0; f < 4; ++f) {
@@ -195,33 +209,49 @@ int Engine::partition(int bx, int by) {
       m.open = b.faces[f].nbr < 0;
       for (const Edge& e : b.faces[f].edges) m.Dleg.push_back(e.gid < 0 ? 1 : D);
     }
+  fused.clear();
   partitioned = true;
   messages_ready = false;
   return 0;
 }
 
-const double2* Engine::fused_tensor(int gid, const int perm[4]) {
+int Engine::set_precision(int p) {
+  if (p < 0 || p > 2) return fail(this, 1, "unknown precision");
+  if (messages_ready) return fail(this, 8, "precision must be set before bbp_init_messages");
+  if (p != precision) fused.clear();
+  precision = p;
+  return 0;
+}
+
+template <typename C>
+const C* Engine::fused_tensor(int gid, const int perm[4]) {
   int code = ((perm[0] * 4 + perm[1]) * 4 + perm[2]) * 4 + perm[3];
   auto key = std::make_pair(gid, code);
   auto it = fused.find(key);
-  if (it != fused.end()) return (const double2*)it->second.p;
+  if (it != fused.end()) return (const C*)it->second.p;
   const auto& nn = site_n[gid];
   size_t tot = 1;
   for (int q = 0; q < 4; ++q) tot *= (size_t)nn[q] * nn[q];
   DBuf& b = fused[key];
-  if (!b.ensure(tot * sizeof(double2), stream)) { fused.erase(key); return nullptr; }
+  if (!b.ensure(tot * sizeof(C), stream)) { fused.erase(key); return nullptr; }
   const double2* t = (const double2*)t_dev.p + (size_t)gid * d * D * D * D * D;
-  if (launch_fuse(t, d, D, nn.data(), nullptr, perm, (double2*)b.p, stream) != cudaSuccess) return nullptr;
-  return (const double2*)b.p;
+  if (launch_fuse(t, d, D, nn.data(), nullptr, perm, (C*)b.p, stream) != cudaSuccess) return nullptr;
+  return (const C*)b.p;
 }
 
 int Engine::init_messages(const double* edge_mats) {
+  return precision == 0 ? init_messages_t<double2>(edge_mats) : init_messages_t<float2>(edge_mats);
+}
+
+template <typename C>
+int Engine::init_messages_t(const double* edge_mats) {
   if (!partitioned) return fail(this, 8, "bbp_partition_blocks must come first");
   if (!edge_mats) return fail(this, 1, "edge_mats is NULL");
   const size_t cap = (size_t)chi * chi * D * D;
-  std::vector<double2> host;
+  std::vector<C> host;
   SweepWork* w = work(0);
   if (!w) return fail(this, 3, "stream creation failed");
+  if (!w->reserve(sizeof(C), 16, 16, 16, 4096, 4, 16)) return fail(this, 2, "work allocation failed");
   for (auto& kv : msgs) {
     Message& m = kv.second;
     const Block& b = geom.blocks[kv.first.first];
@@ -229,8 +259,8 @@ int Engine::init_messages(const double* edge_mats) {
     if (m.open) {
       m.cap = 1;
       for (int which = 0; which < 2; ++which) {
-        if (!m.buf[which].ensure(sizeof(double2) * m.k(), stream)) return fail(this, 2, "message allocation failed");
-        CK(launch_fill((double2*)m.buf[which].p, m.k(), 1.0, 0.0, stream));
+        if (!m.buf[which].ensure(sizeof(C) * m.k(), stream)) return fail(this, 2, "message allocation failed");
+        CK(launch_fill((C*)m.buf[which].p, m.k(), 1.0, 0.0, stream));
         m.sh[which].assign(m.k(), TShape{1, 1, 1});
       }
       m.cur = 0;
@@ -238,21 +268,25 @@ int Engine::init_messages(const double* edge_mats) {
     }
     m.cap = cap;
     for (int which = 0; which < 2; ++which)
-      if (!m.buf[which].ensure(sizeof(double2) * cap * m.k(), stream)) return fail(this, 2, "message allocation failed");
-    host.assign(cap * m.k(), kZero);
+      if (!m.buf[which].ensure(sizeof(C) * cap * m.k(), stream)) return fail(this, 2, "message allocation failed");
+    host.assign(cap * m.k(), zero_of<C>());
     m.sh[0].clear();
     for (int q = 0; q < m.k(); ++q) {
       const Edge& e = f.edges[q];
       int g = b.gids[e.site];
       const double* src = edge_mats + ((size_t)g * 4 + e.slot) * D * D * 2;
-      for (int a = 0; a < D * D; ++a) host[(size_t)q * cap + a] = make_double2(src[2 * a], src[2 * a + 1]);
+      for (int a = 0; a < D * D; ++a) {
+        C v;
+        v.x = (decltype(v.x))src[2 * a];
+        v.y = (decltype(v.y))src[2 * a + 1];
+        host[(size_t)q * cap + a] = v;
+      }
       m.sh[0].push_back(TShape{1, D * D, 1});
     }
     m.cur = 0;
     m.sh[1] = m.sh[0];
-    CK(cudaMemcpyAsync(m.buf[0].p, host.data(), sizeof(double2) * host.size(), cudaMemcpyHostToDevice, stream));
-    if (!w->reserve(16, 16, 16, 4096, 4, 16)) return fail(this, 2, "work allocation failed");
-    int rc = finalize_message(m, 0, *w, nullptr, false);
+    CK(cudaMemcpyAsync(m.buf[0].p, host.data(), sizeof(C) * host.size(), cudaMemcpyHostToDevice, stream));
+    int rc = finalize_message<C>(m, 0, *w, stream, nullptr, false);
     if (rc) return rc;
     CK(cudaStreamSynchronize(stream));
   }
@@ -260,56 +294,71 @@ int Engine::init_messages(const double* edge_mats) {
   return 0;
 }
 
-// Normalise (unit norm, <I|M> > 0) buffer `which` of m on the engine stream;
-// optionally write ||new - old|| into dist_slot (device double).
-int Engine::finalize_message(Message& m, int which, SweepWork& w, double* dist_slot, bool with_distance) {
-  cudaStream_t s = (&w == pool[0] && dist_slot == nullptr) ? stream : w.stream;
-  const int k = m.k();
-  std::vector<double2*> ptr(k);
-  std::vector<int> shp(3 * k);
-  for (int q = 0; q < k; ++q) {
-    ptr[q] = m.tensor(which, q);
-    shp[3 * q] = m.sh[which][q].l;
-    shp[3 * q + 1] = m.sh[which][q].p;
-    shp[3 * q + 2] = m.sh[which][q].r;
+// Normalise (unit norm, <I|M> > 0) buffer `which` of m on stream s;
+// optionally write ||new - old|| (complex128 QR sweep) into dist_slot.
+namespace {
+template <typename C>
+ChainDesc chain_of(const Message& m, int which) {
+  ChainDesc d{};
+  d.k = m.k();
+  for (int q = 0; q < d.k; ++q) {
+    d.T[q] = m.tensor<C>(which, q);
+    d.l[q] = m.sh[which][q].l;
+    d.p[q] = m.sh[which][q].p;
+    d.r[q] = m.sh[which][q].r;
+    d.D[q] = m.Dleg[q];
   }
-  std::vector<int> dl(m.Dleg);
-  CK(cudaMemcpyAsync(w.ptrs, ptr.data(), sizeof(void*) * k, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(w.ints, shp.data(), sizeof(int) * 3 * k, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(w.ints + 3 * 64, dl.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s));
-  CK(launch_msg_normalise(w.ptrs, w.ints, k, w.ints + 3 * 64, (double*)w.k4, s));
+  return d;
+}
+}  // namespace
+
+// Normalise (unit norm, <I|M> > 0) buffer `which` of m on stream s;
+// optionally write ||new - old|| into dist_slot: the norm of the direct-sum
+// MPS (new, -old) reduced by a QR sweep, in the element type (absolute
+// accuracy ~ eps of that type, no sqrt(2 - 2 Re<old|new>) floor).
+template <typename C>
+int Engine::finalize_message(Message& m, int which, SweepWork& w, cudaStream_t s, double* dist_slot,
+                             bool with_distance) {
+  const int k = m.k();
+  if (k > kMaxChain) return fail(this, 1, "message longer than 64 tensors");
+  CK(launch_msg_normalise(chain_of<C>(m, which), sizeof(C) == sizeof(float2), w.k4, s));
   sweep_launches += 1;
   if (!with_distance) return 0;
-  // ||new - old|| by a QR sweep of the direct-sum MPS
   const int old = 1 - which;
-  int kprev = 0;   // rows of the carried R factor
+  const C one = one_of<C>(), zero = zero_of<C>();
+  C* X0 = (C*)w.dX0;
+  C* X1 = (C*)w.dX1;
+  C* Qd = (C*)w.dQ;
+  C* Rd = (C*)w.dR;
+  C* td = (C*)w.dtau;
+  int kprev = 0;
   for (int q = 0; q < k; ++q) {
     const TShape& a = m.sh[which][q];
     const TShape& b = m.sh[old][q];
     const int L = (k == 1 || q == 0) ? 1 : a.l + b.l;
     const int Rr = (k == 1 || q == k - 1) ? 1 : a.r + b.r;
     const int p = a.p;
-    CK(launch_direct_sum(m.tensor(which, q), a.l, a.r, m.tensor(old, q), b.l, b.r, p, q, k, w.dX0, s));
-    double2* X = w.dX0;
+    CK(launch_direct_sum(m.tensor<C>(which, q), a.l, a.r, m.tensor<C>(old, q), b.l, b.r, p, q, k, X0, s));
+    C* X = X0;
     int rows = L;
     if (q > 0) {
-      CK(launch_zgemm('N', 'N', kprev, p * Rr, L, kOne, w.dR, L, 0, w.dX0, p * Rr, 0, kZero, w.dX1, p * Rr, 0, 1, s));
-      X = w.dX1;
+      CK(launch_zgemm('N', 'N', kprev, p * Rr, L, one, Rd, L, 0, X0, p * Rr, 0, zero, X1, p * Rr, 0, 1, s));
+      X = X1;
       rows = kprev;
     }
     const int mrows = rows * p;
-    const int kk = std::min(mrows, Rr);
-    CK(launch_qr(X, mrows, Rr, w.dQ, w.dR, w.tau, s));
-    kprev = kk;
+    CK(launch_qr(X, mrows, Rr, Qd, Rd, td, s));
+    kprev = std::min(mrows, Rr);
     sweep_launches += 3;
   }
-  CK(launch_frob(w.dR, (long long)kprev * 1, dist_slot, s));
+  CK(launch_frob(Rd, (long long)kprev, dist_slot, s));
   sweep_launches += 1;
   return 0;
 }
 
-int Engine::fill_job(const Region& R, const SweepPlan& plan, SweepJob& job,
-                     const std::vector<std::pair<std::array<int, 2>, const double*>>& ops, std::vector<DBuf*>& tmp) {
+template <typename C>
+int Engine::fill_job(const Region& R, const SweepPlan& plan, SweepJob& job, const OpList& ops,
+                     std::vector<DBuf*>& tmp) {
   job.plan = &plan;
   LegDims dims;
   job.node_tensor.assign(plan.nodes.size(), nullptr);
@@ -332,19 +381,19 @@ int Engine::fill_job(const Region& R, const SweepPlan& plan, SweepJob& job,
         for (int q = 0; q < 4; ++q) tot *= (size_t)nn[q] * nn[q];
         DBuf* b = new DBuf();
         tmp.push_back(b);
-        if (!b->ensure(tot * sizeof(double2), stream)) return fail(this, 2, "fused operator allocation failed");
+        if (!b->ensure(tot * sizeof(C), stream)) return fail(this, 2, "fused operator allocation failed");
         const double2* t = (const double2*)t_dev.p + (size_t)n.gid * d * D * D * D * D;
-        CK(launch_fuse(t, d, D, nn.data(), (const double2*)op, perm, (double2*)b->p, stream));
-        job.node_tensor[s] = (const double2*)b->p;
+        CK(launch_fuse(t, d, D, nn.data(), (const double2*)op, perm, (C*)b->p, stream));
+        job.node_tensor[s] = b->p;
       } else {
-        job.node_tensor[s] = fused_tensor(n.gid, perm);
+        job.node_tensor[s] = fused_tensor<C>(n.gid, perm);
         if (!job.node_tensor[s]) return fail(this, 2, "fusion failed");
       }
     } else {
       const Message& m = msgs.at({R.ids[n.msg_inst], n.msg_dir});
       const TShape sh = m.sh[m.cur][n.msg_index];
       job.node_shape[s] = sh;
-      job.node_tensor[s] = m.tensor(m.cur, n.msg_index);
+      job.node_tensor[s] = m.tensor<C>(m.cur, n.msg_index);
       dims.node_dims[s] = {sh.l, sh.p, sh.r, 1};
     }
   }
@@ -352,7 +401,7 @@ int Engine::fill_job(const Region& R, const SweepPlan& plan, SweepJob& job,
   job.start_shape.clear();
   for (const auto& st : plan.start) {
     const Message& m = msgs.at({R.ids[st[0]], st[1]});
-    job.start.push_back(m.tensor(m.cur, st[2]));
+    job.start.push_back(m.tensor<C>(m.cur, st[2]));
     job.start_shape.push_back(m.sh[m.cur][st[2]]);
     dims.start.push_back(m.sh[m.cur][st[2]]);
   }
@@ -361,49 +410,57 @@ int Engine::fill_job(const Region& R, const SweepPlan& plan, SweepJob& job,
   return 0;
 }
 
-// Workspace needed by one sweep job; reserved before any work is enqueued so
-// that no buffer is reallocated while a stream may still use it.
-static void job_needs(const SweepJob& job, int chi, int D, size_t need[6]) {
+// Workspace (in elements, except the SVD bytes) needed by one sweep job.
+void Engine::job_needs(const SweepJob& job, size_t need[7]) const {
   const ShapeTrace& tr = job.tr;
   size_t cap_x = 1;
   for (size_t q = 0; q < job.plan->nodes.size(); ++q)
     if (!job.plan->nodes[q].site) cap_x = std::max(cap_x, (size_t)job.node_shape[q].size());
+  const int mr = (int)std::max<long long>(tr.max_svd_rows, 1), mc = (int)std::max<long long>(tr.max_svd_cols, 1);
   need[0] = std::max<size_t>(need[0], (size_t)tr.max_tensor);
   need[1] = std::max<size_t>(need[1], (size_t)std::max(tr.max_seg, tr.max_tensor));
   need[2] = std::max<size_t>(need[2], cap_x);
-  need[3] = std::max<size_t>(need[3], svd_work_bytes((int)std::max<long long>(tr.max_svd_rows, 1),
-                                                     (int)std::max<long long>(tr.max_svd_cols, 1)));
+  need[3] = std::max<size_t>(need[3], precision == 0 ? svd_work_bytes(mr, mc) : svd_work_bound_c64(mr, mc, chi));
   need[4] = std::max<size_t>(need[4], (size_t)tr.max_len + 6);
   need[5] = std::max<size_t>(need[5], (size_t)4 * chi * chi * D * D + 64);
 }
 
 int Engine::reserve_workers(const std::vector<SweepJob>& jobs, int nstreams) {
   for (int i = 0; i < nstreams; ++i) {
-    size_t need[6] = {1, 1, 1, 256, 4, 16};
-    for (size_t j = i; j < jobs.size(); j += nstreams) job_needs(jobs[j], chi, D, need);
+    size_t need[7] = {1, 1, 1, 256, 4, 16, 0};
+    for (size_t j = i; j < jobs.size(); j += nstreams) job_needs(jobs[j], need);
     SweepWork& w = *pool[i];
-    if (need[0] <= w.cap_t && need[1] <= w.cap_seg && need[2] <= w.cap_x && need[3] <= w.svd_bytes &&
-        need[4] <= w.nslots && need[5] <= w.cap_d && w.arena.p)
+    if (w.elem == elem() && need[0] <= w.cap_t && need[1] <= w.cap_seg && need[2] <= w.cap_x &&
+        need[3] <= w.svd_bytes && need[4] <= w.nslots && need[5] <= w.cap_d && w.arena.p)
       continue;
     CK(cudaStreamSynchronize(w.stream));
     CK(cudaStreamSynchronize(stream));
-    if (!w.reserve(need[0], need[1], need[2], need[3], need[4], need[5]))
+    if (!w.reserve(elem(), need[0], need[1], need[2], need[3], need[4], need[5]))
       return fail(this, 2, "sweep workspace allocation failed");
   }
   return 0;
 }
 
+template <typename C>
 int Engine::run_sweep(SweepJob& job, SweepWork& w) {
   const SweepPlan& plan = *job.plan;
   const ShapeTrace& tr = job.tr;
   cudaStream_t s = w.stream;
   {
-    size_t need[6] = {1, 1, 1, 256, 4, 16};
-    job_needs(job, chi, D, need);
-    if (need[0] > w.cap_t || need[1] > w.cap_seg || need[2] > w.cap_x || need[3] > w.svd_bytes || need[4] > w.nslots ||
-        need[5] > w.cap_d)
+    size_t need[7] = {1, 1, 1, 256, 4, 16, 0};
+    job_needs(job, need);
+    if (w.elem != sizeof(C) || need[0] > w.cap_t || need[1] > w.cap_seg || need[2] > w.cap_x ||
+        need[3] > w.svd_bytes || need[4] > w.nslots || need[5] > w.cap_d)
       return fail(this, 8, "sweep workspace was not reserved");
   }
+  const C one = one_of<C>(), zero = zero_of<C>();
+  auto slot = [&](int i) { return (C*)w.slot[i]; };
+  C* Sb[2] = {(C*)w.S[0], (C*)w.S[1]};
+  C* Rb[2] = {(C*)w.R[0], (C*)w.R[1]};
+  C* qrA = (C*)w.qrA;
+  C* qrQ = (C*)w.qrQ;
+  C* qrR = (C*)w.qrR;
+  C* tau = (C*)w.tau;
 
   std::vector<int> freelist;
   for (int i = (int)w.nslots - 1; i >= 0; --i) freelist.push_back(i);
@@ -415,31 +472,30 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
 
   CK(cudaMemsetAsync(w.logscale, 0, sizeof(double), s));
   CK(cudaMemsetAsync(w.status, 0, sizeof(int), s));
-  // initial boundary [1, start..., 1]
   pos.push_back(take());
   sh.push_back(TShape{1, 1, 1});
-  CK(launch_fill(w.slot[pos.back()], 1, 1.0, 0.0, s));
+  CK(launch_fill(slot(pos.back()), 1, 1.0, 0.0, s));
   for (size_t q = 0; q < job.start.size(); ++q) {
     TShape t = job.start_shape[q];
     pos.push_back(take());
-    CK(launch_copy_tensor(job.start[q], w.slot[pos.back()], t.l, t.p, t.r, plan.start_reversed, s));
+    CK(launch_copy_tensor((const C*)job.start[q], slot(pos.back()), t.l, t.p, t.r, plan.start_reversed, s));
     if (plan.start_reversed) std::swap(t.l, t.r);
     sh.push_back(t);
   }
   pos.push_back(take());
   sh.push_back(TShape{1, 1, 1});
-  CK(launch_fill(w.slot[pos.back()], 1, 1.0, 0.0, s));
+  CK(launch_fill(slot(pos.back()), 1, 1.0, 0.0, s));
   launches += 2 + (long long)job.start.size();
 
   auto qr_move = [&](int c) -> int {   // centre c -> c + 1
     TShape a = sh[c], b = sh[c + 1];
     const int m = a.l * a.p, n = a.r, kk = std::min(m, n);
-    CK(cudaMemcpyAsync(w.qrA, w.slot[pos[c]], sizeof(double2) * (size_t)m * n, cudaMemcpyDeviceToDevice, s));
-    CK(launch_qr(w.qrA, m, n, w.qrQ, w.qrR, w.tau, s));
-    CK(cudaMemcpyAsync(w.slot[pos[c]], w.qrQ, sizeof(double2) * (size_t)m * kk, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(qrA, slot(pos[c]), sizeof(C) * (size_t)m * n, cudaMemcpyDeviceToDevice, s));
+    CK(launch_qr(qrA, m, n, qrQ, qrR, tau, s));
+    CK(cudaMemcpyAsync(slot(pos[c]), qrQ, sizeof(C) * (size_t)m * kk, cudaMemcpyDeviceToDevice, s));
     sh[c].r = kk;
     const int t = take();
-    CK(launch_zgemm('N', 'N', kk, b.p * b.r, n, kOne, w.qrR, n, 0, w.slot[pos[c + 1]], b.p * b.r, 0, kZero, w.slot[t],
+    CK(launch_zgemm('N', 'N', kk, b.p * b.r, n, one, qrR, n, 0, slot(pos[c + 1]), b.p * b.r, 0, zero, slot(t),
                     b.p * b.r, 0, 1, s));
     give(pos[c + 1]);
     pos[c + 1] = t;
@@ -450,13 +506,12 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
   auto lq_move = [&](int c) -> int {   // centre c -> c - 1
     TShape b = sh[c], a = sh[c - 1];
     const int m = b.p * b.r, n = b.l, kk = std::min(m, n);
-    CK(launch_conj_transpose(w.slot[pos[c]], b.l, b.p * b.r, w.qrA, s));
-    CK(launch_qr(w.qrA, m, n, w.qrQ, w.qrR, w.tau, s));
-    CK(launch_conj_transpose(w.qrQ, m, kk, w.slot[pos[c]], s));
+    CK(launch_conj_transpose(slot(pos[c]), b.l, b.p * b.r, qrA, s));
+    CK(launch_qr(qrA, m, n, qrQ, qrR, tau, s));
+    CK(launch_conj_transpose(qrQ, m, kk, slot(pos[c]), s));
     sh[c].l = kk;
     const int t = take();
-    CK(launch_zgemm('N', 'C', a.l * a.p, kk, n, kOne, w.slot[pos[c - 1]], n, 0, w.qrR, n, 0, kZero, w.slot[t], kk, 0, 1,
-                    s));
+    CK(launch_zgemm('N', 'C', a.l * a.p, kk, n, one, slot(pos[c - 1]), n, 0, qrR, n, 0, zero, slot(t), kk, 0, 1, s));
     give(pos[c - 1]);
     pos[c - 1] = t;
     sh[c - 1].r = kk;
@@ -464,7 +519,7 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
     return 0;
   };
   auto normalise = [&](int c) -> int {
-    CK(launch_normalise(w.slot[pos[c]], sh[c].size(), w.logscale, s));
+    CK(launch_normalise(slot(pos[c]), sh[c].size(), w.logscale, s));
     launches += 1;
     return 0;
   };
@@ -480,23 +535,22 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
     const auto& rec = tr.steps[si];
     while (c < st.i) { if (int rc = qr_move(c)) return rc; ++c; }
     while (c > st.j) { if (int rc = lq_move(c)) return rc; --c; }
-    // merge the in-segment into S[l, P, r]
     const int l = sh[st.i].l, r = sh[st.j].r;
-    const double2* Sp;
+    const C* Sp;
     long long P;
     if (st.nin == 1) {
-      Sp = w.slot[pos[st.i]];
+      Sp = slot(pos[st.i]);
       P = sh[st.i].p;
     } else {
-      const double2* cur = w.slot[pos[st.i]];
+      const C* cur = slot(pos[st.i]);
       long long rows = (long long)l * sh[st.i].p;
       int inner = sh[st.i].r;
       int buf = 0;
       for (int q = st.i + 1; q <= st.j; ++q) {
         const int cols = sh[q].p * sh[q].r;
-        CK(launch_zgemm('N', 'N', (int)rows, cols, inner, kOne, cur, inner, 0, w.slot[pos[q]], cols, 0, kZero, w.S[buf],
+        CK(launch_zgemm('N', 'N', (int)rows, cols, inner, one, cur, inner, 0, slot(pos[q]), cols, 0, zero, Sb[buf],
                         cols, 0, 1, s));
-        cur = w.S[buf];
+        cur = Sb[buf];
         buf ^= 1;
         rows *= sh[q].p;
         inner = sh[q].r;
@@ -507,28 +561,27 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
     }
     if (P != rec.P) return fail(this, 8, "sweep: merged dimension disagrees with the plan");
     // contraction R[a, Q, b] = sum_P X[P, Q] S[a, P, b]
-    const double2* X = job.node_tensor[st.node];
+    const C* X = (const C*)job.node_tensor[st.node];
     if (!node.site) {
       const TShape ms = job.node_shape[st.node];
       int perm[3];
       for (int q = 0; q < st.nin; ++q) perm[q] = st.in_leg[q];
       for (int q = 0; q < st.nout; ++q) perm[st.nin + q] = st.out_leg[q];
-      CK(launch_permute3(X, ms.l, ms.p, ms.r, perm, w.X, s));
-      X = w.X;
+      CK(launch_permute3(X, ms.l, ms.p, ms.r, perm, (C*)w.X, s));
+      X = (const C*)w.X;
       ++launches;
     }
     const int Q = rec.Q;
-    CK(launch_zgemm('T', 'N', Q, r, (int)P, kOne, X, Q, 0, Sp, r, P * r, kZero, w.R[0], r, (long long)Q * r, l, s));
+    CK(launch_zgemm('T', 'N', Q, r, (int)P, one, X, Q, 0, Sp, r, P * r, zero, Rb[0], r, (long long)Q * r, l, s));
     ++launches;
     sweep_flops += 8.0 * (double)l * (double)P * (double)Q * (double)r;
-    // split
     std::vector<int> newpos;
     std::vector<TShape> newsh;
     if (st.nout == 0) {
       if (st.i > 0) {
         const TShape a = sh[st.i - 1];
         const int t = take();
-        CK(launch_zgemm('N', 'N', a.l * a.p, r, l, kOne, w.slot[pos[st.i - 1]], l, 0, w.R[0], r, 0, kZero, w.slot[t], r, 0,
+        CK(launch_zgemm('N', 'N', a.l * a.p, r, l, one, slot(pos[st.i - 1]), l, 0, Rb[0], r, 0, zero, slot(t), r, 0,
                         1, s));
         give(pos[st.i - 1]);
         pos[st.i - 1] = t;
@@ -540,8 +593,8 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
       } else {
         const TShape b = sh[st.j + 1];
         const int t = take();
-        CK(launch_zgemm('N', 'N', l, b.p * b.r, r, kOne, w.R[0], r, 0, w.slot[pos[st.j + 1]], b.p * b.r, 0, kZero,
-                        w.slot[t], b.p * b.r, 0, 1, s));
+        CK(launch_zgemm('N', 'N', l, b.p * b.r, r, one, Rb[0], r, 0, slot(pos[st.j + 1]), b.p * b.r, 0, zero, slot(t),
+                        b.p * b.r, 0, 1, s));
         give(pos[st.j + 1]);
         pos[st.j + 1] = t;
         sh[st.j + 1].l = l;
@@ -552,7 +605,7 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
       }
       ++launches;
     } else {
-      const double2* cur = w.R[0];
+      const C* cur = Rb[0];
       int rbuf = 1;
       int ll = l;
       long long rest = Q;
@@ -563,17 +616,17 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
         const long long cols = rest * r;
         const int k = rec.split[q].r;
         const int t = take();
-        CK(launch_svd_trunc(cur, rows, (int)cols, chi, w.slot[t], w.R[rbuf], w.svd, w.status, s));
-        launches += 5;
+        CK(svd_call(cur, rows, (int)cols, chi, slot(t), Rb[rbuf], w.svd, w.status, s, power_iters));
+        launches += sizeof(C) == sizeof(double2) ? 5 : 10 + 4 * power_iters;
         newpos.push_back(t);
         newsh.push_back(TShape{ll, q1, k});
-        cur = w.R[rbuf];
+        cur = Rb[rbuf];
         rbuf ^= 1;
         ll = k;
       }
       const int qlast = rec.out_dims[st.nout - 1];
       const int t = take();
-      CK(cudaMemcpyAsync(w.slot[t], cur, sizeof(double2) * (size_t)ll * qlast * r, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(slot(t), cur, sizeof(C) * (size_t)ll * qlast * r, cudaMemcpyDeviceToDevice, s));
       ++launches;
       newpos.push_back(t);
       newsh.push_back(TShape{ll, qlast, r});
@@ -586,20 +639,19 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
     }
     if (int rc = normalise(c)) return rc;
   }
-  // merge the two end tensors into their neighbours
   const int n = (int)pos.size();
   if (n < 3) return fail(this, 8, "sweep: final boundary too short");
   {
     const int t = take();
-    CK(launch_zgemm('N', 'N', 1, sh[1].p * sh[1].r, sh[0].r, kOne, w.slot[pos[0]], sh[0].r, 0, w.slot[pos[1]],
-                    sh[1].p * sh[1].r, 0, kZero, w.slot[t], sh[1].p * sh[1].r, 0, 1, s));
+    CK(launch_zgemm('N', 'N', 1, sh[1].p * sh[1].r, sh[0].r, one, slot(pos[0]), sh[0].r, 0, slot(pos[1]),
+                    sh[1].p * sh[1].r, 0, zero, slot(t), sh[1].p * sh[1].r, 0, 1, s));
     give(pos[1]);
     pos[1] = t;
     sh[1].l = 1;
     const int t2 = take();
     const TShape b = sh[n - 2];
-    CK(launch_zgemm('N', 'N', b.l * b.p, 1, b.r, kOne, w.slot[pos[n - 2]], b.r, 0, w.slot[pos[n - 1]], 1, 0, kZero,
-                    w.slot[t2], 1, 0, 1, s));
+    CK(launch_zgemm('N', 'N', b.l * b.p, 1, b.r, one, slot(pos[n - 2]), b.r, 0, slot(pos[n - 1]), 1, 0, zero, slot(t2),
+                    1, 0, 1, s));
     give(pos[n - 2]);
     pos[n - 2] = t2;
     sh[n - 2].r = 1;
@@ -610,14 +662,19 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
   for (int q = 0; q < L; ++q) {
     const TShape t = sh[1 + q];
     const int di = plan.out_reversed ? (L - 1 - q) : q;
-    CK(launch_copy_tensor(w.slot[pos[1 + q]], job.dest[di], t.l, t.p, t.r, plan.out_reversed, s));
+    CK(launch_copy_tensor(slot(pos[1 + q]), (C*)job.dest[di], t.l, t.p, t.r, plan.out_reversed, s));
     ++launches;
   }
   sweep_launches += launches;
   return 0;
 }
 
-int Engine::iterate(double tol, int max_iter, int* iters, double* err_out) {
+int Engine::iterate(double tol, int max_iter, int* iters, double* err) {
+  return precision == 0 ? iterate_t<double2>(tol, max_iter, iters, err) : iterate_t<float2>(tol, max_iter, iters, err);
+}
+
+template <typename C>
+int Engine::iterate_t(double tol, int max_iter, int* iters, double* err_out) {
   if (!partitioned) return fail(this, 8, "bbp_partition_blocks must come first");
   if (!messages_ready) return fail(this, 8, "bbp_init_messages must come first");
   if (max_iter < 0 || !(tol >= 0.0)) return fail(this, 1, "tol must be >= 0 and max_iter >= 0");
@@ -643,11 +700,10 @@ int Engine::iterate(double tol, int max_iter, int* iters, double* err_out) {
     sweep_launches = 0;
     sweep_flops = 0.0;
     std::vector<DBuf*> tmp;
-    // fill every job first: lazily fused tensors are launched on the engine stream
     std::vector<SweepJob> jobs(nu);
     for (int u = 0; u < nu && !rc; ++u) {
       const auto& up = ups[u];
-      if ((rc = fill_job(block_regions[up.block], plans.at({up.block, up.face}), jobs[u], {}, tmp))) break;
+      if ((rc = fill_job<C>(block_regions[up.block], plans.at({up.block, up.face}), jobs[u], {}, tmp))) break;
       Message& dst = msgs.at({up.recv_block, up.recv_face});
       for (const TShape& t : jobs[u].tr.final_mps)
         if ((size_t)t.size() > dst.cap) { rc = fail(this, 8, "message tensor exceeds its buffer"); break; }
@@ -663,10 +719,10 @@ int Engine::iterate(double tol, int max_iter, int* iters, double* err_out) {
       Message& dst = msgs.at({up.recv_block, up.recv_face});
       const int nxt = 1 - dst.cur;
       jobs[u].dest.clear();
-      for (int q = 0; q < dst.k(); ++q) jobs[u].dest.push_back(dst.tensor(nxt, q));
+      for (int q = 0; q < dst.k(); ++q) jobs[u].dest.push_back(dst.tensor<C>(nxt, q));
       dst.sh[nxt] = jobs[u].tr.final_mps;
-      if ((rc = run_sweep(jobs[u], w))) break;
-      if ((rc = finalize_message(dst, nxt, w, (double*)dist_dev.p + u, true))) break;
+      if ((rc = run_sweep<C>(jobs[u], w))) break;
+      if ((rc = finalize_message<C>(dst, nxt, w, w.stream, (double*)dist_dev.p + u, true))) break;
     }
     for (DBuf* b : tmp) delete b;
     for (int i = 0; i < nstreams; ++i) {
@@ -679,17 +735,21 @@ int Engine::iterate(double tol, int max_iter, int* iters, double* err_out) {
       CK(cudaMemcpyAsync(&hs[i], pool[i]->status, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
     err = 0.0;
-    bool bad = false;
+    bool nonfinite = false, sweep_limit = false;
     for (int u = 0; u < nu; ++u) {
-      if (!std::isfinite(hd[u])) bad = true;
+      if (!std::isfinite(hd[u])) nonfinite = true;
       err = std::max(err, hd[u]);
     }
-    for (int i = 0; i < nstreams; ++i) bad = bad || hs[i] != 0;
+    for (int i = 0; i < nstreams; ++i) sweep_limit = sweep_limit || hs[i] != 0;
     for (const auto& up : ups) msgs.at({up.recv_block, up.recv_face}).cur ^= 1;
     launches_per_iter = sweep_launches;
     flops_per_iter = sweep_flops;
     ++n_iterations;
-    if (bad) { rc = fail(this, 5, "non-finite message or an SVD that did not converge"); ++it; break; }
+    if (nonfinite || sweep_limit) {
+      rc = fail(this, 5, nonfinite ? "a message became non-finite" : "a Jacobi SVD reached its sweep limit");
+      ++it;
+      break;
+    }
     if (err <= tol) { ++it; break; }
   }
   cudaEventDestroy(fork);
@@ -702,9 +762,15 @@ int Engine::iterate(double tol, int max_iter, int* iters, double* err_out) {
 
 // --------------------------------------------------------------- observables
 
-int Engine::contract_batch(const std::vector<std::vector<std::array<int, 2>>>& coords,
-                           const std::vector<std::vector<std::pair<std::array<int, 2>, const double*>>>& ops,
+int Engine::contract_batch(const std::vector<std::vector<std::array<int, 2>>>& coords, const std::vector<OpList>& ops,
                            std::vector<double>& logscale, std::vector<double>& re, std::vector<double>& im) {
+  return precision == 0 ? contract_batch_t<double2>(coords, ops, logscale, re, im)
+                        : contract_batch_t<float2>(coords, ops, logscale, re, im);
+}
+
+template <typename C>
+int Engine::contract_batch_t(const std::vector<std::vector<std::array<int, 2>>>& coords, const std::vector<OpList>& ops,
+                             std::vector<double>& logscale, std::vector<double>& re, std::vector<double>& im) {
   if (!partitioned || !messages_ready) return fail(this, 8, "partition and messages are required first");
   const int nj = (int)coords.size();
   logscale.assign(nj, 0.0);
@@ -715,7 +781,6 @@ int Engine::contract_batch(const std::vector<std::vector<std::array<int, 2>>>& c
     if (!work(i)) return fail(this, 3, "stream creation failed");
   cudaEvent_t fork;
   CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-  // results: per job (logscale, value) copied into a device staging buffer
   DBuf res;
   if (!res.ensure(sizeof(double) * 4 * nj + 256, stream)) return fail(this, 2, "allocation failed");
   std::vector<DBuf*> tmp;
@@ -729,15 +794,15 @@ int Engine::contract_batch(const std::vector<std::vector<std::array<int, 2>>>& c
     err = compile_sweep(geom, regions[j], TOP, plansv[j]);
     if (!err.empty()) { rc = fail(this, 8, "sweep plan: " + err); break; }
     SweepJob& job = jobs[j];
-    if ((rc = fill_job(regions[j], plansv[j], job, ops[j], tmp))) break;
+    if ((rc = fill_job<C>(regions[j], plansv[j], job, ops[j], tmp))) break;
     DBuf* out = new DBuf();
     tmp.push_back(out);
     size_t tot = 0;
     for (const TShape& t : job.tr.final_mps) tot += (size_t)t.size();
-    if (!out->ensure(sizeof(double2) * tot + 256, stream)) { rc = fail(this, 2, "allocation failed"); break; }
+    if (!out->ensure(sizeof(C) * tot + 256, stream)) { rc = fail(this, 2, "allocation failed"); break; }
     size_t off = 0;
     job.dest.clear();
-    for (const TShape& t : job.tr.final_mps) { job.dest.push_back((double2*)out->p + off); off += (size_t)t.size(); }
+    for (const TShape& t : job.tr.final_mps) { job.dest.push_back((C*)out->p + off); off += (size_t)t.size(); }
   }
   if (!rc) rc = reserve_workers(jobs, nstreams);
   if (!rc) {
@@ -747,30 +812,25 @@ int Engine::contract_batch(const std::vector<std::vector<std::array<int, 2>>>& c
   for (int j = 0; j < nj && !rc; ++j) {
     SweepWork& w = *pool[j % nstreams];
     SweepJob& job = jobs[j];
-    if ((rc = run_sweep(job, w))) break;
-    // plain contraction with the incoming top messages
-    std::vector<double2*> pa, pb;
-    std::vector<int> sa, sb;
-    for (size_t q = 0; q < job.dest.size(); ++q) {
-      pa.push_back(job.dest[q]);
+    if ((rc = run_sweep<C>(job, w))) break;
+    ChainDesc A{}, B{};
+    for (size_t q = 0; q < job.dest.size() && q < (size_t)kMaxChain; ++q) {
       const TShape t = job.tr.final_mps[q];
-      sa.insert(sa.end(), {t.l, t.p, t.r});
+      A.T[A.k] = job.dest[q];
+      A.l[A.k] = t.l; A.p[A.k] = t.p; A.r[A.k] = t.r;
+      ++A.k;
     }
     for (const auto& f : regions[j].side_faces[TOP]) {
       const Message& m = msgs.at({regions[j].ids[f[0]], f[1]});
-      for (int q = 0; q < m.k(); ++q) {
-        pb.push_back(m.tensor(m.cur, q));
+      for (int q = 0; q < m.k() && B.k < kMaxChain; ++q) {
         const TShape t = m.sh[m.cur][q];
-        sb.insert(sb.end(), {t.l, t.p, t.r});
+        B.T[B.k] = m.tensor<C>(m.cur, q);
+        B.l[B.k] = t.l; B.p[B.k] = t.p; B.r[B.k] = t.r;
+        ++B.k;
       }
     }
-    if (pa.size() != pb.size() || pa.size() > 64) { rc = fail(this, 8, "top face mismatch"); break; }
-    const int k = (int)pa.size();
-    CK(cudaMemcpyAsync(w.ptrs, pa.data(), sizeof(void*) * k, cudaMemcpyHostToDevice, w.stream));
-    CK(cudaMemcpyAsync(w.ptrs + 64, pb.data(), sizeof(void*) * k, cudaMemcpyHostToDevice, w.stream));
-    CK(cudaMemcpyAsync(w.ints, sa.data(), sizeof(int) * 3 * k, cudaMemcpyHostToDevice, w.stream));
-    CK(cudaMemcpyAsync(w.ints + 3 * 64, sb.data(), sizeof(int) * 3 * k, cudaMemcpyHostToDevice, w.stream));
-    CK(launch_mps_dot(w.ptrs, w.ptrs + 64, w.ints, w.ints + 3 * 64, k, w.k4, w.scal, w.stream));
+    if (A.k != B.k || job.dest.size() > (size_t)kMaxChain) { rc = fail(this, 8, "top face mismatch"); break; }
+    CK(launch_mps_dot(A, B, sizeof(C) == sizeof(float2), w.k4, w.scal, w.stream));
     double* rp = (double*)res.p + 4 * j;
     CK(cudaMemcpyAsync(rp, w.logscale, sizeof(double), cudaMemcpyDeviceToDevice, w.stream));
     CK(cudaMemcpyAsync(rp + 1, w.scal, sizeof(double2), cudaMemcpyDeviceToDevice, w.stream));
@@ -781,9 +841,7 @@ int Engine::contract_batch(const std::vector<std::vector<std::array<int, 2>>>& c
     CK(cudaStreamWaitEvent(stream, pool[i]->done, 0));
   }
   std::vector<double> h(4 * (size_t)nj);
-  if (!rc) {
-    CK(cudaMemcpyAsync(h.data(), res.p, sizeof(double) * 4 * nj, cudaMemcpyDeviceToHost, stream));
-  }
+  if (!rc) CK(cudaMemcpyAsync(h.data(), res.p, sizeof(double) * 4 * nj, cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
   for (DBuf* b : tmp) delete b;
   cudaEventDestroy(fork);
@@ -796,18 +854,6 @@ int Engine::contract_batch(const std::vector<std::vector<std::array<int, 2>>>& c
     std::memcpy(&st, &h[4 * j + 3], sizeof(int));
     if (st != 0) return fail(this, 5, "an SVD did not converge in a contraction");
   }
-  return 0;
-}
-
-int Engine::contract(const std::vector<std::array<int, 2>>& coords,
-                     const std::vector<std::pair<std::array<int, 2>, const double*>>& ops, double* logscale, double* re,
-                     double* im) {
-  std::vector<double> l, r, i;
-  int rc = contract_batch({coords}, {ops}, l, r, i);
-  if (rc) return rc;
-  *logscale = l[0];
-  *re = r[0];
-  *im = i[0];
   return 0;
 }
 
@@ -850,9 +896,8 @@ int Engine::energy_per_site(double* e) {
   const double* dsx = (const double*)op_dev.p;
   const double* dsy = dsx + 8;
   const double* dsz = dsx + 16;
-  // every bond once
-  std::vector<std::vector<std::array<int, 2>>> C;
-  std::vector<std::vector<std::pair<std::array<int, 2>, const double*>>> O;
+  std::vector<std::vector<std::array<int, 2>>> Cc;
+  std::vector<OpList> O;
   const Lattice& L = geom.lat;
   std::vector<std::array<int, 4>> seen;
   int nb = 0;
@@ -872,22 +917,21 @@ int Engine::energy_per_site(double* e) {
           std::vector<std::array<int, 2>> coords;
           std::array<int, 2> k1, kk2;
           if (int rc = bond_region(g, k, coords, k1, kk2)) return rc;
-          C.push_back(coords);
+          Cc.push_back(coords);
           O.push_back({});
           for (const double* op : {dsx, dsy, dsz}) {
-            C.push_back(coords);
+            Cc.push_back(coords);
             O.push_back({{k1, op}, {kk2, op}});
           }
           ++nb;
         }
       }
   std::vector<double> ls, re, im;
-  if (int rc = contract_batch(C, O, ls, re, im)) return rc;
+  if (int rc = contract_batch(Cc, O, ls, re, im)) return rc;
   double tot = 0.0;
   for (int b = 0; b < nb; ++b) {
     const int j0 = 4 * b;
     for (int a = 1; a <= 3; ++a) {
-      // value_a / value_0 (complex), real part
       double r0 = re[j0], i0 = im[j0], r1 = re[j0 + a], i1 = im[j0 + a];
       double den = r0 * r0 + i0 * i0;
       double scale = std::exp(ls[j0 + a] - ls[j0]);
@@ -898,20 +942,22 @@ int Engine::energy_per_site(double* e) {
   return 0;
 }
 
-int Engine::log_norm(double* out) {
-  std::vector<std::vector<std::array<int, 2>>> C;
-  std::vector<std::vector<std::pair<std::array<int, 2>, const double*>>> O;
+int Engine::log_norm(double* out) { return precision == 0 ? log_norm_t<double2>(out) : log_norm_t<float2>(out); }
+
+template <typename C>
+int Engine::log_norm_t(double* out) {
+  std::vector<std::vector<std::array<int, 2>>> Cc;
+  std::vector<OpList> O;
   for (const Block& b : geom.blocks) {
-    C.push_back({{b.X, b.Y}});
+    Cc.push_back({{b.X, b.Y}});
     O.push_back({});
   }
   std::vector<double> ls, re, im;
-  if (int rc = contract_batch(C, O, ls, re, im)) return rc;
+  if (int rc = contract_batch(Cc, O, ls, re, im)) return rc;
   double total = 0.0;
-  for (size_t b = 0; b < C.size(); ++b) total += ls[b] + 0.5 * std::log(re[b] * re[b] + im[b] * im[b]);
-  // pair terms <M_a->b, M_b->a>
+  for (size_t b = 0; b < Cc.size(); ++b) total += ls[b] + 0.5 * std::log(re[b] * re[b] + im[b] * im[b]);
   SweepWork* w = work(0);
-  if (!w || !w->reserve(16, 16, 16, 4096, 4, 16)) return fail(this, 2, "allocation failed");
+  if (!w || !w->reserve(sizeof(C), 16, 16, 16, 4096, 4, 16)) return fail(this, 2, "allocation failed");
   std::vector<std::pair<std::pair<int, int>, std::pair<int, int>>> pairs;
   for (const auto& u : geom.updates()) {
     auto a = std::make_pair(u.block, u.face), r = std::make_pair(u.recv_block, u.recv_face);
@@ -922,21 +968,8 @@ int Engine::log_norm(double* out) {
   for (auto& pr : pairs) {
     const Message& m1 = msgs.at(pr.first);
     const Message& m2 = msgs.at(pr.second);
-    std::vector<double2*> pa, pb;
-    std::vector<int> sa, sb;
-    for (int q = 0; q < m1.k(); ++q) {
-      pa.push_back(m1.tensor(m1.cur, q));
-      pb.push_back(m2.tensor(m2.cur, q));
-      const TShape x = m1.sh[m1.cur][q], y = m2.sh[m2.cur][q];
-      sa.insert(sa.end(), {x.l, x.p, x.r});
-      sb.insert(sb.end(), {y.l, y.p, y.r});
-    }
-    const int k = m1.k();
-    CK(cudaMemcpyAsync(w->ptrs, pa.data(), sizeof(void*) * k, cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(w->ptrs + 64, pb.data(), sizeof(void*) * k, cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(w->ints, sa.data(), sizeof(int) * 3 * k, cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(w->ints + 3 * 64, sb.data(), sizeof(int) * 3 * k, cudaMemcpyHostToDevice, stream));
-    CK(launch_mps_dot(w->ptrs, w->ptrs + 64, w->ints, w->ints + 3 * 64, k, w->k4, w->scal, stream));
+    CK(launch_mps_dot(chain_of<C>(m1, m1.cur), chain_of<C>(m2, m2.cur), sizeof(C) == sizeof(float2), w->k4, w->scal,
+                      stream));
     double2 v;
     CK(cudaMemcpyAsync(&v, w->scal, sizeof(double2), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
@@ -947,6 +980,12 @@ int Engine::log_norm(double* out) {
 }
 
 int Engine::get_message(int block, int face, int* k, int* shapes, double* data, size_t cap) {
+  return precision == 0 ? get_message_t<double2>(block, face, k, shapes, data, cap)
+                        : get_message_t<float2>(block, face, k, shapes, data, cap);
+}
+
+template <typename C>
+int Engine::get_message_t(int block, int face, int* k, int* shapes, double* data, size_t cap) {
   auto it = msgs.find({block, face});
   if (it == msgs.end()) return fail(this, 1, "no such message");
   const Message& m = it->second;
@@ -957,15 +996,21 @@ int Engine::get_message(int block, int face, int* k, int* shapes, double* data, 
   if (need > cap) return fail(this, 1, "output buffer too small");
   *k = m.k();
   size_t off = 0;
+  std::vector<C> tmp;
   for (int q = 0; q < m.k(); ++q) {
     const TShape t = m.sh[m.cur][q];
     shapes[3 * q] = t.l;
     shapes[3 * q + 1] = t.p;
     shapes[3 * q + 2] = t.r;
-    CK(cudaMemcpyAsync(data + off, m.tensor(m.cur, q), sizeof(double2) * t.size(), cudaMemcpyDeviceToHost, stream));
+    tmp.resize(t.size());
+    CK(cudaMemcpyAsync(tmp.data(), m.tensor<C>(m.cur, q), sizeof(C) * t.size(), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    for (long long e = 0; e < t.size(); ++e) {
+      data[off + 2 * e] = tmp[e].x;
+      data[off + 2 * e + 1] = tmp[e].y;
+    }
     off += 2 * (size_t)t.size();
   }
-  CK(cudaStreamSynchronize(stream));
   return 0;
 }
 

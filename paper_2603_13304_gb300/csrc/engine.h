@@ -1,7 +1,14 @@
 // BlockBP engine: device state, sweep executor, iteration and observables.
+//
+// One implementation serves both precisions: the sweep executor, the
+// iteration driver and the observables are templates on the element type
+// (double2 = complex128 FP64 path, float2 = complex64 mixed path) and are
+// dispatched on `precision`.  Device buffers are untyped; message tensors,
+// fused tensors and sweep workspaces hold elements of the current precision.
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <map>
 #include <string>
 #include <vector>
@@ -29,11 +36,6 @@ struct DBuf {
   DBuf& operator=(const DBuf&) = delete;
 };
 
-struct EngineError {
-  int status;
-  std::string msg;
-};
-
 // ---------------------------------------------------------------- messages
 
 struct Message {
@@ -41,9 +43,9 @@ struct Message {
   std::vector<int> Dleg;               // bond dimension of each fused leg
   std::vector<TShape> sh[2];           // shapes of the two buffers
   DBuf buf[2];
-  size_t cap = 0;                      // complex entries per tensor
+  size_t cap = 0;                      // elements per tensor
   int cur = 0;
-  double2* tensor(int which, int q) const { return (double2*)buf[which].p + (size_t)q * cap; }
+  template <typename C> C* tensor(int which, int q) const { return (C*)buf[which].p + (size_t)q * cap; }
   int k() const { return (int)Dleg.size(); }
 };
 
@@ -53,64 +55,62 @@ struct SweepWork {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   DBuf arena;
-  size_t cap_t = 0, cap_seg = 0, cap_x = 0, svd_bytes = 0, nslots = 0;
-  std::vector<double2*> slot;
-  double2 *S[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
-  double2 *qrA = nullptr, *qrQ = nullptr, *qrR = nullptr, *tau = nullptr, *X = nullptr;
+  size_t elem = 0, cap_t = 0, cap_seg = 0, cap_x = 0, svd_bytes = 0, nslots = 0, cap_d = 0;
+  std::vector<void*> slot;
+  void *S[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
+  void *qrA = nullptr, *qrQ = nullptr, *qrR = nullptr, *tau = nullptr, *X = nullptr;
   void* svd = nullptr;
   double* logscale = nullptr;
   int* status = nullptr;
   double2* scal = nullptr;             // scalar outputs (mps_dot)
-  double2** ptrs = nullptr;            // device pointer tables (K4, dot)
+  void** ptrs = nullptr;               // device pointer tables (K4, dot)
   int* ints = nullptr;                 // device shape tables
-  double2* k4 = nullptr;               // K4 scratch
-  // distance scratch
-  double2 *dX0 = nullptr, *dX1 = nullptr, *dQ = nullptr, *dR = nullptr;
-  size_t cap_d = 0;
-  bool reserve(size_t cap_t, size_t cap_seg, size_t cap_x, size_t svd_bytes, size_t nslots, size_t cap_d);
+  double2* k4 = nullptr;               // K4 scratch (complex128)
+  double2 *dX0 = nullptr, *dX1 = nullptr, *dQ = nullptr, *dR = nullptr, *dtau = nullptr;   // distance (complex128)
+  bool reserve(size_t elem, size_t cap_t, size_t cap_seg, size_t cap_x, size_t svd_bytes, size_t nslots, size_t cap_d);
 };
 
 struct SweepJob {
   const SweepPlan* plan = nullptr;
   ShapeTrace tr;
-  std::vector<const double2*> node_tensor;   // site: fused T permuted (in..., out...); message: raw (l, p, r)
+  std::vector<const void*> node_tensor;      // site: fused T permuted (in..., out...); message: raw (l, p, r)
   std::vector<TShape> node_shape;            // message nodes: tensor shape
-  std::vector<const double2*> start;         // start chain tensors, canonical orientation
+  std::vector<const void*> start;            // start chain tensors, canonical orientation
   std::vector<TShape> start_shape;           // their shapes (canonical orientation)
-  std::vector<double2*> dest;                // final MPS tensors, canonical order
+  std::vector<void*> dest;                   // final MPS tensors, canonical order
 };
+
+using OpList = std::vector<std::pair<std::array<int, 2>, const double*>>;   // (instance, local) -> device d x d c128
 
 class Engine {
  public:
   Geometry geom;
-  int d = 2, D = 2, chi = 8, precision = 0;
+  int d = 2, D = 2, chi = 8, precision = 0, power_iters = 3;
   cudaStream_t stream = nullptr;
   bool partitioned = false;
   std::string last_error;
 
-  DBuf t_dev;                                   // site tensors [n][d][D]^4
+  DBuf t_dev;                                   // site tensors [n][d][D]^4, complex128
   std::vector<std::array<int, 4>> site_n;       // used extent per leg (1 open, D)
-  std::map<std::pair<int, int>, DBuf> fused;    // (gid, perm code) -> fused tensor
+  std::map<std::pair<int, int>, DBuf> fused;    // (gid, perm code) -> fused tensor (current precision)
   std::map<std::pair<int, int>, Message> msgs;  // incoming message per (block, face)
   std::map<std::pair<int, int>, SweepPlan> plans;   // (block, face) -> plan (single-block regions)
   std::vector<Region> block_regions;                // single-block region per block
-  int n_iterations = 0;
   std::vector<SweepWork*> pool;
   DBuf dist_dev, op_dev;
-  std::vector<DBuf*> op_fused;                  // per-call fused operator tensors
   long long launches_per_iter = 0;
   double flops_per_iter = 0.0;
   bool messages_ready = false;
+  int n_iterations = 0;
 
   ~Engine();
+  size_t elem() const { return precision == 0 ? sizeof(double2) : sizeof(float2); }
   int create(int lattice, int Lx, int Ly, int periodic, int d, int D, const double* host_t, cudaStream_t s);
   int partition(int bx, int by);
+  int set_precision(int p);
   int init_messages(const double* edge_mats);
   int iterate(double tol, int max_iter, int* iters, double* err);
-  int contract(const std::vector<std::array<int, 2>>& coords, const std::vector<std::pair<std::array<int, 2>, const double*>>& ops,
-               double* logscale, double* re, double* im);
-  int contract_batch(const std::vector<std::vector<std::array<int, 2>>>& coords,
-                     const std::vector<std::vector<std::pair<std::array<int, 2>, const double*>>>& ops,
+  int contract_batch(const std::vector<std::vector<std::array<int, 2>>>& coords, const std::vector<OpList>& ops,
                      std::vector<double>& logscale, std::vector<double>& re, std::vector<double>& im);
   int bond_region(int g1, int k1, std::vector<std::array<int, 2>>& coords, std::array<int, 2>& key1,
                   std::array<int, 2>& key2);
@@ -120,12 +120,21 @@ class Engine {
 
  private:
   SweepWork* work(size_t i);
-  const double2* fused_tensor(int gid, const int perm[4]);
-  int fill_job(const Region& R, const SweepPlan& plan, SweepJob& job,
-               const std::vector<std::pair<std::array<int, 2>, const double*>>& ops, std::vector<DBuf*>& tmp);
-  int run_sweep(SweepJob& job, SweepWork& w);
+  template <typename C> const C* fused_tensor(int gid, const int perm[4]);
+  template <typename C> int init_messages_t(const double* edge_mats);
+  template <typename C>
+  int fill_job(const Region& R, const SweepPlan& plan, SweepJob& job, const OpList& ops, std::vector<DBuf*>& tmp);
   int reserve_workers(const std::vector<SweepJob>& jobs, int nstreams);
-  int finalize_message(Message& m, int which, SweepWork& w, double* dist_slot, bool with_distance);
+  template <typename C> int run_sweep(SweepJob& job, SweepWork& w);
+  template <typename C>
+  int finalize_message(Message& m, int which, SweepWork& w, cudaStream_t s, double* dist_slot, bool with_distance);
+  template <typename C> int iterate_t(double tol, int max_iter, int* iters, double* err);
+  template <typename C>
+  int contract_batch_t(const std::vector<std::vector<std::array<int, 2>>>& coords, const std::vector<OpList>& ops,
+                       std::vector<double>& logscale, std::vector<double>& re, std::vector<double>& im);
+  template <typename C> int log_norm_t(double* out);
+  template <typename C> int get_message_t(int block, int face, int* k, int* shapes, double* data, size_t cap);
+  void job_needs(const SweepJob& job, size_t need[7]) const;
   long long sweep_launches = 0;
   double sweep_flops = 0.0;
 };

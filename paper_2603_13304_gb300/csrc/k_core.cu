@@ -1,0 +1,1004 @@
+// Complex kernels of the BlockBP message update (sm_103a), templated on the
+// element type: complex128 (double2, the FP64 parity path) and complex64
+// (float2, the mixed path).  Norms, log-scales and message distances
+// accumulate in double in both.
+//
+//  K1 fuse           double-layer (ket-bra) tensor, Sec. 1.2 / Sec. 2.1
+//  gemm              complex GEMM used for merges, contractions and gauge moves
+//  qr                Householder QR (canonical-form moves, Sec. 2.3.3)
+//  K3 svd_trunc      truncated SVD (Sec. 1.1.1, 1.1.3): one-sided (row) Jacobi;
+//                    in complex64, large matrices are first reduced by a
+//                    randomised subspace iteration and Jacobi runs on the
+//                    small projected matrix
+//  K4 msg_*          message normalisation, phase and distance
+//
+// Large Jacobi problems run on a thread-block cluster (one matrix per
+// cluster, cluster barriers between rounds); every loop is bounded.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace bbp {
+
+namespace {
+
+template <typename C> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+
+template <typename C>
+__host__ __device__ __forceinline__ C cx(double x, double y) {
+  C r;
+  r.x = (typename RealOf<C>::T)x;
+  r.y = (typename RealOf<C>::T)y;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {   // conj(a) * b
+  C r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.x * b.y - a.y * b.x;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) {
+  a.x = a.x * (typename RealOf<C>::T)s;
+  a.y = a.y * (typename RealOf<C>::T)s;
+  return a;
+}
+template <typename C> __device__ __forceinline__ typename RealOf<C>::T cabs2(C a) { return a.x * a.x + a.y * a.y; }
+template <typename C> __device__ __forceinline__ double cabs2d(C a) { return (double)a.x * a.x + (double)a.y * a.y; }
+__device__ __forceinline__ double2 c128(double2 a) { return a; }
+__device__ __forceinline__ double2 c128(float2 a) { return make_double2(a.x, a.y); }
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one double; result broadcast to all threads.
+__device__ double block_sum(double v, double* sh) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (lane < nw) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+inline int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)g;
+}
+
+// ------------------------------------------------------------------ K1 fuse
+// Computed in complex128 and rounded to the output type.
+
+template <typename C>
+__global__ void k_fuse(const double2* __restrict__ t, int d, int Dfull, int4 n4, const double2* __restrict__ op,
+                       int4 perm4, C* __restrict__ T, long long total) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int nn[4] = {n4.x, n4.y, n4.z, n4.w};
+  const int pp[4] = {perm4.x, perm4.y, perm4.z, perm4.w};
+  int ket[4], bra[4];
+  long long rem = idx;
+  for (int q = 3; q >= 0; --q) {
+    int leg = pp[q];
+    int f2 = nn[leg] * nn[leg];
+    int f = (int)(rem % f2);
+    rem /= f2;
+    ket[leg] = f / nn[leg];
+    bra[leg] = f % nn[leg];
+  }
+  const long long D = Dfull;
+  const long long sD4 = D * D * D * D;
+  const long long ok = ((ket[0] * D + ket[1]) * D + ket[2]) * D + ket[3];
+  const long long ob = ((bra[0] * D + bra[1]) * D + bra[2]) * D + bra[3];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int s = 0; s < d; ++s) {
+    double2 tb = cconj(t[s * sD4 + ob]);
+    if (op) {
+      for (int sp = 0; sp < d; ++sp) acc = cadd(acc, cmul(op[s * d + sp], cmul(t[sp * sD4 + ok], tb)));
+    } else {
+      acc = cadd(acc, cmul(t[s * sD4 + ok], tb));
+    }
+  }
+  T[idx] = cx<C>(acc.x, acc.y);
+}
+
+// -------------------------------------------------------------------- gemm
+
+constexpr int GT = 32;   // output tile
+constexpr int GK = 16;   // k tile
+
+template <typename C>
+__device__ __forceinline__ C load_op(const C* P, int ld, char op, int r, int c, int R, int Cc) {
+  if (r >= R || c >= Cc) return cx<C>(0, 0);
+  if (op == 'N') return P[(long long)r * ld + c];
+  C v = P[(long long)c * ld + r];
+  return op == 'C' ? cconj(v) : v;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_gemm(char opA, char opB, int M, int N, int K, C alpha, const C* __restrict__ A,
+                                              int lda, long long sA, const C* __restrict__ B, int ldb, long long sB,
+                                              C beta, C* __restrict__ Cm, int ldc, long long sC) {
+  __shared__ C As[GT][GK + 1];
+  __shared__ C Bs[GK][GT + 1];
+  const int bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  Cm += bz * sC;
+  const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  C acc[2][2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) acc[i][j] = cx<C>(0, 0);
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int e = threadIdx.x; e < GT * GK; e += 256) {
+      int i = e / GK, kk = e % GK;
+      As[i][kk] = load_op(A, lda, opA, row0 + i, k0 + kk, M, K);
+      int kb = e / GT, j = e % GT;
+      Bs[kb][j] = load_op(B, ldb, opB, k0 + kb, col0 + j, K, N);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      C a0 = As[ty][kk], a1 = As[ty + 16][kk];
+      C b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      acc[0][0] = cadd(acc[0][0], cmul(a0, b0));
+      acc[0][1] = cadd(acc[0][1], cmul(a0, b1));
+      acc[1][0] = cadd(acc[1][0], cmul(a1, b0));
+      acc[1][1] = cadd(acc[1][1], cmul(a1, b1));
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < M && c < N) {
+        C v = cmul(alpha, acc[i][j]);
+        if (beta.x != 0 || beta.y != 0) v = cadd(v, cmul(beta, Cm[(long long)r * ldc + c]));
+        Cm[(long long)r * ldc + c] = v;
+      }
+    }
+}
+
+// ---------------------------------------------------------------------- QR
+// Householder with real diagonal of R (H = I - tau v v^H, v_j = 1).  One CTA
+// of 256 threads; A (m x n, row-major, ld = n) is overwritten by R and the
+// reflectors.  Lanes map to consecutive columns and warps to row groups, so
+// every row access of the trailing update is a coalesced 32-column stripe.
+
+template <typename C>
+__device__ void cta_householder(C* A, int m, int n, C* tau, double* sh) {
+  const int k = m < n ? m : n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double s_tau[2], s_scale[2];
+  __shared__ C s_w[8][33];
+  for (int j = 0; j < k; ++j) {
+    double part = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) part += cabs2d(A[(long long)i * n + j]);
+    double xn2 = block_sum(part, sh);
+    if (threadIdx.x == 0) {
+      double2 alpha = c128(A[(long long)j * n + j]);
+      if (xn2 == 0.0 && alpha.y == 0.0) {
+        s_tau[0] = s_tau[1] = 0.0;
+        s_scale[0] = s_scale[1] = 0.0;
+      } else {
+        double beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
+        s_tau[0] = (beta - alpha.x) / beta;
+        s_tau[1] = -alpha.y / beta;
+        double dx = alpha.x - beta, dy = alpha.y, dd = dx * dx + dy * dy;
+        s_scale[0] = dx / dd;
+        s_scale[1] = -dy / dd;
+        A[(long long)j * n + j] = cx<C>(beta, 0.0);
+      }
+      tau[j] = cx<C>(s_tau[0], s_tau[1]);
+    }
+    __syncthreads();
+    const C tj = cx<C>(s_tau[0], s_tau[1]), sc = cx<C>(s_scale[0], s_scale[1]);
+    if (tj.x == 0 && tj.y == 0) { __syncthreads(); continue; }
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(long long)i * n + j] = cmul(A[(long long)i * n + j], sc);
+    __syncthreads();
+    // A[j:, c] -= conj(tau) v (v^H A[j:, c]) for c > j, 32 columns at a time
+    const C ctau = cconj(tj);
+    for (int cb = j + 1; cb < n; cb += 32) {
+      const int c = cb + lane;
+      C acc = cx<C>(0, 0);
+      if (c < n)
+        for (int i = j + wid; i < m; i += nw) {
+          C v = (i == j) ? cx<C>(1, 0) : A[(long long)i * n + j];
+          acc = cadd(acc, cmulc(v, A[(long long)i * n + c]));
+        }
+      s_w[wid][lane] = acc;
+      __syncthreads();
+      if (wid == 0) {
+        C t = s_w[0][lane];
+        for (int g = 1; g < nw; ++g) t = cadd(t, s_w[g][lane]);
+        s_w[0][lane] = cmul(ctau, t);
+      }
+      __syncthreads();
+      const C f = s_w[0][lane];
+      if (c < n)
+        for (int i = j + wid; i < m; i += nw) {
+          C v = (i == j) ? cx<C>(1, 0) : A[(long long)i * n + j];
+          A[(long long)i * n + c] = csub(A[(long long)i * n + c], cmul(v, f));
+        }
+      __syncthreads();
+    }
+  }
+}
+
+// Q (m x k, row-major) from the reflectors stored in A (one CTA of 256 threads).
+template <typename C>
+__device__ void cta_form_q(const C* A, int m, int n, const C* tau, C* Q) {
+  const int k = m < n ? m : n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ C s_w[8][33];
+  for (long long e = threadIdx.x; e < (long long)m * k; e += blockDim.x) {
+    int i = (int)(e / k), c = (int)(e % k);
+    Q[e] = cx<C>(i == c ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const C tj = tau[j];
+    if (tj.x == 0 && tj.y == 0) continue;
+    for (int cb = j; cb < k; cb += 32) {
+      const int c = cb + lane;
+      C acc = cx<C>(0, 0);
+      if (c < k)
+        for (int i = j + wid; i < m; i += nw) {
+          C v = (i == j) ? cx<C>(1, 0) : A[(long long)i * n + j];
+          acc = cadd(acc, cmulc(v, Q[(long long)i * k + c]));
+        }
+      s_w[wid][lane] = acc;
+      __syncthreads();
+      if (wid == 0) {
+        C t = s_w[0][lane];
+        for (int g = 1; g < nw; ++g) t = cadd(t, s_w[g][lane]);
+        s_w[0][lane] = cmul(tj, t);
+      }
+      __syncthreads();
+      const C f = s_w[0][lane];
+      if (c < k)
+        for (int i = j + wid; i < m; i += nw) {
+          C v = (i == j) ? cx<C>(1, 0) : A[(long long)i * n + j];
+          Q[(long long)i * k + c] = csub(Q[(long long)i * k + c], cmul(v, f));
+        }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_qr(C* A, int m, int n, C* Q, C* Rm, C* tau) {
+  __shared__ double sh[40];
+  cta_householder(A, m, n, tau, sh);
+  const int k = m < n ? m : n;
+  if (Rm)
+    for (long long e = threadIdx.x; e < (long long)k * n; e += blockDim.x) {
+      int i = (int)(e / n), c = (int)(e % n);
+      Rm[e] = (c >= i) ? A[(long long)i * n + c] : cx<C>(0, 0);
+    }
+  __syncthreads();
+  cta_form_q(A, m, n, tau, Q);
+}
+
+// ---------------------------------------------------------------- K3 Jacobi
+
+template <typename C>
+struct SvdWork {
+  C* G;
+  C* WH;
+  double* sigma;
+  int* idx;
+  int* counters;   // [0..1] rotations per sweep, [2] sweeps, [3] rotations in total
+  double* zn2;     // ||Z||_F^2
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename C>
+__host__ __device__ inline SvdWork<C> carve(void* work, int M, int N) {
+  char* p = (char*)work;
+  SvdWork<C> w;
+  w.G = (C*)p; p += align256(sizeof(C) * (size_t)M * N);
+  w.WH = (C*)p; p += align256(sizeof(C) * (size_t)M * M);
+  w.sigma = (double*)p; p += align256(sizeof(double) * (size_t)M);
+  w.idx = (int*)p; p += align256(sizeof(int) * (size_t)M);
+  w.counters = (int*)p;
+  w.zn2 = (double*)(p + 32);
+  return w;
+}
+
+template <typename C>
+size_t jacobi_bytes(int M, int N) {
+  return align256(sizeof(C) * (size_t)M * N) + align256(sizeof(C) * (size_t)M * M) + align256(sizeof(double) * M) +
+         align256(sizeof(int) * M) + 256;
+}
+
+// Copies Z (or Z^H) into G, sets WH = I and accumulates ||Z||^2 into *zn2;
+// the counters and *zn2 are zeroed by the caller before the launch.
+template <typename C>
+__global__ void k_svd_init(const C* __restrict__ Z, int m, int n, SvdWork<C> w) {
+  __shared__ double sh[40];
+  const int M = m <= n ? m : n, N = m <= n ? n : m;
+  long long tot = (long long)M * N, totw = (long long)M * M;
+  double part = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot + totw;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < tot) {
+      int a = (int)(e / N), c = (int)(e % N);
+      C v = (m <= n) ? Z[(long long)a * n + c] : cconj(Z[(long long)c * n + a]);
+      w.G[e] = v;
+      part += cabs2d(v);
+    } else {
+      long long f = e - tot;
+      int a = (int)(f / M), c = (int)(f % M);
+      w.WH[f] = cx<C>(a == c ? 1.0 : 0.0, 0.0);
+    }
+  }
+  double bs = block_sum(part, sh);
+  if (threadIdx.x == 0) atomicAdd(w.zn2, bs);
+}
+
+template <typename C>
+__device__ __forceinline__ C ldcg(const C* p);
+template <> __device__ __forceinline__ double2 ldcg(const double2* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float2 ldcg(const float2* p) { return __ldcg(p); }
+template <typename C>
+__device__ __forceinline__ void stcg(C* p, C v);
+template <> __device__ __forceinline__ void stcg(double2* p, double2 v) { __stcg(p, v); }
+template <> __device__ __forceinline__ void stcg(float2* p, float2 v) { __stcg(p, v); }
+
+// Rotate rows a, b of G (length N) and of WH (length M) so that they become
+// orthogonal.  Warp-cooperative (all lanes take the same decision: the xor
+// butterfly leaves bitwise identical sums in every lane); returns 1 when a
+// rotation was applied.
+template <typename C>
+__device__ int rotate_pair(C* ra, C* rb, int N, C* wa, C* wb, int M, int lane, double tol,
+                           typename RealOf<C>::T floor) {
+  using R = typename RealOf<C>::T;
+  R al = 0, be = 0, gx = 0, gy = 0;
+  for (int c = lane; c < N; c += 32) {
+    C x = ldcg(ra + c), y = ldcg(rb + c);
+    al += cabs2(x);
+    be += cabs2(y);
+    gx += x.x * y.x + x.y * y.y;      // x * conj(y)
+    gy += x.y * y.x - x.x * y.y;
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  gx = warp_sum(gx);
+  gy = warp_sum(gy);
+  R g = sqrt(gx * gx + gy * gy);
+  if (g == 0 || g <= (R)tol * sqrt(al) * sqrt(be)) return 0;
+  // a row below eps ||Z|| carries nothing at working precision; orthogonalising
+  // it (in subnormal arithmetic, at worst) would never meet the test above
+  if (fmin(al, be) <= floor) return 0;
+  // rows whose norms differ by more than 1e30 (1e15 in complex64) do not
+  // affect each other at working precision; rotating them only churns
+  // rounding noise (and never meets the relative test once a norm is subnormal)
+  const R far = sizeof(R) == 8 ? (R)1e-60 : (R)1e-30;
+  if (fmin(al, be) <= far * fmax(al, be)) return 0;
+  C e = cx<C>(gx / g, gy / g);
+  R zeta = (be - al) / (2 * g);
+  R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+  R cs = (R)1 / sqrt((R)1 + t * t), sn = cs * t;
+  for (int c = lane; c < N; c += 32) {
+    C x = ldcg(ra + c), y = ldcg(rb + c);
+    C ey = cmul(e, y);
+    stcg(ra + c, csub(cscale(x, cs), cscale(ey, sn)));
+    stcg(rb + c, cadd(cscale(x, sn), cscale(ey, cs)));
+  }
+  for (int c = lane; c < M; c += 32) {
+    C x = ldcg(wa + c), y = ldcg(wb + c);
+    C ey = cmul(e, y);
+    stcg(wa + c, csub(cscale(x, cs), cscale(ey, sn)));
+    stcg(wb + c, cadd(cscale(x, sn), cscale(ey, cs)));
+  }
+  return 1;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_jacobi(SvdWork<C> w, int M, int N, double tol, double floor_rel,
+                                                int max_sweeps, int* status) {
+  using R = typename RealOf<C>::T;
+  const R floor = (R)(floor_rel * *w.zn2);
+  cg::cluster_group cl = cg::this_cluster();
+  const int csize = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gw = crank * nw + warp, tw = csize * nw;
+  const int Mp = M + (M & 1);
+  const int npairs = Mp / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int rot = 0;
+    for (int r = 0; r < Mp - 1; ++r) {
+      for (int q = gw; q < npairs; q += tw) {
+        int a, b;
+        if (q == 0) { a = Mp - 1; b = r; }
+        else { a = (r + q) % (Mp - 1); b = (r - q + Mp - 1) % (Mp - 1); }
+        if (a >= M || b >= M) continue;
+        rot += rotate_pair(w.G + (long long)a * N, w.G + (long long)b * N, N, w.WH + (long long)a * M,
+                           w.WH + (long long)b * M, M, lane, tol, floor);
+      }
+      cl.sync();
+    }
+    if (lane == 0 && rot) atomicAdd(&w.counters[sweep & 1], rot);
+    cl.sync();
+    const int total = *(volatile int*)&w.counters[sweep & 1];
+    if (crank == 0 && threadIdx.x == 0) {
+      w.counters[(sweep + 1) & 1] = 0;
+      w.counters[2] = sweep + 1;        // sweeps done
+      w.counters[3] += total;           // rotations applied
+    }
+    cl.sync();
+    if (total == 0) return;
+  }
+  if (crank == 0 && threadIdx.x == 0) *status = 1;   // sweep limit reached
+}
+
+template <typename C>
+__global__ void k_row_norms(SvdWork<C> w, int M, int N) {
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= M) return;
+  double s = 0.0;
+  for (int c = lane; c < N; c += 32) s += cabs2d(w.G[(long long)row * N + c]);
+  s = warp_sum(s);
+  if (lane == 0) w.sigma[row] = sqrt(s);
+}
+
+template <typename C>
+__global__ void k_select(SvdWork<C> w, int M, int k) {
+  for (int a = threadIdx.x; a < M; a += blockDim.x) {
+    double sa = w.sigma[a];
+    int rank = 0;
+    for (int b = 0; b < M; ++b) {
+      double sb = w.sigma[b];
+      rank += (sb > sa) || (sb == sa && b < a);
+    }
+    if (rank < k) w.idx[rank] = a;
+  }
+}
+
+template <typename C>
+__global__ void k_svd_out(SvdWork<C> w, int m, int n, int k, double floor_rel, C* __restrict__ U,
+                          C* __restrict__ Rem) {
+  const double smin = sqrt(floor_rel * *w.zn2);
+  const int M = m <= n ? m : n, N = m <= n ? n : m;
+  long long totU = (long long)m * k, totR = (long long)k * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totU + totR;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < totU) {
+      int i = (int)(e / k), r = (int)(e % k);
+      int a = w.idx[r];
+      if (m <= n) {
+        U[e] = cconj(w.WH[(long long)a * M + i]);
+      } else {
+        double s = w.sigma[a];
+        U[e] = (s > smin && s > 0.0) ? cscale(cconj(w.G[(long long)a * N + i]), 1.0 / s) : cx<C>(0, 0);
+      }
+    } else {
+      long long f = e - totU;
+      int r = (int)(f / n), c = (int)(f % n);
+      int a = w.idx[r];
+      if (m <= n) Rem[f] = w.G[(long long)a * N + c];
+      else Rem[f] = cscale(w.WH[(long long)a * M + c], w.sigma[a]);
+    }
+  }
+}
+
+// Rows below sqrt(floor_rel) ||Z|| are left unrotated (eps^2 of the type).
+template <typename C> constexpr double floor_rel_of() { return sizeof(typename RealOf<C>::T) == 8 ? 1e-32 : 1e-14; }
+
+template <typename C>
+cudaError_t jacobi_svd(const C* Z, int m, int n, int chi, C* U, C* Rem, void* work, int* status, cudaStream_t s,
+                       double tol, int max_sweeps) {
+  const int M = m < n ? m : n, N = m < n ? n : m;
+  const int k = chi < M ? chi : M;
+  SvdWork<C> w = carve<C>(work, M, N);
+  cudaError_t e0 = cudaMemsetAsync(w.counters, 0, 64, s);
+  if (e0 != cudaSuccess) return e0;
+  k_svd_init<C><<<grid_for((long long)M * N + (long long)M * M, 256), 256, 0, s>>>(Z, m, n, w);
+  int cs = (M / 2 + 15) / 16;   // about two pairs per warp per round
+  if (cs < 1) cs = 1;
+  if (cs > 8) cs = 8;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi<C>, w, M, N, tol, floor_rel_of<C>(), max_sweeps, status);
+  if (e != cudaSuccess) return e;
+  k_row_norms<C><<<(M * 32 + 255) / 256, 256, 0, s>>>(w, M, N);
+  k_select<C><<<1, 256, 0, s>>>(w, M, k);
+  k_svd_out<C><<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(w, m, n, k, floor_rel_of<C>(), U,
+                                                                                 Rem);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- randomised range reduction (c64)
+// Z (m x n), b = min(chi + p, m, n) columns: Q0 = orth(Z Omega); q times
+// W = orth(Z^H Q), Q = orth(Z W); B = Q^H Z (b x n); Jacobi on B's rows:
+// B = W_B B'; U = Q W_B[:, top], Rem = B'[top, :].  Omega is a fixed
+// counter-hash sign matrix (the result does not depend on it once the
+// subspace has converged).
+
+__global__ void k_omega(float2* O, int n, int b) {
+  long long tot = (long long)n * b;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    unsigned long long x = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    x ^= x >> 31;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27;
+    x *= 0x94D049BB133111EBull;
+    x ^= x >> 33;
+    O[e] = make_float2((x & 1) ? 1.f : -1.f, (x & 2) ? 1.f : -1.f);
+  }
+}
+
+// One CTA: orthonormalise the columns of Y (rows x b) in place (Householder,
+// explicit Q written back into Y).  scratch: rows*b + b complex.
+__global__ void __launch_bounds__(256) k_orth(float2* Y, int rows, int b, float2* scratch) {
+  __shared__ double sh[40];
+  float2* A = scratch;
+  float2* tau = scratch + (long long)rows * b;
+  for (long long e = threadIdx.x; e < (long long)rows * b; e += blockDim.x) A[e] = Y[e];
+  __syncthreads();
+  cta_householder(A, rows, b, tau, sh);
+  __syncthreads();
+  cta_form_q(A, rows, b, tau, Y);
+}
+
+// U (m x k) = Q (m x b) * conj(WH[idx[r], :])^T ; Rem (k x n) = G[idx[r], :]
+__global__ void k_rand_out(const float2* Q, int m, int b, SvdWork<float2> w, int n, int k, float2* U, float2* Rem) {
+  long long totU = (long long)m * k, totR = (long long)k * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totU + totR;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < totU) {
+      int i = (int)(e / k), r = (int)(e % k);
+      int a = w.idx[r];
+      float2 s = make_float2(0.f, 0.f);
+      for (int j = 0; j < b; ++j) s = cadd(s, cmul(Q[(long long)i * b + j], cconj(w.WH[(long long)a * b + j])));
+      U[e] = s;
+    } else {
+      long long f = e - totU;
+      int r = (int)(f / n), c = (int)(f % n);
+      Rem[f] = w.G[(long long)w.idx[r] * n + c];
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+template <typename C>
+static cudaError_t fuse_t(const double2* t, int d, int Dfull, const int n[4], const double2* op, const int perm[4],
+                          C* T, cudaStream_t s) {
+  long long total = 1;
+  for (int q = 0; q < 4; ++q) total *= (long long)n[q] * n[q];
+  long long blocks = (total + 255) / 256;
+  k_fuse<C><<<(unsigned)blocks, 256, 0, s>>>(t, d, Dfull, make_int4(n[0], n[1], n[2], n[3]), op,
+                                             make_int4(perm[0], perm[1], perm[2], perm[3]), T, total);
+  return cudaGetLastError();
+}
+cudaError_t launch_fuse(const double2* t, int d, int D, const int n[4], const double2* op, const int perm[4], double2* T,
+                        cudaStream_t s) {
+  return fuse_t(t, d, D, n, op, perm, T, s);
+}
+cudaError_t launch_fuse(const double2* t, int d, int D, const int n[4], const double2* op, const int perm[4], float2* T,
+                        cudaStream_t s) {
+  return fuse_t(t, d, D, n, op, perm, T, s);
+}
+
+template <typename C>
+static cudaError_t gemm_t(char opA, char opB, int M, int N, int K, C alpha, const C* A, int lda, long long sA,
+                          const C* B, int ldb, long long sB, C beta, C* Cm, int ldc, long long sC, int batch,
+                          cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, batch);
+  k_gemm<C><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, Cm, ldc, sC);
+  return cudaGetLastError();
+}
+cudaError_t launch_zgemm(char opA, char opB, int M, int N, int K, double2 alpha, const double2* A, int lda,
+                         long long sA, const double2* B, int ldb, long long sB, double2 beta, double2* C, int ldc,
+                         long long sC, int batch, cudaStream_t s) {
+  return gemm_t(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, s);
+}
+cudaError_t launch_zgemm(char opA, char opB, int M, int N, int K, float2 alpha, const float2* A, int lda, long long sA,
+                         const float2* B, int ldb, long long sB, float2 beta, float2* C, int ldc, long long sC,
+                         int batch, cudaStream_t s) {
+  return gemm_t(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, s);
+}
+
+cudaError_t launch_qr(double2* A, int m, int n, double2* Q, double2* R, double2* tau, cudaStream_t s) {
+  k_qr<double2><<<1, 256, 0, s>>>(A, m, n, Q, R, tau);
+  return cudaGetLastError();
+}
+cudaError_t launch_qr(float2* A, int m, int n, float2* Q, float2* R, float2* tau, cudaStream_t s) {
+  k_qr<float2><<<1, 256, 0, s>>>(A, m, n, Q, R, tau);
+  return cudaGetLastError();
+}
+
+size_t svd_work_bytes(int m, int n) {
+  int M = m < n ? m : n, N = m < n ? n : m;
+  return jacobi_bytes<double2>(M, N);
+}
+
+cudaError_t launch_svd_trunc(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work,
+                             int* status, cudaStream_t s) {
+  return jacobi_svd<double2>(Z, m, n, chi, U, Rem, work, status, s, 1e-14, 60);
+}
+
+// Relative orthogonality a complex64 Jacobi sweep can reach on rows of
+// length N: rounding in the dot products is about sqrt(N) eps_32.
+static double jacobi_tol_c64(int N) { return std::max(2e-6, 3e-7 * std::sqrt((double)N)); }
+
+// complex64: randomised reduction when the matrix is large, else plain Jacobi
+int rand_block(int m, int n, int chi) {
+  int M = m < n ? m : n;
+  int b = chi + (chi >= 16 ? chi / 2 : 8);
+  return b < M ? b : M;
+}
+
+size_t svd_work_bytes_c64(int m, int n, int chi) {
+  int M = m < n ? m : n, N = m < n ? n : m;
+  const int b = rand_block(m, n, chi);
+  if (b >= M) return jacobi_bytes<float2>(M, N);
+  // Omega/W (n x b), Q (m x b), X (max(m,n) x b), orth scratch, B (b x n), Jacobi(b, n)
+  size_t z = sizeof(float2);
+  return align256(z * (size_t)n * b) + align256(z * (size_t)m * b) + align256(z * (size_t)N * b) +
+         align256(z * ((size_t)N * b + b)) + jacobi_bytes<float2>(b, n) + 256;
+}
+
+size_t svd_work_bound_c64(int max_min, int max_max, int chi) {
+  const int b = chi + (chi >= 16 ? chi / 2 : 8);
+  const size_t z = sizeof(float2);
+  const size_t N = (size_t)max_max;
+  size_t rnd = 3 * align256(z * N * b) + align256(z * (N * b + b)) + jacobi_bytes<float2>(b, (int)N) + 256;
+  return std::max(rnd, jacobi_bytes<float2>(max_min, max_max));
+}
+
+cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, float2* Rem, void* work, int* status,
+                             cudaStream_t s, int power_iters) {
+  const int M = m < n ? m : n;
+  const int b = rand_block(m, n, chi);
+  if (b >= M) return jacobi_svd<float2>(Z, m, n, chi, U, Rem, work, status, s, jacobi_tol_c64(std::max(m, n)), 60);
+  const int k = chi < M ? chi : M;
+  const int N = m < n ? n : m;
+  size_t z = sizeof(float2);
+  char* p = (char*)work;
+  float2* W = (float2*)p; p += align256(z * (size_t)n * b);
+  float2* Q = (float2*)p; p += align256(z * (size_t)m * b);
+  float2* X = (float2*)p; p += align256(z * (size_t)N * b);
+  float2* orth = (float2*)p; p += align256(z * ((size_t)N * b + b));
+  void* jw = p;
+  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+  cudaError_t e;
+  k_omega<<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
+  // Q = orth(Z W)
+  if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
+  k_orth<<<1, 256, 0, s>>>(Q, m, b, orth);
+  for (int it = 0; it < power_iters; ++it) {
+    if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
+    k_orth<<<1, 256, 0, s>>>(W, n, b, orth);
+    if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
+    k_orth<<<1, 256, 0, s>>>(Q, m, b, orth);
+  }
+  // B = Q^H Z (b x n) into X, then Jacobi on its rows (b <= n here)
+  if ((e = launch_zgemm('C', 'N', b, n, m, one, Q, b, 0, Z, n, 0, zero, X, n, 0, 1, s)) != cudaSuccess) return e;
+  SvdWork<float2> w = carve<float2>(jw, b, n);
+  if ((e = cudaMemsetAsync(w.counters, 0, 64, s)) != cudaSuccess) return e;
+  k_svd_init<float2><<<grid_for((long long)b * n + (long long)b * b, 256), 256, 0, s>>>(X, b, n, w);
+  int cs = (b / 2 + 15) / 16;
+  if (cs < 1) cs = 1;
+  if (cs > 8) cs = 8;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if ((e = cudaLaunchKernelEx(&cfg, k_jacobi<float2>, w, b, n, jacobi_tol_c64(n), floor_rel_of<float2>(), 60,
+                              status)) != cudaSuccess)
+    return e;
+  k_row_norms<float2><<<(b * 32 + 255) / 256, 256, 0, s>>>(w, b, n);
+  k_select<float2><<<1, 256, 0, s>>>(w, b, k);
+  k_rand_out<<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(Q, m, b, w, n, k, U, Rem);
+  return cudaGetLastError();
+}
+
+cudaError_t svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, cudaStream_t s) {
+  const int M = m < n ? m : n, N = m < n ? n : m;
+  SvdWork<double2> w = carve<double2>(const_cast<void*>(work), M, N);
+  int c[4];
+  cudaError_t e = cudaMemcpyAsync(c, w.counters, sizeof(c), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  *sweeps = c[2];
+  *rotations = c[3];
+  return e;
+}
+
+// --------------------------------------------------------------- normalise
+
+namespace {
+template <typename C>
+__global__ void __launch_bounds__(1024) k_normalise(C* A, long long n, double* logscale) {
+  __shared__ double sh[40];
+  double part = 0.0;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) part += cabs2d(A[e]);
+  double s = block_sum(part, sh);
+  double nrm = sqrt(s);
+  if (nrm > 0.0) {
+    double inv = 1.0 / nrm;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) A[e] = cscale(A[e], inv);
+    if (threadIdx.x == 0) *logscale += log(nrm);
+  } else if (threadIdx.x == 0) {
+    *logscale = -INFINITY;
+  }
+}
+
+template <typename C>
+__global__ void k_copy_tensor(const C* __restrict__ src, C* __restrict__ dst, int l, int p, int r, int tr) {
+  long long tot = (long long)l * p * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    if (!tr) { dst[e] = src[e]; continue; }
+    int a = (int)(e / ((long long)p * r));
+    int q = (int)((e / r) % p);
+    int b = (int)(e % r);
+    dst[((long long)b * p + q) * l + a] = src[e];
+  }
+}
+
+template <typename C>
+__global__ void k_fill(C* A, long long n, double re, double im) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    A[e] = cx<C>(re, im);
+}
+
+template <typename C>
+__global__ void k_conj_transpose(const C* __restrict__ src, int rows, int cols, C* __restrict__ dst) {
+  long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / cols), j = (int)(e % cols);
+    dst[(long long)j * rows + i] = cconj(src[e]);
+  }
+}
+
+template <typename C>
+__global__ void k_permute3(const C* __restrict__ src, int d0, int d1, int d2, int3 perm, C* __restrict__ dst) {
+  const int dims[3] = {d0, d1, d2};
+  const int pp[3] = {perm.x, perm.y, perm.z};
+  const int od[3] = {dims[pp[0]], dims[pp[1]], dims[pp[2]]};
+  long long tot = (long long)d0 * d1 * d2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int o[3];
+    o[2] = (int)(e % od[2]);
+    o[1] = (int)((e / od[2]) % od[1]);
+    o[0] = (int)(e / ((long long)od[2] * od[1]));
+    int sidx[3];
+    for (int q = 0; q < 3; ++q) sidx[pp[q]] = o[q];
+    dst[e] = src[((long long)sidx[0] * d1 + sidx[1]) * d2 + sidx[2]];
+  }
+}
+
+// ---------------------------------------------------------------------- K4
+// <M|M> by the transfer chain, <I|M> by the identity chain (both in
+// complex128); the first tensor is scaled by |tr| / (tr sqrt(<M|M>)).  One CTA.
+template <typename C>
+__global__ void __launch_bounds__(256) k_msg_normalise(ChainDesc d, double2* work) {
+  __shared__ double2 s_fac;
+  double2* E = work;                   // l x l
+  double2* E2 = work + 64 * 64;        // r x r
+  double2* F = work + 2 * 64 * 64;     // l x p x r scratch
+  double2* v = work + 2 * 64 * 64 + 64 * 64 * 64;   // identity chain (2 x 64)
+  if (threadIdx.x == 0) { E[0] = make_double2(1.0, 0.0); v[0] = make_double2(1.0, 0.0); }
+  __syncthreads();
+  for (int q = 0; q < d.k; ++q) {
+    const int l = d.l[q], p = d.p[q], r = d.r[q];
+    const C* A = (const C*)d.T[q];
+    for (long long e = threadIdx.x; e < (long long)l * p * r; e += blockDim.x) {
+      int l2 = (int)(e / ((long long)p * r)), pp = (int)((e / r) % p), r1 = (int)(e % r);
+      double2 s = make_double2(0.0, 0.0);
+      for (int l1 = 0; l1 < l; ++l1) s = cadd(s, cmulc(c128(A[((long long)l1 * p + pp) * r + r1]), E[l1 * l + l2]));
+      F[e] = s;
+    }
+    __syncthreads();
+    const int D = d.D[q];
+    for (int e = threadIdx.x; e < r; e += blockDim.x) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int a = 0; a < l; ++a)
+        for (int kk = 0; kk < D; ++kk) s = cadd(s, cmul(v[a], c128(A[((long long)a * p + kk * D + kk) * r + e])));
+      v[64 + e] = s;
+    }
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      int r1 = e / r, r2 = e % r;
+      double2 s = make_double2(0.0, 0.0);
+      for (int l2 = 0; l2 < l; ++l2)
+        for (int pp = 0; pp < p; ++pp)
+          s = cadd(s, cmul(F[((long long)l2 * p + pp) * r + r1], c128(A[((long long)l2 * p + pp) * r + r2])));
+      E2[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) E[e] = E2[e];
+    for (int e = threadIdx.x; e < r; e += blockDim.x) v[e] = v[64 + e];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double nrm2 = E[0].x;
+    double2 tr = v[0];
+    double at = sqrt(tr.x * tr.x + tr.y * tr.y);
+    double2 f = make_double2(nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 1.0, 0.0);
+    if (at > 0.0) f = cmul(f, make_double2(tr.x / at, -tr.y / at));   // |tr| / tr
+    s_fac = f;
+  }
+  __syncthreads();
+  const double2 f = s_fac;
+  C* T0 = (C*)d.T[0];
+  const long long n0 = (long long)d.l[0] * d.p[0] * d.r[0];
+  for (long long e = threadIdx.x; e < n0; e += blockDim.x) {
+    double2 x = cmul(c128(T0[e]), f);
+    T0[e] = cx<C>(x.x, x.y);
+  }
+}
+
+// direct sum of (a, -b) at chain position pos of k
+template <typename C>
+__global__ void k_direct_sum(const C* a, int la, int ra, const C* b, int lb, int rb, int p, int pos, int k, C* out) {
+  int L = (k == 1 || pos == 0) ? 1 : la + lb;
+  int R = (k == 1 || pos == k - 1) ? 1 : ra + rb;
+  long long tot = (long long)L * p * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int x = (int)(e / ((long long)p * R)), q = (int)((e / R) % p), y = (int)(e % R);
+    C v = cx<C>(0, 0);
+    if (k == 1) {
+      v = csub(a[q], b[q]);
+    } else if (pos == 0) {
+      if (y < ra) v = a[(long long)q * ra + y];
+      else v = cscale(b[(long long)q * rb + (y - ra)], -1.0);
+    } else if (pos == k - 1) {
+      if (x < la) v = a[(long long)x * p + q];
+      else v = b[(long long)(x - la) * p + q];
+    } else {
+      if (x < la && y < ra) v = a[((long long)x * p + q) * ra + y];
+      else if (x >= la && y >= ra) v = b[((long long)(x - la) * p + q) * rb + (y - ra)];
+    }
+    out[e] = v;
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(1024) k_frob(const C* R, long long n, double* out) {
+  __shared__ double sh[40];
+  double part = 0.0;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) part += cabs2d(R[e]);
+  double s = block_sum(part, sh);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+// value = sum prod A_q B_q over shared legs: E'[x][y] = sum_{i,j,p} E[i][j] a[i][p][x] b[j][p][y],
+// in two steps through F[j][p][x] = sum_i E[i][j] a[i][p][x].  One CTA; work as for K4.
+template <typename C>
+__global__ void __launch_bounds__(256) k_mps_dot(ChainDesc A, ChainDesc B, double2* work, double2* out) {
+  double2* E = work;
+  double2* E2 = work + 64 * 64;
+  double2* F = work + 2 * 64 * 64;
+  if (threadIdx.x == 0) E[0] = make_double2(1.0, 0.0);
+  __syncthreads();
+  for (int q = 0; q < A.k; ++q) {
+    const int p = A.p[q], ra = A.r[q], rb = B.r[q];
+    const int la = A.l[q], lb = B.l[q];
+    const C* a = (const C*)A.T[q];
+    const C* b = (const C*)B.T[q];
+    for (long long e = threadIdx.x; e < (long long)lb * p * ra; e += blockDim.x) {
+      int j = (int)(e / ((long long)p * ra)), pp = (int)((e / ra) % p), x = (int)(e % ra);
+      double2 s = make_double2(0.0, 0.0);
+      for (int i = 0; i < la; ++i) s = cadd(s, cmul(E[i * lb + j], c128(a[((long long)i * p + pp) * ra + x])));
+      F[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ra * rb; e += blockDim.x) {
+      int x = e / rb, y = e % rb;
+      double2 s = make_double2(0.0, 0.0);
+      for (int j = 0; j < lb; ++j)
+        for (int pp = 0; pp < p; ++pp)
+          s = cadd(s, cmul(F[((long long)j * p + pp) * ra + x], c128(b[((long long)j * p + pp) * rb + y])));
+      E2[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ra * rb; e += blockDim.x) E[e] = E2[e];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = E[0];
+}
+}  // namespace
+
+#define BBP_INSTANTIATE(C)                                                                                          \
+  cudaError_t launch_normalise(C* A, long long n, double* logscale, cudaStream_t s) {                              \
+    k_normalise<C><<<1, 1024, 0, s>>>(A, n, logscale);                                                             \
+    return cudaGetLastError();                                                                                     \
+  }                                                                                                                \
+  cudaError_t launch_copy_tensor(const C* src, C* dst, int l, int p, int r, bool transpose, cudaStream_t s) {       \
+    k_copy_tensor<C><<<grid_for((long long)l * p * r, 256), 256, 0, s>>>(src, dst, l, p, r, transpose ? 1 : 0);    \
+    return cudaGetLastError();                                                                                     \
+  }                                                                                                                \
+  cudaError_t launch_fill(C* A, long long n, double re, double im, cudaStream_t s) {                               \
+    k_fill<C><<<grid_for(n, 256), 256, 0, s>>>(A, n, re, im);                                                      \
+    return cudaGetLastError();                                                                                     \
+  }                                                                                                                \
+  cudaError_t launch_conj_transpose(const C* src, int rows, int cols, C* dst, cudaStream_t s) {                     \
+    k_conj_transpose<C><<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(src, rows, cols, dst);               \
+    return cudaGetLastError();                                                                                     \
+  }                                                                                                                \
+  cudaError_t launch_permute3(const C* src, int d0, int d1, int d2, const int perm[3], C* dst, cudaStream_t s) {   \
+    k_permute3<C><<<grid_for((long long)d0 * d1 * d2, 256), 256, 0, s>>>(src, d0, d1, d2,                          \
+                                                                      make_int3(perm[0], perm[1], perm[2]), dst);   \
+    return cudaGetLastError();                                                                                     \
+  }                                                                                                                \
+  cudaError_t launch_direct_sum(const C* a, int la, int ra, const C* b, int lb, int rb, int p, int pos, int k,     \
+                                C* out, cudaStream_t s) {                                                          \
+    long long tot = (long long)(la + lb) * p * (ra + rb);                                                          \
+    k_direct_sum<C><<<grid_for(tot, 256), 256, 0, s>>>(a, la, ra, b, lb, rb, p, pos, k, out);                      \
+    return cudaGetLastError();                                                                                     \
+  }                                                                                                                \
+  cudaError_t launch_frob(const C* R, long long n, double* dist, cudaStream_t s) {                                 \
+    k_frob<C><<<1, 1024, 0, s>>>(R, n, dist);                                                                      \
+    return cudaGetLastError();                                                                                     \
+  }
+
+BBP_INSTANTIATE(double2)
+BBP_INSTANTIATE(float2)
+
+cudaError_t launch_msg_normalise(const ChainDesc& m, bool c64, double2* work, cudaStream_t s) {
+  if (c64) k_msg_normalise<float2><<<1, 256, 0, s>>>(m, work);
+  else k_msg_normalise<double2><<<1, 256, 0, s>>>(m, work);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mps_dot(const ChainDesc& a, const ChainDesc& b, bool c64, double2* work, double2* out,
+                           cudaStream_t s) {
+  if (c64) k_mps_dot<float2><<<1, 256, 0, s>>>(a, b, work, out);
+  else k_mps_dot<double2><<<1, 256, 0, s>>>(a, b, work, out);
+  return cudaGetLastError();
+}
+
+}  // namespace bbp
