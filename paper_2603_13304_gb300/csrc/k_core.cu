@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "kernels.h"
@@ -309,6 +310,76 @@ __global__ void __launch_bounds__(256) k_qr(C* A, int m, int n, C* Q, C* Rm, C* 
   cta_form_q(A, m, n, tau, Q);
 }
 
+// Q formed in place over the reflectors (first k columns of A, row stride n):
+// Q = H_0 ... H_{k-1} [I; 0], accumulated backwards.  One CTA of 256 threads.
+template <typename C>
+__device__ void cta_form_q_inplace(C* A, int m, int n, const C* tau) {
+  const int k = m < n ? m : n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ C s_w2[8][33];
+  for (int i = k - 1; i >= 0; --i) {
+    const C ti = tau[i];
+    if (i < k - 1) {
+      if (threadIdx.x == 0) A[(long long)i * n + i] = cx<C>(1, 0);
+      __syncthreads();
+      for (int cb = i + 1; cb < k; cb += 32) {
+        const int c = cb + lane;
+        C acc = cx<C>(0, 0);
+        if (c < k)
+          for (int r = i + wid; r < m; r += nw) acc = cadd(acc, cmulc(A[(long long)r * n + i], A[(long long)r * n + c]));
+        s_w2[wid][lane] = acc;
+        __syncthreads();
+        if (wid == 0) {
+          C t = s_w2[0][lane];
+          for (int g = 1; g < nw; ++g) t = cadd(t, s_w2[g][lane]);
+          s_w2[0][lane] = cmul(ti, t);
+        }
+        __syncthreads();
+        const C f = s_w2[0][lane];
+        if (c < k)
+          for (int r = i + wid; r < m; r += nw)
+            A[(long long)r * n + c] = csub(A[(long long)r * n + c], cmul(A[(long long)r * n + i], f));
+        __syncthreads();
+      }
+    }
+    for (int r = i + 1 + threadIdx.x; r < m; r += blockDim.x)
+      A[(long long)r * n + i] = cmul(cx<C>(-ti.x, -ti.y), A[(long long)r * n + i]);
+    for (int r = threadIdx.x; r < i; r += blockDim.x) A[(long long)r * n + i] = cx<C>(0, 0);
+    if (threadIdx.x == 0) A[(long long)i * n + i] = cx<C>(1.0 - ti.x, -ti.y);
+    __syncthreads();
+  }
+}
+
+// dynamic shared memory of the staged kernels: the 227 KB opt-in per CTA less
+// a margin for their static shared arrays
+constexpr int kSmemMax = 211 * 1024;
+
+// QR with the matrix staged in shared memory (m * n * sizeof(C) <= kSmemMax):
+// A (row-major, read only) -> Q (m x k) and R (k x n, may be null).
+template <typename C>
+__global__ void __launch_bounds__(256) k_qr_smem(const C* __restrict__ Ag, int m, int n, C* __restrict__ Q,
+                                                 C* __restrict__ Rm, C* tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* A = (C*)smem_raw;
+  __shared__ double sh[40];
+  const long long mn = (long long)m * n;
+  for (long long e = threadIdx.x; e < mn; e += blockDim.x) A[e] = Ag[e];
+  __syncthreads();
+  cta_householder(A, m, n, tau, sh);
+  const int k = m < n ? m : n;
+  if (Rm)
+    for (long long e = threadIdx.x; e < (long long)k * n; e += blockDim.x) {
+      int i = (int)(e / n), c = (int)(e % n);
+      Rm[e] = (c >= i) ? A[(long long)i * n + c] : cx<C>(0, 0);
+    }
+  __syncthreads();
+  cta_form_q_inplace(A, m, n, tau);
+  for (long long e = threadIdx.x; e < (long long)m * k; e += blockDim.x) {
+    int i = (int)(e / k), c = (int)(e % k);
+    Q[e] = A[(long long)i * n + c];
+  }
+}
+
 // ---------------------------------------------------------------- K3 Jacobi
 
 template <typename C>
@@ -375,18 +446,25 @@ template <typename C>
 __device__ __forceinline__ void stcg(C* p, C v);
 template <> __device__ __forceinline__ void stcg(double2* p, double2 v) { __stcg(p, v); }
 template <> __device__ __forceinline__ void stcg(float2* p, float2 v) { __stcg(p, v); }
+// rows in global memory bypass L1 (other CTAs of the cluster rotate them);
+// rows in shared memory are plain accesses
+template <bool kGlobal, typename C> __device__ __forceinline__ C ldrow(const C* p) { return kGlobal ? ldcg(p) : *p; }
+template <bool kGlobal, typename C> __device__ __forceinline__ void strow(C* p, C v) {
+  if (kGlobal) stcg(p, v);
+  else *p = v;
+}
 
 // Rotate rows a, b of G (length N) and of WH (length M) so that they become
 // orthogonal.  Warp-cooperative (all lanes take the same decision: the xor
 // butterfly leaves bitwise identical sums in every lane); returns 1 when a
 // rotation was applied.
-template <typename C>
+template <bool kGlobal, typename C>
 __device__ int rotate_pair(C* ra, C* rb, int N, C* wa, C* wb, int M, int lane, double tol,
                            typename RealOf<C>::T floor) {
   using R = typename RealOf<C>::T;
   R al = 0, be = 0, gx = 0, gy = 0;
   for (int c = lane; c < N; c += 32) {
-    C x = ldcg(ra + c), y = ldcg(rb + c);
+    C x = ldrow<kGlobal>(ra + c), y = ldrow<kGlobal>(rb + c);
     al += cabs2(x);
     be += cabs2(y);
     gx += x.x * y.x + x.y * y.y;      // x * conj(y)
@@ -411,16 +489,16 @@ __device__ int rotate_pair(C* ra, C* rb, int N, C* wa, C* wb, int M, int lane, d
   R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
   R cs = (R)1 / sqrt((R)1 + t * t), sn = cs * t;
   for (int c = lane; c < N; c += 32) {
-    C x = ldcg(ra + c), y = ldcg(rb + c);
+    C x = ldrow<kGlobal>(ra + c), y = ldrow<kGlobal>(rb + c);
     C ey = cmul(e, y);
-    stcg(ra + c, csub(cscale(x, cs), cscale(ey, sn)));
-    stcg(rb + c, cadd(cscale(x, sn), cscale(ey, cs)));
+    strow<kGlobal>(ra + c, csub(cscale(x, cs), cscale(ey, sn)));
+    strow<kGlobal>(rb + c, cadd(cscale(x, sn), cscale(ey, cs)));
   }
   for (int c = lane; c < M; c += 32) {
-    C x = ldcg(wa + c), y = ldcg(wb + c);
+    C x = ldrow<kGlobal>(wa + c), y = ldrow<kGlobal>(wb + c);
     C ey = cmul(e, y);
-    stcg(wa + c, csub(cscale(x, cs), cscale(ey, sn)));
-    stcg(wb + c, cadd(cscale(x, sn), cscale(ey, cs)));
+    strow<kGlobal>(wa + c, csub(cscale(x, cs), cscale(ey, sn)));
+    strow<kGlobal>(wb + c, cadd(cscale(x, sn), cscale(ey, cs)));
   }
   return 1;
 }
@@ -444,7 +522,7 @@ __global__ void __launch_bounds__(256) k_jacobi(SvdWork<C> w, int M, int N, doub
         if (q == 0) { a = Mp - 1; b = r; }
         else { a = (r + q) % (Mp - 1); b = (r - q + Mp - 1) % (Mp - 1); }
         if (a >= M || b >= M) continue;
-        rot += rotate_pair(w.G + (long long)a * N, w.G + (long long)b * N, N, w.WH + (long long)a * M,
+        rot += rotate_pair<true>(w.G + (long long)a * N, w.G + (long long)b * N, N, w.WH + (long long)a * M,
                            w.WH + (long long)b * M, M, lane, tol, floor);
       }
       cl.sync();
@@ -461,6 +539,58 @@ __global__ void __launch_bounds__(256) k_jacobi(SvdWork<C> w, int M, int N, doub
     if (total == 0) return;
   }
   if (crank == 0 && threadIdx.x == 0) *status = 1;   // sweep limit reached
+}
+
+// One-CTA Jacobi with G and WH resident in shared memory
+// ((M*N + M*M) * sizeof(C) <= kSmemMax); same rounds, tests and counters as
+// k_jacobi, __syncthreads between rounds.
+template <typename C>
+__global__ void __launch_bounds__(1024) k_jacobi_smem(SvdWork<C> w, int M, int N, double tol, double floor_rel,
+                                                     int max_sweeps, int* status) {
+  using R = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* G = (C*)smem_raw;
+  C* WH = G + (long long)M * N;
+  __shared__ int s_rot;
+  const R floor = (R)(floor_rel * *w.zn2);
+  for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) G[e] = w.G[e];
+  for (long long e = threadIdx.x; e < (long long)M * M; e += blockDim.x) WH[e] = w.WH[e];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int Mp = M + (M & 1);
+  const int npairs = Mp / 2;
+  int sweeps = 0, rot_total = 0;
+  bool converged = false;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    int rot = 0;
+    for (int r = 0; r < Mp - 1; ++r) {
+      for (int q = warp; q < npairs; q += nw) {
+        int a, b;
+        if (q == 0) { a = Mp - 1; b = r; }
+        else { a = (r + q) % (Mp - 1); b = (r - q + Mp - 1) % (Mp - 1); }
+        if (a >= M || b >= M) continue;
+        rot += rotate_pair<false>(G + (long long)a * N, G + (long long)b * N, N, WH + (long long)a * M,
+                             WH + (long long)b * M, M, lane, tol, floor);
+      }
+      __syncthreads();
+    }
+    if (lane == 0 && rot) atomicAdd(&s_rot, rot);
+    __syncthreads();
+    const int total = s_rot;
+    ++sweeps;
+    rot_total += total;
+    __syncthreads();
+    if (total == 0) { converged = true; break; }
+  }
+  for (long long e = threadIdx.x; e < (long long)M * N; e += blockDim.x) w.G[e] = G[e];
+  for (long long e = threadIdx.x; e < (long long)M * M; e += blockDim.x) w.WH[e] = WH[e];
+  if (threadIdx.x == 0) {
+    w.counters[2] = sweeps;
+    w.counters[3] = rot_total;
+    if (!converged) *status = 1;
+  }
 }
 
 template <typename C>
@@ -517,15 +647,32 @@ __global__ void k_svd_out(SvdWork<C> w, int m, int n, int k, double floor_rel, C
 // Rows below sqrt(floor_rel) ||Z|| are left unrotated (eps^2 of the type).
 template <typename C> constexpr double floor_rel_of() { return sizeof(typename RealOf<C>::T) == 8 ? 1e-32 : 1e-14; }
 
+// Large dynamic shared memory is opt-in, once per kernel and device.
+template <auto kKernel>
+cudaError_t smem_optin() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kKernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
+// Jacobi on the M x N rows of w: in shared memory when G and WH fit (one CTA,
+// one warp per pair), else on a cluster of up to 8 CTAs.
 template <typename C>
-cudaError_t jacobi_svd(const C* Z, int m, int n, int chi, C* U, C* Rem, void* work, int* status, cudaStream_t s,
-                       double tol, int max_sweeps) {
-  const int M = m < n ? m : n, N = m < n ? n : m;
-  const int k = chi < M ? chi : M;
-  SvdWork<C> w = carve<C>(work, M, N);
-  cudaError_t e0 = cudaMemsetAsync(w.counters, 0, 64, s);
-  if (e0 != cudaSuccess) return e0;
-  k_svd_init<C><<<grid_for((long long)M * N + (long long)M * M, 256), 256, 0, s>>>(Z, m, n, w);
+cudaError_t launch_jacobi(SvdWork<C> w, int M, int N, double tol, int max_sweeps, int* status, cudaStream_t s) {
+  const size_t jsm = sizeof(C) * ((size_t)M * N + (size_t)M * M);
+  if (jsm <= (size_t)kSmemMax) {
+    cudaError_t e = smem_optin<k_jacobi_smem<C>>();
+    if (e != cudaSuccess) return e;
+    const int threads = std::min(1024, 32 * std::max(1, (M + 1) / 2));
+    k_jacobi_smem<C><<<1, threads, jsm, s>>>(w, M, N, tol, floor_rel_of<C>(), max_sweeps, status);
+    return cudaGetLastError();
+  }
   int cs = (M / 2 + 15) / 16;   // about two pairs per warp per round
   if (cs < 1) cs = 1;
   if (cs > 8) cs = 8;
@@ -540,7 +687,19 @@ cudaError_t jacobi_svd(const C* Z, int m, int n, int chi, C* U, C* Rem, void* wo
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_jacobi<C>, w, M, N, tol, floor_rel_of<C>(), max_sweeps, status);
+  return cudaLaunchKernelEx(&cfg, k_jacobi<C>, w, M, N, tol, floor_rel_of<C>(), max_sweeps, status);
+}
+
+template <typename C>
+cudaError_t jacobi_svd(const C* Z, int m, int n, int chi, C* U, C* Rem, void* work, int* status, cudaStream_t s,
+                       double tol, int max_sweeps) {
+  const int M = m < n ? m : n, N = m < n ? n : m;
+  const int k = chi < M ? chi : M;
+  SvdWork<C> w = carve<C>(work, M, N);
+  cudaError_t e0 = cudaMemsetAsync(w.counters, 0, 64, s);
+  if (e0 != cudaSuccess) return e0;
+  k_svd_init<C><<<grid_for((long long)M * N + (long long)M * M, 256), 256, 0, s>>>(Z, m, n, w);
+  cudaError_t e = launch_jacobi(w, M, N, tol, max_sweeps, status, s);
   if (e != cudaSuccess) return e;
   k_row_norms<C><<<(M * 32 + 255) / 256, 256, 0, s>>>(w, M, N);
   k_select<C><<<1, 256, 0, s>>>(w, M, k);
@@ -567,6 +726,20 @@ __global__ void k_omega(float2* O, int n, int b) {
     x ^= x >> 33;
     O[e] = make_float2((x & 1) ? 1.f : -1.f, (x & 2) ? 1.f : -1.f);
   }
+}
+
+// One CTA: orthonormalise the columns of Y (rows x b) in place with the panel
+// staged in shared memory (rows * b * 8 <= kSmemMax).
+__global__ void __launch_bounds__(256) k_orth_smem(float2* Y, int rows, int b, float2* tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* A = (float2*)smem_raw;
+  __shared__ double sh[40];
+  for (long long e = threadIdx.x; e < (long long)rows * b; e += blockDim.x) A[e] = Y[e];
+  __syncthreads();
+  cta_householder(A, rows, b, tau, sh);
+  __syncthreads();
+  cta_form_q_inplace(A, rows, b, tau);
+  for (long long e = threadIdx.x; e < (long long)rows * b; e += blockDim.x) Y[e] = A[e];
 }
 
 // One CTA: orthonormalise the columns of Y (rows x b) in place (Householder,
@@ -644,13 +817,23 @@ cudaError_t launch_zgemm(char opA, char opB, int M, int N, int K, float2 alpha, 
   return gemm_t(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, s);
 }
 
-cudaError_t launch_qr(double2* A, int m, int n, double2* Q, double2* R, double2* tau, cudaStream_t s) {
-  k_qr<double2><<<1, 256, 0, s>>>(A, m, n, Q, R, tau);
+template <typename C>
+static cudaError_t qr_t(C* A, int m, int n, C* Q, C* R, C* tau, cudaStream_t s) {
+  const size_t sm = sizeof(C) * (size_t)m * n;
+  if (sm <= (size_t)kSmemMax) {
+    cudaError_t e = smem_optin<k_qr_smem<C>>();
+    if (e != cudaSuccess) return e;
+    k_qr_smem<C><<<1, 256, sm, s>>>(A, m, n, Q, R, tau);
+  } else {
+    k_qr<C><<<1, 256, 0, s>>>(A, m, n, Q, R, tau);
+  }
   return cudaGetLastError();
 }
+cudaError_t launch_qr(double2* A, int m, int n, double2* Q, double2* R, double2* tau, cudaStream_t s) {
+  return qr_t(A, m, n, Q, R, tau, s);
+}
 cudaError_t launch_qr(float2* A, int m, int n, float2* Q, float2* R, float2* tau, cudaStream_t s) {
-  k_qr<float2><<<1, 256, 0, s>>>(A, m, n, Q, R, tau);
-  return cudaGetLastError();
+  return qr_t(A, m, n, Q, R, tau, s);
 }
 
 size_t svd_work_bytes(int m, int n) {
@@ -709,37 +892,27 @@ cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, 
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
   cudaError_t e;
   k_omega<<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
+  const bool staged = z * (size_t)N * b <= (size_t)kSmemMax;
+  if (staged && (e = smem_optin<k_orth_smem>()) != cudaSuccess) return e;
+  auto orthonormalise = [&](float2* Y, int rows) {
+    if (staged) k_orth_smem<<<1, 256, z * (size_t)rows * b, s>>>(Y, rows, b, orth);
+    else k_orth<<<1, 256, 0, s>>>(Y, rows, b, orth);
+  };
   // Q = orth(Z W)
   if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
-  k_orth<<<1, 256, 0, s>>>(Q, m, b, orth);
+  orthonormalise(Q, m);
   for (int it = 0; it < power_iters; ++it) {
     if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
-    k_orth<<<1, 256, 0, s>>>(W, n, b, orth);
+    orthonormalise(W, n);
     if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
-    k_orth<<<1, 256, 0, s>>>(Q, m, b, orth);
+    orthonormalise(Q, m);
   }
   // B = Q^H Z (b x n) into X, then Jacobi on its rows (b <= n here)
   if ((e = launch_zgemm('C', 'N', b, n, m, one, Q, b, 0, Z, n, 0, zero, X, n, 0, 1, s)) != cudaSuccess) return e;
   SvdWork<float2> w = carve<float2>(jw, b, n);
   if ((e = cudaMemsetAsync(w.counters, 0, 64, s)) != cudaSuccess) return e;
   k_svd_init<float2><<<grid_for((long long)b * n + (long long)b * b, 256), 256, 0, s>>>(X, b, n, w);
-  int cs = (b / 2 + 15) / 16;
-  if (cs < 1) cs = 1;
-  if (cs > 8) cs = 8;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cs, 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if ((e = cudaLaunchKernelEx(&cfg, k_jacobi<float2>, w, b, n, jacobi_tol_c64(n), floor_rel_of<float2>(), 60,
-                              status)) != cudaSuccess)
-    return e;
+  if ((e = launch_jacobi(w, b, n, jacobi_tol_c64(n), 60, status, s)) != cudaSuccess) return e;
   k_row_norms<float2><<<(b * 32 + 255) / 256, 256, 0, s>>>(w, b, n);
   k_select<float2><<<1, 256, 0, s>>>(w, b, k);
   k_rand_out<<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(Q, m, b, w, n, k, U, Rem);
