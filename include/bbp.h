@@ -194,6 +194,27 @@ bbp_status bbp_k_svd_stats(const void* work, int m, int n, int* sweeps, long lon
  * = Q (m x k) R (k x n), k = min(m, n); tau: device scratch of k complex. */
 bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, void* stream);
 
+/* K2 on the tensor cores (tcgen05.mma, TMEM accumulator, TMA-fed operands).
+ * Real GEMM C (M x N, device fp32, row stride ldc) = alpha * A * B with
+ * A row-major M x K (row stride lda) and B given transposed, Bt row-major
+ * N x K (row stride ldb).  bf16 = 0: TF32 operands stored as fp32;
+ * bf16 = 1: BF16 operands.  A and Bt must be 16-byte aligned and lda, ldb
+ * multiples of 16 bytes; ragged M, N, K are zero-filled by TMA.  err: device
+ * int set to 1 when a pipeline wait timed out (never cleared). */
+bbp_status bbp_k_tc_gemm(int bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C, long long ldc,
+                         int M, int N, int K, float alpha, int* err, void* stream);
+
+/* The absorb contraction of Sec. 2.3.3 on the tensor cores:
+ * R[a] (Q x r) = X^T (Q x P) S[a] (P x r) for a < l, complex, row-major,
+ * X: P x Q, S: l x P x r, R: l x Q x r; c64 = 1 for complex64 data, 0 for
+ * complex128.  Both operands are scaled by a power of two and split into
+ * high and low parts in the operand type (bf16 = 0: TF32, 1: BF16); the three
+ * products hi*hi + hi*lo + lo*hi accumulate in FP32 in one real GEMM.  work:
+ * device scratch of bbp_k_tc_absorb_bytes(...) bytes; err as above. */
+size_t bbp_k_tc_absorb_bytes(int bf16, int P, int Q, int l, int r);
+bbp_status bbp_k_tc_absorb(int bf16, int c64, const void* X, int P, int Q, const void* S, int l, int r, void* R,
+                           void* work, int* err, void* stream);
+
 /* Host-side plan of one boundary-MPS sweep (no GPU needed): for block `block`
  * and out face `face`, the swallow order as (kind, id) pairs: kind 0 = site
  * (id = global site id), kind 1 = message tensor (id = face * 1024 + index),

@@ -344,6 +344,29 @@ bbp_status bbp_k_svd_stats(const void* work, int m, int n, int* sweeps, long lon
   return cuda_status(bbp::svd_stats(work, m, n, sweeps, rotations, (cudaStream_t)stream));
 }
 
+bbp_status bbp_k_tc_gemm(int bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C, long long ldc,
+                         int M, int N, int K, float alpha, int* err, void* stream) {
+  if (!A || !Bt || !C || !err || M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N)
+    return set_err(BBP_ERR_ARG, "bad arguments");
+  return cuda_status(bbp::launch_tc_gemm(bf16 != 0, A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err,
+                                         (cudaStream_t)stream));
+}
+
+size_t bbp_k_tc_absorb_bytes(int bf16, int P, int Q, int l, int r) {
+  return (P > 0 && Q > 0 && l > 0 && r > 0) ? bbp::tc_absorb_bytes(bf16 != 0, P, Q, l, r) : 0;
+}
+
+bbp_status bbp_k_tc_absorb(int bf16, int c64, const void* X, int P, int Q, const void* S, int l, int r, void* R,
+                           void* work, int* err, void* stream) {
+  if (!X || !S || !R || !work || !err || P < 1 || Q < 1 || l < 1 || r < 1) return set_err(BBP_ERR_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c64)
+    return cuda_status(bbp::launch_tc_absorb(bf16 != 0, (const float2*)X, P, Q, (const float2*)S, l, r, (float2*)R,
+                                             work, err, st));
+  return cuda_status(bbp::launch_tc_absorb(bf16 != 0, (const double2*)X, P, Q, (const double2*)S, l, r, (double2*)R,
+                                           work, err, st));
+}
+
 bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, void* stream) {
   if (!A || !Q || !R || !tau || m < 1 || n < 1) return set_err(BBP_ERR_ARG, "bad arguments");
   return cuda_status(bbp::launch_qr((double2*)A, m, n, (double2*)Q, (double2*)R, (double2*)tau, (cudaStream_t)stream));

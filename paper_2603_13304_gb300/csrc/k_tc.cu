@@ -1,0 +1,470 @@
+// Tensor-core GEMM for the absorb contraction (K2, Sec. 1.1.3 / Sec. 2.3.3):
+// tcgen05.mma with the accumulator in TMEM, operands staged into shared
+// memory by TMA (128-byte swizzle, K-major), a 4-stage mbarrier pipeline.
+//
+// Real GEMM  C (M x N, fp32, row-major) = alpha * A (M x K) * B (K x N)
+// with A given K-major (row-major M x K) and B given as B^T (row-major
+// N x K).  Operands are TF32 (kind::tf32, 32-bit storage) or BF16
+// (kind::f16).  One CTA of 128 threads computes a 128 x BN tile:
+//   warp 0, one lane : TMA producer
+//   warp 1, one lane : MMA issuer (tcgen05.mma, tcgen05.commit -> mbarrier)
+//   warps 0-3        : epilogue, TMEM lanes 32w..32w+31 -> rows of C
+// Every mbarrier wait is bounded by the global timer; on expiry the kernel
+// records an error, drains its own TMA copies and MMAs (bounded), releases
+// TMEM and returns.
+//
+// The complex contraction R[a] = X^T S[a] (batched over a) runs as one real
+// GEMM: X^T and S are split into high and low parts in the operand type
+// (value = hi + lo, each scaled by a power of two so that its largest
+// magnitude is about 1), and the K dimension concatenates
+//   A = [ Re hi, -Im hi | Re hi, -Im hi | Re lo, -Im lo ]   (rows q)
+//       [ Im hi,  Re hi | Im hi,  Re hi | Im lo,  Re lo ]   (rows Q + q)
+//   B = [ Re hi ; Im hi ; Re lo ; Im lo ; Re hi ; Im hi ]
+// so that hi*hi + hi*lo + lo*hi accumulates in FP32 in one pass.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "kernels.h"
+
+namespace bbp {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kStages = 4;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+// Wait for the phase of the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = saddr(bar);
+  unsigned long long t0 = 0;
+  for (long long it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it == 0) t0 = gtimer();
+    else if (gtimer() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          saddr(dst)),
+      "l"(map), "r"(saddr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (the layout TMA writes for a 128-byte-wide box).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t a) {
+  uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+template <bool kBF16>
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  if constexpr (kBF16)
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(
+            tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor: FP32 accumulator, A/B K-major, M = 128, N = BN.
+template <bool kBF16, int BN>
+__host__ __device__ constexpr uint32_t idesc_of() {
+  const uint32_t fmt = kBF16 ? 1u : 2u;   // BF16 (kind::f16) or TF32 (kind::tf32)
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+template <bool kBF16, int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, float* __restrict__ C,
+              int M, int N, int K, long long ldc, float alpha, int* err) {
+  constexpr int kEs = kBF16 ? 2 : 4;
+  constexpr int kBKe = 128 / kEs;               // K elements per stage (one 128-byte row)
+  constexpr int kUmmaK = 32 / kEs;              // K elements per tcgen05.mma
+  constexpr int kABytes = kBM * 128, kBBytes = BN * 128, kStageBytes = kABytes + kBBytes;
+  constexpr uint32_t kIdesc = idesc_of<kBF16, BN>();
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM;
+  const int kt = (K + kBKe - 1) / kBKe;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s_tmem)),
+                 "r"((uint32_t)BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int k = 0; k < kt; ++k) {
+      const int s = k % kStages;
+      const uint32_t ph = (uint32_t)(k / kStages) & 1u;
+      if (k >= kStages && !mbar_wait(&empty[s], ph ^ 1u)) {
+        s_fail = 1;
+        break;
+      }
+      mbar_expect_tx(&full[s], kStageBytes);
+      tma_load_2d(base + s * kStageBytes, &tA, &full[s], k * kBKe, m0);
+      tma_load_2d(base + s * kStageBytes + kABytes, &tB, &full[s], k * kBKe, n0);
+      ++issued;
+    }
+    // no copy of ours may still be in flight when the CTA exits
+    for (int k = issued - kStages < 0 ? 0 : issued - kStages; k < issued; ++k)
+      if (!mbar_wait(&full[k % kStages], (uint32_t)(k / kStages) & 1u)) s_fail = 1;
+  } else if (warp == 1 && lane == 0) {
+    for (int k = 0; k < kt; ++k) {
+      const int s = k % kStages;
+      if (!mbar_wait(&full[s], (uint32_t)(k / kStages) & 1u)) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a = saddr(base + s * kStageBytes), b = a + kABytes;
+#pragma unroll
+      for (int kk = 0; kk < kBKe / kUmmaK; ++kk)
+        umma<kBF16>(tmem, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), kIdesc, (k | kk) != 0);
+      umma_commit(&empty[s]);
+    }
+    umma_commit(&done);   // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+  if (!mbar_wait(&done, 0)) s_fail = 1;
+  __syncwarp();   // tcgen05.ld below is warp-collective
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (row < M && kt > 0) {
+      float* out = C + (long long)row * ldc + n0 + c0;
+      const int lim = N - n0 - c0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < lim) out[j] = alpha * __uint_as_float(v[j]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+  if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+}
+
+// ------------------------------------------------------------ host: TMA maps
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// rows x cols row-major operand (cols = K, contiguous), box = box_rows x 128 bytes
+bool make_map(CUtensorMap* m, const void* ptr, bool bf16, int rows, int cols, long long ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int es = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <bool kBF16, int BN>
+cudaError_t tc_launch(const void* A, long long lda, const void* Bt, long long ldb, float* C, long long ldc, int M, int N,
+                      int K, float alpha, int* err, cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  constexpr int smem = kStages * (kBM + BN) * 128 + 1024;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_tc_gemm<kBF16, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, kBF16, M, K, lda, kBM) || !make_map(&tb, Bt, kBF16, N, K, ldb, BN))
+    return cudaErrorInvalidValue;
+  dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM);
+  k_tc_gemm<kBF16, BN><<<grid, 128, smem, s>>>(ta, tb, C, M, N, K, ldc, alpha, err);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------- complex <-> real packing
+
+template <bool kBF16> struct Op;
+template <> struct Op<false> {
+  using T = float;
+  static __device__ __forceinline__ float round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+  }
+  static __device__ __forceinline__ float store(float x) { return x; }
+};
+template <> struct Op<true> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ float round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+  static __device__ __forceinline__ __nv_bfloat16 store(float x) { return __float2bfloat16_rn(x); }
+};
+
+template <typename C> __device__ __forceinline__ double2 ld_c(const C* p, long long i);
+template <> __device__ __forceinline__ double2 ld_c(const double2* p, long long i) { return p[i]; }
+template <> __device__ __forceinline__ double2 ld_c(const float2* p, long long i) {
+  float2 v = p[i];
+  return make_double2(v.x, v.y);
+}
+
+// largest |Re|, |Im| of n complex entries -> *out (as the bits of a
+// non-negative float, so atomicMax on int orders them)
+template <typename C>
+__global__ void k_absmax(const C* __restrict__ x, long long n, int* out) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 v = ld_c(x, i);
+    m = fmaxf(m, fmaxf(fabsf((float)v.x), fabsf((float)v.y)));
+  }
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_int(m));
+}
+
+// power-of-two scale bringing the largest magnitude near 1
+__device__ __forceinline__ float pow2_scale(const int* amax) {
+  const float m = __int_as_float(*amax);
+  if (!(m > 0.f) || !isfinite(m)) return 1.f;
+  return exp2f(-(float)ilogbf(m));
+}
+
+// A operand from X (P x Q complex, row-major): rows q and Q + q, K index
+// laid out [hi | hi | lo] x [Re/Im block of P]; row stride lda >= 6P.
+template <bool kBF16, typename C>
+__global__ void k_pack_a(const C* __restrict__ X, int P, int Q, const int* amax, typename Op<kBF16>::T* A, long long lda) {
+  using O = Op<kBF16>;
+  const float sc = pow2_scale(amax);
+  const long long tot = (long long)Q * lda;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e / lda), kk = (int)(e % lda);
+    float v0 = 0.f, v1 = 0.f;   // rows q (real part) and Q + q (imaginary part)
+    if (kk < 6 * P) {
+      const int blk = kk / (2 * P), rem = kk % (2 * P), p = rem % P;
+      const bool im_half = rem >= P;
+      double2 x = ld_c(X, (long long)p * Q + q);
+      float xr = (float)x.x * sc, xi = (float)x.y * sc;
+      float hr = O::round(xr), hi = O::round(xi);
+      if (blk == 2) {
+        xr = O::round(xr - hr);
+        xi = O::round(xi - hi);
+      } else {
+        xr = hr;
+        xi = hi;
+      }
+      // row q: [Re, -Im]; row Q + q: [Im, Re]
+      v0 = im_half ? -xi : xr;
+      v1 = im_half ? xr : xi;
+    }
+    A[(long long)q * lda + kk] = O::store(v0);
+    A[(long long)(Q + q) * lda + kk] = O::store(v1);
+  }
+}
+
+// B^T operand from S (l x P x r complex): row n = a * r + c, K index laid
+// out [hi | lo | hi] x [Re/Im block of P]; row stride ldb >= 6P.
+template <bool kBF16, typename C>
+__global__ void k_pack_b(const C* __restrict__ S, int l, int P, int r, const int* amax, typename Op<kBF16>::T* B,
+                         long long ldb) {
+  using O = Op<kBF16>;
+  const float sc = pow2_scale(amax);
+  const long long N = (long long)l * r;
+  const long long tot = N * ldb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long n = e / ldb;
+    const int kk = (int)(e % ldb);
+    float v = 0.f;
+    if (kk < 6 * P) {
+      const int blk = kk / (2 * P), rem = kk % (2 * P), p = rem % P;
+      const bool im_half = rem >= P;
+      const int a = (int)(n / r), c = (int)(n % r);
+      double2 x = ld_c(S, ((long long)a * P + p) * r + c);
+      float xv = (float)(im_half ? x.y : x.x) * sc;
+      float h = O::round(xv);
+      v = (blk == 1) ? O::round(xv - h) : h;
+    }
+    B[e] = O::store(v);
+  }
+}
+
+template <typename C> __device__ __forceinline__ C mk(double re, double im);
+template <> __device__ __forceinline__ double2 mk(double re, double im) { return make_double2(re, im); }
+template <> __device__ __forceinline__ float2 mk(double re, double im) { return make_float2((float)re, (float)im); }
+
+// R[a][q][c] = (Cr[q][a r + c] + i Ci[q][a r + c]) / (scale_A scale_B)
+template <typename C>
+__global__ void k_unpack(const float* __restrict__ Cm, long long ldc, int Q, int l, int r, const int* amax_a,
+                         const int* amax_b, C* R) {
+  const double inv = 1.0 / ((double)pow2_scale(amax_a) * (double)pow2_scale(amax_b));
+  const long long tot = (long long)l * Q * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % r);
+    const long long t = e / r;
+    const int q = (int)(t % Q), a = (int)(t / Q);
+    const long long n = (long long)a * r + c;
+    R[e] = mk<C>(Cm[(long long)q * ldc + n] * inv, Cm[(long long)(Q + q) * ldc + n] * inv);
+  }
+}
+
+int grid_of(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ public
+
+cudaError_t launch_tc_gemm(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
+                           long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  const int es = bf16 ? 2 : 4;
+  if ((lda * es) % 16 || (ldb * es) % 16 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15)) return cudaErrorInvalidValue;
+  if (N > 64) {
+    return bf16 ? tc_launch<true, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s)
+                : tc_launch<false, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s);
+  }
+  return bf16 ? tc_launch<true, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s)
+              : tc_launch<false, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s);
+}
+
+long long tc_ld(int P) { return ((6LL * P + 31) / 32) * 32; }
+
+size_t tc_absorb_bytes(bool bf16, int P, int Q, int l, int r) {
+  const size_t es = bf16 ? 2 : 4;
+  const size_t ld = (size_t)tc_ld(P);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  return al(2 * (size_t)Q * ld * es) + al((size_t)l * r * ld * es) + al(sizeof(float) * 2 * (size_t)Q * l * r) + 256;
+}
+
+template <typename C>
+static cudaError_t tc_absorb_t(bool bf16, const C* X, int P, int Q, const C* S, int l, int r, C* R, void* work,
+                               int* err, cudaStream_t s) {
+  const size_t es = bf16 ? 2 : 4;
+  const long long ld = tc_ld(P);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  char* p = (char*)work;
+  void* A = p;
+  p += al(2 * (size_t)Q * ld * es);
+  void* B = p;
+  p += al((size_t)l * r * ld * es);
+  float* Cm = (float*)p;
+  p += al(sizeof(float) * 2 * (size_t)Q * l * r);
+  int* amax = (int*)p;   // [0] X, [1] S
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(amax, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
+  k_absmax<C><<<grid_of((long long)P * Q), 256, 0, s>>>(X, (long long)P * Q, amax);
+  k_absmax<C><<<grid_of((long long)l * P * r), 256, 0, s>>>(S, (long long)l * P * r, amax + 1);
+  if (bf16) {
+    k_pack_a<true, C><<<grid_of((long long)Q * ld), 256, 0, s>>>(X, P, Q, amax, (__nv_bfloat16*)A, ld);
+    k_pack_b<true, C><<<grid_of((long long)l * r * ld), 256, 0, s>>>(S, l, P, r, amax + 1, (__nv_bfloat16*)B, ld);
+  } else {
+    k_pack_a<false, C><<<grid_of((long long)Q * ld), 256, 0, s>>>(X, P, Q, amax, (float*)A, ld);
+    k_pack_b<false, C><<<grid_of((long long)l * r * ld), 256, 0, s>>>(S, l, P, r, amax + 1, (float*)B, ld);
+  }
+  const int N = l * r;
+  if ((e = launch_tc_gemm(bf16, A, ld, B, ld, Cm, N, 2 * Q, N, (int)ld, 1.0f, err, s)) != cudaSuccess) return e;
+  k_unpack<C><<<grid_of((long long)l * Q * r), 256, 0, s>>>(Cm, N, Q, l, r, amax, amax + 1, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_absorb(bool bf16, const double2* X, int P, int Q, const double2* S, int l, int r, double2* R,
+                             void* work, int* err, cudaStream_t s) {
+  return tc_absorb_t(bf16, X, P, Q, S, l, r, R, work, err, s);
+}
+cudaError_t launch_tc_absorb(bool bf16, const float2* X, int P, int Q, const float2* S, int l, int r, float2* R,
+                             void* work, int* err, cudaStream_t s) {
+  return tc_absorb_t(bf16, X, P, Q, S, l, r, R, work, err, s);
+}
+
+}  // namespace bbp

@@ -98,6 +98,18 @@ cudaError_t launch_frob(const float2* R, long long n, double* dist, cudaStream_t
 cudaError_t launch_mps_dot(const ChainDesc& a, const ChainDesc& b, bool c64, double2* work, double2* out,
                            cudaStream_t s);
 
+// K2 on tcgen05 (k_tc.cu): real GEMM C = alpha * A * Bt^T, A (M x K) and Bt
+// (N x K) row-major in TF32 (fp32 storage) or BF16, C fp32; *err = 1 when a
+// pipeline wait timed out.  The complex absorb R[a] = X^T S[a] runs as one
+// split-precision real GEMM (hi*hi + hi*lo + lo*hi).
+cudaError_t launch_tc_gemm(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
+                           long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s);
+size_t tc_absorb_bytes(bool bf16, int P, int Q, int l, int r);
+cudaError_t launch_tc_absorb(bool bf16, const double2* X, int P, int Q, const double2* S, int l, int r, double2* R,
+                             void* work, int* err, cudaStream_t s);
+cudaError_t launch_tc_absorb(bool bf16, const float2* X, int P, int Q, const float2* S, int l, int r, float2* R,
+                             void* work, int* err, cudaStream_t s);
+
 // Allocation-free truncated SVD (k_noalloc.cu): scratch in a fixed device
 // array of noalloc_scratch_bytes(); *too_large is set when svd_work_bytes(m, n)
 // exceeds it (nothing is launched then).
