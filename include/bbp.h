@@ -90,9 +90,21 @@ bbp_status bbp_partition_blocks(bbp_ctx* ctx, int bx, int by);
  *   large matrix to chi + chi/2 directions by a randomised subspace iteration
  *   (3 power steps) before an exact one-sided Jacobi on the reduced matrix;
  *   message norms, phases, distances and log-scales stay double.
+ * BBP_TF32 / BBP_BF16 -- as BBP_FP32, with the absorb contraction (the
+ *   dense X^T S product of each swallow) on the tensor cores: both operands
+ *   scaled by a power of two and split into high and low TF32 (or BF16)
+ *   parts, hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM (tcgen05).
+ *   A pipeline wait that times out makes bbp_iterate return BBP_ERR_TIMEOUT.
  * Must be called before bbp_init_messages.  alpha must be 1 (undamped
  * update).  seed is reserved. */
 bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, uint64_t seed);
+
+/* Execution options (no counterpart in the thesis; they change how the same
+ * arithmetic is scheduled, not what it computes).  use_graphs = 1 (default)
+ * captures one synchronous iteration, every sweep of it forked over up to
+ * max_streams CUDA streams (1..64, default 16), into a CUDA graph and
+ * replays it while shapes and buffers stay the same; 0 launches eagerly. */
+bbp_status bbp_set_execution(bbp_ctx* ctx, int use_graphs, int max_streams);
 
 /* Initial messages (Alg. 1, "random MPS"): every incoming message becomes a
  * bond-1 MPS whose leg j carries the D x D matrix edge_mats[s][k] of the

@@ -82,13 +82,24 @@ bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, u
   (void)seed;
   if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
   if (chi < 1 || chi > 64) return set_err(BBP_ERR_ARG, "chi must be 1..64");
-  if (precision != BBP_FP64 && precision != BBP_FP32)
-    return set_err(BBP_ERR_ARG, "precision must be BBP_FP64 or BBP_FP32");
+  if (precision != BBP_FP64 && precision != BBP_FP32 && precision != BBP_TF32 && precision != BBP_BF16)
+    return set_err(BBP_ERR_ARG, "precision must be BBP_FP64, BBP_TF32, BBP_BF16 or BBP_FP32");
   if (alpha != 1.0) return set_err(BBP_ERR_ARG, "only the undamped update (alpha = 1) is implemented");
   if (ctx->eng.messages_ready) return set_err(BBP_ERR_STATE, "options must be set before bbp_init_messages");
   int rc = ctx->eng.set_precision(precision == BBP_FP64 ? 0 : 1);
   if (rc) return from(ctx, rc);
+  ctx->eng.tc_mode = precision == BBP_TF32 ? 1 : precision == BBP_BF16 ? 2 : 0;
+  ctx->eng.drop_graphs();
   ctx->eng.chi = chi;
+  return BBP_OK;
+}
+
+bbp_status bbp_set_execution(bbp_ctx* ctx, int use_graphs, int max_streams) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (max_streams < 1 || max_streams > 64) return set_err(BBP_ERR_ARG, "max_streams must be 1..64");
+  ctx->eng.drop_graphs();
+  ctx->eng.use_graphs = use_graphs != 0;
+  ctx->eng.max_streams = max_streams;
   return BBP_OK;
 }
 

@@ -90,11 +90,12 @@ int fail(Engine* e, int status, const std::string& msg) {
 
 // ------------------------------------------------------------ sweep work
 
-bool SweepWork::reserve(size_t el, size_t ct, size_t cs, size_t cx, size_t sb, size_t ns, size_t cd) {
+bool SweepWork::reserve(size_t el, size_t ct, size_t cs, size_t cx, size_t sb, size_t ns, size_t cd, size_t tb) {
   if (el == elem && ct <= cap_t && cs <= cap_seg && cx <= cap_x && sb <= svd_bytes && ns <= nslots && cd <= cap_d &&
-      arena.p)
+      tb <= tc_bytes && arena.p)
     return true;
-  if (el != elem) { cap_t = cap_seg = cap_x = svd_bytes = nslots = cap_d = 0; }
+  if (el != elem) { cap_t = cap_seg = cap_x = svd_bytes = nslots = cap_d = tc_bytes = 0; }
+  tc_bytes = std::max(tb, tc_bytes);
   elem = el;
   cap_t = std::max(ct, cap_t);
   cap_seg = std::max(cs, cap_seg);
@@ -105,7 +106,7 @@ bool SweepWork::reserve(size_t el, size_t ct, size_t cs, size_t cx, size_t sb, s
   const size_t z = elem, zd = sizeof(double2);
   size_t total = nslots * al(cap_t * z) + 4 * al(cap_seg * z) + 3 * al(cap_t * z) + al(4096 * z) + al(cap_x * z) +
                  al(svd_bytes) + 256 * 4 + al(64 * sizeof(void*) * 2) + al(64 * 3 * 2 * sizeof(int)) +
-                 al((2 * 64 * 64 + 64 * 64 * 64 + 256) * zd) + 4 * al(cap_d * zd) + al(4096 * zd);
+                 al((2 * 64 * 64 + 64 * 64 * 64 + 256) * zd) + 4 * al(cap_d * zd) + al(4096 * zd) + al(tc_bytes);
   if (!arena.ensure(total, stream)) return false;
   char* p = (char*)arena.p;
   slot.assign(nslots, nullptr);
@@ -130,12 +131,51 @@ bool SweepWork::reserve(size_t el, size_t ct, size_t cs, size_t cx, size_t sb, s
   dQ = (double2*)p; p += al(cap_d * zd);
   dR = (double2*)p; p += al(cap_d * zd);
   dtau = (double2*)p; p += al(4096 * zd);
+  tc = tc_bytes ? (void*)p : nullptr;
+  p += al(tc_bytes);
   return true;
 }
 
 // ---------------------------------------------------------------- engine
 
+void Engine::drop_graphs() {
+  for (auto& g : graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = IterGraph();
+  }
+}
+
+// FNV-1a over everything a captured iteration bakes in: job tensors and
+// shapes, destination buffers and the workspace arenas.
+unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int nstreams) const {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xff;
+      h *= 1099511628211ull;
+    }
+  };
+  auto mixs = [&](const TShape& t) { mix((unsigned long long)t.l); mix((unsigned long long)t.p); mix((unsigned long long)t.r); };
+  mix((unsigned long long)precision);
+  mix((unsigned long long)chi);
+  mix((unsigned long long)power_iters);
+  mix((unsigned long long)nstreams);
+  mix((unsigned long long)(uintptr_t)dist_dev.p);
+  for (int i = 0; i < nstreams; ++i) mix((unsigned long long)(uintptr_t)pool[i]->arena.p);
+  for (const SweepJob& j : jobs) {
+    mix((unsigned long long)(uintptr_t)j.plan);
+    for (const void* p : j.node_tensor) mix((unsigned long long)(uintptr_t)p);
+    for (const TShape& t : j.node_shape) mixs(t);
+    for (const void* p : j.start) mix((unsigned long long)(uintptr_t)p);
+    for (const TShape& t : j.start_shape) mixs(t);
+    for (const void* p : j.dest) mix((unsigned long long)(uintptr_t)p);
+    for (const TShape& t : j.tr.final_mps) mixs(t);
+  }
+  return h;
+}
+
 Engine::~Engine() {
+  drop_graphs();
   for (SweepWork* w : pool) {
     if (w->stream) cudaStreamSynchronize(w->stream);
     w->arena.release();
@@ -170,6 +210,10 @@ int Engine::create(int lattice, int Lx, int Ly, int periodic, int d_, int D_, co
   geom.lat.periodic = periodic != 0;
   const int n = geom.lat.n_sites();
   const size_t per = (size_t)d * D * D * D * D;
+  {
+    cudaError_t ae = init_kernel_attributes();
+    if (ae != cudaSuccess) return fail(this, 3, std::string("kernel attributes: ") + cudaGetErrorString(ae));
+  }
   if (!t_dev.ensure(sizeof(double2) * per * n, s)) return fail(this, 2, "device allocation of site tensors failed");
   CK(cudaMemcpyAsync(t_dev.p, host_t, sizeof(double2) * per * n, cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
@@ -251,7 +295,7 @@ int Engine::init_messages_t(const double* edge_mats) {
   std::vector<C> host;
   SweepWork* w = work(0);
   if (!w) return fail(this, 3, "stream creation failed");
-  if (!w->reserve(sizeof(C), 16, 16, 16, 4096, 4, 16)) return fail(this, 2, "work allocation failed");
+  if (!w->reserve(sizeof(C), 16, 16, 16, 4096, 4, 16, 0)) return fail(this, 2, "work allocation failed");
   for (auto& kv : msgs) {
     Message& m = kv.second;
     const Block& b = geom.blocks[kv.first.first];
@@ -423,6 +467,9 @@ void Engine::job_needs(const SweepJob& job, size_t need[7]) const {
   need[3] = std::max<size_t>(need[3], precision == 0 ? svd_work_bytes(mr, mc) : svd_work_bound_c64(mr, mc, chi));
   need[4] = std::max<size_t>(need[4], (size_t)tr.max_len + 6);
   need[5] = std::max<size_t>(need[5], (size_t)4 * chi * chi * D * D + 64);
+  if (tc_mode && precision != 0)
+    for (const auto& st : tr.steps)
+      need[6] = std::max<size_t>(need[6], tc_absorb_bytes(tc_mode == 2, st.P, st.Q, st.l, st.r));
 }
 
 int Engine::reserve_workers(const std::vector<SweepJob>& jobs, int nstreams) {
@@ -431,11 +478,11 @@ int Engine::reserve_workers(const std::vector<SweepJob>& jobs, int nstreams) {
     for (size_t j = i; j < jobs.size(); j += nstreams) job_needs(jobs[j], need);
     SweepWork& w = *pool[i];
     if (w.elem == elem() && need[0] <= w.cap_t && need[1] <= w.cap_seg && need[2] <= w.cap_x &&
-        need[3] <= w.svd_bytes && need[4] <= w.nslots && need[5] <= w.cap_d && w.arena.p)
+        need[3] <= w.svd_bytes && need[4] <= w.nslots && need[5] <= w.cap_d && need[6] <= w.tc_bytes && w.arena.p)
       continue;
     CK(cudaStreamSynchronize(w.stream));
     CK(cudaStreamSynchronize(stream));
-    if (!w.reserve(elem(), need[0], need[1], need[2], need[3], need[4], need[5]))
+    if (!w.reserve(elem(), need[0], need[1], need[2], need[3], need[4], need[5], need[6]))
       return fail(this, 2, "sweep workspace allocation failed");
   }
   return 0;
@@ -450,7 +497,7 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
     size_t need[7] = {1, 1, 1, 256, 4, 16, 0};
     job_needs(job, need);
     if (w.elem != sizeof(C) || need[0] > w.cap_t || need[1] > w.cap_seg || need[2] > w.cap_x ||
-        need[3] > w.svd_bytes || need[4] > w.nslots || need[5] > w.cap_d)
+        need[3] > w.svd_bytes || need[4] > w.nslots || need[5] > w.cap_d || need[6] > w.tc_bytes)
       return fail(this, 8, "sweep workspace was not reserved");
   }
   const C one = one_of<C>(), zero = zero_of<C>();
@@ -471,7 +518,7 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
   long long launches = 0;
 
   CK(cudaMemsetAsync(w.logscale, 0, sizeof(double), s));
-  CK(cudaMemsetAsync(w.status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(w.status, 0, 2 * sizeof(int), s));
   pos.push_back(take());
   sh.push_back(TShape{1, 1, 1});
   CK(launch_fill(slot(pos.back()), 1, 1.0, 0.0, s));
@@ -572,8 +619,14 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
       ++launches;
     }
     const int Q = rec.Q;
-    CK(launch_zgemm('T', 'N', Q, r, (int)P, one, X, Q, 0, Sp, r, P * r, zero, Rb[0], r, (long long)Q * r, l, s));
-    ++launches;
+    if (tc_mode && sizeof(C) == sizeof(float2)) {
+      // split TF32 / BF16 on the tensor cores, FP32 accumulation
+      CK(launch_tc_absorb(tc_mode == 2, X, (int)P, Q, Sp, l, r, Rb[0], w.tc, w.status + 1, s));
+      launches += 6;
+    } else {
+      CK(launch_zgemm('T', 'N', Q, r, (int)P, one, X, Q, 0, Sp, r, P * r, zero, Rb[0], r, (long long)Q * r, l, s));
+      ++launches;
+    }
     sweep_flops += 8.0 * (double)l * (double)P * (double)Q * (double)r;
     std::vector<int> newpos;
     std::vector<TShape> newsh;
@@ -685,14 +738,16 @@ int Engine::iterate_t(double tol, int max_iter, int* iters, double* err_out) {
     if (err_out) *err_out = 0.0;
     return 0;
   }
-  if (!dist_dev.ensure(sizeof(double) * nu + 256, stream)) return fail(this, 2, "allocation failed");
-  const int nstreams = std::min(nu, 16);
+  // per update: distance (double) and the SVD status of its sweep (int)
+  if (!dist_dev.ensure(sizeof(double) * nu + 2 * sizeof(int) * nu + 256, stream)) return fail(this, 2, "allocation failed");
+  int* status_dev = (int*)((double*)dist_dev.p + nu);
+  const int nstreams = std::max(1, std::min(nu, max_streams));
   for (int i = 0; i < nstreams; ++i)
     if (!work(i)) return fail(this, 3, "stream creation failed");
   cudaEvent_t fork;
   CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
   std::vector<double> hd(nu);
-  std::vector<int> hs(nstreams);
+  std::vector<int> hs(2 * nu);
   double err = INFINITY;
   int it = 0;
   int rc = 0;
@@ -708,31 +763,74 @@ int Engine::iterate_t(double tol, int max_iter, int* iters, double* err_out) {
       for (const TShape& t : jobs[u].tr.final_mps)
         if ((size_t)t.size() > dst.cap) { rc = fail(this, 8, "message tensor exceeds its buffer"); break; }
     }
-    if (!rc) rc = reserve_workers(jobs, nstreams);
-    if (!rc) {
-      CK(cudaEventRecord(fork, stream));
-      for (int i = 0; i < nstreams; ++i) CK(cudaStreamWaitEvent(pool[i]->stream, fork, 0));
-    }
+    // destinations and their shapes (host bookkeeping, also when replaying)
+    int parity = 0;
     for (int u = 0; u < nu && !rc; ++u) {
-      SweepWork& w = *pool[u % nstreams];
       const auto& up = ups[u];
       Message& dst = msgs.at({up.recv_block, up.recv_face});
       const int nxt = 1 - dst.cur;
+      parity = nxt;
       jobs[u].dest.clear();
       for (int q = 0; q < dst.k(); ++q) jobs[u].dest.push_back(dst.tensor<C>(nxt, q));
       dst.sh[nxt] = jobs[u].tr.final_mps;
-      if ((rc = run_sweep<C>(jobs[u], w))) break;
-      if ((rc = finalize_message<C>(dst, nxt, w, w.stream, (double*)dist_dev.p + u, true))) break;
+    }
+    if (!rc) rc = reserve_workers(jobs, nstreams);
+    // the whole iteration: fork onto the worker streams, one sweep and one
+    // finalisation per update, join
+    auto enqueue = [&]() -> int {
+      CK(cudaEventRecord(fork, stream));
+      for (int i = 0; i < nstreams; ++i) CK(cudaStreamWaitEvent(pool[i]->stream, fork, 0));
+      int e = 0;
+      for (int u = 0; u < nu && !e; ++u) {
+        SweepWork& w = *pool[u % nstreams];
+        const auto& up = ups[u];
+        Message& dst = msgs.at({up.recv_block, up.recv_face});
+        if ((e = run_sweep<C>(jobs[u], w))) break;
+        if ((e = finalize_message<C>(dst, 1 - dst.cur, w, w.stream, (double*)dist_dev.p + u, true))) break;
+        CK(cudaMemcpyAsync(status_dev + 2 * u, w.status, 2 * sizeof(int), cudaMemcpyDeviceToDevice, w.stream));
+      }
+      for (int i = 0; i < nstreams; ++i) {
+        CK(cudaEventRecord(pool[i]->done, pool[i]->stream));
+        CK(cudaStreamWaitEvent(stream, pool[i]->done, 0));
+      }
+      return e;
+    };
+    if (!rc && !use_graphs) {
+      rc = enqueue();
+    } else if (!rc) {
+      IterGraph& g = graphs[parity];
+      const unsigned long long sig = iter_signature(jobs, nstreams);
+      if (!g.exec || g.sig != sig) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = IterGraph();
+        CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue();
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(stream, &graph);
+        if (!rc && ce != cudaSuccess) rc = fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
+        if (!rc) {
+          ce = cudaGraphInstantiate(&g.exec, graph, 0);
+          if (ce != cudaSuccess) rc = fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (!rc) {
+          g.sig = sig;
+          g.launches = sweep_launches;
+          g.flops = sweep_flops;
+        } else {
+          g = IterGraph();
+        }
+      }
+      if (!rc) {
+        CK(cudaGraphLaunch(g.exec, stream));
+        sweep_launches = g.launches;
+        sweep_flops = g.flops;
+      }
     }
     for (DBuf* b : tmp) delete b;
-    for (int i = 0; i < nstreams; ++i) {
-      CK(cudaEventRecord(pool[i]->done, pool[i]->stream));
-      CK(cudaStreamWaitEvent(stream, pool[i]->done, 0));
-    }
     if (rc) break;
     CK(cudaMemcpyAsync(hd.data(), dist_dev.p, sizeof(double) * nu, cudaMemcpyDeviceToHost, stream));
-    for (int i = 0; i < nstreams; ++i)
-      CK(cudaMemcpyAsync(&hs[i], pool[i]->status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(hs.data(), status_dev, 2 * sizeof(int) * nu, cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
     err = 0.0;
     bool nonfinite = false, sweep_limit = false;
@@ -740,11 +838,20 @@ int Engine::iterate_t(double tol, int max_iter, int* iters, double* err_out) {
       if (!std::isfinite(hd[u])) nonfinite = true;
       err = std::max(err, hd[u]);
     }
-    for (int i = 0; i < nstreams; ++i) sweep_limit = sweep_limit || hs[i] != 0;
+    bool tc_timeout = false;
+    for (int u = 0; u < nu; ++u) {
+      sweep_limit = sweep_limit || hs[2 * u] != 0;
+      tc_timeout = tc_timeout || hs[2 * u + 1] != 0;
+    }
     for (const auto& up : ups) msgs.at({up.recv_block, up.recv_face}).cur ^= 1;
     launches_per_iter = sweep_launches;
     flops_per_iter = sweep_flops;
     ++n_iterations;
+    if (tc_timeout) {
+      rc = fail(this, 7, "a tensor-core pipeline wait timed out");
+      ++it;
+      break;
+    }
     if (nonfinite || sweep_limit) {
       rc = fail(this, 5, nonfinite ? "a message became non-finite" : "a Jacobi SVD reached its sweep limit");
       ++it;
@@ -957,7 +1064,7 @@ int Engine::log_norm_t(double* out) {
   double total = 0.0;
   for (size_t b = 0; b < Cc.size(); ++b) total += ls[b] + 0.5 * std::log(re[b] * re[b] + im[b] * im[b]);
   SweepWork* w = work(0);
-  if (!w || !w->reserve(sizeof(C), 16, 16, 16, 4096, 4, 16)) return fail(this, 2, "allocation failed");
+  if (!w || !w->reserve(sizeof(C), 16, 16, 16, 4096, 4, 16, 0)) return fail(this, 2, "allocation failed");
   std::vector<std::pair<std::pair<int, int>, std::pair<int, int>>> pairs;
   for (const auto& u : geom.updates()) {
     auto a = std::make_pair(u.block, u.face), r = std::make_pair(u.recv_block, u.recv_face);

@@ -55,19 +55,21 @@ struct SweepWork {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   DBuf arena;
-  size_t elem = 0, cap_t = 0, cap_seg = 0, cap_x = 0, svd_bytes = 0, nslots = 0, cap_d = 0;
+  size_t elem = 0, cap_t = 0, cap_seg = 0, cap_x = 0, svd_bytes = 0, nslots = 0, cap_d = 0, tc_bytes = 0;
   std::vector<void*> slot;
   void *S[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
   void *qrA = nullptr, *qrQ = nullptr, *qrR = nullptr, *tau = nullptr, *X = nullptr;
   void* svd = nullptr;
+  void* tc = nullptr;                  // tensor-core absorb scratch (packed operands, FP32 product)
   double* logscale = nullptr;
-  int* status = nullptr;
+  int* status = nullptr;               // [0] SVD sweep limit, [1] tensor-core pipeline timeout
   double2* scal = nullptr;             // scalar outputs (mps_dot)
   void** ptrs = nullptr;               // device pointer tables (K4, dot)
   int* ints = nullptr;                 // device shape tables
   double2* k4 = nullptr;               // K4 scratch (complex128)
   double2 *dX0 = nullptr, *dX1 = nullptr, *dQ = nullptr, *dR = nullptr, *dtau = nullptr;   // distance (complex128)
-  bool reserve(size_t elem, size_t cap_t, size_t cap_seg, size_t cap_x, size_t svd_bytes, size_t nslots, size_t cap_d);
+  bool reserve(size_t elem, size_t cap_t, size_t cap_seg, size_t cap_x, size_t svd_bytes, size_t nslots, size_t cap_d,
+               size_t tc_bytes);
 };
 
 struct SweepJob {
@@ -86,6 +88,9 @@ class Engine {
  public:
   Geometry geom;
   int d = 2, D = 2, chi = 8, precision = 0, power_iters = 3;
+  int tc_mode = 0;                     // absorb contraction: 0 SIMT GEMM, 1 tcgen05 TF32 split, 2 tcgen05 BF16 split
+  bool use_graphs = true;              // replay a captured CUDA graph per iteration
+  int max_streams = 16;                // sweep jobs run on up to this many streams
   cudaStream_t stream = nullptr;
   bool partitioned = false;
   std::string last_error;
@@ -135,6 +140,21 @@ class Engine {
   template <typename C> int log_norm_t(double* out);
   template <typename C> int get_message_t(int block, int face, int* k, int* shapes, double* data, size_t cap);
   void job_needs(const SweepJob& job, size_t need[7]) const;
+  // one captured iteration per message-buffer parity, valid while the
+  // signature (shapes and device pointers of every job) is unchanged
+  struct IterGraph {
+    unsigned long long sig = 0;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    double flops = 0.0;
+  };
+  IterGraph graphs[2];
+
+ public:
+  void drop_graphs();
+
+ private:
+  unsigned long long iter_signature(const std::vector<SweepJob>& jobs, int nstreams) const;
   long long sweep_launches = 0;
   double sweep_flops = 0.0;
 };

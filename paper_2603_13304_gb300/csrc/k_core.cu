@@ -1174,4 +1174,16 @@ cudaError_t launch_mps_dot(const ChainDesc& a, const ChainDesc& b, bool c64, dou
   return cudaGetLastError();
 }
 
+// Large-shared-memory opt-ins of every staged kernel on the current device
+// (done once up front so that no attribute call falls inside a stream capture).
+cudaError_t init_kernel_attributes() {
+  cudaError_t e;
+  if ((e = smem_optin<k_qr_smem<double2>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_qr_smem<float2>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_jacobi_smem<double2>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_jacobi_smem<float2>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_orth_smem>()) != cudaSuccess) return e;
+  return init_tc_attributes();
+}
+
 }  // namespace bbp

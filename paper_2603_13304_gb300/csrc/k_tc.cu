@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -254,15 +255,27 @@ bool make_map(CUtensorMap* m, const void* ptr, bool bf16, int rows, int cols, lo
   return r == CUDA_SUCCESS;
 }
 
+template <int BN> constexpr int tc_smem() { return kStages * (kBM + BN) * 128 + 1024; }
+
+// Dynamic shared memory opt-in, once per kernel and device.
+template <bool kBF16, int BN>
+cudaError_t tc_optin() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_tc_gemm<kBF16, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<BN>());
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 template <bool kBF16, int BN>
 cudaError_t tc_launch(const void* A, long long lda, const void* Bt, long long ldb, float* C, long long ldc, int M, int N,
                       int K, float alpha, int* err, cudaStream_t s) {
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  constexpr int smem = kStages * (kBM + BN) * 128 + 1024;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_tc_gemm<kBF16, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  });
+  constexpr int smem = tc_smem<BN>();
+  cudaError_t attr_err = tc_optin<kBF16, BN>();
   if (attr_err != cudaSuccess) return attr_err;
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, kBF16, M, K, lda, kBM) || !make_map(&tb, Bt, kBF16, N, K, ldb, BN))
@@ -404,6 +417,14 @@ int grid_of(long long n) {
 }  // namespace
 
 // ------------------------------------------------------------------ public
+
+cudaError_t init_tc_attributes() {
+  cudaError_t e;
+  if ((e = tc_optin<false, 64>()) != cudaSuccess) return e;
+  if ((e = tc_optin<false, 128>()) != cudaSuccess) return e;
+  if ((e = tc_optin<true, 64>()) != cudaSuccess) return e;
+  return tc_optin<true, 128>();
+}
 
 cudaError_t launch_tc_gemm(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
                            long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s) {

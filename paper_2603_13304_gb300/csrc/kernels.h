@@ -29,6 +29,11 @@ cudaError_t launch_zgemm(char opA, char opB, int M, int N, int K, float2 alpha, 
                          long long strideA, const float2* B, int ldb, long long strideB, float2 beta, float2* C,
                          int ldc, long long strideC, int batch, cudaStream_t s);
 
+// Opt-in of large dynamic shared memory for every staged kernel on the
+// current device; call once before any stream capture.
+cudaError_t init_kernel_attributes();
+cudaError_t init_tc_attributes();
+
 // Householder QR of A (m x n, row-major, overwritten): Q (m x k), R (k x n),
 // k = min(m, n).  tau: k complex scratch.  One CTA per matrix.
 cudaError_t launch_qr(double2* A, int m, int n, double2* Q, double2* R, double2* tau, cudaStream_t s);
