@@ -98,38 +98,31 @@ class ClockSampler:
 
 # -------------------------------------------------------------- our engine
 
-def svd_roofline(P, torch, m=512, n=512, chi=32, reps=3):
-    """Time the dominant kernel (FP64 one-sided Jacobi truncated SVD at the
-    workload's bulk shape) with CUDA events; count its flops from the sweeps
-    and rotations it reports."""
-    import numpy as np
-    rng = np.random.default_rng(0)
-    k = min(m, n)
-    U, _ = np.linalg.qr(rng.standard_normal((m, k)) + 1j * rng.standard_normal((m, k)))
-    V, _ = np.linalg.qr(rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k)))
-    s = np.sort(0.9 ** np.arange(k) * (1 + 0.1 * rng.random(k)))[::-1]
-    Z = torch.from_numpy((U * s) @ V.conj().T).cuda()
-    Ud = torch.zeros(m * chi, dtype=torch.complex128, device="cuda")
-    Rd = torch.zeros(chi * n, dtype=torch.complex128, device="cuda")
-    work = torch.zeros(P.bbp_k_svd_work_bytes(m, n) // 16 + 16, dtype=torch.complex128, device="cuda")
-    st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    stream = torch.cuda.current_stream()
-    P.bbp_k_svd_trunc(Z, m, n, chi, Ud, Rd, work, st)          # warm-up
-    torch.cuda.synchronize()
-    times, flops = [], []
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        P.bbp_k_svd_trunc(Z, m, n, chi, Ud, Rd, work, st)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) * 1e-3)
-        sweeps, rot = P.bbp_k_svd_stats(work, m, n)
-        M, N = min(m, n), max(m, n)
-        flops.append(sweeps * (M * (M - 1) / 2) * 16.0 * N + rot * 18.0 * (N + M))
-    t = statistics.mean(times)
-    f = statistics.mean(flops)
-    return {"kernel": "k_jacobi (FP64 one-sided Jacobi SVD, 512 x 512, chi 32)", "seconds": t, "flops": f}
+# Roofline of the dominant kernel class, timed live inside the timed region
+# with CUDA events on the streams its launches run on (library-side timer).
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 ALU
+# peak: 152 SMs x 2 FP64 FMA x 2 x 2.07 GHz; tensor peaks from the measured
+# BF16 burst figure (TF32 at half the BF16 rate).
+KERNELS = {
+    "jacobi": (1, "one-sided Jacobi SVD of the reduced matrix (k_jacobi_smem / k_jacobi)"),
+    "orth": (2, "range orthonormalisation, Householder in shared memory (k_orth_smem)"),
+    "qr": (3, "Householder QR of the canonical moves (k_qr_smem / k_qr)"),
+    "tc": (4, "tcgen05 split-precision absorb GEMM (k_tc_gemm)"),
+    "absorb": (5, "SIMT complex absorb GEMM (k_gemm)"),
+}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16 = 1911.2
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        bf16 = float(mp.get("bf16_tflops", bf16))
+    except (OSError, ValueError):
+        pass
+    return {"fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "fp64": 152 * 2 * 2 * 2.07e9 / 1e12, "bf16": bf16,
+            "tf32": bf16 / 2}
 
 
 def run_ours(args, rank, world):
@@ -144,19 +137,32 @@ def run_ours(args, rank, world):
     w = WORKLOAD
     t, em = make_inputs(w)
     stream = torch.cuda.current_stream()
-    prec = P.FP32 if args.precision == "fp32" else P.FP64
+    prec = {"tf32": P.TF32, "bf16": P.BF16, "fp32": P.FP32, "fp64": P.FP64}[args.precision]
 
     def setup():
         ctx = P.bbp_create_peps(P.KAGOME, w["Lx"], w["Ly"], 1, w["d"], w["D"], t)
         P.bbp_partition_blocks(ctx, w["L"], w["L"])
         P.bbp_set_options(ctx, w["chi"], prec)
+        P.bbp_set_execution(ctx, not args.no_graphs, 16)
         P.bbp_init_messages(ctx, em)
         return ctx
 
+    cls, kdesc = KERNELS[args.roofline_kernel]
+    P.bbp_ktimer_select(cls)              # before the first capture: the graphs carry the events
     ctx = setup()
     _, n_updates, n_sites = P.bbp_info(ctx)
+    # settle: from the bond-1 initial messages the bond dimensions grow for a
+    # few iterations; iterate until the work per iteration stops changing
+    prev = None
+    for _ in range(12):
+        P.bbp_iterate(ctx, 0.0, 1)
+        cur = P.bbp_stats(ctx)
+        if cur == prev:
+            break
+        prev = cur
     for _ in range(args.warmup):
         P.bbp_iterate(ctx, 0.0, 1)
+    P.bbp_ktimer_read()                   # discard the warm-up launches
     # L2 flush buffer (larger than the 126 MB L2), rewritten between timed steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     if world > 1:
@@ -176,6 +182,8 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         host_secs = time.perf_counter() - h0
     secs = e0.elapsed_time(e1) * 1e-3
+    k_n, k_ms, k_flops = P.bbp_ktimer_read()
+    P.bbp_ktimer_select(0)
     launches, flops_iter = P.bbp_stats(ctx)
     if world > 1:
         import torch.distributed as dist
@@ -189,13 +197,14 @@ def run_ours(args, rank, world):
     # end to end through the C ABI with host buffers: upload, iterate, read back
     tp = torch.from_numpy(np.ascontiguousarray(t)).pin_memory()
     ep = torch.from_numpy(np.ascontiguousarray(em)).pin_memory()
+    n_e2e = args.warmup + args.steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx = P.bbp_create_peps(P.KAGOME, w["Lx"], w["Ly"], 1, w["d"], w["D"], tp.numpy())
     P.bbp_partition_blocks(ctx, w["L"], w["L"])
     P.bbp_set_options(ctx, w["chi"], prec)
     P.bbp_init_messages(ctx, ep.numpy())
-    P.bbp_iterate(ctx, 0.0, args.steps)
+    P.bbp_iterate(ctx, 0.0, n_e2e)
     d2h = 0
     for b in range(3):
         for f in range(4):
@@ -204,16 +213,23 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     e2e_secs = time.perf_counter() - t0
     P.bbp_destroy(ctx)
-    e2e = {"value": n_updates * args.steps / e2e_secs, "unit": "message updates/s",
-           "h2d_bytes_per_step": (t.nbytes + em.nbytes) / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+    e2e = {"value": n_updates * n_e2e / e2e_secs, "unit": "message updates/s",
+           "h2d_bytes_per_step": (t.nbytes + em.nbytes) / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
+           "iterations": n_e2e, "note": "create, upload, init, all iterations from the initial messages, read back"}
 
     roof = None
-    if rank == 0:
-        r = svd_roofline(P, torch)
-        achieved = r["flops"] / r["seconds"] / 1e12
-        peak = 152 * 2 * 2 * 2.07e9 / 1e12     # FP64 FMA units x clock
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": r["kernel"], "launch_s": r["seconds"]}
+    if rank == 0 and k_n > 0:
+        pk = peaks()
+        bound, unit = ("tensor", "TFLOP/s") if args.roofline_kernel == "tc" else ("alu", "TFLOP/s")
+        key = {"tc": args.precision if args.precision in ("tf32", "bf16") else "tf32"}.get(
+            args.roofline_kernel, "fp64" if args.precision == "fp64" else "fp32")
+        per_launch_s = k_ms * 1e-3 / k_n
+        achieved = k_flops / k_n / per_launch_s / 1e12
+        roof = {"bound": bound, "achieved": achieved, "peak": pk[key], "unit": unit, "frac": achieved / pk[key],
+                "traffic": None, "kernel": kdesc, "peak_kind": key + (" tensor, measured bf16 burst" if bound == "tensor"
+                                                                      else " ALU, unit counts x 2.07 GHz"),
+                "launches_per_step": k_n / args.steps, "launch_us": per_launch_s * 1e6,
+                "share_of_step": k_ms * 1e-3 / secs}
     return {
         "value": value, "secs": secs, "host_secs": host_secs, "n_updates": n_updates, "n_sites": n_sites, "energy": energy,
         "clocks": clk.summary(), "launches": launches, "flops_iter": flops_iter, "e2e": e2e, "roofline": roof,
@@ -222,10 +238,11 @@ def run_ours(args, rank, world):
 
 # ---------------------------------------------------------------- oracle
 
-def oracle_sample(w, n_updates_sample: int):
-    """Time the FP64 oracle on a bounded sample: the first iteration's first
-    message updates (bond-1 inputs), then the same updates with full-bond
-    inputs after one iteration.  Returns updates/s over the timed updates."""
+def oracle_sample(w, iterations: int):
+    """Time the FP64 oracle on a bounded sample of the workload: after one
+    untimed iteration from the initial messages (so that every input has
+    full bond), `iterations` full synchronous iterations (all message updates
+    each).  Returns (updates/s, seconds, updates)."""
     from oracle.blockbp import BlockBP
     from oracle.geometry import Geometry
     t, em = make_inputs(w)
@@ -233,12 +250,13 @@ def oracle_sample(w, n_updates_sample: int):
     bb = BlockBP(geom, t, chi=w["chi"])
     bb.init_messages(em)
     bb.step()                                # full-bond messages
-    ups = geom.updates()[:n_updates_sample]
+    n = 0
     t0 = time.perf_counter()
-    for (bid, face, _) in ups:
-        bb.update_message(bid, face)
+    for _ in range(iterations):
+        bb.step()
+        n += len(geom.updates())
     dt = time.perf_counter() - t0
-    return len(ups) / dt, dt
+    return n / dt, dt, n
 
 
 def blas_threads():
@@ -255,7 +273,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16", "fp32", "fp64"])
+    ap.add_argument("--roofline-kernel", default="jacobi", choices=sorted(KERNELS))
+    ap.add_argument("--no-graphs", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -267,16 +287,14 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        per_step = []
         for _ in range(args.warmup):
-            oracle_sample(w, 2)
+            oracle_sample(w, 1)
         t_all = 0.0
         n_all = 0
         for _ in range(args.steps):
-            v, dt = oracle_sample(w, 2)
-            per_step.append(v)
+            _, dt, n = oracle_sample(w, 1)
             t_all += dt
-            n_all += 2
+            n_all += n
         value = n_all / t_all
         cores = blas_threads()
         line = {"metric": "BlockBP message updates/s", "value": value, "unit": "message updates/s", "n_gpus": 0,
@@ -284,7 +302,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                 "data": "synthetic", "config": config, "impl": "reference",
                 "cpu_baseline": {"value": value, "unit": "message updates/s", "cores": cores, "kind": "oracle",
-                                 "sample": "2 message updates (full-bond inputs) of the workload per step"},
+                                 "sample": "one full BlockBP iteration (12 message updates, full-bond inputs) per step"},
                 "e2e": {"value": value, "unit": "message updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -301,16 +319,18 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt = oracle_sample(w, 2)
+        v, dt, n = oracle_sample(w, 3)
         cpu = {"value": v, "unit": "message updates/s", "cores": blas_threads(), "kind": "oracle",
-               "sample": f"2 message updates with full-bond inputs ({dt:.1f} s of CPU work)"}
+               "sample": f"3 full iterations ({n} message updates, full-bond inputs; {dt:.1f} s of CPU work)"}
     line = {
         "metric": "BlockBP message updates/s", "value": res["value"], "unit": "message updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * res["secs"] / args.steps, "host_ms_per_step": 1e3 * res["host_secs"] / args.steps,
         "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64+f64" if args.precision == "fp32" else "c128", "data": "synthetic",
-        "config": dict(config, precision=args.precision),
+        "vs_baseline": None, "dtype": {"fp64": "c128", "fp32": "c64+f64", "tf32": "tf32x3+c64+f64", "bf16": "bf16x3+c64+f64"}[args.precision], "data": "synthetic",
+        "config": dict(config, precision=args.precision,
+                       execution="eager launches" if args.no_graphs else "CUDA-graph replay of each iteration",
+                       streams=16),
         "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["launches"] * args.steps,
         "roofline": res["roofline"], "cpu_baseline": cpu,
         "energy_per_site": res["energy"], "absorb_tflop_per_step": res["flops_iter"] / 1e12,

@@ -355,6 +355,14 @@ bbp_status bbp_k_svd_stats(const void* work, int m, int n, int* sweeps, long lon
   return cuda_status(bbp::svd_stats(work, m, n, sweeps, rotations, (cudaStream_t)stream));
 }
 
+void bbp_ktimer_select(int kernel_class) { bbp::ktimer_select(kernel_class); }
+
+bbp_status bbp_ktimer_read(long long* launches, double* ms, double* flops) {
+  if (!launches || !ms || !flops) return set_err(BBP_ERR_ARG, "bad arguments");
+  bbp::ktimer_read(launches, ms, flops);
+  return BBP_OK;
+}
+
 bbp_status bbp_k_tc_gemm(int bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C, long long ldc,
                          int M, int N, int K, float alpha, int* err, void* stream) {
   if (!A || !Bt || !C || !err || M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N)

@@ -139,9 +139,10 @@ bool SweepWork::reserve(size_t el, size_t ct, size_t cs, size_t cx, size_t sb, s
 // ---------------------------------------------------------------- engine
 
 void Engine::drop_graphs() {
-  for (auto& g : graphs) {
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    g = IterGraph();
+  for (int p = 0; p < 2; ++p) {
+    if (graphs[p].exec) cudaGraphExecDestroy(graphs[p].exec);
+    graphs[p] = IterGraph();
+    ktimer_drop_tag(graph_tag(p));
   }
 }
 
@@ -176,6 +177,12 @@ unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int
 
 Engine::~Engine() {
   drop_graphs();
+  if (root) {
+    cudaStreamSynchronize(root);
+    cudaStreamDestroy(root);
+  }
+  if (root_in) cudaEventDestroy(root_in);
+  if (root_out) cudaEventDestroy(root_out);
   for (SweepWork* w : pool) {
     if (w->stream) cudaStreamSynchronize(w->stream);
     w->arena.release();
@@ -374,7 +381,6 @@ int Engine::finalize_message(Message& m, int which, SweepWork& w, cudaStream_t s
   C* X1 = (C*)w.dX1;
   C* Qd = (C*)w.dQ;
   C* Rd = (C*)w.dR;
-  C* td = (C*)w.dtau;
   int kprev = 0;
   for (int q = 0; q < k; ++q) {
     const TShape& a = m.sh[which][q];
@@ -391,7 +397,7 @@ int Engine::finalize_message(Message& m, int which, SweepWork& w, cudaStream_t s
       rows = kprev;
     }
     const int mrows = rows * p;
-    CK(launch_qr(X, mrows, Rr, Qd, Rd, td, s));
+    CK(launch_qr_r(X, mrows, Rr, Rd, Qd, X == X1 ? X0 : X1, s));
     kprev = std::min(mrows, Rr);
     sweep_launches += 3;
   }
@@ -624,6 +630,7 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
       CK(launch_tc_absorb(tc_mode == 2, X, (int)P, Q, Sp, l, r, Rb[0], w.tc, w.status + 1, s));
       launches += 6;
     } else {
+      KTimerScope timer(KC_ABSORB, s, 8.0 * l * (double)P * Q * r);
       CK(launch_zgemm('T', 'N', Q, r, (int)P, one, X, Q, 0, Sp, r, P * r, zero, Rb[0], r, (long long)Q * r, l, s));
       ++launches;
     }
@@ -798,33 +805,60 @@ int Engine::iterate_t(double tol, int max_iter, int* iters, double* err_out) {
     if (!rc && !use_graphs) {
       rc = enqueue();
     } else if (!rc) {
-      IterGraph& g = graphs[parity];
-      const unsigned long long sig = iter_signature(jobs, nstreams);
-      if (!g.exec || g.sig != sig) {
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-        g = IterGraph();
-        CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue();
-        cudaGraph_t graph = nullptr;
-        cudaError_t ce = cudaStreamEndCapture(stream, &graph);
-        if (!rc && ce != cudaSuccess) rc = fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
-        if (!rc) {
-          ce = cudaGraphInstantiate(&g.exec, graph, 0);
-          if (ce != cudaSuccess) rc = fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
-        }
-        if (graph) cudaGraphDestroy(graph);
-        if (!rc) {
+      // capture and replay on a private non-blocking root stream, ordered
+      // after the caller's stream and before whatever the caller enqueues next
+      if (!root) {
+        CK(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&root_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&root_out, cudaEventDisableTiming));
+      }
+      CK(cudaEventRecord(root_in, stream));
+      CK(cudaStreamWaitEvent(root, root_in, 0));
+      const cudaStream_t user = stream;
+      stream = root;
+      auto replay = [&]() -> int {
+        IterGraph& g = graphs[parity];
+        const unsigned long long sig = iter_signature(jobs, nstreams);
+        if (!g.exec || g.sig != sig) {
+          if (g.exec) cudaGraphExecDestroy(g.exec);
+          g = IterGraph();
+          const long long tag = graph_tag(parity);
+          ktimer_drop_tag(tag);
+          ktimer_set_tag(tag);
+          cudaError_t ce = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+          if (ce != cudaSuccess) {
+            ktimer_set_tag(-1);
+            return fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
+          }
+          int e = enqueue();
+          cudaGraph_t graph = nullptr;
+          ce = cudaStreamEndCapture(stream, &graph);
+          ktimer_set_tag(-1);
+          if (!e && ce != cudaSuccess) e = fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
+          if (!e) {
+            ce = cudaGraphInstantiate(&g.exec, graph, 0);
+            if (ce != cudaSuccess) e = fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
+          }
+          if (graph) cudaGraphDestroy(graph);
+          if (e) {
+            g = IterGraph();
+            return e;
+          }
           g.sig = sig;
           g.launches = sweep_launches;
           g.flops = sweep_flops;
-        } else {
-          g = IterGraph();
         }
-      }
-      if (!rc) {
-        CK(cudaGraphLaunch(g.exec, stream));
+        cudaError_t le = cudaGraphLaunch(g.exec, stream);
+        if (le != cudaSuccess) return fail(this, 3, std::string("graph launch: ") + cudaGetErrorString(le));
         sweep_launches = g.launches;
         sweep_flops = g.flops;
+        return 0;
+      };
+      rc = replay();
+      stream = user;
+      if (!rc) {
+        CK(cudaEventRecord(root_out, root));
+        CK(cudaStreamWaitEvent(stream, root_out, 0));
       }
     }
     for (DBuf* b : tmp) delete b;
@@ -832,6 +866,7 @@ int Engine::iterate_t(double tol, int max_iter, int* iters, double* err_out) {
     CK(cudaMemcpyAsync(hd.data(), dist_dev.p, sizeof(double) * nu, cudaMemcpyDeviceToHost, stream));
     CK(cudaMemcpyAsync(hs.data(), status_dev, 2 * sizeof(int) * nu, cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    if (ktimer_class()) ktimer_collect(use_graphs ? graph_tag(parity) : -1);
     err = 0.0;
     bool nonfinite = false, sweep_limit = false;
     for (int u = 0; u < nu; ++u) {

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <array>
+#include <cstdint>
 #include <map>
 #include <string>
 #include <vector>
@@ -149,6 +150,9 @@ class Engine {
     double flops = 0.0;
   };
   IterGraph graphs[2];
+  cudaStream_t root = nullptr;         // private capture root (the caller's stream may be the legacy one)
+  cudaEvent_t root_in = nullptr, root_out = nullptr;
+  long long graph_tag(int parity) const { return (long long)(((uintptr_t)this >> 4) * 2 + (uintptr_t)parity); }
 
  public:
   void drop_graphs();

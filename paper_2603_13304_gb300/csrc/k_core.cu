@@ -310,73 +310,162 @@ __global__ void __launch_bounds__(256) k_qr(C* A, int m, int n, C* Q, C* Rm, C* 
   cta_form_q(A, m, n, tau, Q);
 }
 
-// Q formed in place over the reflectors (first k columns of A, row stride n):
-// Q = H_0 ... H_{k-1} [I; 0], accumulated backwards.  One CTA of 256 threads.
-template <typename C>
-__device__ void cta_form_q_inplace(C* A, int m, int n, const C* tau) {
-  const int k = m < n ? m : n;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ C s_w2[8][33];
-  for (int i = k - 1; i >= 0; --i) {
-    const C ti = tau[i];
-    if (i < k - 1) {
-      if (threadIdx.x == 0) A[(long long)i * n + i] = cx<C>(1, 0);
-      __syncthreads();
-      for (int cb = i + 1; cb < k; cb += 32) {
-        const int c = cb + lane;
-        C acc = cx<C>(0, 0);
-        if (c < k)
-          for (int r = i + wid; r < m; r += nw) acc = cadd(acc, cmulc(A[(long long)r * n + i], A[(long long)r * n + c]));
-        s_w2[wid][lane] = acc;
-        __syncthreads();
-        if (wid == 0) {
-          C t = s_w2[0][lane];
-          for (int g = 1; g < nw; ++g) t = cadd(t, s_w2[g][lane]);
-          s_w2[0][lane] = cmul(ti, t);
-        }
-        __syncthreads();
-        const C f = s_w2[0][lane];
-        if (c < k)
-          for (int r = i + wid; r < m; r += nw)
-            A[(long long)r * n + c] = csub(A[(long long)r * n + c], cmul(A[(long long)r * n + i], f));
-        __syncthreads();
-      }
-    }
-    for (int r = i + 1 + threadIdx.x; r < m; r += blockDim.x)
-      A[(long long)r * n + i] = cmul(cx<C>(-ti.x, -ti.y), A[(long long)r * n + i]);
-    for (int r = threadIdx.x; r < i; r += blockDim.x) A[(long long)r * n + i] = cx<C>(0, 0);
-    if (threadIdx.x == 0) A[(long long)i * n + i] = cx<C>(1.0 - ti.x, -ti.y);
-    __syncthreads();
-  }
-}
-
 // dynamic shared memory of the staged kernels: the 227 KB opt-in per CTA less
 // a margin for their static shared arrays
 constexpr int kSmemMax = 211 * 1024;
 
-// QR with the matrix staged in shared memory (m * n * sizeof(C) <= kSmemMax):
-// A (row-major, read only) -> Q (m x k) and R (k x n, may be null).
+// QR with the matrix staged in shared memory, column-major with a padded
+// column stride (m + 1), one warp per column (column c belongs to warp
+// c % 32, lanes run over rows).  Householder step j: every warp applies
+// H_j to its columns right of j, reading the unscaled column j; the owner
+// of column j + 1 then forms the next reflector's parameters, and the owner
+// of column j writes v_j and beta_j once nobody reads column j any more;
+// one barrier per step.  Q is formed in place backwards, the next reflector
+// prefetched into a double buffer, again one barrier per step.  Same
+// convention as cta_householder: R has a real diagonal beta_j,
+// Q = H_0 ... H_{k-1}, H = I - tau v v^H.
 template <typename C>
-__global__ void __launch_bounds__(256) k_qr_smem(const C* __restrict__ Ag, int m, int n, C* __restrict__ Q,
-                                                 C* __restrict__ Rm, C* tau) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* A = (C*)smem_raw;
-  __shared__ double sh[40];
-  const long long mn = (long long)m * n;
-  for (long long e = threadIdx.x; e < mn; e += blockDim.x) A[e] = Ag[e];
-  __syncthreads();
-  cta_householder(A, m, n, tau, sh);
-  const int k = m < n ? m : n;
-  if (Rm)
-    for (long long e = threadIdx.x; e < (long long)k * n; e += blockDim.x) {
-      int i = (int)(e / n), c = (int)(e % n);
-      Rm[e] = (c >= i) ? A[(long long)i * n + c] : cx<C>(0, 0);
+struct TsqrSmem {
+  static size_t bytes(int m, int n) {
+    const int k = m < n ? m : n;
+    return sizeof(C) * ((size_t)(m + 1) * n + 2 * (size_t)m + 3 * (size_t)k + 8);
+  }
+};
+
+template <typename C>
+__device__ void tsqr_params(const C* col, int j, int m, C* s_tau, C* s_sc, C* s_beta) {
+  // reflector of column j (rows j..m-1); computed by one warp
+  using R = typename RealOf<C>::T;
+  const int lane = threadIdx.x & 31;
+  R xn2 = 0;
+  for (int r = j + 1 + lane; r < m; r += 32) xn2 += cabs2(col[r]);
+  xn2 = warp_sum(xn2);
+  if (lane == 0) {
+    const C alpha = col[j];
+    if (xn2 == (R)0 && alpha.y == (R)0) {
+      s_tau[j] = cx<C>(0, 0);
+      s_sc[j] = cx<C>(0, 0);
+      s_beta[j] = alpha;
+    } else {
+      const double ax = alpha.x, ay = alpha.y;
+      const double beta = -copysign(sqrt(ax * ax + ay * ay + (double)xn2), ax);
+      const double dx = ax - beta, dy = ay, dd = dx * dx + dy * dy;
+      s_tau[j] = cx<C>((beta - ax) / beta, -ay / beta);
+      s_sc[j] = cx<C>(dx / dd, -dy / dd);
+      s_beta[j] = cx<C>(beta, 0.0);
     }
+  }
+}
+
+// Row blocks: CTA b factorises rows [b rb, min(m_all, (b + 1) rb)) of Ag
+// (row-major, n columns).  With Q == null only R is produced; with more than
+// one CTA each writes an n x n R (zero rows below its k) at Rm + b n n, so
+// that the stacked R's can be factorised again (TSQR, R only).
+template <typename C>
+__global__ void __launch_bounds__(1024) k_tsqr_smem(const C* __restrict__ Ag, int m_all, int n, C* __restrict__ Q,
+                                                    C* __restrict__ Rm, int rb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int row0 = blockIdx.x * rb;
+  const int m = min(rb, m_all - row0);
+  Ag += (size_t)row0 * n;
+  if (gridDim.x > 1) Rm += (size_t)blockIdx.x * n * n;
+  const int k = m < n ? m : n;
+  const int ld = m + 1;
+  C* A = (C*)smem_raw;                       // column c at A + c * ld
+  C* vbuf = A + (size_t)ld * n;              // 2 x m
+  C* s_tau = vbuf + 2 * (size_t)m;
+  C* s_sc = s_tau + k;
+  C* s_beta = s_sc + k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (long long e = threadIdx.x; e < (long long)m * n; e += blockDim.x) {
+    const int r = (int)(e / n), c = (int)(e % n);
+    A[(size_t)c * ld + r] = Ag[e];
+  }
   __syncthreads();
-  cta_form_q_inplace(A, m, n, tau);
+  if (warp == 0 && k > 0) tsqr_params(A, 0, m, s_tau, s_sc, s_beta);
+  __syncthreads();
+  // ---- factorisation
+  for (int j = 0; j < k; ++j) {
+    const C* cj = A + (size_t)j * ld;
+    const C tj = s_tau[j], sc = s_sc[j];
+    const C ctau = cconj(tj);
+    if (j > 0 && warp == (j - 1) % nw) {     // finalise column j - 1 (no longer read)
+      C* cp = A + (size_t)(j - 1) * ld;
+      const C scp = s_sc[j - 1];
+      for (int r = j + lane; r < m; r += 32) cp[r] = cmul(cp[r], scp);
+      if (lane == 0) cp[j - 1] = s_beta[j - 1];
+    }
+    if (!(tj.x == 0 && tj.y == 0)) {
+      for (int c = j + 1 + ((warp - (j + 1)) % nw + nw) % nw; c < n; c += nw) {
+        C* cc = A + (size_t)c * ld;
+        C acc = cx<C>(0, 0);
+        for (int r = j + 1 + lane; r < m; r += 32) acc = cadd(acc, cmulc(cj[r], cc[r]));
+        acc.x = warp_sum(acc.x);
+        acc.y = warp_sum(acc.y);
+        // v^H a = a_j + conj(sc) sum conj(x_r) a_r
+        const C dot = cadd(cc[j], cmulc(sc, acc));
+        const C f = cmul(ctau, dot);       // a -= conj(tau) v (v^H a)
+        const C fs = cmul(f, sc);
+        for (int r = j + 1 + lane; r < m; r += 32) cc[r] = csub(cc[r], cmul(cj[r], fs));
+        if (lane == 0) cc[j] = csub(cc[j], f);
+      }
+    }
+    __syncwarp();
+    if (j + 1 < k && warp == (j + 1) % nw) tsqr_params(A + (size_t)(j + 1) * ld, j + 1, m, s_tau, s_sc, s_beta);
+    __syncthreads();
+  }
+  if (k > 0 && warp == (k - 1) % nw) {
+    C* cp = A + (size_t)(k - 1) * ld;
+    const C scp = s_sc[k - 1];
+    for (int r = k + lane; r < m; r += 32) cp[r] = cmul(cp[r], scp);
+    if (lane == 0) cp[k - 1] = s_beta[k - 1];
+  }
+  __syncthreads();
+  if (Rm) {
+    const int krows = gridDim.x > 1 ? n : k;
+    for (long long e = threadIdx.x; e < (long long)krows * n; e += blockDim.x) {
+      const int i = (int)(e / n), c = (int)(e % n);
+      Rm[e] = (i < k && c >= i) ? A[(size_t)c * ld + i] : cx<C>(0, 0);
+    }
+  }
+  if (!Q) return;
+  // ---- Q = H_0 ... H_{k-1} [I; 0], backwards, in place over columns 0..k-1
+  if (warp == (k - 1) % nw && k > 0) {
+    const C* cp = A + (size_t)(k - 1) * ld;
+    for (int r = k - 1 + lane; r < m; r += 32) vbuf[((k - 1) & 1) * m + r] = (r == k - 1) ? cx<C>(1, 0) : cp[r];
+  }
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    const C* v = vbuf + (i & 1) * m;
+    const C ti = s_tau[i];
+    for (int c = i + 1 + ((warp - (i + 1)) % nw + nw) % nw; c < k; c += nw) {
+      C* cc = A + (size_t)c * ld;
+      C acc = cx<C>(0, 0);
+      for (int r = i + lane; r < m; r += 32) acc = cadd(acc, cmulc(v[r], cc[r]));
+      acc.x = warp_sum(acc.x);
+      acc.y = warp_sum(acc.y);
+      const C f = cmul(ti, acc);
+      for (int r = i + lane; r < m; r += 32) cc[r] = csub(cc[r], cmul(v[r], f));
+    }
+    if (warp == i % nw) {                   // column i := e_i - tau_i v_i
+      C* ci = A + (size_t)i * ld;
+      const C mt = cx<C>(-ti.x, -ti.y);
+      for (int r = lane; r < m; r += 32) {
+        C q = cx<C>(0, 0);
+        if (r == i) q = cx<C>(1.0 - ti.x, -ti.y);
+        else if (r > i) q = cmul(mt, v[r]);
+        ci[r] = q;
+      }
+    }
+    if (i > 0 && warp == (i - 1) % nw) {    // prefetch v_{i-1}
+      const C* cp = A + (size_t)(i - 1) * ld;
+      for (int r = i - 1 + lane; r < m; r += 32) vbuf[((i - 1) & 1) * m + r] = (r == i - 1) ? cx<C>(1, 0) : cp[r];
+    }
+    __syncthreads();
+  }
   for (long long e = threadIdx.x; e < (long long)m * k; e += blockDim.x) {
-    int i = (int)(e / k), c = (int)(e % k);
-    Q[e] = A[(long long)i * n + c];
+    const int r = (int)(e / k), c = (int)(e % k);
+    Q[e] = A[(size_t)c * ld + r];
   }
 }
 
@@ -503,9 +592,16 @@ __device__ int rotate_pair(C* ra, C* rb, int N, C* wa, C* wb, int M, int lane, d
   return 1;
 }
 
+// Algorithmic flops of a one-sided Jacobi run: every sweep tests M(M-1)/2
+// pairs (two squared norms and one complex inner product over N: 16 N), every
+// applied rotation updates two rows of G and two of WH (18 per element pair).
+__device__ __forceinline__ double jacobi_flops(int sweeps, long long rotations, int M, int N) {
+  return (double)sweeps * 0.5 * M * (M - 1) * 16.0 * N + (double)rotations * 18.0 * (N + M);
+}
+
 template <typename C>
 __global__ void __launch_bounds__(256) k_jacobi(SvdWork<C> w, int M, int N, double tol, double floor_rel,
-                                                int max_sweeps, int* status) {
+                                                int max_sweeps, int* status, double* flops) {
   using R = typename RealOf<C>::T;
   const R floor = (R)(floor_rel * *w.zn2);
   cg::cluster_group cl = cg::this_cluster();
@@ -536,9 +632,15 @@ __global__ void __launch_bounds__(256) k_jacobi(SvdWork<C> w, int M, int N, doub
       w.counters[3] += total;           // rotations applied
     }
     cl.sync();
-    if (total == 0) return;
+    if (total == 0) {
+      if (flops && crank == 0 && threadIdx.x == 0) atomicAdd(flops, jacobi_flops(sweep + 1, w.counters[3], M, N));
+      return;
+    }
   }
-  if (crank == 0 && threadIdx.x == 0) *status = 1;   // sweep limit reached
+  if (crank == 0 && threadIdx.x == 0) {
+    *status = 1;   // sweep limit reached
+    if (flops) atomicAdd(flops, jacobi_flops(max_sweeps, w.counters[3], M, N));
+  }
 }
 
 // One-CTA Jacobi with G and WH resident in shared memory
@@ -546,7 +648,7 @@ __global__ void __launch_bounds__(256) k_jacobi(SvdWork<C> w, int M, int N, doub
 // k_jacobi, __syncthreads between rounds.
 template <typename C>
 __global__ void __launch_bounds__(1024) k_jacobi_smem(SvdWork<C> w, int M, int N, double tol, double floor_rel,
-                                                     int max_sweeps, int* status) {
+                                                     int max_sweeps, int* status, double* flops) {
   using R = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* G = (C*)smem_raw;
@@ -590,6 +692,7 @@ __global__ void __launch_bounds__(1024) k_jacobi_smem(SvdWork<C> w, int M, int N
     w.counters[2] = sweeps;
     w.counters[3] = rot_total;
     if (!converged) *status = 1;
+    if (flops) atomicAdd(flops, jacobi_flops(sweeps, rot_total, M, N));
   }
 }
 
@@ -665,12 +768,14 @@ cudaError_t smem_optin() {
 // one warp per pair), else on a cluster of up to 8 CTAs.
 template <typename C>
 cudaError_t launch_jacobi(SvdWork<C> w, int M, int N, double tol, int max_sweeps, int* status, cudaStream_t s) {
+  KTimerScope timer(KC_JACOBI, s, 0.0);
+  double* flops = ktimer_device_flops(KC_JACOBI);
   const size_t jsm = sizeof(C) * ((size_t)M * N + (size_t)M * M);
   if (jsm <= (size_t)kSmemMax) {
     cudaError_t e = smem_optin<k_jacobi_smem<C>>();
     if (e != cudaSuccess) return e;
     const int threads = std::min(1024, 32 * std::max(1, (M + 1) / 2));
-    k_jacobi_smem<C><<<1, threads, jsm, s>>>(w, M, N, tol, floor_rel_of<C>(), max_sweeps, status);
+    k_jacobi_smem<C><<<1, threads, jsm, s>>>(w, M, N, tol, floor_rel_of<C>(), max_sweeps, status, flops);
     return cudaGetLastError();
   }
   int cs = (M / 2 + 15) / 16;   // about two pairs per warp per round
@@ -687,7 +792,7 @@ cudaError_t launch_jacobi(SvdWork<C> w, int M, int N, double tol, int max_sweeps
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_jacobi<C>, w, M, N, tol, floor_rel_of<C>(), max_sweeps, status);
+  return cudaLaunchKernelEx(&cfg, k_jacobi<C>, w, M, N, tol, floor_rel_of<C>(), max_sweeps, status, flops);
 }
 
 template <typename C>
@@ -726,20 +831,6 @@ __global__ void k_omega(float2* O, int n, int b) {
     x ^= x >> 33;
     O[e] = make_float2((x & 1) ? 1.f : -1.f, (x & 2) ? 1.f : -1.f);
   }
-}
-
-// One CTA: orthonormalise the columns of Y (rows x b) in place with the panel
-// staged in shared memory (rows * b * 8 <= kSmemMax).
-__global__ void __launch_bounds__(256) k_orth_smem(float2* Y, int rows, int b, float2* tau) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* A = (float2*)smem_raw;
-  __shared__ double sh[40];
-  for (long long e = threadIdx.x; e < (long long)rows * b; e += blockDim.x) A[e] = Y[e];
-  __syncthreads();
-  cta_householder(A, rows, b, tau, sh);
-  __syncthreads();
-  cta_form_q_inplace(A, rows, b, tau);
-  for (long long e = threadIdx.x; e < (long long)rows * b; e += blockDim.x) Y[e] = A[e];
 }
 
 // One CTA: orthonormalise the columns of Y (rows x b) in place (Householder,
@@ -819,16 +910,52 @@ cudaError_t launch_zgemm(char opA, char opB, int M, int N, int K, float2 alpha, 
 
 template <typename C>
 static cudaError_t qr_t(C* A, int m, int n, C* Q, C* R, C* tau, cudaStream_t s) {
-  const size_t sm = sizeof(C) * (size_t)m * n;
+  KTimerScope timer(KC_QR, s, qr_flops(m, n));
+  const size_t sm = TsqrSmem<C>::bytes(m, n);
   if (sm <= (size_t)kSmemMax) {
-    cudaError_t e = smem_optin<k_qr_smem<C>>();
+    cudaError_t e = smem_optin<k_tsqr_smem<C>>();
     if (e != cudaSuccess) return e;
-    k_qr_smem<C><<<1, 256, sm, s>>>(A, m, n, Q, R, tau);
+    k_tsqr_smem<C><<<1, 1024, sm, s>>>(A, m, n, Q, R, m);
   } else {
     k_qr<C><<<1, 256, 0, s>>>(A, m, n, Q, R, tau);
   }
   return cudaGetLastError();
 }
+// R factor only (Q discarded): row blocks that fit shared memory are
+// factorised independently and their R's stacked and factorised again.
+template <typename C>
+static cudaError_t qr_r_t(const C* A, int m, int n, C* R, C* scratch0, C* scratch1, cudaStream_t s) {
+  KTimerScope timer(KC_QR, s, 0.5 * qr_flops(m, n));
+  cudaError_t e = smem_optin<k_tsqr_smem<C>>();
+  if (e != cudaSuccess) return e;
+  if (TsqrSmem<C>::bytes(n, n) > (size_t)kSmemMax) return cudaErrorInvalidValue;
+  int rb = 32;
+  while (TsqrSmem<C>::bytes(rb + 32, n) <= (size_t)kSmemMax) rb += 32;
+  if (rb < 2 * n) return cudaErrorInvalidValue;   // stacking would not shrink the problem
+  const C* src = A;
+  int rows = m;
+  C* bufs[2] = {scratch0, scratch1};
+  int which = 0;
+  for (int level = 0; level < 16 && TsqrSmem<C>::bytes(rows, n) > (size_t)kSmemMax; ++level) {
+    const int nb = (rows + rb - 1) / rb;
+    k_tsqr_smem<C><<<nb, 1024, TsqrSmem<C>::bytes(rb, n), s>>>(src, rows, n, nullptr, bufs[which], rb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    src = bufs[which];
+    rows = nb * n;
+    which ^= 1;
+  }
+  if (TsqrSmem<C>::bytes(rows, n) > (size_t)kSmemMax) return cudaErrorInvalidValue;
+  k_tsqr_smem<C><<<1, 1024, TsqrSmem<C>::bytes(rows, n), s>>>(src, rows, n, nullptr, R, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qr_r(const double2* A, int m, int n, double2* R, double2* s0, double2* s1, cudaStream_t s) {
+  return qr_r_t(A, m, n, R, s0, s1, s);
+}
+cudaError_t launch_qr_r(const float2* A, int m, int n, float2* R, float2* s0, float2* s1, cudaStream_t s) {
+  return qr_r_t(A, m, n, R, s0, s1, s);
+}
+
 cudaError_t launch_qr(double2* A, int m, int n, double2* Q, double2* R, double2* tau, cudaStream_t s) {
   return qr_t(A, m, n, Q, R, tau, s);
 }
@@ -892,10 +1019,11 @@ cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, 
   const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
   cudaError_t e;
   k_omega<<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
-  const bool staged = z * (size_t)N * b <= (size_t)kSmemMax;
-  if (staged && (e = smem_optin<k_orth_smem>()) != cudaSuccess) return e;
+  const bool staged = TsqrSmem<float2>::bytes(N, b) <= (size_t)kSmemMax;
+  if (staged && (e = smem_optin<k_tsqr_smem<float2>>()) != cudaSuccess) return e;
   auto orthonormalise = [&](float2* Y, int rows) {
-    if (staged) k_orth_smem<<<1, 256, z * (size_t)rows * b, s>>>(Y, rows, b, orth);
+    KTimerScope timer(KC_ORTH, s, qr_flops(rows, b));
+    if (staged) k_tsqr_smem<float2><<<1, 1024, TsqrSmem<float2>::bytes(rows, b), s>>>(Y, rows, b, Y, nullptr, rows);
     else k_orth<<<1, 256, 0, s>>>(Y, rows, b, orth);
   };
   // Q = orth(Z W)
@@ -1178,11 +1306,10 @@ cudaError_t launch_mps_dot(const ChainDesc& a, const ChainDesc& b, bool c64, dou
 // (done once up front so that no attribute call falls inside a stream capture).
 cudaError_t init_kernel_attributes() {
   cudaError_t e;
-  if ((e = smem_optin<k_qr_smem<double2>>()) != cudaSuccess) return e;
-  if ((e = smem_optin<k_qr_smem<float2>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_tsqr_smem<double2>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_tsqr_smem<float2>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_smem<double2>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_smem<float2>>()) != cudaSuccess) return e;
-  if ((e = smem_optin<k_orth_smem>()) != cudaSuccess) return e;
   return init_tc_attributes();
 }
 

@@ -281,6 +281,7 @@ cudaError_t tc_launch(const void* A, long long lda, const void* Bt, long long ld
   if (!make_map(&ta, A, kBF16, M, K, lda, kBM) || !make_map(&tb, Bt, kBF16, N, K, ldb, BN))
     return cudaErrorInvalidValue;
   dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM);
+  KTimerScope timer(KC_TC, s, 2.0 * M * N * K);
   k_tc_gemm<kBF16, BN><<<grid, 128, smem, s>>>(ta, tb, C, M, N, K, ldc, alpha, err);
   return cudaGetLastError();
 }

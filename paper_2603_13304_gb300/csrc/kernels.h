@@ -39,6 +39,13 @@ cudaError_t init_tc_attributes();
 cudaError_t launch_qr(double2* A, int m, int n, double2* Q, double2* R, double2* tau, cudaStream_t s);
 cudaError_t launch_qr(float2* A, int m, int n, float2* Q, float2* R, float2* tau, cudaStream_t s);
 
+// R factor only of A (m x n, row-major, not modified): k x n, k = min(m, n),
+// upper triangular with a real diagonal.  Tall inputs are split into row
+// blocks whose R's are stacked and factorised again; s0, s1: scratch of
+// m * n elements each.  Requires an n x n panel to fit shared memory.
+cudaError_t launch_qr_r(const double2* A, int m, int n, double2* R, double2* s0, double2* s1, cudaStream_t s);
+cudaError_t launch_qr_r(const float2* A, int m, int n, float2* R, float2* s0, float2* s1, cudaStream_t s);
+
 // Truncated SVD Z (m x n) = U S V^H keeping k = min(chi, m, n) triplets with
 // the largest singular values: writes U (m x k) and Rem = S V^H (k x n).
 // complex128: exact one-sided (row) Jacobi.  complex64: Jacobi when
@@ -114,6 +121,34 @@ cudaError_t launch_tc_absorb(bool bf16, const double2* X, int P, int Q, const do
                              void* work, int* err, cudaStream_t s);
 cudaError_t launch_tc_absorb(bool bf16, const float2* X, int P, int Q, const float2* S, int l, int r, float2* R,
                              void* work, int* err, cudaStream_t s);
+
+// Live timing of one kernel class (ktimer.cpp): every launch of the selected
+// class is bracketed by CUDA events on its stream; totals of launches,
+// milliseconds and algorithmic flops accumulate until read.
+enum KernelClass { KC_NONE = 0, KC_JACOBI = 1, KC_ORTH = 2, KC_QR = 3, KC_TC = 4, KC_ABSORB = 5 };
+void ktimer_select(int cls);
+int ktimer_class();
+double* ktimer_device_flops(int cls);        // device accumulator for kernels that count their own flops
+void ktimer_set_tag(long long tag);          // tag of pairs recorded by this thread (-1: eager)
+void ktimer_drop_tag(long long tag);
+void ktimer_collect(long long tag);          // after a synchronise: add the pairs of `tag`
+void ktimer_read(long long* n, double* ms, double* flops);
+struct KTimerScope {
+  KTimerScope(int cls, cudaStream_t s, double flops);
+  ~KTimerScope();
+  KTimerScope(const KTimerScope&) = delete;
+  KTimerScope& operator=(const KTimerScope&) = delete;
+
+ private:
+  cudaStream_t s_ = nullptr;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+// Complex Householder QR with the explicit Q, 8 real flops per complex
+// multiply-add: 2 x 8 (2 a k^2 - 2 k^3 / 3), a = max(m, n), k = min(m, n).
+inline double qr_flops(int m, int n) {
+  const double a = m > n ? m : n, k = m < n ? m : n;
+  return 16.0 * (2.0 * a * k * k - 2.0 * k * k * k / 3.0);
+}
 
 // Allocation-free truncated SVD (k_noalloc.cu): scratch in a fixed device
 // array of noalloc_scratch_bytes(); *too_large is set when svd_work_bytes(m, n)

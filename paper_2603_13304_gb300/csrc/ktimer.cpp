@@ -1,0 +1,131 @@
+// Live timing of one kernel class with CUDA events on its launch stream.
+//
+// When a class is selected, every launch of it is bracketed by a pair of
+// events recorded on the stream it is launched on (with the external-record
+// flag, so that inside a stream capture the pair becomes event nodes of the
+// graph and every replay re-records it).  Pairs recorded eagerly are read
+// once and dropped; pairs baked into a captured graph carry that graph's tag
+// and are re-read after each replay until the graph is dropped.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "kernels.h"
+
+namespace bbp {
+
+namespace {
+
+struct Pair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  double flops = 0.0;
+  long long tag = -1;
+};
+
+std::mutex g_mu;
+int g_class = 0;
+std::vector<Pair> g_pairs;
+long long g_n = 0;
+double g_ms = 0.0, g_flops = 0.0;
+double* g_dev_flops = nullptr;   // kernels that count their own work add here
+thread_local long long t_tag = -1;
+
+void destroy(Pair& p) {
+  if (p.a) cudaEventDestroy(p.a);
+  if (p.b) cudaEventDestroy(p.b);
+  p.a = p.b = nullptr;
+}
+
+}  // namespace
+
+void ktimer_select(int cls) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (Pair& p : g_pairs) destroy(p);
+  g_pairs.clear();
+  g_class = cls;
+  g_n = 0;
+  g_ms = g_flops = 0.0;
+  if (cls && !g_dev_flops) {
+    if (cudaMalloc(&g_dev_flops, sizeof(double)) != cudaSuccess) g_dev_flops = nullptr;
+  }
+  if (g_dev_flops) cudaMemset(g_dev_flops, 0, sizeof(double));
+}
+
+int ktimer_class() { return g_class; }
+
+double* ktimer_device_flops(int cls) { return (g_class && g_class == cls) ? g_dev_flops : nullptr; }
+
+void ktimer_set_tag(long long tag) { t_tag = tag; }
+
+void ktimer_drop_tag(long long tag) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  std::vector<Pair> keep;
+  for (Pair& p : g_pairs) {
+    if (p.tag == tag) destroy(p);
+    else keep.push_back(p);
+  }
+  g_pairs.swap(keep);
+}
+
+KTimerScope::KTimerScope(int cls, cudaStream_t s, double flops) : s_(s) {
+  if (!g_class || cls != g_class) return;
+  Pair p;
+  if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) {
+    destroy(p);
+    return;
+  }
+  p.flops = flops;
+  p.tag = t_tag;
+  if (cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal) != cudaSuccess) {
+    destroy(p);
+    return;
+  }
+  a_ = p.a;
+  b_ = p.b;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_pairs.push_back(p);
+}
+
+KTimerScope::~KTimerScope() {
+  if (b_) cudaEventRecordWithFlags(b_, s_, cudaEventRecordExternal);
+}
+
+// Add the pairs of `tag` (all completed: the caller has synchronised) to the
+// totals; eager pairs (tag -1) are dropped afterwards.
+void ktimer_collect(long long tag) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_class) return;
+  std::vector<Pair> keep;
+  for (Pair& p : g_pairs) {
+    if (p.tag != tag) {
+      keep.push_back(p);
+      continue;
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_ms += ms;
+      g_flops += p.flops;
+      ++g_n;
+    }
+    if (tag == -1) destroy(p);
+    else keep.push_back(p);
+  }
+  g_pairs.swap(keep);
+}
+
+void ktimer_read(long long* n, double* ms, double* flops) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  double dev = 0.0;
+  if (g_dev_flops) {
+    cudaMemcpy(&dev, g_dev_flops, sizeof(double), cudaMemcpyDeviceToHost);
+    cudaMemset(g_dev_flops, 0, sizeof(double));
+  }
+  *n = g_n;
+  *ms = g_ms;
+  *flops = g_flops + dev;
+  g_n = 0;
+  g_ms = g_flops = 0.0;
+}
+
+}  // namespace bbp
