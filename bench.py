@@ -109,6 +109,7 @@ KERNELS = {
     "qr": (3, "Householder QR of the canonical moves (k_qr_smem / k_qr)"),
     "tc": (4, "tcgen05 split-precision absorb GEMM (k_tc_gemm)"),
     "absorb": (5, "SIMT complex absorb GEMM (k_gemm)"),
+    "gemm": (6, "every SIMT complex GEMM (k_gemm)"),
 }
 
 

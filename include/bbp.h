@@ -165,6 +165,18 @@ bbp_status bbp_stats(bbp_ctx* ctx, long long* launches_per_iter, double* flops_p
 const char* bbp_last_error(const bbp_ctx* ctx);
 void bbp_destroy(bbp_ctx* ctx);
 
+/* Live kernel timing (no counterpart in the thesis): select one kernel class
+ * (0 off, 1 one-sided Jacobi, 2 randomised-range orthonormalisation,
+ * 3 Householder QR, 4 tensor-core GEMM, 5 SIMT absorb GEMM, 6 every SIMT
+ * complex GEMM); every later
+ * launch of it, eager or inside a captured iteration, is bracketed by CUDA
+ * events on its own stream.  bbp_iterate adds the completed launches;
+ * bbp_ktimer_read returns launches, total milliseconds and algorithmic flops
+ * since the last read (and resets them).  Selecting clears all records;
+ * select before the iterations whose graphs should carry the events. */
+void bbp_ktimer_select(int kernel_class);
+bbp_status bbp_ktimer_read(long long* launches, double* ms, double* flops);
+
 /* ---------------------------------------------------------------------
  * Kernel-level entry points (device pointers, for unit tests and tools).
  * All take a cudaStream_t and return after enqueueing the work.

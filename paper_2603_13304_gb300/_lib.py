@@ -294,7 +294,7 @@ def bbp_set_execution(ctx, use_graphs: bool = True, max_streams: int = 16):
     _check(lib().bbp_set_execution(ctx, int(use_graphs), int(max_streams)), ctx)
 
 
-KT_JACOBI, KT_ORTH, KT_QR, KT_TC, KT_ABSORB = 1, 2, 3, 4, 5
+KT_JACOBI, KT_ORTH, KT_QR, KT_TC, KT_ABSORB, KT_GEMM = 1, 2, 3, 4, 5, 6
 
 
 def bbp_ktimer_select(kernel_class: int):

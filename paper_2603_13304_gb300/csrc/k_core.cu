@@ -334,33 +334,41 @@ struct TsqrSmem {
 
 template <typename C>
 __device__ void tsqr_params(const C* col, int j, int m, C* s_tau, C* s_sc, C* s_beta) {
-  // reflector of column j (rows j..m-1); computed by one warp
+  // reflector of column j (rows j..m-1); computed by one warp in the
+  // element's real type, with the column scaled by its largest magnitude
+  // first so that tiny columns neither underflow nor divide by zero
   using R = typename RealOf<C>::T;
   const int lane = threadIdx.x & 31;
+  const C alpha = col[j];
+  R amax = fmax(fabs(alpha.x), fabs(alpha.y));
+  for (int r = j + 1 + lane; r < m; r += 32) amax = fmax(amax, fmax(fabs(col[r].x), fabs(col[r].y)));
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  const R sa = (amax > (R)0 && isfinite(amax)) ? (R)1 / amax : (R)0;
   R xn2 = 0;
-  for (int r = j + 1 + lane; r < m; r += 32) xn2 += cabs2(col[r]);
+  for (int r = j + 1 + lane; r < m; r += 32) xn2 += cabs2(cscale(col[r], sa));
   xn2 = warp_sum(xn2);
   if (lane == 0) {
-    const C alpha = col[j];
-    if (xn2 == (R)0 && alpha.y == (R)0) {
-      s_tau[j] = cx<C>(0, 0);
-      s_sc[j] = cx<C>(0, 0);
-      s_beta[j] = alpha;
-    } else {
-      const double ax = alpha.x, ay = alpha.y;
-      const double beta = -copysign(sqrt(ax * ax + ay * ay + (double)xn2), ax);
-      const double dx = ax - beta, dy = ay, dd = dx * dx + dy * dy;
-      s_tau[j] = cx<C>((beta - ax) / beta, -ay / beta);
-      s_sc[j] = cx<C>(dx / dd, -dy / dd);
-      s_beta[j] = cx<C>(beta, 0.0);
+    C tau = cx<C>(0, 0), sc = cx<C>(0, 0), beta = alpha;
+    if (sa > (R)0 && !(xn2 == (R)0 && alpha.y == (R)0)) {
+      const R ax = alpha.x * sa, ay = alpha.y * sa;          // scaled, |.| <= 1
+      const R bs = -copysign(sqrt(ax * ax + ay * ay + xn2), ax);
+      const R dx = ax - bs, dy = ay, dd = dx * dx + dy * dy;
+      const R ib = (R)1 / bs, idd = sa / dd;                 // 1 / (alpha - beta) = sa conj(d') / |d'|^2
+      tau = cx<C>((bs - ax) * ib, -ay * ib);
+      sc = cx<C>(dx * idd, -dy * idd);
+      beta = cx<C>(bs * amax, 0.0);
+      if (!(isfinite(tau.x) && isfinite(tau.y) && isfinite(sc.x) && isfinite(sc.y) && isfinite(beta.x))) {
+        tau = cx<C>(0, 0);                                     // leave the column as it is
+        sc = cx<C>(0, 0);
+        beta = alpha;
+      }
     }
+    s_tau[j] = tau;
+    s_sc[j] = sc;
+    s_beta[j] = beta;
   }
 }
 
-// Row blocks: CTA b factorises rows [b rb, min(m_all, (b + 1) rb)) of Ag
-// (row-major, n columns).  With Q == null only R is produced; with more than
-// one CTA each writes an n x n R (zero rows below its k) at Rm + b n n, so
-// that the stacked R's can be factorised again (TSQR, R only).
 template <typename C>
 __global__ void __launch_bounds__(1024) k_tsqr_smem(const C* __restrict__ Ag, int m_all, int n, C* __restrict__ Q,
                                                     C* __restrict__ Rm, int rb) {
@@ -709,11 +717,14 @@ __global__ void k_row_norms(SvdWork<C> w, int M, int N) {
 
 template <typename C>
 __global__ void k_select(SvdWork<C> w, int M, int k) {
+  // a total order (non-finite norms rank last), so ranks 0..M-1 are a permutation
   for (int a = threadIdx.x; a < M; a += blockDim.x) {
     double sa = w.sigma[a];
+    if (!(sa >= 0.0) || !isfinite(sa)) sa = -1.0;
     int rank = 0;
     for (int b = 0; b < M; ++b) {
       double sb = w.sigma[b];
+      if (!(sb >= 0.0) || !isfinite(sb)) sb = -1.0;
       rank += (sb > sa) || (sb == sa && b < a);
     }
     if (rank < k) w.idx[rank] = a;
@@ -730,7 +741,7 @@ __global__ void k_svd_out(SvdWork<C> w, int m, int n, int k, double floor_rel, C
        e += (long long)gridDim.x * blockDim.x) {
     if (e < totU) {
       int i = (int)(e / k), r = (int)(e % k);
-      int a = w.idx[r];
+      int a = min(max(w.idx[r], 0), M - 1);
       if (m <= n) {
         U[e] = cconj(w.WH[(long long)a * M + i]);
       } else {
@@ -740,7 +751,7 @@ __global__ void k_svd_out(SvdWork<C> w, int m, int n, int k, double floor_rel, C
     } else {
       long long f = e - totU;
       int r = (int)(f / n), c = (int)(f % n);
-      int a = w.idx[r];
+      int a = min(max(w.idx[r], 0), M - 1);
       if (m <= n) Rem[f] = w.G[(long long)a * N + c];
       else Rem[f] = cscale(w.WH[(long long)a * M + c], w.sigma[a]);
     }
@@ -847,20 +858,41 @@ __global__ void __launch_bounds__(256) k_orth(float2* Y, int rows, int b, float2
 }
 
 // U (m x k) = Q (m x b) * conj(WH[idx[r], :])^T ; Rem (k x n) = G[idx[r], :]
+// U = Q WH[top]^H (m x k) and Rem = G'[top] W^H (k x n), where the Jacobi
+// rotated L = R_W^H (b x b) into G' = WH L.
+__global__ void k_rand_out_lw(const float2* __restrict__ Q, int m, int b, SvdWork<float2> w,
+                              const float2* __restrict__ W, int n, int k, float2* U, float2* Rem) {
+  long long totU = (long long)m * k, totR = (long long)k * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totU + totR;
+       e += (long long)gridDim.x * blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (e < totU) {
+      const int i = (int)(e / k), a = min(max(w.idx[(int)(e % k)], 0), b - 1);
+      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(Q[(long long)i * b + j], cconj(w.WH[(long long)a * b + j])));
+      U[e] = acc;
+    } else {
+      const long long f = e - totU;
+      const int a = min(max(w.idx[(int)(f / n)], 0), b - 1), c = (int)(f % n);
+      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(w.G[(long long)a * b + j], cconj(W[(long long)c * b + j])));
+      Rem[f] = acc;
+    }
+  }
+}
+
 __global__ void k_rand_out(const float2* Q, int m, int b, SvdWork<float2> w, int n, int k, float2* U, float2* Rem) {
   long long totU = (long long)m * k, totR = (long long)k * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totU + totR;
        e += (long long)gridDim.x * blockDim.x) {
     if (e < totU) {
       int i = (int)(e / k), r = (int)(e % k);
-      int a = w.idx[r];
+      int a = min(max(w.idx[r], 0), b - 1);
       float2 s = make_float2(0.f, 0.f);
       for (int j = 0; j < b; ++j) s = cadd(s, cmul(Q[(long long)i * b + j], cconj(w.WH[(long long)a * b + j])));
       U[e] = s;
     } else {
       long long f = e - totU;
       int r = (int)(f / n), c = (int)(f % n);
-      Rem[f] = w.G[(long long)w.idx[r] * n + c];
+      Rem[f] = w.G[(long long)min(max(w.idx[r], 0), b - 1) * n + c];
     }
   }
 }
@@ -893,6 +925,7 @@ static cudaError_t gemm_t(char opA, char opB, int M, int N, int K, C alpha, cons
                           const C* B, int ldb, long long sB, C beta, C* Cm, int ldc, long long sC, int batch,
                           cudaStream_t s) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  KTimerScope timer(KC_GEMM, s, 8.0 * M * N * (double)K * batch);
   dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, batch);
   k_gemm<C><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, Cm, ldc, sC);
   return cudaGetLastError();
@@ -1034,6 +1067,26 @@ cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, 
     orthonormalise(W, n);
     if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
     orthonormalise(Q, m);
+  }
+  if (staged) {
+    // last half step keeps R: Z^H Q = W R_W, so B = Q^H Z = R_W^H W^H and the
+    // Jacobi runs on the b x b matrix L = R_W^H instead of the b x n matrix B
+    if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
+    float2* Rw = X;
+    float2* L = X + (size_t)b * b;
+    {
+      KTimerScope timer(KC_ORTH, s, qr_flops(n, b));
+      k_tsqr_smem<float2><<<1, 1024, TsqrSmem<float2>::bytes(n, b), s>>>(W, n, b, W, Rw, n);
+    }
+    if ((e = launch_conj_transpose(Rw, b, b, L, s)) != cudaSuccess) return e;
+    SvdWork<float2> w = carve<float2>(jw, b, b);
+    if ((e = cudaMemsetAsync(w.counters, 0, 64, s)) != cudaSuccess) return e;
+    k_svd_init<float2><<<grid_for(2LL * b * b, 256), 256, 0, s>>>(L, b, b, w);
+    if ((e = launch_jacobi(w, b, b, jacobi_tol_c64(n), 60, status, s)) != cudaSuccess) return e;
+    k_row_norms<float2><<<(b * 32 + 255) / 256, 256, 0, s>>>(w, b, b);
+    k_select<float2><<<1, 256, 0, s>>>(w, b, k);
+    k_rand_out_lw<<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(Q, m, b, w, W, n, k, U, Rem);
+    return cudaGetLastError();
   }
   // B = Q^H Z (b x n) into X, then Jacobi on its rows (b <= n here)
   if ((e = launch_zgemm('C', 'N', b, n, m, one, Q, b, 0, Z, n, 0, zero, X, n, 0, 1, s)) != cudaSuccess) return e;

@@ -125,7 +125,7 @@ cudaError_t launch_tc_absorb(bool bf16, const float2* X, int P, int Q, const flo
 // Live timing of one kernel class (ktimer.cpp): every launch of the selected
 // class is bracketed by CUDA events on its stream; totals of launches,
 // milliseconds and algorithmic flops accumulate until read.
-enum KernelClass { KC_NONE = 0, KC_JACOBI = 1, KC_ORTH = 2, KC_QR = 3, KC_TC = 4, KC_ABSORB = 5 };
+enum KernelClass { KC_NONE = 0, KC_JACOBI = 1, KC_ORTH = 2, KC_QR = 3, KC_TC = 4, KC_ABSORB = 5, KC_GEMM = 6 };
 void ktimer_select(int cls);
 int ktimer_class();
 double* ktimer_device_flops(int cls);        // device accumulator for kernels that count their own flops
@@ -142,6 +142,7 @@ struct KTimerScope {
  private:
   cudaStream_t s_ = nullptr;
   cudaEvent_t a_ = nullptr, b_ = nullptr;
+  bool external_ = false;
 };
 // Complex Householder QR with the explicit Q, 8 real flops per complex
 // multiply-add: 2 x 8 (2 a k^2 - 2 k^3 / 3), a = max(m, n), k = min(m, n).

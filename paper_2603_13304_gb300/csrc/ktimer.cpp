@@ -2,8 +2,8 @@
 //
 // When a class is selected, every launch of it is bracketed by a pair of
 // events recorded on the stream it is launched on (with the external-record
-// flag, so that inside a stream capture the pair becomes event nodes of the
-// graph and every replay re-records it).  Pairs recorded eagerly are read
+// flag when the stream is being captured, so that the pair becomes event
+// nodes of the graph and every replay re-records it).  Pairs recorded eagerly are read
 // once and dropped; pairs baked into a captured graph carry that graph's tag
 // and are re-read after each replay until the graph is dropped.
 #include <cuda_runtime.h>
@@ -77,7 +77,15 @@ KTimerScope::KTimerScope(int cls, cudaStream_t s, double flops) : s_(s) {
   }
   p.flops = flops;
   p.tag = t_tag;
-  if (cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal) != cudaSuccess) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    destroy(p);
+    return;
+  }
+  external_ = cs == cudaStreamCaptureStatusActive;
+  if ((external_ ? cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal) : cudaEventRecord(p.a, s)) != cudaSuccess) {
+    cudaGetLastError();   // a failed timing record must not surface as the launch's error
     destroy(p);
     return;
   }
@@ -88,7 +96,9 @@ KTimerScope::KTimerScope(int cls, cudaStream_t s, double flops) : s_(s) {
 }
 
 KTimerScope::~KTimerScope() {
-  if (b_) cudaEventRecordWithFlags(b_, s_, cudaEventRecordExternal);
+  if (!b_) return;
+  if ((external_ ? cudaEventRecordWithFlags(b_, s_, cudaEventRecordExternal) : cudaEventRecord(b_, s_)) != cudaSuccess)
+    cudaGetLastError();
 }
 
 // Add the pairs of `tag` (all completed: the caller has synchronised) to the
