@@ -87,9 +87,11 @@ bbp_status bbp_partition_blocks(bbp_ctx* ctx, int bx, int by);
  * precision: BBP_FP64 -- every tensor complex128, exact one-sided Jacobi
  *   truncation (the reference path, agrees with the FP64 oracle to 1e-10);
  * BBP_FP32 -- tensors and contractions complex64; each truncation reduces a
- *   large matrix to chi + chi/2 directions by a randomised subspace iteration
- *   (3 power steps) before an exact one-sided Jacobi on the reduced matrix;
- *   message norms, phases, distances and log-scales stay double.
+ *   large matrix Z to b = chi + max(8, chi/2) directions by a randomised
+ *   subspace iteration (bbp_set_power_iters steps, default 1; Householder
+ *   orthonormalisation) and runs an exact one-sided Jacobi on the b x b
+ *   factor of Q^H Z; message norms, phases, distances and log-scales stay
+ *   double.
  * BBP_TF32 / BBP_BF16 -- as BBP_FP32, with the absorb contraction (the
  *   dense X^T S product of each swallow) on the tensor cores: both operands
  *   scaled by a power of two and split into high and low TF32 (or BF16)
@@ -98,6 +100,13 @@ bbp_status bbp_partition_blocks(bbp_ctx* ctx, int bx, int by);
  * Must be called before bbp_init_messages.  alpha must be 1 (undamped
  * update).  seed is reserved. */
 bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, uint64_t seed);
+
+/* Randomised truncation of the complex64 modes (no counterpart in the
+ * thesis, whose truncation is an exact SVD): number of subspace-iteration
+ * power steps before the reduced Jacobi, 0..8 (default 1).  Fewer steps are
+ * faster and less accurate when the spectrum decays slowly; BBP_FP64 is
+ * unaffected (exact Jacobi). */
+bbp_status bbp_set_power_iters(bbp_ctx* ctx, int power_iters);
 
 /* Execution options (no counterpart in the thesis; they change how the same
  * arithmetic is scheduled, not what it computes).  use_graphs = 1 (default)

@@ -27,7 +27,7 @@ EXPORTS = [
     "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
     "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message",
     "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
-    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_ktimer_select", "bbp_ktimer_read",
+    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters", "bbp_ktimer_select", "bbp_ktimer_read",
     "bbp_k_tc_absorb_bytes", "bbp_k_tc_absorb", "bbp_plan_debug",
 ]
 
@@ -73,6 +73,7 @@ _PROTOS = {
     "bbp_k_svd_stats": (_i, [_vp, _i, _i, _ip, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "bbp_k_qr": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
     "bbp_set_execution": (_i, [_vp, _i, _i]),
+    "bbp_set_power_iters": (_i, [_vp, _i]),
     "bbp_ktimer_select": (None, [_i]),
     "bbp_ktimer_read": (_i, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)]),
@@ -292,6 +293,10 @@ def bbp_k_qr(A, m: int, n: int, Q, R, tau, stream=None):
 
 def bbp_set_execution(ctx, use_graphs: bool = True, max_streams: int = 16):
     _check(lib().bbp_set_execution(ctx, int(use_graphs), int(max_streams)), ctx)
+
+
+def bbp_set_power_iters(ctx, power_iters: int):
+    _check(lib().bbp_set_power_iters(ctx, int(power_iters)), ctx)
 
 
 KT_JACOBI, KT_ORTH, KT_QR, KT_TC, KT_ABSORB, KT_GEMM = 1, 2, 3, 4, 5, 6

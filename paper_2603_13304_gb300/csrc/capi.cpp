@@ -94,6 +94,14 @@ bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, u
   return BBP_OK;
 }
 
+bbp_status bbp_set_power_iters(bbp_ctx* ctx, int power_iters) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (power_iters < 0 || power_iters > 8) return set_err(BBP_ERR_ARG, "power_iters must be 0..8");
+  ctx->eng.drop_graphs();
+  ctx->eng.power_iters = power_iters;
+  return BBP_OK;
+}
+
 bbp_status bbp_set_execution(bbp_ctx* ctx, int use_graphs, int max_streams) {
   if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
   if (max_streams < 1 || max_streams > 64) return set_err(BBP_ERR_ARG, "max_streams must be 1..64");

@@ -326,9 +326,9 @@ constexpr int kSmemMax = 211 * 1024;
 // Q = H_0 ... H_{k-1}, H = I - tau v v^H.
 template <typename C>
 struct TsqrSmem {
-  static size_t bytes(int m, int n) {
+  static size_t bytes(int m, int n) {   // column-major (m + 1) x n or row-major m x (n + 1) panel
     const int k = m < n ? m : n;
-    return sizeof(C) * ((size_t)(m + 1) * n + 2 * (size_t)m + 3 * (size_t)k + 8);
+    return sizeof(C) * ((size_t)m * n + (size_t)(m > n ? m : n) + 2 * (size_t)m + 3 * (size_t)k + 8);
   }
 };
 
@@ -475,6 +475,243 @@ __global__ void __launch_bounds__(1024) k_tsqr_smem(const C* __restrict__ Ag, in
     const int r = (int)(e / k), c = (int)(e % k);
     Q[e] = A[(size_t)c * ld + r];
   }
+}
+
+
+// complex64 variant of k_tsqr_smem: the panel is kept row-major with an odd
+// row stride (n + 1, so that a warp reading one column down 32 rows touches
+// distinct banks), global loads and stores run along rows, and the columns a
+// warp works on are cached in registers: lane l holds rows l + 32 i,
+// i < MAXR (m <= 32 MAXR), so every column pass issues its loads back to
+// back; 16 warps.  Same steps, barriers and results as k_tsqr_smem.
+template <int MAXR>
+__device__ __forceinline__ void tsqr_params_reg(const float2* A, int ldr, int c, int j, int m, float2* s_tau,
+                                                float2* s_sc, float2* s_beta) {
+  const int lane = threadIdx.x & 31;
+  float2 x[MAXR];
+#pragma unroll
+  for (int i = 0; i < MAXR; ++i) {
+    const int r = lane + 32 * i;
+    x[i] = (r > j && r < m) ? A[(size_t)r * ldr + c] : make_float2(0.f, 0.f);
+  }
+  const float2 alpha = A[(size_t)j * ldr + c];
+  float amax = fmaxf(fabsf(alpha.x), fabsf(alpha.y));
+#pragma unroll
+  for (int i = 0; i < MAXR; ++i) amax = fmaxf(amax, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  const float sa = (amax > 0.f && isfinite(amax)) ? 1.f / amax : 0.f;
+  float xn2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < MAXR; ++i) xn2 += (x[i].x * sa) * (x[i].x * sa) + (x[i].y * sa) * (x[i].y * sa);
+  xn2 = warp_sum(xn2);
+  if (lane == 0) {
+    float2 tau = make_float2(0.f, 0.f), sc = make_float2(0.f, 0.f), beta = alpha;
+    if (sa > 0.f && !(xn2 == 0.f && alpha.y == 0.f)) {
+      const float ax = alpha.x * sa, ay = alpha.y * sa;
+      const float bs = -copysignf(sqrtf(ax * ax + ay * ay + xn2), ax);
+      const float dx = ax - bs, dy = ay, dd = dx * dx + dy * dy;
+      const float ib = 1.f / bs, idd = sa / dd;
+      tau = make_float2((bs - ax) * ib, -ay * ib);
+      sc = make_float2(dx * idd, -dy * idd);
+      beta = make_float2(bs * amax, 0.f);
+      if (!(isfinite(tau.x) && isfinite(tau.y) && isfinite(sc.x) && isfinite(sc.y) && isfinite(beta.x))) {
+        tau = make_float2(0.f, 0.f);
+        sc = make_float2(0.f, 0.f);
+        beta = alpha;
+      }
+    }
+    s_tau[j] = tau;
+    s_sc[j] = sc;
+    s_beta[j] = beta;
+  }
+}
+
+inline size_t tsqr_reg_bytes(int m, int n) {
+  const int k = m < n ? m : n;
+  return sizeof(float2) * ((size_t)m * (n + 1) + 2 * (size_t)m + 3 * (size_t)k + 8);
+}
+
+template <int MAXR>
+__global__ void __launch_bounds__(512, 1) k_tsqr_reg(const float2* __restrict__ Ag, int m_all, int n, float2* Q,
+                                                     float2* Rm, int rb) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int row0 = blockIdx.x * rb;
+  const int m = min(rb, m_all - row0);
+  Ag += (size_t)row0 * n;
+  if (gridDim.x > 1) Rm += (size_t)blockIdx.x * n * n;
+  const int k = m < n ? m : n;
+  const int ldr = n + 1;
+  C* A = (C*)smem_raw;                       // (r, c) at A[r * ldr + c]
+  C* vbuf = A + (size_t)m * ldr;
+  C* s_tau = vbuf + 2 * (size_t)m;
+  C* s_sc = s_tau + k;
+  C* s_beta = s_sc + k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c0 = 0; c0 < n; c0 += 64)
+    for (int r0 = warp * 4; r0 < m; r0 += nw * 4) {
+      C v[4][2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = r0 + q, c = c0 + lane + 32 * h;
+          v[q][h] = (r < m && c < n) ? Ag[(size_t)r * n + c] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = r0 + q, c = c0 + lane + 32 * h;
+          if (r < m && c < n) A[(size_t)r * ldr + c] = v[q][h];
+        }
+    }
+  __syncthreads();
+  if (warp == 0 && k > 0) tsqr_params_reg<MAXR>(A, ldr, 0, 0, m, s_tau, s_sc, s_beta);
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    const C tj = s_tau[j], sc = s_sc[j];
+    const C ctau = cconj(tj);
+    if (j > 0 && warp == (j - 1) % nw) {     // finalise column j - 1
+      const C scp = s_sc[j - 1];
+      for (int r = j + lane; r < m; r += 32) A[(size_t)r * ldr + j - 1] = cmul(A[(size_t)r * ldr + j - 1], scp);
+      if (lane == 0) A[(size_t)(j - 1) * ldr + j - 1] = s_beta[j - 1];
+    }
+    const int c0 = j + 1 + ((warp - (j + 1)) % nw + nw) % nw;
+    if (!(tj.x == 0.f && tj.y == 0.f) && c0 < n) {
+      C xj[MAXR];
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) {
+        const int r = lane + 32 * i;
+        xj[i] = (r > j && r < m) ? A[(size_t)r * ldr + j] : make_float2(0.f, 0.f);
+      }
+      for (int c = c0; c < n; c += nw) {
+        C y[MAXR];
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i) {
+          const int r = lane + 32 * i;
+          y[i] = (r > j && r < m) ? A[(size_t)r * ldr + c] : make_float2(0.f, 0.f);
+        }
+        C a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < MAXR; i += 2) {
+          a0 = cadd(a0, cmulc(xj[i], y[i]));
+          if (i + 1 < MAXR) a1 = cadd(a1, cmulc(xj[i + 1], y[i + 1]));
+        }
+        C acc = cadd(a0, a1);
+        acc.x = warp_sum(acc.x);
+        acc.y = warp_sum(acc.y);
+        const C ajc = A[(size_t)j * ldr + c];
+        const C dot = cadd(ajc, cmulc(sc, acc));
+        const C f = cmul(ctau, dot);
+        const C fs = cmul(f, sc);
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i) {
+          const int r = lane + 32 * i;
+          if (r > j && r < m) A[(size_t)r * ldr + c] = csub(y[i], cmul(xj[i], fs));
+        }
+        __syncwarp();
+        if (lane == 0) A[(size_t)j * ldr + c] = csub(ajc, f);
+      }
+    }
+    __syncwarp();
+    if (j + 1 < k && warp == (j + 1) % nw) tsqr_params_reg<MAXR>(A, ldr, j + 1, j + 1, m, s_tau, s_sc, s_beta);
+    __syncthreads();
+  }
+  if (k > 0 && warp == (k - 1) % nw) {
+    const C scp = s_sc[k - 1];
+    for (int r = k + lane; r < m; r += 32) A[(size_t)r * ldr + k - 1] = cmul(A[(size_t)r * ldr + k - 1], scp);
+    if (lane == 0) A[(size_t)(k - 1) * ldr + k - 1] = s_beta[k - 1];
+  }
+  __syncthreads();
+  if (Rm) {
+    const int krows = gridDim.x > 1 ? n : k;
+    for (int i = warp; i < krows; i += nw)
+      for (int c = lane; c < n; c += 32)
+        Rm[(size_t)i * n + c] = (i < k && c >= i) ? A[(size_t)i * ldr + c] : make_float2(0.f, 0.f);
+  }
+  if (!Q) return;
+  if (k > 0 && warp == (k - 1) % nw)
+    for (int r = k - 1 + lane; r < m; r += 32)
+      vbuf[((k - 1) & 1) * m + r] = (r == k - 1) ? make_float2(1.f, 0.f) : A[(size_t)r * ldr + k - 1];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    const C* v = vbuf + (i & 1) * m;
+    const C ti = s_tau[i];
+    const int c0 = i + 1 + ((warp - (i + 1)) % nw + nw) % nw;
+    const bool own_i = warp == i % nw;
+    if (c0 < k || own_i) {
+      C vv[MAXR];
+#pragma unroll
+      for (int q = 0; q < MAXR; ++q) {
+        const int r = lane + 32 * q;
+        vv[q] = (r >= i && r < m) ? v[r] : make_float2(0.f, 0.f);
+      }
+      for (int c = c0; c < k; c += nw) {
+        C y[MAXR];
+#pragma unroll
+        for (int q = 0; q < MAXR; ++q) {
+          const int r = lane + 32 * q;
+          y[q] = (r >= i && r < m) ? A[(size_t)r * ldr + c] : make_float2(0.f, 0.f);
+        }
+        C a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < MAXR; q += 2) {
+          a0 = cadd(a0, cmulc(vv[q], y[q]));
+          if (q + 1 < MAXR) a1 = cadd(a1, cmulc(vv[q + 1], y[q + 1]));
+        }
+        C acc = cadd(a0, a1);
+        acc.x = warp_sum(acc.x);
+        acc.y = warp_sum(acc.y);
+        const C f = cmul(ti, acc);
+#pragma unroll
+        for (int q = 0; q < MAXR; ++q) {
+          const int r = lane + 32 * q;
+          if (r >= i && r < m) A[(size_t)r * ldr + c] = csub(y[q], cmul(vv[q], f));
+        }
+      }
+      if (own_i) {                          // column i := e_i - tau_i v_i
+        const C mt = make_float2(-ti.x, -ti.y);
+#pragma unroll
+        for (int q = 0; q < MAXR; ++q) {
+          const int r = lane + 32 * q;
+          if (r < m)
+            A[(size_t)r * ldr + i] =
+                (r == i) ? make_float2(1.f - ti.x, -ti.y) : (r > i ? cmul(mt, vv[q]) : make_float2(0.f, 0.f));
+        }
+      }
+    }
+    if (i > 0 && warp == (i - 1) % nw)
+      for (int r = i - 1 + lane; r < m; r += 32)
+        vbuf[((i - 1) & 1) * m + r] = (r == i - 1) ? make_float2(1.f, 0.f) : A[(size_t)r * ldr + i - 1];
+    __syncthreads();
+  }
+  for (int r = warp; r < m; r += nw)
+    for (int c = lane; c < k; c += 32) Q[(size_t)r * k + c] = A[(size_t)r * ldr + c];
+}
+
+// One staged QR launch (grid = row blocks): the register-cached kernel for
+// complex64 panels of at most 512 rows per block, the generic one otherwise.
+template <typename C>
+cudaError_t tsqr_launch(const C* Ag, int m_all, int n, C* Q, C* Rm, int rb, cudaStream_t s);
+
+template <>
+cudaError_t tsqr_launch<float2>(const float2* Ag, int m_all, int n, float2* Q, float2* Rm, int rb, cudaStream_t s) {
+  const int nb = (m_all + rb - 1) / rb;
+  const size_t sr = tsqr_reg_bytes(rb, n);
+  if (rb <= 128 && sr <= (size_t)kSmemMax) k_tsqr_reg<4><<<nb, 512, sr, s>>>(Ag, m_all, n, Q, Rm, rb);
+  else if (rb <= 256 && sr <= (size_t)kSmemMax) k_tsqr_reg<8><<<nb, 512, sr, s>>>(Ag, m_all, n, Q, Rm, rb);
+  else if (rb <= 512 && sr <= (size_t)kSmemMax) k_tsqr_reg<16><<<nb, 512, sr, s>>>(Ag, m_all, n, Q, Rm, rb);
+  else k_tsqr_smem<float2><<<nb, 1024, TsqrSmem<float2>::bytes(rb, n), s>>>(Ag, m_all, n, Q, Rm, rb);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t tsqr_launch<double2>(const double2* Ag, int m_all, int n, double2* Q, double2* Rm, int rb,
+                                 cudaStream_t s) {
+  const int nb = (m_all + rb - 1) / rb;
+  k_tsqr_smem<double2><<<nb, 1024, TsqrSmem<double2>::bytes(rb, n), s>>>(Ag, m_all, n, Q, Rm, rb);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- K3 Jacobi
@@ -946,9 +1183,8 @@ static cudaError_t qr_t(C* A, int m, int n, C* Q, C* R, C* tau, cudaStream_t s) 
   KTimerScope timer(KC_QR, s, qr_flops(m, n));
   const size_t sm = TsqrSmem<C>::bytes(m, n);
   if (sm <= (size_t)kSmemMax) {
-    cudaError_t e = smem_optin<k_tsqr_smem<C>>();
+    cudaError_t e = tsqr_launch<C>(A, m, n, Q, R, m, s);
     if (e != cudaSuccess) return e;
-    k_tsqr_smem<C><<<1, 1024, sm, s>>>(A, m, n, Q, R, m);
   } else {
     k_qr<C><<<1, 256, 0, s>>>(A, m, n, Q, R, tau);
   }
@@ -959,8 +1195,7 @@ static cudaError_t qr_t(C* A, int m, int n, C* Q, C* R, C* tau, cudaStream_t s) 
 template <typename C>
 static cudaError_t qr_r_t(const C* A, int m, int n, C* R, C* scratch0, C* scratch1, cudaStream_t s) {
   KTimerScope timer(KC_QR, s, 0.5 * qr_flops(m, n));
-  cudaError_t e = smem_optin<k_tsqr_smem<C>>();
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   if (TsqrSmem<C>::bytes(n, n) > (size_t)kSmemMax) return cudaErrorInvalidValue;
   int rb = 32;
   while (TsqrSmem<C>::bytes(rb + 32, n) <= (size_t)kSmemMax) rb += 32;
@@ -971,15 +1206,13 @@ static cudaError_t qr_r_t(const C* A, int m, int n, C* R, C* scratch0, C* scratc
   int which = 0;
   for (int level = 0; level < 16 && TsqrSmem<C>::bytes(rows, n) > (size_t)kSmemMax; ++level) {
     const int nb = (rows + rb - 1) / rb;
-    k_tsqr_smem<C><<<nb, 1024, TsqrSmem<C>::bytes(rb, n), s>>>(src, rows, n, nullptr, bufs[which], rb);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = tsqr_launch<C>(src, rows, n, nullptr, bufs[which], rb, s)) != cudaSuccess) return e;
     src = bufs[which];
     rows = nb * n;
     which ^= 1;
   }
   if (TsqrSmem<C>::bytes(rows, n) > (size_t)kSmemMax) return cudaErrorInvalidValue;
-  k_tsqr_smem<C><<<1, 1024, TsqrSmem<C>::bytes(rows, n), s>>>(src, rows, n, nullptr, R, rows);
-  return cudaGetLastError();
+  return tsqr_launch<C>(src, rows, n, nullptr, R, rows, s);
 }
 
 cudaError_t launch_qr_r(const double2* A, int m, int n, double2* R, double2* s0, double2* s1, cudaStream_t s) {
@@ -1053,10 +1286,9 @@ cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, 
   cudaError_t e;
   k_omega<<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
   const bool staged = TsqrSmem<float2>::bytes(N, b) <= (size_t)kSmemMax;
-  if (staged && (e = smem_optin<k_tsqr_smem<float2>>()) != cudaSuccess) return e;
   auto orthonormalise = [&](float2* Y, int rows) {
     KTimerScope timer(KC_ORTH, s, qr_flops(rows, b));
-    if (staged) k_tsqr_smem<float2><<<1, 1024, TsqrSmem<float2>::bytes(rows, b), s>>>(Y, rows, b, Y, nullptr, rows);
+    if (staged) tsqr_launch<float2>(Y, rows, b, Y, nullptr, rows, s);
     else k_orth<<<1, 256, 0, s>>>(Y, rows, b, orth);
   };
   // Q = orth(Z W)
@@ -1076,7 +1308,7 @@ cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, 
     float2* L = X + (size_t)b * b;
     {
       KTimerScope timer(KC_ORTH, s, qr_flops(n, b));
-      k_tsqr_smem<float2><<<1, 1024, TsqrSmem<float2>::bytes(n, b), s>>>(W, n, b, W, Rw, n);
+      if ((e = tsqr_launch<float2>(W, n, b, W, Rw, n, s)) != cudaSuccess) return e;
     }
     if ((e = launch_conj_transpose(Rw, b, b, L, s)) != cudaSuccess) return e;
     SvdWork<float2> w = carve<float2>(jw, b, b);
@@ -1361,6 +1593,9 @@ cudaError_t init_kernel_attributes() {
   cudaError_t e;
   if ((e = smem_optin<k_tsqr_smem<double2>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_tsqr_smem<float2>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_tsqr_reg<4>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_tsqr_reg<8>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_tsqr_reg<16>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_smem<double2>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_smem<float2>>()) != cudaSuccess) return e;
   return init_tc_attributes();
