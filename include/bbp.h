@@ -174,6 +174,56 @@ bbp_status bbp_stats(bbp_ctx* ctx, long long* launches_per_iter, double* flops_p
 const char* bbp_last_error(const bbp_ctx* ctx);
 void bbp_destroy(bbp_ctx* ctx);
 
+/* ---------------------------------------------------------------------
+ * Many problems on one GPU (no counterpart in the thesis).
+ * ------------------------------------------------------------------- */
+
+/* Iterate n contexts together: each round launches one synchronous
+ * iteration of every context that has not converged (each on its own
+ * streams, so they overlap on the device) and then reads all their errors;
+ * a context leaves when its error <= tol or it fails.  Per context:
+ * iterations done, final error and status (BBP_NOT_CONVERGED after
+ * max_iter rounds).  Returns BBP_OK, BBP_NOT_CONVERGED, or the first
+ * failure among the contexts. */
+bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int max_iter, int* iters_out, double* err_out,
+                             int* status_out);
+
+/* A BlockBP job for the server: the arguments of bbp_create_peps,
+ * bbp_partition_blocks, bbp_set_options and bbp_init_messages, the stopping
+ * rule (tol, max_iter), the worker streams of its context (<= 0: 4) and the
+ * power steps of the complex64 truncation (< 0: 1).  Host arrays are copied
+ * by bbp_server_submit. */
+typedef struct {
+  int lattice, Lx, Ly, periodic, d, D, bx, by, chi, precision;
+  double tol;
+  int max_iter, streams, power_iters;
+  const double* host_tensors; /* complex128 [n_sites][d][D]^4 */
+  const double* edge_mats;    /* complex128 [n_sites][4][D][D] */
+} bbp_job;
+
+typedef struct bbp_server bbp_server;
+
+/* Continuous batching: queued jobs are admitted in arrival order while the
+ * sum of the admitted jobs' footprints (bbp_job_footprint_bytes) stays
+ * within hbm_budget_bytes and fewer than max_active are resident; admitted
+ * jobs keep their messages on the device and each is relaunched as soon as
+ * its previous iteration completes; a job finishes at error <= tol, at
+ * max_iter iterations or on failure.  One thread drives a server. */
+bbp_status bbp_server_create(bbp_server** out, size_t hbm_budget_bytes, int max_active);
+size_t bbp_job_footprint_bytes(const bbp_job* job);
+bbp_status bbp_server_submit(bbp_server* s, const bbp_job* job, long long* id_out);
+/* Admit, launch, wait up to timeout_ms for an iteration to complete, finish
+ * and retire; reports the queue, resident and finished counts. */
+bbp_status bbp_server_step(bbp_server* s, double timeout_ms, int* n_queued, int* n_active, int* n_finished);
+/* Finished jobs not yet taken (up to cap): id, status, iterations, final
+ * error, seconds queued and seconds from submit to completion. */
+bbp_status bbp_server_poll(bbp_server* s, long long* ids, int* status, int* iters, double* err, double* wait_s,
+                           double* latency_s, int cap, int* n_out);
+/* Remove a finished job; with ctx_out its context passes to the caller (who
+ * destroys it with bbp_destroy), otherwise it is destroyed. */
+bbp_status bbp_server_take(bbp_server* s, long long id, bbp_ctx** ctx_out);
+void bbp_server_destroy(bbp_server* s);
+
 /* Live kernel timing (no counterpart in the thesis): select one kernel class
  * (0 off, 1 one-sided Jacobi, 2 randomised-range orthonormalisation,
  * 3 Householder QR, 4 tensor-core GEMM, 5 SIMT absorb GEMM, 6 every SIMT

@@ -27,7 +27,9 @@ EXPORTS = [
     "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
     "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message",
     "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
-    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters", "bbp_ktimer_select", "bbp_ktimer_read",
+    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
+    "bbp_batch_iterate", "bbp_server_create", "bbp_job_footprint_bytes", "bbp_server_submit", "bbp_server_step",
+    "bbp_server_poll", "bbp_server_take", "bbp_server_destroy", "bbp_ktimer_select", "bbp_ktimer_read",
     "bbp_k_tc_absorb_bytes", "bbp_k_tc_absorb", "bbp_plan_debug",
 ]
 
@@ -74,6 +76,15 @@ _PROTOS = {
     "bbp_k_qr": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
     "bbp_set_execution": (_i, [_vp, _i, _i]),
     "bbp_set_power_iters": (_i, [_vp, _i]),
+    "bbp_batch_iterate": (_i, [ctypes.POINTER(_vp), _i, ctypes.c_double, _i, _ip, ctypes.POINTER(ctypes.c_double), _ip]),
+    "bbp_server_create": (_i, [ctypes.POINTER(_vp), ctypes.c_size_t, _i]),
+    "bbp_job_footprint_bytes": (ctypes.c_size_t, [_vp]),
+    "bbp_server_submit": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "bbp_server_step": (_i, [_vp, ctypes.c_double, _ip, _ip, _ip]),
+    "bbp_server_poll": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _ip, _ip, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _i, _ip]),
+    "bbp_server_take": (_i, [_vp, ctypes.c_longlong, ctypes.POINTER(_vp)]),
+    "bbp_server_destroy": (None, [_vp]),
     "bbp_ktimer_select": (None, [_i]),
     "bbp_ktimer_read": (_i, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)]),
@@ -335,3 +346,80 @@ def bbp_plan_debug(lattice, Lx, Ly, periodic, bx, by, block, face):
     _check(lib().bbp_plan_debug(lattice, Lx, Ly, int(periodic), bx, by, block, face, _iptr(out), out.size,
                                 ctypes.byref(n)))
     return out[:4 * n.value].reshape(-1, 4)
+
+# ------------------------------------------------------- many problems
+
+def bbp_batch_iterate(ctxs, tol: float, max_iter: int):
+    """Iterate several contexts together; returns (status, iters, errs, statuses)."""
+    n = len(ctxs)
+    arr = (_vp * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    iters = np.zeros(n, dtype=np.int32)
+    errs = np.zeros(n, dtype=np.float64)
+    st = np.zeros(n, dtype=np.int32)
+    rc = lib().bbp_batch_iterate(arr, n, tol, max_iter, _iptr(iters),
+                                 errs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _iptr(st))
+    return int(rc), iters, errs, st
+
+
+class bbp_job(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("lattice", "Lx", "Ly", "periodic", "d", "D", "bx", "by", "chi",
+                                            "precision")] + \
+               [("tol", ctypes.c_double)] + [(k, ctypes.c_int) for k in ("max_iter", "streams", "power_iters")] + \
+               [("host_tensors", _vp), ("edge_mats", _vp)]
+
+
+def make_job(lattice, Lx, Ly, periodic, d, D, bx, by, chi, precision, tensors, edge_mats, tol, max_iter,
+             streams=4, power_iters=1):
+    """A job description; keeps references to the host arrays until submitted."""
+    t = np.ascontiguousarray(tensors, dtype=np.complex128)
+    e = np.ascontiguousarray(edge_mats, dtype=np.complex128)
+    j = bbp_job(lattice, Lx, Ly, int(periodic), d, D, bx, by, chi, precision, tol, max_iter, streams, power_iters,
+                t.ctypes.data, e.ctypes.data)
+    j._keep = (t, e)
+    return j
+
+
+def bbp_job_footprint_bytes(job) -> int:
+    return int(lib().bbp_job_footprint_bytes(ctypes.byref(job)))
+
+
+def bbp_server_create(hbm_budget_bytes: int, max_active: int):
+    s = _vp()
+    _check(lib().bbp_server_create(ctypes.byref(s), int(hbm_budget_bytes), int(max_active)))
+    return s
+
+
+def bbp_server_submit(server, job) -> int:
+    jid = ctypes.c_longlong()
+    _check(lib().bbp_server_submit(server, ctypes.byref(job), ctypes.byref(jid)))
+    return jid.value
+
+
+def bbp_server_step(server, timeout_ms: float = 50.0):
+    q, a, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().bbp_server_step(server, float(timeout_ms), ctypes.byref(q), ctypes.byref(a), ctypes.byref(f)))
+    return q.value, a.value, f.value
+
+
+def bbp_server_poll(server, cap: int = 4096):
+    ids = np.zeros(cap, dtype=np.int64)
+    st = np.zeros(cap, dtype=np.int32)
+    it = np.zeros(cap, dtype=np.int32)
+    err, wait, lat = (np.zeros(cap, dtype=np.float64) for _ in range(3))
+    n = ctypes.c_int()
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    _check(lib().bbp_server_poll(server, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _iptr(st), _iptr(it),
+                                 dp(err), dp(wait), dp(lat), cap, ctypes.byref(n)))
+    k = n.value
+    return [dict(id=int(ids[i]), status=int(st[i]), iters=int(it[i]), err=float(err[i]), wait_s=float(wait[i]),
+                 latency_s=float(lat[i])) for i in range(k)]
+
+
+def bbp_server_take(server, job_id: int, keep_context: bool = False):
+    c = _vp()
+    _check(lib().bbp_server_take(server, int(job_id), ctypes.byref(c) if keep_context else None))
+    return c if keep_context else None
+
+
+def bbp_server_destroy(server):
+    lib().bbp_server_destroy(server)

@@ -10,12 +10,10 @@
 #include <vector>
 
 #include "../../include/bbp.h"
+#include "ctx.h"
 #include "engine.h"
 #include "kernels.h"
 
-struct bbp_ctx {
-  bbp::Engine eng;
-};
 
 namespace {
 thread_local std::string g_err;

@@ -182,7 +182,9 @@ Engine::~Engine() {
     cudaStreamDestroy(root);
   }
   if (root_in) cudaEventDestroy(root_in);
+  if (root_in2) cudaEventDestroy(root_in2);
   if (root_out) cudaEventDestroy(root_out);
+  if (h_dist) cudaFreeHost(h_dist);
   for (SweepWork* w : pool) {
     if (w->stream) cudaStreamSynchronize(w->stream);
     w->arena.release();
@@ -729,175 +731,208 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
   return 0;
 }
 
-int Engine::iterate(double tol, int max_iter, int* iters, double* err) {
-  return precision == 0 ? iterate_t<double2>(tol, max_iter, iters, err) : iterate_t<float2>(tol, max_iter, iters, err);
-}
+// ------------------------------------------------------------ iteration
+//
+// One synchronous iteration (Alg. 1: every message update of the network
+// from the current messages, then all replaced at once) runs on a private
+// root stream: fork over the worker streams, one sweep and one finalisation
+// per update, join, and the distances and statuses copied to pinned host
+// memory.  iter_begin orders the root after the caller's stream, iter_end
+// orders the caller's stream after the last iteration; in between any
+// number of iter_launch / iter_finish pairs, which is what lets several
+// contexts (bbp_batch_iterate, the server) keep iterations in flight at once.
 
-template <typename C>
-int Engine::iterate_t(double tol, int max_iter, int* iters, double* err_out) {
+int Engine::iter_begin() {
   if (!partitioned) return fail(this, 8, "bbp_partition_blocks must come first");
   if (!messages_ready) return fail(this, 8, "bbp_init_messages must come first");
-  if (max_iter < 0 || !(tol >= 0.0)) return fail(this, 1, "tol must be >= 0 and max_iter >= 0");
+  const int nu = (int)geom.updates().size();
+  if (!dist_dev.ensure(sizeof(double) * nu + 2 * sizeof(int) * nu + 256, stream)) return fail(this, 2, "allocation failed");
+  if (h_cap < (size_t)nu) {
+    if (h_dist) cudaFreeHost(h_dist);
+    h_dist = nullptr;
+    h_cap = 0;
+    CK(cudaHostAlloc((void**)&h_dist, (sizeof(double) + 2 * sizeof(int)) * (size_t)std::max(nu, 1),
+                     cudaHostAllocDefault));
+    h_cap = (size_t)nu;
+  }
+  if (!root) {
+    CK(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&root_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&root_out, cudaEventDisableTiming));
+  }
+  CK(cudaEventRecord(root_in, stream));
+  CK(cudaStreamWaitEvent(root, root_in, 0));
+  return 0;
+}
+
+int Engine::iter_end() {
+  if (!root) return 0;
+  CK(cudaEventRecord(root_out, root));
+  CK(cudaStreamWaitEvent(stream, root_out, 0));
+  return 0;
+}
+
+int Engine::iter_launch() { return precision == 0 ? iter_launch_t<double2>() : iter_launch_t<float2>(); }
+
+template <typename C>
+int Engine::iter_launch_t() {
   const auto ups = geom.updates();
   const int nu = (int)ups.size();
-  if (nu == 0) {
-    if (iters) *iters = 0;
-    if (err_out) *err_out = 0.0;
-    return 0;
-  }
-  // per update: distance (double) and the SVD status of its sweep (int)
-  if (!dist_dev.ensure(sizeof(double) * nu + 2 * sizeof(int) * nu + 256, stream)) return fail(this, 2, "allocation failed");
+  in_flight = false;
+  if (nu == 0) return 0;
   int* status_dev = (int*)((double*)dist_dev.p + nu);
   const int nstreams = std::max(1, std::min(nu, max_streams));
   for (int i = 0; i < nstreams; ++i)
     if (!work(i)) return fail(this, 3, "stream creation failed");
-  cudaEvent_t fork;
-  CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-  std::vector<double> hd(nu);
-  std::vector<int> hs(2 * nu);
-  double err = INFINITY;
-  int it = 0;
+  sweep_launches = 0;
+  sweep_flops = 0.0;
+  std::vector<DBuf*> tmp;
+  std::vector<SweepJob> jobs(nu);
   int rc = 0;
-  for (; it < max_iter; ++it) {
-    sweep_launches = 0;
-    sweep_flops = 0.0;
-    std::vector<DBuf*> tmp;
-    std::vector<SweepJob> jobs(nu);
-    for (int u = 0; u < nu && !rc; ++u) {
+  for (int u = 0; u < nu && !rc; ++u) {
+    const auto& up = ups[u];
+    if ((rc = fill_job<C>(block_regions[up.block], plans.at({up.block, up.face}), jobs[u], {}, tmp))) break;
+    Message& dst = msgs.at({up.recv_block, up.recv_face});
+    for (const TShape& t : jobs[u].tr.final_mps)
+      if ((size_t)t.size() > dst.cap) { rc = fail(this, 8, "message tensor exceeds its buffer"); break; }
+  }
+  for (DBuf* b : tmp) delete b;      // no operator insertions in an iteration
+  if (rc) return rc;
+  // destinations and their shapes (host bookkeeping, also when replaying)
+  int parity = 0;
+  for (int u = 0; u < nu; ++u) {
+    const auto& up = ups[u];
+    Message& dst = msgs.at({up.recv_block, up.recv_face});
+    const int nxt = 1 - dst.cur;
+    parity = nxt;
+    jobs[u].dest.clear();
+    for (int q = 0; q < dst.k(); ++q) jobs[u].dest.push_back(dst.tensor<C>(nxt, q));
+    dst.sh[nxt] = jobs[u].tr.final_mps;
+  }
+  if ((rc = reserve_workers(jobs, nstreams))) return rc;
+  cudaEvent_t fork = root_in2;
+  // fork onto the worker streams, one sweep and one finalisation per update, join
+  auto enqueue = [&]() -> int {
+    CK(cudaEventRecord(fork, root));
+    for (int i = 0; i < nstreams; ++i) CK(cudaStreamWaitEvent(pool[i]->stream, fork, 0));
+    int e = 0;
+    for (int u = 0; u < nu && !e; ++u) {
+      SweepWork& w = *pool[u % nstreams];
       const auto& up = ups[u];
-      if ((rc = fill_job<C>(block_regions[up.block], plans.at({up.block, up.face}), jobs[u], {}, tmp))) break;
       Message& dst = msgs.at({up.recv_block, up.recv_face});
-      for (const TShape& t : jobs[u].tr.final_mps)
-        if ((size_t)t.size() > dst.cap) { rc = fail(this, 8, "message tensor exceeds its buffer"); break; }
+      if ((e = run_sweep<C>(jobs[u], w))) break;
+      if ((e = finalize_message<C>(dst, 1 - dst.cur, w, w.stream, (double*)dist_dev.p + u, true))) break;
+      CK(cudaMemcpyAsync(status_dev + 2 * u, w.status, 2 * sizeof(int), cudaMemcpyDeviceToDevice, w.stream));
     }
-    // destinations and their shapes (host bookkeeping, also when replaying)
-    int parity = 0;
-    for (int u = 0; u < nu && !rc; ++u) {
-      const auto& up = ups[u];
-      Message& dst = msgs.at({up.recv_block, up.recv_face});
-      const int nxt = 1 - dst.cur;
-      parity = nxt;
-      jobs[u].dest.clear();
-      for (int q = 0; q < dst.k(); ++q) jobs[u].dest.push_back(dst.tensor<C>(nxt, q));
-      dst.sh[nxt] = jobs[u].tr.final_mps;
+    for (int i = 0; i < nstreams; ++i) {
+      CK(cudaEventRecord(pool[i]->done, pool[i]->stream));
+      CK(cudaStreamWaitEvent(root, pool[i]->done, 0));
     }
-    if (!rc) rc = reserve_workers(jobs, nstreams);
-    // the whole iteration: fork onto the worker streams, one sweep and one
-    // finalisation per update, join
-    auto enqueue = [&]() -> int {
-      CK(cudaEventRecord(fork, stream));
-      for (int i = 0; i < nstreams; ++i) CK(cudaStreamWaitEvent(pool[i]->stream, fork, 0));
-      int e = 0;
-      for (int u = 0; u < nu && !e; ++u) {
-        SweepWork& w = *pool[u % nstreams];
-        const auto& up = ups[u];
-        Message& dst = msgs.at({up.recv_block, up.recv_face});
-        if ((e = run_sweep<C>(jobs[u], w))) break;
-        if ((e = finalize_message<C>(dst, 1 - dst.cur, w, w.stream, (double*)dist_dev.p + u, true))) break;
-        CK(cudaMemcpyAsync(status_dev + 2 * u, w.status, 2 * sizeof(int), cudaMemcpyDeviceToDevice, w.stream));
+    return e;
+  };
+  if (!root_in2) {
+    CK(cudaEventCreateWithFlags(&root_in2, cudaEventDisableTiming));
+    fork = root_in2;
+  }
+  if (!use_graphs) {
+    rc = enqueue();
+  } else {
+    IterGraph& g = graphs[parity];
+    const unsigned long long sig = iter_signature(jobs, nstreams);
+    if (!g.exec || g.sig != sig) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g = IterGraph();
+      const long long tag = graph_tag(parity);
+      ktimer_drop_tag(tag);
+      ktimer_set_tag(tag);
+      cudaError_t ce = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) {
+        ktimer_set_tag(-1);
+        return fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
       }
-      for (int i = 0; i < nstreams; ++i) {
-        CK(cudaEventRecord(pool[i]->done, pool[i]->stream));
-        CK(cudaStreamWaitEvent(stream, pool[i]->done, 0));
+      int e = enqueue();
+      cudaGraph_t graph = nullptr;
+      ce = cudaStreamEndCapture(root, &graph);
+      ktimer_set_tag(-1);
+      if (!e && ce != cudaSuccess) e = fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
+      if (!e) {
+        ce = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (ce != cudaSuccess) e = fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
       }
-      return e;
-    };
-    if (!rc && !use_graphs) {
-      rc = enqueue();
-    } else if (!rc) {
-      // capture and replay on a private non-blocking root stream, ordered
-      // after the caller's stream and before whatever the caller enqueues next
-      if (!root) {
-        CK(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&root_in, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&root_out, cudaEventDisableTiming));
+      if (graph) cudaGraphDestroy(graph);
+      if (e) {
+        g = IterGraph();
+        return e;
       }
-      CK(cudaEventRecord(root_in, stream));
-      CK(cudaStreamWaitEvent(root, root_in, 0));
-      const cudaStream_t user = stream;
-      stream = root;
-      auto replay = [&]() -> int {
-        IterGraph& g = graphs[parity];
-        const unsigned long long sig = iter_signature(jobs, nstreams);
-        if (!g.exec || g.sig != sig) {
-          if (g.exec) cudaGraphExecDestroy(g.exec);
-          g = IterGraph();
-          const long long tag = graph_tag(parity);
-          ktimer_drop_tag(tag);
-          ktimer_set_tag(tag);
-          cudaError_t ce = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
-          if (ce != cudaSuccess) {
-            ktimer_set_tag(-1);
-            return fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
-          }
-          int e = enqueue();
-          cudaGraph_t graph = nullptr;
-          ce = cudaStreamEndCapture(stream, &graph);
-          ktimer_set_tag(-1);
-          if (!e && ce != cudaSuccess) e = fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
-          if (!e) {
-            ce = cudaGraphInstantiate(&g.exec, graph, 0);
-            if (ce != cudaSuccess) e = fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
-          }
-          if (graph) cudaGraphDestroy(graph);
-          if (e) {
-            g = IterGraph();
-            return e;
-          }
-          g.sig = sig;
-          g.launches = sweep_launches;
-          g.flops = sweep_flops;
-        }
-        cudaError_t le = cudaGraphLaunch(g.exec, stream);
-        if (le != cudaSuccess) return fail(this, 3, std::string("graph launch: ") + cudaGetErrorString(le));
-        sweep_launches = g.launches;
-        sweep_flops = g.flops;
-        return 0;
-      };
-      rc = replay();
-      stream = user;
-      if (!rc) {
-        CK(cudaEventRecord(root_out, root));
-        CK(cudaStreamWaitEvent(stream, root_out, 0));
-      }
+      g.sig = sig;
+      g.launches = sweep_launches;
+      g.flops = sweep_flops;
     }
-    for (DBuf* b : tmp) delete b;
-    if (rc) break;
-    CK(cudaMemcpyAsync(hd.data(), dist_dev.p, sizeof(double) * nu, cudaMemcpyDeviceToHost, stream));
-    CK(cudaMemcpyAsync(hs.data(), status_dev, 2 * sizeof(int) * nu, cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
-    if (ktimer_class()) ktimer_collect(use_graphs ? graph_tag(parity) : -1);
-    err = 0.0;
-    bool nonfinite = false, sweep_limit = false;
-    for (int u = 0; u < nu; ++u) {
-      if (!std::isfinite(hd[u])) nonfinite = true;
-      err = std::max(err, hd[u]);
-    }
-    bool tc_timeout = false;
-    for (int u = 0; u < nu; ++u) {
-      sweep_limit = sweep_limit || hs[2 * u] != 0;
-      tc_timeout = tc_timeout || hs[2 * u + 1] != 0;
-    }
-    for (const auto& up : ups) msgs.at({up.recv_block, up.recv_face}).cur ^= 1;
-    launches_per_iter = sweep_launches;
-    flops_per_iter = sweep_flops;
-    ++n_iterations;
-    if (tc_timeout) {
-      rc = fail(this, 7, "a tensor-core pipeline wait timed out");
-      ++it;
-      break;
-    }
-    if (nonfinite || sweep_limit) {
-      rc = fail(this, 5, nonfinite ? "a message became non-finite" : "a Jacobi SVD reached its sweep limit");
-      ++it;
-      break;
-    }
+    cudaError_t le = cudaGraphLaunch(g.exec, root);
+    if (le != cudaSuccess) return fail(this, 3, std::string("graph launch: ") + cudaGetErrorString(le));
+    sweep_launches = g.launches;
+    sweep_flops = g.flops;
+  }
+  if (rc) return rc;
+  double* hd = h_dist;
+  int* hs = (int*)(h_dist + nu);
+  CK(cudaMemcpyAsync(hd, dist_dev.p, sizeof(double) * nu, cudaMemcpyDeviceToHost, root));
+  CK(cudaMemcpyAsync(hs, status_dev, 2 * sizeof(int) * nu, cudaMemcpyDeviceToHost, root));
+  CK(cudaEventRecord(root_out, root));
+  launched_parity = parity;
+  in_flight = true;
+  return 0;
+}
+
+int Engine::iter_finish(double* err_out) {
+  const auto ups = geom.updates();
+  const int nu = (int)ups.size();
+  if (nu == 0) {
+    if (err_out) *err_out = 0.0;
+    return 0;
+  }
+  if (!in_flight) return fail(this, 8, "no iteration in flight");
+  in_flight = false;
+  CK(cudaEventSynchronize(root_out));
+  if (ktimer_class()) ktimer_collect(use_graphs ? graph_tag(launched_parity) : -1);
+  const double* hd = h_dist;
+  const int* hs = (const int*)(h_dist + nu);
+  double err = 0.0;
+  bool nonfinite = false, sweep_limit = false, tc_timeout = false;
+  for (int u = 0; u < nu; ++u) {
+    if (!std::isfinite(hd[u])) nonfinite = true;
+    err = std::max(err, hd[u]);
+    sweep_limit = sweep_limit || hs[2 * u] != 0;
+    tc_timeout = tc_timeout || hs[2 * u + 1] != 0;
+  }
+  for (const auto& up : ups) msgs.at({up.recv_block, up.recv_face}).cur ^= 1;
+  launches_per_iter = sweep_launches;
+  flops_per_iter = sweep_flops;
+  ++n_iterations;
+  if (err_out) *err_out = err;
+  if (tc_timeout) return fail(this, 7, "a tensor-core pipeline wait timed out");
+  if (nonfinite || sweep_limit)
+    return fail(this, 5, nonfinite ? "a message became non-finite" : "a Jacobi SVD reached its sweep limit");
+  return 0;
+}
+
+int Engine::iterate(double tol, int max_iter, int* iters, double* err_out) {
+  if (max_iter < 0 || !(tol >= 0.0)) return fail(this, 1, "tol must be >= 0 and max_iter >= 0");
+  int rc = iter_begin();
+  if (rc) return rc;
+  double err = geom.updates().empty() ? 0.0 : INFINITY;
+  int it = 0;
+  for (; it < max_iter && !geom.updates().empty(); ++it) {
+    if ((rc = iter_launch())) break;
+    rc = iter_finish(&err);
+    if (rc) { ++it; break; }
     if (err <= tol) { ++it; break; }
   }
-  cudaEventDestroy(fork);
+  const int rc2 = iter_end();
   if (iters) *iters = it;
   if (err_out) *err_out = err;
   if (rc) return rc;
+  if (rc2) return rc2;
   if (err > tol) return fail(this, 6, "max_iter reached before the messages converged");
   return 0;
 }

@@ -116,6 +116,13 @@ class Engine {
   int set_precision(int p);
   int init_messages(const double* edge_mats);
   int iterate(double tol, int max_iter, int* iters, double* err);
+  // split iteration (several contexts in flight): begin, then launch/finish
+  // pairs, then end; see engine.cpp
+  int iter_begin();
+  int iter_launch();
+  int iter_finish(double* err);
+  int iter_end();
+  bool iter_ready() const { return root_out && cudaEventQuery(root_out) == cudaSuccess; }
   int contract_batch(const std::vector<std::vector<std::array<int, 2>>>& coords, const std::vector<OpList>& ops,
                      std::vector<double>& logscale, std::vector<double>& re, std::vector<double>& im);
   int bond_region(int g1, int k1, std::vector<std::array<int, 2>>& coords, std::array<int, 2>& key1,
@@ -134,7 +141,7 @@ class Engine {
   template <typename C> int run_sweep(SweepJob& job, SweepWork& w);
   template <typename C>
   int finalize_message(Message& m, int which, SweepWork& w, cudaStream_t s, double* dist_slot, bool with_distance);
-  template <typename C> int iterate_t(double tol, int max_iter, int* iters, double* err);
+  template <typename C> int iter_launch_t();
   template <typename C>
   int contract_batch_t(const std::vector<std::vector<std::array<int, 2>>>& coords, const std::vector<OpList>& ops,
                        std::vector<double>& logscale, std::vector<double>& re, std::vector<double>& im);
@@ -150,8 +157,12 @@ class Engine {
     double flops = 0.0;
   };
   IterGraph graphs[2];
-  cudaStream_t root = nullptr;         // private capture root (the caller's stream may be the legacy one)
-  cudaEvent_t root_in = nullptr, root_out = nullptr;
+  cudaStream_t root = nullptr;         // private root of every iteration (and of its capture)
+  cudaEvent_t root_in = nullptr, root_in2 = nullptr, root_out = nullptr;
+  double* h_dist = nullptr;            // pinned: per-update distances, then 2 status ints per update
+  size_t h_cap = 0;
+  bool in_flight = false;
+  int launched_parity = 0;
   long long graph_tag(int parity) const { return (long long)(((uintptr_t)this >> 4) * 2 + (uintptr_t)parity); }
 
  public:

@@ -1244,10 +1244,14 @@ cudaError_t launch_svd_trunc(const double2* Z, int m, int n, int chi, double2* U
 static double jacobi_tol_c64(int N) { return std::max(2e-6, 3e-7 * std::sqrt((double)N)); }
 
 // complex64: randomised reduction when the matrix is large, else plain Jacobi
+// Reduced size of the randomised truncation: b = chi + max(8, chi / 2)
+// directions; matrices whose smaller side is at most max(2 b, 64) take the
+// exact Jacobi path instead (returns min(m, n)), where the subspace
+// iteration would save little and its accuracy depends on the spectrum.
 int rand_block(int m, int n, int chi) {
-  int M = m < n ? m : n;
-  int b = chi + (chi >= 16 ? chi / 2 : 8);
-  return b < M ? b : M;
+  const int M = m < n ? m : n;
+  const int b = chi + (chi >= 16 ? chi / 2 : 8);
+  return (M <= std::max(2 * b, 64)) ? M : b;
 }
 
 size_t svd_work_bytes_c64(int m, int n, int chi) {
