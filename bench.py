@@ -105,8 +105,9 @@ class ClockSampler:
 # BF16 burst figure (TF32 at half the BF16 rate).
 KERNELS = {
     "jacobi": (1, "one-sided Jacobi SVD of the reduced matrix (k_jacobi_smem / k_jacobi)"),
-    "orth": (2, "range orthonormalisation, Householder in shared memory (k_orth_smem)"),
-    "qr": (3, "Householder QR of the canonical moves (k_qr_smem / k_qr)"),
+    "orth": (2, "range orthonormalisation of the randomised truncation, Householder panel in shared memory "
+                "(k_tsqr_reg, one CTA per panel)"),
+    "qr": (3, "Householder QR of the canonical moves and distances (k_tsqr_reg / k_tsqr_smem)"),
     "tc": (4, "tcgen05 split-precision absorb GEMM (k_tc_gemm)"),
     "absorb": (5, "SIMT complex absorb GEMM (k_gemm)"),
     "gemm": (6, "every SIMT complex GEMM (k_gemm)"),
@@ -172,15 +173,19 @@ def run_ours(args, rank, world):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0 = time.perf_counter()
         torch.cuda.nvtx.range_push("timed")     # lets a profiler select the timed launches
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         e0.record(stream)
-        for _ in range(args.steps):
+        for i in range(args.steps):
             flush.zero_()
+            marks[i].record(stream)
             P.bbp_iterate(ctx, 0.0, 1)
+        marks[args.steps].record(stream)
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         host_secs = time.perf_counter() - h0
     secs = e0.elapsed_time(e1) * 1e-3
+    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
     launches, flops_iter = P.bbp_stats(ctx)
     # second pass, same steps, with the dominant kernel class bracketed by
     # CUDA events on its own streams (events in the graph perturb the step,
@@ -239,15 +244,149 @@ def run_ours(args, rank, world):
         per_launch_s = k_ms * 1e-3 / k_n
         achieved = k_flops / k_n / per_launch_s / 1e12
         roof = {"bound": bound, "achieved": achieved, "peak": pk[key], "unit": unit, "frac": achieved / pk[key],
+                # the factorisation kernels run one CTA per launch on one SM
+                "frac_of_one_sm": achieved / (pk[key] / 152),
                 "traffic": None, "kernel": kdesc, "peak_kind": key + (" tensor, measured bf16 burst" if bound == "tensor"
                                                                       else " ALU, unit counts x 2.07 GHz"),
                 "launches_per_step": k_n / args.steps, "launch_us": per_launch_s * 1e6,
                 "kernel_ms_per_step_all_streams": k_ms / args.steps,
                 "timer_pass_ms_per_step": 1e3 * timer_pass_secs / args.steps}
     return {
-        "value": value, "secs": secs, "host_secs": host_secs, "n_updates": n_updates, "n_sites": n_sites, "energy": energy,
+        "value": value, "secs": secs, "host_secs": host_secs, "step_ms": step_ms, "n_updates": n_updates, "n_sites": n_sites, "energy": energy,
         "clocks": clk.summary(), "launches": launches, "flops_iter": flops_iter, "e2e": e2e, "roofline": roof,
     }
+
+
+# -------------------------------------------------- many networks, serving
+
+def job_mix(n, seed, precision, max_D=4, chis=(8, 16, 32)):
+    """A seeded mix of small BlockBP problems: square 4x4 (2x2 blocks) and
+    6x6 (3x3 blocks) open lattices with i.i.d. Gaussian tensors normalised
+    by their largest singular value, and the Kagome 6x2 super-cell (L = 2)
+    near a random dimer-singlet state with 1e-2 noise; D uniform in
+    2..max_D, chi uniform in `chis`."""
+    import numpy as np
+    import synthetic as syn
+    import paper_2603_13304_gb300 as P
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(n):
+        kind = rng.integers(3)
+        D = int(rng.integers(2, max_D + 1))
+        chi = int(rng.choice(chis))
+        s = int(rng.integers(1 << 30))
+        if kind == 0:
+            t = syn.gaussian_peps(16, 2, D, seed=s)
+            jobs.append(dict(lattice=P.SQUARE, Lx=4, Ly=4, periodic=0, bx=2, by=2, D=D, chi=chi, t=t,
+                             em=syn.initial_edge_matrices(16, D, seed=s + 1)))
+        elif kind == 1:
+            t = syn.gaussian_peps(36, 2, D, seed=s)
+            jobs.append(dict(lattice=P.SQUARE, Lx=6, Ly=6, periodic=0, bx=3, by=3, D=D, chi=chi, t=t,
+                             em=syn.initial_edge_matrices(36, D, seed=s + 1)))
+        else:
+            nb = syn.kagome_neighbours(6, 2)
+            t = syn.dimer_singlet_peps(nb, 2, D, seed=s, noise=1e-2, noise_seed=s + 1)
+            jobs.append(dict(lattice=P.KAGOME, Lx=6, Ly=2, periodic=1, bx=2, by=2, D=D, chi=chi, t=t,
+                             em=syn.initial_edge_matrices(36, D, seed=s + 2)))
+        jobs[-1]["precision"] = precision
+    return jobs
+
+
+def run_batched(n_networks, steps, warmup, precision):
+    """All message updates of n_networks independent networks, one
+    synchronous iteration of every network per round (bbp_batch_iterate)."""
+    import torch
+    import paper_2603_13304_gb300 as P
+    jobs = job_mix(n_networks, 4, precision)
+    ctxs = []
+    n_updates = 0
+    for j in jobs:
+        c = P.bbp_create_peps(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["t"])
+        P.bbp_partition_blocks(c, j["bx"], j["by"])
+        P.bbp_set_options(c, j["chi"], precision)
+        P.bbp_set_execution(c, True, 2)
+        P.bbp_init_messages(c, j["em"])
+        n_updates += P.bbp_info(c)[1]
+        ctxs.append(c)
+    for _ in range(warmup + 4):          # settle the bond dimensions, capture the graphs
+        P.bbp_batch_iterate(ctxs, 0.0, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(steps):
+        P.bbp_batch_iterate(ctxs, 0.0, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    host = time.perf_counter() - t0
+    secs = e0.elapsed_time(e1) * 1e-3
+    for c in ctxs:
+        P.bbp_destroy(c)
+    return {"networks": n_networks, "message_updates_per_round": n_updates, "rounds": steps,
+            "value": n_updates * steps / max(secs, host), "unit": "message updates/s",
+            "ms_per_round": 1e3 * max(secs, host) / steps,
+            "mix": "square 4x4 (2x2 blocks) / 6x6 (3x3 blocks), Kagome 6x2 (L=2); D 2..4, chi 8/16/32; seed 4"}
+
+
+def run_serving(n_jobs, rate, precision, tol=1e-6, max_iter=40):
+    """Poisson arrivals (seed 5) of a job mix into the server; each job runs
+    to tol; returns throughput and latency percentiles, and the same trace
+    run one job at a time (bbp_iterate on each in arrival order)."""
+    import numpy as np
+    import torch
+    import paper_2603_13304_gb300 as P
+    jobs = job_mix(n_jobs, 5, precision, max_D=3, chis=(8, 16))
+    rng = np.random.default_rng(5)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
+    srv = P.bbp_server_create(200 << 30, 64)
+    lat, waits, iters, stat = {}, {}, {}, {}
+    t0 = time.perf_counter()
+    nxt = 0
+    ids = {}
+    while len(lat) < n_jobs:
+        now = time.perf_counter() - t0
+        while nxt < n_jobs and arrivals[nxt] <= now:
+            j = jobs[nxt]
+            job = P.make_job(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["bx"], j["by"], j["chi"],
+                             precision, j["t"], j["em"], tol, max_iter, 2, 1)
+            ids[P.bbp_server_submit(srv, job)] = nxt
+            nxt += 1
+        P.bbp_server_step(srv, 2.0)
+        for r in P.bbp_server_poll(srv):
+            k = ids[r["id"]]
+            lat[k], waits[k], iters[k], stat[k] = r["latency_s"], r["wait_s"], r["iters"], r["status"]
+            P.bbp_server_take(srv, r["id"])
+    wall = time.perf_counter() - t0
+    P.bbp_server_destroy(srv)
+    # the same trace, one job at a time
+    t1 = time.perf_counter()
+    seq_lat = []
+    clock = 0.0
+    for k, j in enumerate(jobs):
+        start = max(clock, arrivals[k])
+        s0 = time.perf_counter()
+        c = P.bbp_create_peps(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["t"])
+        P.bbp_partition_blocks(c, j["bx"], j["by"])
+        P.bbp_set_options(c, j["chi"], precision)
+        P.bbp_init_messages(c, j["em"])
+        try:
+            P.bbp_iterate(c, tol, max_iter)
+        except P.BBPError:
+            pass
+        torch.cuda.synchronize()
+        P.bbp_destroy(c)
+        clock = start + (time.perf_counter() - s0)
+        seq_lat.append(clock - arrivals[k])
+    seq_wall = time.perf_counter() - t1
+    L = np.array([lat[k] for k in range(n_jobs)])
+    S = np.array(seq_lat)
+    return {"jobs": n_jobs, "arrival_rate_per_s": rate, "tol": tol, "max_iter": max_iter,
+            "throughput_jobs_per_s": n_jobs / wall, "p50_ms": 1e3 * float(np.percentile(L, 50)),
+            "p99_ms": 1e3 * float(np.percentile(L, 99)), "mean_iters": float(np.mean([iters[k] for k in iters])),
+            "converged": int(sum(1 for k in stat if stat[k] == 0)),
+            "one_at_a_time": {"throughput_jobs_per_s": n_jobs / seq_wall, "p50_ms": 1e3 * float(np.percentile(S, 50)),
+                              "p99_ms": 1e3 * float(np.percentile(S, 99))},
+            "mix": "square 4x4 / 6x6, Kagome 6x2; D 2..3, chi 8/16; seed 5; 2 streams per job"}
 
 
 # ---------------------------------------------------------------- oracle
@@ -288,8 +427,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16", "fp32", "fp64"])
-    ap.add_argument("--roofline-kernel", default="jacobi", choices=sorted(KERNELS))
+    ap.add_argument("--roofline-kernel", default="orth", choices=sorted(KERNELS))
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--batch", type=int, default=64, help="networks in the batched measurement (0: skip)")
+    ap.add_argument("--serve", type=int, default=48, help="jobs in the serving measurement (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -336,10 +478,14 @@ def main():
         v, dt, n = oracle_sample(w, 3)
         cpu = {"value": v, "unit": "message updates/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"3 full iterations ({n} message updates, full-bond inputs; {dt:.1f} s of CPU work)"}
+    prec_code = {"tf32": 1, "bf16": 2, "fp32": 3, "fp64": 0}[args.precision]
+    batched = run_batched(args.batch, args.steps, args.warmup, prec_code) if args.batch > 0 and world == 1 else None
+    serving = run_serving(args.serve, args.serve_rate, prec_code) if args.serve > 0 and world == 1 else None
     line = {
         "metric": "BlockBP message updates/s", "value": res["value"], "unit": "message updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * res["secs"] / args.steps, "host_ms_per_step": 1e3 * res["host_secs"] / args.steps,
+        "step_ms": [round(x, 3) for x in res["step_ms"]],
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "c128", "fp32": "c64+f64", "tf32": "tf32x3+c64+f64", "bf16": "bf16x3+c64+f64"}[args.precision], "data": "synthetic",
         "config": dict(config, precision=args.precision,
@@ -348,6 +494,7 @@ def main():
         "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["launches"] * args.steps,
         "roofline": res["roofline"], "cpu_baseline": cpu,
         "energy_per_site": res["energy"], "absorb_tflop_per_step": res["flops_iter"] / 1e12,
+        "batched": batched, "serving": serving,
     }
     print(json.dumps(line))
     if world > 1:
