@@ -127,6 +127,19 @@ def peaks():
             "tf32": bf16 / 2}
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (a replicated job takes as long as its
+    slowest rank); works on whichever backend the process group uses."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -203,11 +216,7 @@ def run_ours(args, rank, world):
     timer_pass_secs = time.perf_counter() - t1
     k_n, k_ms, k_flops = P.bbp_ktimer_read()
     P.bbp_ktimer_select(0)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([secs], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        secs = float(tt.item())
+    secs = max_over_ranks(secs, world)
     value = world * n_updates * args.steps / secs
     energy = P.bbp_energy_per_site(ctx) if rank == 0 else None
     P.bbp_destroy(ctx)

@@ -175,6 +175,39 @@ unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int
   return h;
 }
 
+// What a captured iteration reads, without simulating it: every message's
+// current shapes and buffers, the fused tensors' buffers and the workspaces.
+// Equal input signatures imply equal job signatures (the plans are fixed).
+unsigned long long Engine::input_signature(int nstreams) const {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xff;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((unsigned long long)precision);
+  mix((unsigned long long)tc_mode);
+  mix((unsigned long long)chi);
+  mix((unsigned long long)power_iters);
+  mix((unsigned long long)nstreams);
+  mix((unsigned long long)(uintptr_t)dist_dev.p);
+  for (int i = 0; i < nstreams && i < (int)pool.size(); ++i) mix((unsigned long long)(uintptr_t)pool[i]->arena.p);
+  for (const auto& kv : msgs) {
+    const Message& m = kv.second;
+    mix((unsigned long long)m.cur);
+    mix((unsigned long long)(uintptr_t)m.buf[0].p);
+    mix((unsigned long long)(uintptr_t)m.buf[1].p);
+    for (const TShape& t : m.sh[m.cur]) {
+      mix((unsigned long long)t.l);
+      mix((unsigned long long)t.p);
+      mix((unsigned long long)t.r);
+    }
+  }
+  for (const auto& kv : fused) mix((unsigned long long)(uintptr_t)kv.second.p);
+  return h;
+}
+
 Engine::~Engine() {
   drop_graphs();
   if (root) {
@@ -786,6 +819,25 @@ int Engine::iter_launch_t() {
     if (!work(i)) return fail(this, 3, "stream creation failed");
   sweep_launches = 0;
   sweep_flops = 0.0;
+  if (use_graphs) {
+    // replay without rebuilding the jobs when nothing the graph reads changed
+    const int par = 1 - msgs.at({ups[0].recv_block, ups[0].recv_face}).cur;
+    IterGraph& g = graphs[par];
+    if (g.exec && g.in_sig == input_signature(nstreams) && (int)g.out_shapes.size() == nu) {
+      for (int u = 0; u < nu; ++u) msgs.at({ups[u].recv_block, ups[u].recv_face}).sh[par] = g.out_shapes[u];
+      CK(cudaGraphLaunch(g.exec, root));
+      sweep_launches = g.launches;
+      sweep_flops = g.flops;
+      double* hd = h_dist;
+      int* hs = (int*)(h_dist + nu);
+      CK(cudaMemcpyAsync(hd, dist_dev.p, sizeof(double) * nu, cudaMemcpyDeviceToHost, root));
+      CK(cudaMemcpyAsync(hs, status_dev, 2 * sizeof(int) * nu, cudaMemcpyDeviceToHost, root));
+      CK(cudaEventRecord(root_out, root));
+      launched_parity = par;
+      in_flight = true;
+      return 0;
+    }
+  }
   std::vector<DBuf*> tmp;
   std::vector<SweepJob> jobs(nu);
   int rc = 0;
@@ -798,6 +850,7 @@ int Engine::iter_launch_t() {
   }
   for (DBuf* b : tmp) delete b;      // no operator insertions in an iteration
   if (rc) return rc;
+  const unsigned long long in_sig = input_signature(nstreams);   // before the destinations change shape
   // destinations and their shapes (host bookkeeping, also when replaying)
   int parity = 0;
   for (int u = 0; u < nu; ++u) {
@@ -868,6 +921,9 @@ int Engine::iter_launch_t() {
       g.launches = sweep_launches;
       g.flops = sweep_flops;
     }
+    g.in_sig = in_sig;
+    g.out_shapes.resize(nu);
+    for (int u = 0; u < nu; ++u) g.out_shapes[u] = jobs[u].tr.final_mps;
     cudaError_t le = cudaGraphLaunch(g.exec, root);
     if (le != cudaSuccess) return fail(this, 3, std::string("graph launch: ") + cudaGetErrorString(le));
     sweep_launches = g.launches;

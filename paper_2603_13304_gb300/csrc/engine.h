@@ -152,10 +152,13 @@ class Engine {
   // signature (shapes and device pointers of every job) is unchanged
   struct IterGraph {
     unsigned long long sig = 0;
+    unsigned long long in_sig = 0;     // inputs only: message shapes and buffers, workspaces
     cudaGraphExec_t exec = nullptr;
     long long launches = 0;
     double flops = 0.0;
+    std::vector<std::vector<TShape>> out_shapes;   // per update: the outgoing message's shapes
   };
+  unsigned long long input_signature(int nstreams) const;
   IterGraph graphs[2];
   cudaStream_t root = nullptr;         // private root of every iteration (and of its capture)
   cudaEvent_t root_in = nullptr, root_in2 = nullptr, root_out = nullptr;

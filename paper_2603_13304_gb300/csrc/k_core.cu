@@ -1413,34 +1413,42 @@ __global__ void k_permute3(const C* __restrict__ src, int d0, int d1, int d2, in
 
 // ---------------------------------------------------------------------- K4
 // <M|M> by the transfer chain, <I|M> by the identity chain (both in
-// complex128); the first tensor is scaled by |tr| / (tr sqrt(<M|M>)).  One CTA.
+// complex128); the first tensor is scaled by |tr| / (tr sqrt(<M|M>)).
+// One cluster of kK4Cluster CTAs: every phase of a transfer step splits its
+// outputs over the cluster's threads and ends at a cluster barrier (the
+// intermediates live in the global work buffer), so the complex128 work of
+// one message runs on kK4Cluster SMs' FP64 units.
+constexpr int kK4Cluster = 8;
+
 template <typename C>
 __global__ void __launch_bounds__(256) k_msg_normalise(ChainDesc d, double2* work) {
-  __shared__ double2 s_fac;
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
+  const int tid = crank * blockDim.x + threadIdx.x, nth = csize * blockDim.x;
   double2* E = work;                   // l x l
   double2* E2 = work + 64 * 64;        // r x r
   double2* F = work + 2 * 64 * 64;     // l x p x r scratch
-  double2* v = work + 2 * 64 * 64 + 64 * 64 * 64;   // identity chain (2 x 64)
-  if (threadIdx.x == 0) { E[0] = make_double2(1.0, 0.0); v[0] = make_double2(1.0, 0.0); }
-  __syncthreads();
+  double2* v = work + 2 * 64 * 64 + 64 * 64 * 64;   // identity chain (2 x 64), then the factor at v[128]
+  if (tid == 0) { E[0] = make_double2(1.0, 0.0); v[0] = make_double2(1.0, 0.0); }
+  cl.sync();
   for (int q = 0; q < d.k; ++q) {
     const int l = d.l[q], p = d.p[q], r = d.r[q];
     const C* A = (const C*)d.T[q];
-    for (long long e = threadIdx.x; e < (long long)l * p * r; e += blockDim.x) {
+    for (long long e = tid; e < (long long)l * p * r; e += nth) {
       int l2 = (int)(e / ((long long)p * r)), pp = (int)((e / r) % p), r1 = (int)(e % r);
       double2 s = make_double2(0.0, 0.0);
       for (int l1 = 0; l1 < l; ++l1) s = cadd(s, cmulc(c128(A[((long long)l1 * p + pp) * r + r1]), E[l1 * l + l2]));
       F[e] = s;
     }
-    __syncthreads();
     const int D = d.D[q];
-    for (int e = threadIdx.x; e < r; e += blockDim.x) {
+    for (int e = tid; e < r; e += nth) {
       double2 s = make_double2(0.0, 0.0);
       for (int a = 0; a < l; ++a)
         for (int kk = 0; kk < D; ++kk) s = cadd(s, cmul(v[a], c128(A[((long long)a * p + kk * D + kk) * r + e])));
       v[64 + e] = s;
     }
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    cl.sync();
+    for (int e = tid; e < r * r; e += nth) {
       int r1 = e / r, r2 = e % r;
       double2 s = make_double2(0.0, 0.0);
       for (int l2 = 0; l2 < l; ++l2)
@@ -1448,24 +1456,24 @@ __global__ void __launch_bounds__(256) k_msg_normalise(ChainDesc d, double2* wor
           s = cadd(s, cmul(F[((long long)l2 * p + pp) * r + r1], c128(A[((long long)l2 * p + pp) * r + r2])));
       E2[e] = s;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) E[e] = E2[e];
-    for (int e = threadIdx.x; e < r; e += blockDim.x) v[e] = v[64 + e];
-    __syncthreads();
+    cl.sync();
+    for (int e = tid; e < r * r; e += nth) E[e] = E2[e];
+    for (int e = tid; e < r; e += nth) v[e] = v[64 + e];
+    cl.sync();
   }
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double nrm2 = E[0].x;
     double2 tr = v[0];
     double at = sqrt(tr.x * tr.x + tr.y * tr.y);
     double2 f = make_double2(nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 1.0, 0.0);
     if (at > 0.0) f = cmul(f, make_double2(tr.x / at, -tr.y / at));   // |tr| / tr
-    s_fac = f;
+    v[128] = f;
   }
-  __syncthreads();
-  const double2 f = s_fac;
+  cl.sync();
+  const double2 f = v[128];
   C* T0 = (C*)d.T[0];
   const long long n0 = (long long)d.l[0] * d.p[0] * d.r[0];
-  for (long long e = threadIdx.x; e < n0; e += blockDim.x) {
+  for (long long e = tid; e < n0; e += nth) {
     double2 x = cmul(c128(T0[e]), f);
     T0[e] = cx<C>(x.x, x.y);
   }
@@ -1506,27 +1514,30 @@ __global__ void __launch_bounds__(1024) k_frob(const C* R, long long n, double* 
 }
 
 // value = sum prod A_q B_q over shared legs: E'[x][y] = sum_{i,j,p} E[i][j] a[i][p][x] b[j][p][y],
-// in two steps through F[j][p][x] = sum_i E[i][j] a[i][p][x].  One CTA; work as for K4.
+// in two steps through F[j][p][x] = sum_i E[i][j] a[i][p][x].  One cluster of
+// kK4Cluster CTAs (phases separated by cluster barriers); work as for K4.
 template <typename C>
 __global__ void __launch_bounds__(256) k_mps_dot(ChainDesc A, ChainDesc B, double2* work, double2* out) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int tid = (int)cl.block_rank() * blockDim.x + threadIdx.x, nth = (int)cl.num_blocks() * blockDim.x;
   double2* E = work;
   double2* E2 = work + 64 * 64;
   double2* F = work + 2 * 64 * 64;
-  if (threadIdx.x == 0) E[0] = make_double2(1.0, 0.0);
-  __syncthreads();
+  if (tid == 0) E[0] = make_double2(1.0, 0.0);
+  cl.sync();
   for (int q = 0; q < A.k; ++q) {
     const int p = A.p[q], ra = A.r[q], rb = B.r[q];
     const int la = A.l[q], lb = B.l[q];
     const C* a = (const C*)A.T[q];
     const C* b = (const C*)B.T[q];
-    for (long long e = threadIdx.x; e < (long long)lb * p * ra; e += blockDim.x) {
+    for (long long e = tid; e < (long long)lb * p * ra; e += nth) {
       int j = (int)(e / ((long long)p * ra)), pp = (int)((e / ra) % p), x = (int)(e % ra);
       double2 s = make_double2(0.0, 0.0);
       for (int i = 0; i < la; ++i) s = cadd(s, cmul(E[i * lb + j], c128(a[((long long)i * p + pp) * ra + x])));
       F[e] = s;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < ra * rb; e += blockDim.x) {
+    cl.sync();
+    for (int e = tid; e < ra * rb; e += nth) {
       int x = e / rb, y = e % rb;
       double2 s = make_double2(0.0, 0.0);
       for (int j = 0; j < lb; ++j)
@@ -1534,11 +1545,11 @@ __global__ void __launch_bounds__(256) k_mps_dot(ChainDesc A, ChainDesc B, doubl
           s = cadd(s, cmul(F[((long long)j * p + pp) * ra + x], c128(b[((long long)j * p + pp) * rb + y])));
       E2[e] = s;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < ra * rb; e += blockDim.x) E[e] = E2[e];
-    __syncthreads();
+    cl.sync();
+    for (int e = tid; e < ra * rb; e += nth) E[e] = E2[e];
+    cl.sync();
   }
-  if (threadIdx.x == 0) *out = E[0];
+  if (tid == 0) *out = E[0];
 }
 }  // namespace
 
@@ -1579,16 +1590,36 @@ BBP_INSTANTIATE(double2)
 BBP_INSTANTIATE(float2)
 
 cudaError_t launch_msg_normalise(const ChainDesc& m, bool c64, double2* work, cudaStream_t s) {
-  if (c64) k_msg_normalise<float2><<<1, 256, 0, s>>>(m, work);
-  else k_msg_normalise<double2><<<1, 256, 0, s>>>(m, work);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kK4Cluster, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kK4Cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (c64) return cudaLaunchKernelEx(&cfg, k_msg_normalise<float2>, m, work);
+  return cudaLaunchKernelEx(&cfg, k_msg_normalise<double2>, m, work);
 }
 
 cudaError_t launch_mps_dot(const ChainDesc& a, const ChainDesc& b, bool c64, double2* work, double2* out,
                            cudaStream_t s) {
-  if (c64) k_mps_dot<float2><<<1, 256, 0, s>>>(a, b, work, out);
-  else k_mps_dot<double2><<<1, 256, 0, s>>>(a, b, work, out);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kK4Cluster, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kK4Cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (c64) return cudaLaunchKernelEx(&cfg, k_mps_dot<float2>, a, b, work, out);
+  return cudaLaunchKernelEx(&cfg, k_mps_dot<double2>, a, b, work, out);
 }
 
 // Large-shared-memory opt-ins of every staged kernel on the current device
