@@ -834,6 +834,7 @@ int Engine::iter_launch_t() {
       CK(cudaMemcpyAsync(hs, status_dev, 2 * sizeof(int) * nu, cudaMemcpyDeviceToHost, root));
       CK(cudaEventRecord(root_out, root));
       launched_parity = par;
+      launched_graph = true;
       in_flight = true;
       return 0;
     }
@@ -887,7 +888,14 @@ int Engine::iter_launch_t() {
     CK(cudaEventCreateWithFlags(&root_in2, cudaEventDisableTiming));
     fork = root_in2;
   }
-  if (!use_graphs) {
+  // capture only once the inputs repeat: while the bond dimensions still
+  // grow (the first iterations from bond-1 messages) every iteration would
+  // need a new graph, and instantiating it costs more than launching eagerly
+  const bool stable = in_sig == last_in_sig[parity];
+  last_in_sig[parity] = in_sig;
+  const bool replayable = graphs[parity].exec && graphs[parity].sig == iter_signature(jobs, nstreams);
+  launched_graph = use_graphs && (stable || replayable);
+  if (!launched_graph) {
     rc = enqueue();
   } else {
     IterGraph& g = graphs[parity];
@@ -950,7 +958,7 @@ int Engine::iter_finish(double* err_out) {
   if (!in_flight) return fail(this, 8, "no iteration in flight");
   in_flight = false;
   CK(cudaEventSynchronize(root_out));
-  if (ktimer_class()) ktimer_collect(use_graphs ? graph_tag(launched_parity) : -1);
+  if (ktimer_class()) ktimer_collect(launched_graph ? graph_tag(launched_parity) : -1);
   const double* hd = h_dist;
   const int* hs = (const int*)(h_dist + nu);
   double err = 0.0;

@@ -160,11 +160,13 @@ class Engine {
   };
   unsigned long long input_signature(int nstreams) const;
   IterGraph graphs[2];
+  unsigned long long last_in_sig[2] = {0, 0};   // inputs of the last iteration of each parity
   cudaStream_t root = nullptr;         // private root of every iteration (and of its capture)
   cudaEvent_t root_in = nullptr, root_in2 = nullptr, root_out = nullptr;
   double* h_dist = nullptr;            // pinned: per-update distances, then 2 status ints per update
   size_t h_cap = 0;
   bool in_flight = false;
+  bool launched_graph = false;         // the iteration in flight is a graph replay
   int launched_parity = 0;
   long long graph_tag(int parity) const { return (long long)(((uintptr_t)this >> 4) * 2 + (uintptr_t)parity); }
 
