@@ -9,10 +9,13 @@
 // fits the budget and a slot is free, keeps every admitted job's messages
 // resident, relaunches each job as soon as its previous iteration has
 // completed (no round barrier), and retires a job when its message error
-// reaches its tolerance, its iteration limit is hit, or it fails.
+// reaches its tolerance, its iteration limit is hit, or it fails.  The host
+// work of different contexts (context set-up, sweep preparation, graph
+// capture, launches) runs on a few host threads at once.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -32,6 +35,34 @@ double now_s() {
 }
 
 int n_sites_of(int lattice, int Lx, int Ly) { return lattice == BBP_KAGOME ? 3 * Lx * Ly : Lx * Ly; }
+
+// Host threads that prepare and enqueue the iterations of different
+// contexts at once: a context's host work (shape simulation, graph capture
+// or eager launches) is independent of every other context's.
+int host_threads() {
+  static const int n = [] {
+    const unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(8u, h ? h : 1u));
+  }();
+  return n;
+}
+
+template <typename F>
+void parallel_for(size_t n, F&& f) {
+  const int T = (int)std::min<size_t>(n, (size_t)host_threads());
+  if (T <= 1) {
+    for (size_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<size_t> next{0};
+  std::vector<std::thread> ts;
+  ts.reserve(T);
+  for (int t = 0; t < T; ++t)
+    ts.emplace_back([&] {
+      for (size_t i; (i = next.fetch_add(1)) < n;) f(i);
+    });
+  for (auto& t : ts) t.join();
+}
 
 }  // namespace
 
@@ -54,11 +85,18 @@ extern "C" bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int m
       else active.push_back(i);
     }
     for (int round = 0; round < max_iter && !active.empty(); ++round) {
+      std::vector<int> rcs(active.size(), 0);
+      parallel_for(active.size(), [&](size_t a) {
+        try {
+          rcs[a] = ctxs[active[a]]->eng.iter_launch();
+        } catch (...) {
+          rcs[a] = BBP_ERR_CUDA;
+        }
+      });
       std::vector<int> launched;
-      for (int i : active) {
-        const int rc = ctxs[i]->eng.iter_launch();
-        if (rc) status_out[i] = rc;
-        else launched.push_back(i);
+      for (size_t a = 0; a < active.size(); ++a) {
+        if (rcs[a]) status_out[active[a]] = rcs[a];
+        else launched.push_back(active[a]);
       }
       std::vector<int> next;
       for (int i : launched) {
@@ -214,27 +252,47 @@ extern "C" bbp_status bbp_server_step(bbp_server* s, double timeout_ms, int* n_q
   if (!s) return BBP_ERR_ARG;
   try {
     // admission: arrival order, footprint within budget, free slot
-    while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
+    std::vector<bbp_server::Job*> admitted;
+    while (!s->queue.empty() && (int)(s->active.size() + admitted.size()) < s->max_active) {
       bbp_server::Job* j = s->queue.front();
-      if (s->used + j->bytes > s->budget && !s->active.empty()) break;
+      if (s->used + j->bytes > s->budget && !(s->active.empty() && admitted.empty())) break;
       s->queue.pop_front();
       s->used += j->bytes;
       j->t_start = now_s();
-      const int rc = start_job(j);
-      if (rc) {
-        j->status = rc;
+      admitted.push_back(j);
+    }
+    std::vector<int> rcs(admitted.size(), 0);
+    parallel_for(admitted.size(), [&](size_t a) {
+      try {
+        rcs[a] = start_job(admitted[a]);
+      } catch (...) {
+        rcs[a] = BBP_ERR_CUDA;
+      }
+    });
+    for (size_t a = 0; a < admitted.size(); ++a) {
+      bbp_server::Job* j = admitted[a];
+      if (rcs[a]) {
+        j->status = rcs[a];
         j->t_done = now_s();
         s->finished.push_back(j);
       } else {
         s->active.push_back(j);
       }
     }
-    for (bbp_server::Job* j : s->active) {
-      if (j->in_flight) continue;
-      const int rc = j->ctx->eng.iter_launch();
+    std::vector<bbp_server::Job*> idle;
+    for (bbp_server::Job* j : s->active)
+      if (!j->in_flight && j->status == BBP_OK) idle.push_back(j);
+    parallel_for(idle.size(), [&](size_t a) {
+      bbp_server::Job* j = idle[a];
+      int rc;
+      try {
+        rc = j->ctx->eng.iter_launch();
+      } catch (...) {
+        rc = BBP_ERR_CUDA;
+      }
       if (rc) j->status = rc;
       else j->in_flight = true;
-    }
+    });
     const double t0 = now_s();
     std::vector<bbp_server::Job*> keep;
     for (; !s->active.empty();) {
