@@ -168,7 +168,10 @@ size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int
 bbp_status bbp_info(bbp_ctx* ctx, int* n_blocks, int* n_updates, int* n_sites);
 
 /* Statistics of the last bbp_iterate call: kernel launches per iteration and
- * the algorithmic flops of one iteration (see the design doc for the flop model). */
+ * the algorithmic flops of one iteration, counted as 8 l P Q r real flops for
+ * every absorb contraction (one complex multiply-add = 8 flops; l, r the
+ * outer bonds of the merged segment, P, Q the in- and out-leg products);
+ * factorisations are not counted. */
 bbp_status bbp_stats(bbp_ctx* ctx, long long* launches_per_iter, double* flops_per_iter);
 
 const char* bbp_last_error(const bbp_ctx* ctx);
