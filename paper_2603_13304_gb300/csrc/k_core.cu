@@ -1419,6 +1419,7 @@ __global__ void k_permute3(const C* __restrict__ src, int d0, int d1, int d2, in
 // intermediates live in the global work buffer), so the complex128 work of
 // one message runs on kK4Cluster SMs' FP64 units.
 constexpr int kK4Cluster = 8;
+constexpr int kK4Split = 4;   // lanes per output of the r x r phase (divides 32)
 
 template <typename C>
 __global__ void __launch_bounds__(256) k_msg_normalise(ChainDesc d, double2* work) {
@@ -1448,13 +1449,21 @@ __global__ void __launch_bounds__(256) k_msg_normalise(ChainDesc d, double2* wor
       v[64 + e] = s;
     }
     cl.sync();
-    for (int e = tid; e < r * r; e += nth) {
-      int r1 = e / r, r2 = e % r;
+    // r x r outputs of l p terms each: kK4Split consecutive lanes share one
+    // output (strided terms, shuffle sum), so every thread has work
+    for (int eb = (tid >> 5) * (32 / kK4Split); eb < r * r; eb += (nth >> 5) * (32 / kK4Split)) {
+      const int e = eb + (threadIdx.x & 31) / kK4Split, sub = threadIdx.x % kK4Split;
       double2 s = make_double2(0.0, 0.0);
-      for (int l2 = 0; l2 < l; ++l2)
-        for (int pp = 0; pp < p; ++pp)
-          s = cadd(s, cmul(F[((long long)l2 * p + pp) * r + r1], c128(A[((long long)l2 * p + pp) * r + r2])));
-      E2[e] = s;
+      if (e < r * r) {
+        const int r1 = e / r, r2 = e % r;
+        for (int t = sub; t < l * p; t += kK4Split)
+          s = cadd(s, cmul(F[(long long)t * r + r1], c128(A[(long long)t * r + r2])));
+      }
+      for (int o = 1; o < kK4Split; o <<= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (e < r * r && sub == 0) E2[e] = s;
     }
     cl.sync();
     for (int e = tid; e < r * r; e += nth) E[e] = E2[e];
@@ -1537,13 +1546,19 @@ __global__ void __launch_bounds__(256) k_mps_dot(ChainDesc A, ChainDesc B, doubl
       F[e] = s;
     }
     cl.sync();
-    for (int e = tid; e < ra * rb; e += nth) {
-      int x = e / rb, y = e % rb;
+    for (int eb = (tid >> 5) * (32 / kK4Split); eb < ra * rb; eb += (nth >> 5) * (32 / kK4Split)) {
+      const int e = eb + (threadIdx.x & 31) / kK4Split, sub = threadIdx.x % kK4Split;
       double2 s = make_double2(0.0, 0.0);
-      for (int j = 0; j < lb; ++j)
-        for (int pp = 0; pp < p; ++pp)
-          s = cadd(s, cmul(F[((long long)j * p + pp) * ra + x], c128(b[((long long)j * p + pp) * rb + y])));
-      E2[e] = s;
+      if (e < ra * rb) {
+        const int x = e / rb, y = e % rb;
+        for (int t = sub; t < lb * p; t += kK4Split)
+          s = cadd(s, cmul(F[(long long)t * ra + x], c128(b[(long long)t * rb + y])));
+      }
+      for (int o = 1; o < kK4Split; o <<= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (e < ra * rb && sub == 0) E2[e] = s;
     }
     cl.sync();
     for (int e = tid; e < ra * rb; e += nth) E[e] = E2[e];
