@@ -1192,14 +1192,35 @@ static cudaError_t qr_t(C* A, int m, int n, C* Q, C* R, C* tau, cudaStream_t s) 
 }
 // R factor only (Q discarded): row blocks that fit shared memory are
 // factorised independently and their R's stacked and factorised again.
+// R factor of a panel too wide for the staged kernels: Householder in
+// global memory over A (overwritten), the reflector scalars in shared memory.
+template <typename C>
+__global__ void __launch_bounds__(256) k_qr_r_global(C* A, int m, int n, C* __restrict__ Rm) {
+  __shared__ double sh[40];
+  __shared__ C s_tau[512];
+  cta_householder(A, m, n, s_tau, sh);
+  __syncthreads();
+  const int k = m < n ? m : n;
+  for (long long e = threadIdx.x; e < (long long)k * n; e += blockDim.x) {
+    const int i = (int)(e / n), c = (int)(e % n);
+    Rm[e] = (c >= i) ? A[(long long)i * n + c] : cx<C>(0, 0);
+  }
+}
+
 template <typename C>
 static cudaError_t qr_r_t(const C* A, int m, int n, C* R, C* scratch0, C* scratch1, cudaStream_t s) {
   KTimerScope timer(KC_QR, s, 0.5 * qr_flops(m, n));
   cudaError_t e;
-  if (TsqrSmem<C>::bytes(n, n) > (size_t)kSmemMax) return cudaErrorInvalidValue;
   int rb = 32;
   while (TsqrSmem<C>::bytes(rb + 32, n) <= (size_t)kSmemMax) rb += 32;
-  if (rb < 2 * n) return cudaErrorInvalidValue;   // stacking would not shrink the problem
+  if (TsqrSmem<C>::bytes(n, n) > (size_t)kSmemMax || rb < 2 * n) {
+    // stacking would not shrink the problem: one CTA over a copy in global memory
+    if (std::min(m, n) > 512) return cudaErrorInvalidValue;
+    if ((e = cudaMemcpyAsync(scratch0, A, sizeof(C) * (size_t)m * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return e;
+    k_qr_r_global<C><<<1, 256, 0, s>>>(scratch0, m, n, R);
+    return cudaGetLastError();
+  }
   const C* src = A;
   int rows = m;
   C* bufs[2] = {scratch0, scratch1};

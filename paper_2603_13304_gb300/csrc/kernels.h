@@ -42,7 +42,8 @@ cudaError_t launch_qr(float2* A, int m, int n, float2* Q, float2* R, float2* tau
 // R factor only of A (m x n, row-major, not modified): k x n, k = min(m, n),
 // upper triangular with a real diagonal.  Tall inputs are split into row
 // blocks whose R's are stacked and factorised again; s0, s1: scratch of
-// m * n elements each.  Requires an n x n panel to fit shared memory.
+// m * n elements each.  Panels too wide for that (n x n beyond shared memory,
+// or row blocks shorter than 2n) are factorised by one CTA over a copy in s0.
 cudaError_t launch_qr_r(const double2* A, int m, int n, double2* R, double2* s0, double2* s1, cudaStream_t s);
 cudaError_t launch_qr_r(const float2* A, int m, int n, float2* R, float2* s0, float2* s1, cudaStream_t s);
 
