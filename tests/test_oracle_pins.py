@@ -348,3 +348,30 @@ def test_square_blocks():
     for b in geom.blocks:
         assert len(b.sites) == 9
         assert sorted(len(b.faces[d].edges) for d in range(4)) == [3, 3, 3, 3]
+
+
+@pytest.mark.parametrize("L", [2, 3])
+def test_translation_invariant_kagome_gives_equal_block_messages(L):
+    """With the same three site tensors in every unit cell and the same
+    initial edge matrices in every cell, a translation by L unit cells maps
+    every block of the 3L x L super-cell onto the next one (Sec. 2.3.1,
+    periodic super-cell): after any number of synchronous iterations each
+    face of every block carries the same message.  A wrong periodic
+    neighbour, face or re-homed corner site breaks the equality."""
+    Lx, Ly, D = 3 * L, L, 2
+    n = 3 * Lx * Ly
+    cell = syn.gaussian_peps(3, 2, D, seed=41)
+    t = np.stack([cell[s % 3] for s in range(n)])
+    em_cell = syn.initial_edge_matrices(3, D, seed=42)
+    em = np.stack([em_cell[s % 3] for s in range(n)])
+    geom = Geometry.kagome(Lx, Ly, L)
+    assert len(geom.blocks) == 3
+    bb = BlockBP(geom, t, chi=4)
+    bb.init_messages(em)
+    for _ in range(2):
+        bb.step()
+    for face in range(4):
+        dense = [tn.mps_dense(bb.msgs[(b, face)]) for b in range(3) if (b, face) in bb.msgs]
+        assert len(dense) == 3
+        for other in dense[1:]:
+            assert np.abs(other - dense[0]).max() < 1e-12
