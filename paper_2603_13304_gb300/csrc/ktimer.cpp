@@ -8,6 +8,7 @@
 // and are re-read after each replay until the graph is dropped.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -24,7 +25,7 @@ struct Pair {
 };
 
 std::mutex g_mu;
-int g_class = 0;
+std::atomic<int> g_class{0};   // read on every launch path without the lock
 std::vector<Pair> g_pairs;
 long long g_n = 0;
 double g_ms = 0.0, g_flops = 0.0;
@@ -52,9 +53,12 @@ void ktimer_select(int cls) {
   if (g_dev_flops) cudaMemset(g_dev_flops, 0, sizeof(double));
 }
 
-int ktimer_class() { return g_class; }
+int ktimer_class() { return g_class.load(std::memory_order_relaxed); }
 
-double* ktimer_device_flops(int cls) { return (g_class && g_class == cls) ? g_dev_flops : nullptr; }
+double* ktimer_device_flops(int cls) {
+  const int c = g_class.load(std::memory_order_relaxed);
+  return (c && c == cls) ? g_dev_flops : nullptr;
+}
 
 void ktimer_set_tag(long long tag) { t_tag = tag; }
 
@@ -69,7 +73,8 @@ void ktimer_drop_tag(long long tag) {
 }
 
 KTimerScope::KTimerScope(int cls, cudaStream_t s, double flops) : s_(s) {
-  if (!g_class || cls != g_class) return;
+  const int c = g_class.load(std::memory_order_relaxed);
+  if (!c || cls != c) return;
   Pair p;
   if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) {
     destroy(p);
