@@ -14,7 +14,8 @@ Readings (the thesis leaves these open):
 * A: a message is normalised to unit norm <M|M> = 1 as a vector over its
   fused legs, and its global phase is fixed so that its contraction with the
   ket-bra identity <I|M> is real and positive; the change of a message is the
-  gauge-invariant distance ||M_new - M_old|| = sqrt(max(0, 2 - 2 Re<M_old|M_new>)).
+  gauge-invariant distance ||M_new - M_old||, evaluated as the norm of the
+  direct-sum MPS (new, -old) (see message_distance).
 * B: initial messages are bond-1 MPS built from per-leg D x D positive
   semi-definite matrices supplied as input (see ``synthetic``).
 * F: log Z_BP = sum_a log Z_a - sum_{pairs (a,b)} log <M_a->b, M_b->a>,
@@ -29,7 +30,7 @@ import math
 
 import numpy as np
 
-from . import tn
+from . import learning, tn
 from .geometry import TOP, Geometry, DIR_VEC
 from .region import block_region, build_region
 
@@ -76,9 +77,16 @@ def message_distance(old: list, new: list) -> float:
 
 
 class BlockBP:
-    def __init__(self, geom: Geometry, tensors: np.ndarray, chi: int):
+    def __init__(self, geom: Geometry, tensors: np.ndarray, chi: int, alpha: float = 1.0,
+                 hermitise: bool = False):
+        """alpha: learning step (1 = plain replacement); hermitise: replace
+        each new message by its Hermitian part (see oracle.learning)."""
+        if not 0.0 <= alpha <= 1.0:
+            raise ValueError("alpha must lie in [0, 1]")
         self.geom = geom
         self.chi = chi
+        self.alpha = alpha
+        self.hermitise = hermitise
         self.t = np.asarray(tensors, dtype=np.complex128)
         if self.t.shape[0] != geom.n_sites:
             raise ValueError("one tensor per site expected")
@@ -154,7 +162,13 @@ class BlockBP:
         """One synchronous iteration (Alg. 1); returns the largest change."""
         new = {}
         for (bid, d, recv) in self.geom.updates():
-            new[recv] = self.update_message(bid, d)
+            m = self.update_message(bid, d)
+            dims = self.face_dims(*recv)
+            if self.hermitise:
+                m = normalise_message(learning.hermitise(m, dims, self.chi), dims)
+            if self.alpha != 1.0:
+                m = normalise_message(learning.learned(m, self.msgs[recv], self.alpha, self.chi), dims)
+            new[recv] = m
         err = 0.0
         for key, m in new.items():
             err = max(err, message_distance(self.msgs[key], m))
