@@ -101,11 +101,14 @@ bbp_status bbp_partition_blocks(bbp_ctx* ctx, int bx, int by);
  * update).  seed is reserved. */
 bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, uint64_t seed);
 
-/* Randomised truncation of the complex64 modes (no counterpart in the
- * thesis, whose truncation is an exact SVD): number of subspace-iteration
- * power steps before the reduced Jacobi, 0..8 (default 1).  Fewer steps are
- * faster and less accurate when the spectrum decays slowly; BBP_FP64 is
- * unaffected (exact Jacobi). */
+/* Randomised truncation (no counterpart in the thesis, whose truncation is
+ * an exact SVD): number of subspace-iteration power steps before the reduced
+ * SVD, 0..8, for the precision already set by bbp_set_options: complex64
+ * modes (default 1, b = chi + max(8, chi/2) directions) or BBP_FP64
+ * (default 6, b = 2 chi directions, which reaches the exact truncation to
+ * rounding on the BlockBP splits; smaller matrices always take the exact
+ * one-sided Jacobi).  Fewer steps are faster and less accurate when the
+ * spectrum decays slowly. */
 bbp_status bbp_set_power_iters(bbp_ctx* ctx, int power_iters);
 
 /* Execution options (no counterpart in the thesis; they change how the same
@@ -265,10 +268,10 @@ bbp_status bbp_k_svd_trunc(const double* Z, int m, int n, int chi, double* U, do
  * scratch is a fixed device array of 8 MiB + 64 KiB that every GPU loading
  * the library holds until exit, enough for bbp_k_svd_work_bytes(m, n) up to
  * that size (e.g. 512 x 512).  Larger sizes return BBP_ERR_ARG.  It calls no
- * allocator.  The first call on a device looks up the array's device address
- * (with that device current); make that first call before any stream
- * capture.  All calls on a device share the array: calls that overlap on the
- * same GPU race. */
+ * allocator.  The first call on a device loads the array there (CUDA loads
+ * modules lazily) and looks up its device address (with that device
+ * current); make that first call before any stream capture.  All calls on a
+ * device share the array: calls that overlap on the same GPU race. */
 bbp_status bbp_k_svd_trunc_noalloc(const double* Z, int m, int n, int chi, double* U, double* Rem, int* status,
                                    void* stream);
 
@@ -279,6 +282,32 @@ bbp_status bbp_k_svd_stats(const void* work, int m, int n, int* sweeps, long lon
 /* Householder QR (Sec. 2.3.3 canonical moves): A (m x n, device, destroyed)
  * = Q (m x k) R (k x n), k = min(m, n); tau: device scratch of k complex. */
 bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, void* stream);
+
+/* Householder QR of tall panels (Sec. 2.3.3 canonical moves; the range
+ * orthonormalisation of the truncation) on a cluster of up to 16 CTAs, each
+ * holding a row slice in shared memory.  A: device, batch panels of m x n
+ * (m >= n, row-major, not modified) at a stride of m * n elements; Q (m x n
+ * per panel, may equal A) and R (n x n per panel, upper triangular with a
+ * real diagonal) are written when not NULL.  c64 = 1: complex64 entries,
+ * 0: complex128.  BBP_ERR_ARG when m < n or the panel does not fit
+ * (bbp_k_panel_cluster returns 0 for it); otherwise the number of CTAs of
+ * the cluster that one panel takes. */
+int bbp_k_panel_cluster(int c64, int m, int n);
+bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R, int batch, void* stream);
+
+/* The engine's truncated SVD (Sec. 1.1.1) with the randomised range
+ * reduction (see bbp_set_power_iters): Z (m x n, device, row-major) -> U
+ * (m x k) and Rem = S V^H (k x n), k = min(chi, m, n), chi <= 64.
+ * c64 = 1: complex64 entries; a subspace iteration with b = chi +
+ * max(8, chi/2) directions whose b x b reduced factor is finished in
+ * complex128.  c64 = 0: complex128 entries, b = 2 chi directions, the
+ * reduced factor by complex128 Jacobi.  Matrices too small to gain from the
+ * reduction take the exact one-sided Jacobi.  power_iters: 0..8.  work:
+ * device scratch of bbp_k_svd_work_bytes_rand(c64, m, n, chi) bytes; status
+ * as for bbp_k_svd_trunc. */
+size_t bbp_k_svd_work_bytes_rand(int c64, int m, int n, int chi);
+bbp_status bbp_k_svd_trunc_rand(int c64, const void* Z, int m, int n, int chi, void* U, void* Rem, void* work,
+                                int* status, int power_iters, void* stream);
 
 /* K2 on the tensor cores (tcgen05.mma, TMEM accumulator, TMA-fed operands).
  * Real GEMM C (M x N, device fp32, row stride ldc) = alpha * A * B with

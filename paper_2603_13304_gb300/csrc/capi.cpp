@@ -96,7 +96,8 @@ bbp_status bbp_set_power_iters(bbp_ctx* ctx, int power_iters) {
   if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
   if (power_iters < 0 || power_iters > 8) return set_err(BBP_ERR_ARG, "power_iters must be 0..8");
   ctx->eng.drop_graphs();
-  ctx->eng.power_iters = power_iters;
+  if (ctx->eng.precision == 0) ctx->eng.power_iters64 = power_iters;
+  else ctx->eng.power_iters = power_iters;
   return BBP_OK;
 }
 
@@ -390,6 +391,40 @@ bbp_status bbp_k_tc_absorb(int bf16, int c64, const void* X, int P, int Q, const
                                              work, err, st));
   return cuda_status(bbp::launch_tc_absorb(bf16 != 0, (const double2*)X, P, Q, (const double2*)S, l, r, (double2*)R,
                                            work, err, st));
+}
+
+int bbp_k_panel_cluster(int c64, int m, int n) {
+  return bbp::panel_cluster(m, n, c64 ? sizeof(float2) : sizeof(double2));
+}
+
+bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R, int batch, void* stream) {
+  if (!A || m < 1 || n < 1 || m < n || batch < 1) return set_err(BBP_ERR_ARG, "bad arguments");
+  if (bbp_k_panel_cluster(c64, m, n) == 0) return set_err(BBP_ERR_ARG, "panel too large for a 16-CTA cluster");
+  if (cudaError_t ae = bbp::init_kernel_attributes()) return cuda_status(ae);
+  const long long stride = (long long)m * n;
+  if (c64)
+    return cuda_status(bbp::launch_panel_qr((const float2*)A, m, n, (float2*)Q, (float2*)R, batch, stride,
+                                            (cudaStream_t)stream));
+  return cuda_status(bbp::launch_panel_qr((const double2*)A, m, n, (double2*)Q, (double2*)R, batch, stride,
+                                          (cudaStream_t)stream));
+}
+
+size_t bbp_k_svd_work_bytes_rand(int c64, int m, int n, int chi) {
+  if (m < 1 || n < 1 || chi < 1) return 0;
+  return c64 ? bbp::svd_work_bytes_c64(m, n, chi) : bbp::svd_work_bytes_rand64(m, n, chi);
+}
+
+bbp_status bbp_k_svd_trunc_rand(int c64, const void* Z, int m, int n, int chi, void* U, void* Rem, void* work,
+                                int* status, int power_iters, void* stream) {
+  if (!Z || !U || !Rem || !work || !status || m < 1 || n < 1 || chi < 1 || power_iters < 0 || power_iters > 8)
+    return set_err(BBP_ERR_ARG, "bad arguments");
+  if (std::min(m, n) > 4096 || chi > 64) return set_err(BBP_ERR_ARG, "matrix too large");
+  if (cudaError_t ae = bbp::init_kernel_attributes()) return cuda_status(ae);
+  if (c64)
+    return cuda_status(bbp::launch_svd_trunc((const float2*)Z, m, n, chi, (float2*)U, (float2*)Rem, work, status,
+                                             (cudaStream_t)stream, power_iters));
+  return cuda_status(bbp::launch_svd_trunc_rand64((const double2*)Z, m, n, chi, (double2*)U, (double2*)Rem, work,
+                                                  status, (cudaStream_t)stream, power_iters));
 }
 
 bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, void* stream) {

@@ -29,10 +29,19 @@ template <> float2 zero_of<float2>() { return make_float2(0.f, 0.f); }
 
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
-// truncated SVD of one split, per element type
+// truncated SVD of one split, per element type (complex128: the randomised
+// subspace iteration with b = 2 chi, exact Jacobi for small splits)
 cudaError_t svd_call(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work, int* status,
-                     cudaStream_t s, int) {
-  return launch_svd_trunc(Z, m, n, chi, U, Rem, work, status, s);
+                     cudaStream_t s, int power_iters) {
+  return launch_svd_trunc_rand64(Z, m, n, chi, U, Rem, work, status, s, power_iters);
+}
+
+// launches of one truncated SVD (statistics only)
+long long svd_launches(int m, int n, int chi, bool c64, int q) {
+  const int M = std::min(m, n);
+  const int b = c64 ? rand_block(m, n, chi) : rand_block64(m, n, chi);
+  if (b >= M) return 5;
+  return 12 + 4 * q + (c64 ? 1 : 0);
 }
 cudaError_t svd_call(const float2* Z, int m, int n, int chi, float2* U, float2* Rem, void* work, int* status,
                      cudaStream_t s, int power_iters) {
@@ -76,6 +85,18 @@ void DBuf::release() {
   p = nullptr;
   bytes = 0;
 }
+
+// Makes `dev` current for the scope and restores the caller's device after.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    if (dev < 0 || cudaGetDevice(&prev) != cudaSuccess || prev == dev) { prev = -1; return; }
+    if (cudaSetDevice(dev) != cudaSuccess) prev = -1;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 int fail(Engine* e, int status, const std::string& msg) {
   if (e) e->last_error = msg;
@@ -160,6 +181,7 @@ unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int
   mix((unsigned long long)precision);
   mix((unsigned long long)chi);
   mix((unsigned long long)power_iters);
+  mix((unsigned long long)power_iters64);
   mix((unsigned long long)nstreams);
   mix((unsigned long long)(uintptr_t)dist_dev.p);
   for (int i = 0; i < nstreams; ++i) mix((unsigned long long)(uintptr_t)pool[i]->arena.p);
@@ -190,6 +212,7 @@ unsigned long long Engine::input_signature(int nstreams) const {
   mix((unsigned long long)tc_mode);
   mix((unsigned long long)chi);
   mix((unsigned long long)power_iters);
+  mix((unsigned long long)power_iters64);
   mix((unsigned long long)nstreams);
   mix((unsigned long long)(uintptr_t)dist_dev.p);
   for (int i = 0; i < nstreams && i < (int)pool.size(); ++i) mix((unsigned long long)(uintptr_t)pool[i]->arena.p);
@@ -246,6 +269,7 @@ int Engine::create(int lattice, int Lx, int Ly, int periodic, int d_, int D_, co
   d = d_;
   D = D_;
   stream = s;
+  if (cudaGetDevice(&device) != cudaSuccess) return fail(this, 3, "no current CUDA device");
   geom.lat.kind = lattice;
   geom.lat.Lx = Lx;
   geom.lat.Ly = Ly;
@@ -505,7 +529,7 @@ void Engine::job_needs(const SweepJob& job, size_t need[7]) const {
   need[0] = std::max<size_t>(need[0], (size_t)tr.max_tensor);
   need[1] = std::max<size_t>(need[1], (size_t)std::max(tr.max_seg, tr.max_tensor));
   need[2] = std::max<size_t>(need[2], cap_x);
-  need[3] = std::max<size_t>(need[3], precision == 0 ? svd_work_bytes(mr, mc) : svd_work_bound_c64(mr, mc, chi));
+  need[3] = std::max<size_t>(need[3], precision == 0 ? svd_work_bound_rand64(mr, mc, chi) : svd_work_bound_c64(mr, mc, chi));
   need[4] = std::max<size_t>(need[4], (size_t)tr.max_len + 6);
   need[5] = std::max<size_t>(need[5], (size_t)4 * chi * chi * D * D + 64);
   if (tc_mode && precision != 0)
@@ -711,8 +735,10 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
         const long long cols = rest * r;
         const int k = rec.split[q].r;
         const int t = take();
-        CK(svd_call(cur, rows, (int)cols, chi, slot(t), Rb[rbuf], w.svd, w.status, s, power_iters));
-        launches += sizeof(C) == sizeof(double2) ? 5 : 10 + 4 * power_iters;
+        const bool c64 = sizeof(C) == sizeof(float2);
+        const int qsteps = c64 ? power_iters : power_iters64;
+        CK(svd_call(cur, rows, (int)cols, chi, slot(t), Rb[rbuf], w.svd, w.status, s, qsteps));
+        launches += svd_launches(rows, (int)cols, chi, c64, qsteps);
         newpos.push_back(t);
         newsh.push_back(TShape{ll, q1, k});
         cur = Rb[rbuf];
@@ -776,6 +802,7 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
 // contexts (bbp_batch_iterate, the server) keep iterations in flight at once.
 
 int Engine::iter_begin() {
+  DeviceScope ds(device);
   if (!partitioned) return fail(this, 8, "bbp_partition_blocks must come first");
   if (!messages_ready) return fail(this, 8, "bbp_init_messages must come first");
   const int nu = (int)geom.updates().size();
@@ -799,13 +826,17 @@ int Engine::iter_begin() {
 }
 
 int Engine::iter_end() {
+  DeviceScope ds(device);
   if (!root) return 0;
   CK(cudaEventRecord(root_out, root));
   CK(cudaStreamWaitEvent(stream, root_out, 0));
   return 0;
 }
 
-int Engine::iter_launch() { return precision == 0 ? iter_launch_t<double2>() : iter_launch_t<float2>(); }
+int Engine::iter_launch() {
+  DeviceScope ds(device);
+  return precision == 0 ? iter_launch_t<double2>() : iter_launch_t<float2>();
+}
 
 template <typename C>
 int Engine::iter_launch_t() {
@@ -949,6 +980,7 @@ int Engine::iter_launch_t() {
 }
 
 int Engine::iter_finish(double* err_out) {
+  DeviceScope ds(device);
   const auto ups = geom.updates();
   const int nu = (int)ups.size();
   if (nu == 0) {

@@ -88,11 +88,12 @@ using OpList = std::vector<std::pair<std::array<int, 2>, const double*>>;   // (
 class Engine {
  public:
   Geometry geom;
-  int d = 2, D = 2, chi = 8, precision = 0, power_iters = 1;
+  int d = 2, D = 2, chi = 8, precision = 0, power_iters = 1, power_iters64 = 6;
   int tc_mode = 0;                     // absorb contraction: 0 SIMT GEMM, 1 tcgen05 TF32 split, 2 tcgen05 BF16 split
   bool use_graphs = true;              // replay a captured CUDA graph per iteration
   int max_streams = 16;                // sweep jobs run on up to this many streams
   cudaStream_t stream = nullptr;
+  int device = -1;                     // device current at create(); every iteration call runs on it
   bool partitioned = false;
   std::string last_error;
 

@@ -1068,7 +1068,8 @@ cudaError_t jacobi_svd(const C* Z, int m, int n, int chi, C* U, C* Rem, void* wo
 // counter-hash sign matrix (the result does not depend on it once the
 // subspace has converged).
 
-__global__ void k_omega(float2* O, int n, int b) {
+template <typename C>
+__global__ void k_omega(C* O, int n, int b) {
   long long tot = (long long)n * b;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     unsigned long long x = (unsigned long long)e * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
@@ -1077,59 +1078,102 @@ __global__ void k_omega(float2* O, int n, int b) {
     x ^= x >> 27;
     x *= 0x94D049BB133111EBull;
     x ^= x >> 33;
-    O[e] = make_float2((x & 1) ? 1.f : -1.f, (x & 2) ? 1.f : -1.f);
+    O[e] = cx<C>((x & 1) ? 1.0 : -1.0, (x & 2) ? 1.0 : -1.0);
   }
 }
 
-// One CTA: orthonormalise the columns of Y (rows x b) in place (Householder,
-// explicit Q written back into Y).  scratch: rows*b + b complex.
-__global__ void __launch_bounds__(256) k_orth(float2* Y, int rows, int b, float2* scratch) {
-  __shared__ double sh[40];
-  float2* A = scratch;
-  float2* tau = scratch + (long long)rows * b;
-  for (long long e = threadIdx.x; e < (long long)rows * b; e += blockDim.x) A[e] = Y[e];
+// FP64 finish of the reduced SVD (complex64 modes).  After the complex64
+// Jacobi, the rows of G' = WH L (b x b) are orthogonal to complex64 accuracy
+// and idx holds the k largest.  The rows of G' and WH are promoted to
+// complex128 and every pair (kept, discarded) is rotated once more in double
+// arithmetic, which makes the kept rows orthogonal to the discarded ones to
+// double accuracy (the rotations within either set do not change the kept
+// subspace); then the row norms and the choice of the k largest rows are
+// taken in double.  One CTA; G' in shared memory, WH in global memory.
+__global__ void __launch_bounds__(1024) k_jacobi_cut64(SvdWork<float2> w, int b, int k, double2* __restrict__ G64,
+                                                       double2* __restrict__ WH64, double* __restrict__ sig64,
+                                                       int* __restrict__ idx64) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* G = (double2*)smem_raw;           // b x b
+  int* kept = (int*)(G + (size_t)b * b);     // k
+  int* disc = kept + k;                      // b - k
+  int* mark = disc + (b - k);                // b
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    G[e] = c128(w.G[e]);
+    WH64[e] = c128(w.WH[e]);
+  }
+  for (int e = threadIdx.x; e < b; e += blockDim.x) mark[e] = 0;
   __syncthreads();
-  cta_householder(A, rows, b, tau, sh);
+  for (int e = threadIdx.x; e < k; e += blockDim.x) {
+    const int a = min(max(w.idx[e], 0), b - 1);
+    kept[e] = a;
+    mark[a] = 1;
+  }
   __syncthreads();
-  cta_form_q(A, rows, b, tau, Y);
-}
-
-// U (m x k) = Q (m x b) * conj(WH[idx[r], :])^T ; Rem (k x n) = G[idx[r], :]
-// U = Q WH[top]^H (m x k) and Rem = G'[top] W^H (k x n), where the Jacobi
-// rotated L = R_W^H (b x b) into G' = WH L.
-__global__ void k_rand_out_lw(const float2* __restrict__ Q, int m, int b, SvdWork<float2> w,
-                              const float2* __restrict__ W, int n, int k, float2* U, float2* Rem) {
-  long long totU = (long long)m * k, totR = (long long)k * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totU + totR;
-       e += (long long)gridDim.x * blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    if (e < totU) {
-      const int i = (int)(e / k), a = min(max(w.idx[(int)(e % k)], 0), b - 1);
-      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(Q[(long long)i * b + j], cconj(w.WH[(long long)a * b + j])));
-      U[e] = acc;
-    } else {
-      const long long f = e - totU;
-      const int a = min(max(w.idx[(int)(f / n)], 0), b - 1), c = (int)(f % n);
-      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(w.G[(long long)a * b + j], cconj(W[(long long)c * b + j])));
-      Rem[f] = acc;
+  if (threadIdx.x == 0) {
+    int q = 0;
+    for (int a = 0; a < b; ++a)
+      if (!mark[a] && q < b - k) disc[q++] = a;
+    for (; q < b - k; ++q) disc[q] = -1;     // duplicate indices in idx (never expected)
+  }
+  __syncthreads();
+  const int nd = b - k;
+  const double floor = 1e-32 * (double)*w.zn2;   // eps^2 of double, as in the complex128 Jacobi
+  if (nd > 0 && k > 0) {
+    const int nbig = k >= nd ? k : nd, nsmall = k >= nd ? nd : k;
+    const int* big = k >= nd ? kept : disc;
+    const int* small = k >= nd ? disc : kept;
+    for (int r = 0; r < nbig; ++r) {         // round r: pairs (big[(p + r) % nbig], small[p]), disjoint
+      for (int p = warp; p < nsmall; p += nw) {
+        const int a = big[(p + r) % nbig], c = small[p];
+        if (a < 0 || c < 0) continue;
+        rotate_pair<false>(G + (size_t)a * b, G + (size_t)c * b, b, WH64 + (size_t)a * b, WH64 + (size_t)c * b, b,
+                           lane, 1e-15, floor);
+      }
+      __syncthreads();
     }
   }
+  for (int row = warp; row < b; row += nw) {
+    double sq = 0.0;
+    for (int c = lane; c < b; c += 32) sq += cabs2d(G[(size_t)row * b + c]);
+    sq = warp_sum(sq);
+    if (lane == 0) sig64[row] = sqrt(sq);
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < b; a += blockDim.x) {   // total order, non-finite norms last
+    double sa = sig64[a];
+    if (!(sa >= 0.0) || !isfinite(sa)) sa = -1.0;
+    int rank = 0;
+    for (int c = 0; c < b; ++c) {
+      double sc = sig64[c];
+      if (!(sc >= 0.0) || !isfinite(sc)) sc = -1.0;
+      rank += (sc > sa) || (sc == sa && c < a);
+    }
+    if (rank < k) idx64[rank] = a;
+  }
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) G64[e] = G[e];
 }
 
-__global__ void k_rand_out(const float2* Q, int m, int b, SvdWork<float2> w, int n, int k, float2* U, float2* Rem) {
+// U = Q WH[top]^H (m x k) and Rem = G'[top] W^H (k x n): WH and G' of the
+// reduced SVD in complex128, Q and W in the path's element type.
+template <typename C>
+__global__ void k_rand_out64(const C* __restrict__ Q, int m, int b, const double2* __restrict__ WH64,
+                             const double2* __restrict__ G64, const int* __restrict__ idx64, const C* __restrict__ W,
+                             int n, int k, C* U, C* Rem) {
   long long totU = (long long)m * k, totR = (long long)k * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totU + totR;
        e += (long long)gridDim.x * blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
     if (e < totU) {
-      int i = (int)(e / k), r = (int)(e % k);
-      int a = min(max(w.idx[r], 0), b - 1);
-      float2 s = make_float2(0.f, 0.f);
-      for (int j = 0; j < b; ++j) s = cadd(s, cmul(Q[(long long)i * b + j], cconj(w.WH[(long long)a * b + j])));
-      U[e] = s;
+      const int i = (int)(e / k), a = min(max(idx64[(int)(e % k)], 0), b - 1);
+      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(c128(Q[(long long)i * b + j]), cconj(WH64[(long long)a * b + j])));
+      U[e] = cx<C>(acc.x, acc.y);
     } else {
-      long long f = e - totU;
-      int r = (int)(f / n), c = (int)(f % n);
-      Rem[f] = w.G[(long long)min(max(w.idx[r], 0), b - 1) * n + c];
+      const long long f = e - totU;
+      const int a = min(max(idx64[(int)(f / n)], 0), b - 1), c = (int)(f % n);
+      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(G64[(long long)a * b + j], cconj(c128(W[(long long)c * b + j]))));
+      Rem[f] = cx<C>(acc.x, acc.y);
     }
   }
 }
@@ -1210,30 +1254,31 @@ __global__ void __launch_bounds__(256) k_qr_r_global(C* A, int m, int n, C* __re
 template <typename C>
 static cudaError_t qr_r_t(const C* A, int m, int n, C* R, C* scratch0, C* scratch1, cudaStream_t s) {
   KTimerScope timer(KC_QR, s, 0.5 * qr_flops(m, n));
-  cudaError_t e;
+  if (TsqrSmem<C>::bytes(m, n) <= (size_t)kSmemMax) return tsqr_launch<C>(A, m, n, nullptr, R, m, s);
   int rb = 32;
   while (TsqrSmem<C>::bytes(rb + 32, n) <= (size_t)kSmemMax) rb += 32;
-  if (TsqrSmem<C>::bytes(n, n) > (size_t)kSmemMax || rb < 2 * n) {
-    // stacking would not shrink the problem: one CTA over a copy in global memory
-    if (std::min(m, n) > 512) return cudaErrorInvalidValue;
-    if ((e = cudaMemcpyAsync(scratch0, A, sizeof(C) * (size_t)m * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-      return e;
-    k_qr_r_global<C><<<1, 256, 0, s>>>(scratch0, m, n, R);
-    return cudaGetLastError();
-  }
   const C* src = A;
   int rows = m;
   C* bufs[2] = {scratch0, scratch1};
   int which = 0;
-  for (int level = 0; level < 16 && TsqrSmem<C>::bytes(rows, n) > (size_t)kSmemMax; ++level) {
+  cudaError_t e;
+  for (int level = 0; level < 16; ++level) {
+    // the stacked panel fits one CTA or one cluster: finish there
+    if (TsqrSmem<C>::bytes(rows, n) <= (size_t)kSmemMax) return tsqr_launch<C>(src, rows, n, nullptr, R, rows, s);
+    if (rows >= n && panel_cluster(rows, n, sizeof(C)) > 0) return launch_panel_qr(src, rows, n, nullptr, R, 1, 0, s);
+    if (rb <= n) break;   // stacking row blocks would not shrink the panel
     const int nb = (rows + rb - 1) / rb;
     if ((e = tsqr_launch<C>(src, rows, n, nullptr, bufs[which], rb, s)) != cudaSuccess) return e;
     src = bufs[which];
     rows = nb * n;
     which ^= 1;
   }
-  if (TsqrSmem<C>::bytes(rows, n) > (size_t)kSmemMax) return cudaErrorInvalidValue;
-  return tsqr_launch<C>(src, rows, n, nullptr, R, rows, s);
+  // one CTA over a copy in global memory (panels wider than any staging)
+  if (std::min(m, n) > 512) return cudaErrorInvalidValue;
+  if ((e = cudaMemcpyAsync(scratch0, A, sizeof(C) * (size_t)m * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  k_qr_r_global<C><<<1, 256, 0, s>>>(scratch0, m, n, R);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_qr_r(const double2* A, int m, int n, double2* R, double2* s0, double2* s1, cudaStream_t s) {
@@ -1275,22 +1320,126 @@ int rand_block(int m, int n, int chi) {
   return (M <= std::max(2 * b, 64)) ? M : b;
 }
 
+// Scratch of the randomised truncation: W (n x b), Q (m x b), R_W and L
+// (b x b each), the Jacobi of L in the element type, and the complex128
+// reduced factor (G64, WH64: b x b; sig64, idx64: b).
+template <typename C>
+static size_t rand_work_bytes(int m, int n, int b) {
+  const size_t z = sizeof(C), zd = sizeof(double2);
+  return align256(z * (size_t)n * b) + align256(z * (size_t)m * b) + 2 * align256(z * (size_t)b * b) +
+         jacobi_bytes<C>(b, b) + 2 * align256(zd * (size_t)b * b) + align256(sizeof(double) * b) +
+         align256(sizeof(int) * b) + 256;
+}
+
 size_t svd_work_bytes_c64(int m, int n, int chi) {
   int M = m < n ? m : n, N = m < n ? n : m;
   const int b = rand_block(m, n, chi);
   if (b >= M) return jacobi_bytes<float2>(M, N);
-  // Omega/W (n x b), Q (m x b), X (max(m,n) x b), orth scratch, B (b x n), Jacobi(b, n)
-  size_t z = sizeof(float2);
-  return align256(z * (size_t)n * b) + align256(z * (size_t)m * b) + align256(z * (size_t)N * b) +
-         align256(z * ((size_t)N * b + b)) + jacobi_bytes<float2>(b, n) + 256;
+  return rand_work_bytes<float2>(m, n, b);
 }
 
 size_t svd_work_bound_c64(int max_min, int max_max, int chi) {
   const int b = chi + (chi >= 16 ? chi / 2 : 8);
-  const size_t z = sizeof(float2);
-  const size_t N = (size_t)max_max;
-  size_t rnd = 3 * align256(z * N * b) + align256(z * (N * b + b)) + jacobi_bytes<float2>(b, (int)N) + 256;
-  return std::max(rnd, jacobi_bytes<float2>(max_min, max_max));
+  return std::max(rand_work_bytes<float2>(max_max, max_max, b), jacobi_bytes<float2>(max_min, max_max));
+}
+
+// complex128 (the 1e-10 parity path): b = 2 chi directions, so that the
+// subspace iteration with the default six power steps reaches the exact
+// truncation to rounding on the spectra of the BlockBP splits; matrices whose
+// smaller side is at most max(2 b, 64) take the exact Jacobi.
+int rand_block64(int m, int n, int chi) {
+  const int M = m < n ? m : n;
+  const int b = 2 * chi;
+  return (M <= std::max(2 * b, 64)) ? M : b;
+}
+
+size_t svd_work_bytes_rand64(int m, int n, int chi) {
+  int M = m < n ? m : n, N = m < n ? n : m;
+  const int b = rand_block64(m, n, chi);
+  if (b >= M) return jacobi_bytes<double2>(M, N);
+  return rand_work_bytes<double2>(m, n, b);
+}
+
+size_t svd_work_bound_rand64(int max_min, int max_max, int chi) {
+  return std::max(rand_work_bytes<double2>(max_max, max_max, 2 * chi), jacobi_bytes<double2>(max_min, max_max));
+}
+
+static size_t cut64_smem(int b, int k) { return sizeof(double2) * (size_t)b * b + sizeof(int) * (size_t)(2 * b + 8); }
+
+// Orthonormalise the columns of Y (rows x b) in place; R (b x b) too when R
+// is not null: one CTA when the panel fits its shared memory, a cluster of
+// CTAs otherwise.
+template <typename C>
+static cudaError_t orth_panel(C* Y, int rows, int b, C* R, cudaStream_t s) {
+  if (TsqrSmem<C>::bytes(rows, b) <= (size_t)kSmemMax) {
+    KTimerScope timer(KC_ORTH, s, qr_flops(rows, b));
+    return tsqr_launch<C>(Y, rows, b, Y, R, rows, s);
+  }
+  return launch_panel_qr(Y, rows, b, Y, R, 1, 0, s);
+}
+
+// Randomised truncated SVD of Z (m x n) with b directions and q power steps:
+// Q = orth(Z Omega); q times W = orth(Z^H Q), Q = orth(Z W); then
+// Z^H Q = W R_W, so that B = Q^H Z = R_W^H W^H and the SVD runs on the b x b
+// factor L = R_W^H.  Its one-sided Jacobi gives G' = WH L (rows sigma_i v_i^H
+// in the W basis); U = Q WH[top]^H and Rem = G'[top] W^H.  complex64: the
+// Jacobi runs in complex64 and is finished in complex128 (k_jacobi_cut64);
+// complex128: the Jacobi runs in complex128.
+template <typename C>
+static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* Rem, void* work, int* status,
+                            cudaStream_t s, int power_iters, double jtol) {
+  const int M = m < n ? m : n;
+  const int k = chi < M ? chi : M;
+  const bool c64 = sizeof(C) == sizeof(float2);
+  if (c64 && cut64_smem(b, k) > (size_t)kSmemMax) return cudaErrorInvalidValue;
+  const size_t z = sizeof(C), zd = sizeof(double2);
+  char* p = (char*)work;
+  C* W = (C*)p; p += align256(z * (size_t)n * b);
+  C* Q = (C*)p; p += align256(z * (size_t)m * b);
+  C* Rw = (C*)p; p += align256(z * (size_t)b * b);
+  C* L = (C*)p; p += align256(z * (size_t)b * b);
+  void* jw = p; p += jacobi_bytes<C>(b, b);
+  double2* G64 = (double2*)p; p += align256(zd * (size_t)b * b);
+  double2* WH64 = (double2*)p; p += align256(zd * (size_t)b * b);
+  double* sig64 = (double*)p; p += align256(sizeof(double) * b);
+  int* idx64 = (int*)p;
+  const C one = cx<C>(1.0, 0.0), zero = cx<C>(0.0, 0.0);
+  cudaError_t e;
+  k_omega<C><<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
+  if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
+  if ((e = orth_panel<C>(Q, m, b, nullptr, s)) != cudaSuccess) return e;
+  for (int it = 0; it < power_iters; ++it) {
+    if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
+    if ((e = orth_panel<C>(W, n, b, nullptr, s)) != cudaSuccess) return e;
+    if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
+    if ((e = orth_panel<C>(Q, m, b, nullptr, s)) != cudaSuccess) return e;
+  }
+  if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
+  if ((e = orth_panel<C>(W, n, b, Rw, s)) != cudaSuccess) return e;
+  if ((e = launch_conj_transpose(Rw, b, b, L, s)) != cudaSuccess) return e;
+  SvdWork<C> w = carve<C>(jw, b, b);
+  if ((e = cudaMemsetAsync(w.counters, 0, 64, s)) != cudaSuccess) return e;
+  k_svd_init<C><<<grid_for(2LL * b * b, 256), 256, 0, s>>>(L, b, b, w);
+  if ((e = launch_jacobi(w, b, b, jtol, 60, status, s)) != cudaSuccess) return e;
+  k_row_norms<C><<<(b * 32 + 255) / 256, 256, 0, s>>>(w, b, b);
+  k_select<C><<<1, 256, 0, s>>>(w, b, k);
+  const double2* WHo;
+  const double2* Go;
+  const int* idxo;
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if ((e = smem_optin<k_jacobi_cut64>()) != cudaSuccess) return e;
+    k_jacobi_cut64<<<1, 1024, cut64_smem(b, k), s>>>(w, b, k, G64, WH64, sig64, idx64);
+    WHo = WH64;
+    Go = G64;
+    idxo = idx64;
+  } else {
+    WHo = w.WH;
+    Go = w.G;
+    idxo = w.idx;
+  }
+  k_rand_out64<C><<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(Q, m, b, WHo, Go, idxo, W, n, k,
+                                                                                  U, Rem);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, float2* Rem, void* work, int* status,
@@ -1298,63 +1447,15 @@ cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, 
   const int M = m < n ? m : n;
   const int b = rand_block(m, n, chi);
   if (b >= M) return jacobi_svd<float2>(Z, m, n, chi, U, Rem, work, status, s, jacobi_tol_c64(std::max(m, n)), 60);
-  const int k = chi < M ? chi : M;
-  const int N = m < n ? n : m;
-  size_t z = sizeof(float2);
-  char* p = (char*)work;
-  float2* W = (float2*)p; p += align256(z * (size_t)n * b);
-  float2* Q = (float2*)p; p += align256(z * (size_t)m * b);
-  float2* X = (float2*)p; p += align256(z * (size_t)N * b);
-  float2* orth = (float2*)p; p += align256(z * ((size_t)N * b + b));
-  void* jw = p;
-  const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-  cudaError_t e;
-  k_omega<<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
-  const bool staged = TsqrSmem<float2>::bytes(N, b) <= (size_t)kSmemMax;
-  auto orthonormalise = [&](float2* Y, int rows) {
-    KTimerScope timer(KC_ORTH, s, qr_flops(rows, b));
-    if (staged) tsqr_launch<float2>(Y, rows, b, Y, nullptr, rows, s);
-    else k_orth<<<1, 256, 0, s>>>(Y, rows, b, orth);
-  };
-  // Q = orth(Z W)
-  if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
-  orthonormalise(Q, m);
-  for (int it = 0; it < power_iters; ++it) {
-    if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
-    orthonormalise(W, n);
-    if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
-    orthonormalise(Q, m);
-  }
-  if (staged) {
-    // last half step keeps R: Z^H Q = W R_W, so B = Q^H Z = R_W^H W^H and the
-    // Jacobi runs on the b x b matrix L = R_W^H instead of the b x n matrix B
-    if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
-    float2* Rw = X;
-    float2* L = X + (size_t)b * b;
-    {
-      KTimerScope timer(KC_ORTH, s, qr_flops(n, b));
-      if ((e = tsqr_launch<float2>(W, n, b, W, Rw, n, s)) != cudaSuccess) return e;
-    }
-    if ((e = launch_conj_transpose(Rw, b, b, L, s)) != cudaSuccess) return e;
-    SvdWork<float2> w = carve<float2>(jw, b, b);
-    if ((e = cudaMemsetAsync(w.counters, 0, 64, s)) != cudaSuccess) return e;
-    k_svd_init<float2><<<grid_for(2LL * b * b, 256), 256, 0, s>>>(L, b, b, w);
-    if ((e = launch_jacobi(w, b, b, jacobi_tol_c64(n), 60, status, s)) != cudaSuccess) return e;
-    k_row_norms<float2><<<(b * 32 + 255) / 256, 256, 0, s>>>(w, b, b);
-    k_select<float2><<<1, 256, 0, s>>>(w, b, k);
-    k_rand_out_lw<<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(Q, m, b, w, W, n, k, U, Rem);
-    return cudaGetLastError();
-  }
-  // B = Q^H Z (b x n) into X, then Jacobi on its rows (b <= n here)
-  if ((e = launch_zgemm('C', 'N', b, n, m, one, Q, b, 0, Z, n, 0, zero, X, n, 0, 1, s)) != cudaSuccess) return e;
-  SvdWork<float2> w = carve<float2>(jw, b, n);
-  if ((e = cudaMemsetAsync(w.counters, 0, 64, s)) != cudaSuccess) return e;
-  k_svd_init<float2><<<grid_for((long long)b * n + (long long)b * b, 256), 256, 0, s>>>(X, b, n, w);
-  if ((e = launch_jacobi(w, b, n, jacobi_tol_c64(n), 60, status, s)) != cudaSuccess) return e;
-  k_row_norms<float2><<<(b * 32 + 255) / 256, 256, 0, s>>>(w, b, n);
-  k_select<float2><<<1, 256, 0, s>>>(w, b, k);
-  k_rand_out<<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(Q, m, b, w, n, k, U, Rem);
-  return cudaGetLastError();
+  return rand_svd<float2>(Z, m, n, chi, b, U, Rem, work, status, s, power_iters, jacobi_tol_c64(n));
+}
+
+cudaError_t launch_svd_trunc_rand64(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work,
+                                    int* status, cudaStream_t s, int power_iters) {
+  const int M = m < n ? m : n;
+  const int b = rand_block64(m, n, chi);
+  if (b >= M) return jacobi_svd<double2>(Z, m, n, chi, U, Rem, work, status, s, 1e-14, 60);
+  return rand_svd<double2>(Z, m, n, chi, b, U, Rem, work, status, s, power_iters, 1e-14);
 }
 
 cudaError_t svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, cudaStream_t s) {
@@ -1669,6 +1770,8 @@ cudaError_t init_kernel_attributes() {
   if ((e = smem_optin<k_tsqr_reg<16>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_smem<double2>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_smem<float2>>()) != cudaSuccess) return e;
+  if ((e = smem_optin<k_jacobi_cut64>()) != cudaSuccess) return e;
+  if ((e = init_panel_attributes()) != cudaSuccess) return e;
   return init_tc_attributes();
 }
 

@@ -4,13 +4,17 @@
 // code running inside a CUDA-graph capture of someone else's stream, real-time
 // loops that must not enter the allocator (cudaMalloc synchronises the
 // device), or hosts whose allocator is owned by another runtime.  For them
-// this file keeps the SVD scratch in a fixed device array that the library
-// reserves when it is loaded, so a call needs no allocation at all.
+// this file keeps the SVD scratch in a fixed device array, so a call needs no
+// allocation of its own.
 //
-// The array below is a host-side stand-in in host code: its device address is
-// looked up with cudaGetSymbolAddress, once per device, with that device
-// current, the first time the entry point runs there.  That first call should
-// therefore happen before any stream capture starts.
+// The array is created on a device when this module is loaded there.  With
+// CUDA's lazy module loading (the default) that happens at the first call of
+// the entry point on that device, which also looks up the array's device
+// address (cudaGetSymbolAddress, once per device, with that device current;
+// the array's name is only a host-side stand-in in host code).  That first
+// call should therefore come before any stream capture starts.  The kernel
+// timer (bbp_ktimer_select) does not time launches inside a capture that the
+// library did not start, so a selected timer class records nothing there.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -62,6 +62,15 @@ cudaError_t launch_svd_trunc(const double2* Z, int m, int n, int chi, double2* U
                              int* status, cudaStream_t s);
 cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, float2* Rem, void* work, int* status,
                              cudaStream_t s, int power_iters);
+// complex128 randomised truncation (the engine's FP64 path): b = 2 chi
+// directions, power_iters power steps (six by default), the b x b factor by
+// complex128 Jacobi; small matrices (min(m, n) <= max(4 chi, 64)) take the
+// exact Jacobi.
+int rand_block64(int m, int n, int chi);
+size_t svd_work_bytes_rand64(int m, int n, int chi);
+size_t svd_work_bound_rand64(int max_min, int max_max, int chi);
+cudaError_t launch_svd_trunc_rand64(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work,
+                                    int* status, cudaStream_t s, int power_iters);
 // Sweeps and rotations of the last complex128 launch_svd_trunc that used `work` (synchronises s).
 cudaError_t svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, cudaStream_t s);
 
@@ -151,6 +160,20 @@ inline double qr_flops(int m, int n) {
   const double a = m > n ? m : n, k = m < n ? m : n;
   return 16.0 * (2.0 * a * k * k - 2.0 * k * k * k / 3.0);
 }
+
+// Householder QR of tall panels on a cluster of up to kPanelMaxCluster CTAs
+// (k_panel.cu): A (m x n, m >= n, row-major, not modified) = Q (m x n) R
+// (n x n, upper triangular, real diagonal); Q or R may be null.  Q may alias
+// A.  batch panels at a stride of `stride` elements (R at n * n).
+// panel_cluster: the cluster size used for an m x n panel of elem-byte
+// entries (0 when it does not fit 16 CTAs' shared memory).
+constexpr int kPanelMaxCluster = 16;
+int panel_cluster(int m, int n, size_t elem);
+cudaError_t init_panel_attributes();
+cudaError_t launch_panel_qr(const float2* A, int m, int n, float2* Q, float2* R, int batch, long long stride,
+                            cudaStream_t s);
+cudaError_t launch_panel_qr(const double2* A, int m, int n, double2* Q, double2* R, int batch, long long stride,
+                            cudaStream_t s);
 
 // Allocation-free truncated SVD (k_noalloc.cu): scratch in a fixed device
 // array of noalloc_scratch_bytes(); *too_large is set when svd_work_bytes(m, n)

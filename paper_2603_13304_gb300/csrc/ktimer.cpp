@@ -22,12 +22,14 @@ struct Pair {
   cudaEvent_t a = nullptr, b = nullptr;
   double flops = 0.0;
   long long tag = -1;
+  long long gen = 0;   // selection during which the pair was recorded
 };
 
 std::mutex g_mu;
 std::atomic<int> g_class{0};   // read on every launch path without the lock
 std::vector<Pair> g_pairs;
 long long g_n = 0;
+long long g_gen = 0;
 double g_ms = 0.0, g_flops = 0.0;
 double* g_dev_flops = nullptr;   // kernels that count their own work add here
 thread_local long long t_tag = -1;
@@ -40,10 +42,19 @@ void destroy(Pair& p) {
 
 }  // namespace
 
+// A new selection drops the eager pairs only: pairs with a graph tag are
+// event nodes of a captured graph that a live context may replay, so they
+// stay valid until that graph is dropped (ktimer_drop_tag); they are no
+// longer counted, because they belong to an earlier selection.
 void ktimer_select(int cls) {
   std::lock_guard<std::mutex> lk(g_mu);
-  for (Pair& p : g_pairs) destroy(p);
-  g_pairs.clear();
+  std::vector<Pair> keep;
+  for (Pair& p : g_pairs) {
+    if (p.tag == -1) destroy(p);
+    else keep.push_back(p);
+  }
+  g_pairs.swap(keep);
+  ++g_gen;
   g_class = cls;
   g_n = 0;
   g_ms = g_flops = 0.0;
@@ -89,6 +100,12 @@ KTimerScope::KTimerScope(int cls, cudaStream_t s, double flops) : s_(s) {
     return;
   }
   external_ = cs == cudaStreamCaptureStatusActive;
+  // a capture that the engine did not start (no graph tag): the caller's
+  // graph would own the events, which eager collection destroys; not timed
+  if (external_ && p.tag == -1) {
+    destroy(p);
+    return;
+  }
   if ((external_ ? cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal) : cudaEventRecord(p.a, s)) != cudaSuccess) {
     cudaGetLastError();   // a failed timing record must not surface as the launch's error
     destroy(p);
@@ -97,6 +114,7 @@ KTimerScope::KTimerScope(int cls, cudaStream_t s, double flops) : s_(s) {
   a_ = p.a;
   b_ = p.b;
   std::lock_guard<std::mutex> lk(g_mu);
+  p.gen = g_gen;
   g_pairs.push_back(p);
 }
 
@@ -118,7 +136,7 @@ void ktimer_collect(long long tag) {
       continue;
     }
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+    if (p.gen == g_gen && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       g_ms += ms;
       g_flops += p.flops;
       ++g_n;

@@ -47,6 +47,8 @@ int host_threads() {
   return n;
 }
 
+// The workers start on the calling thread's current device (a new host
+// thread would otherwise start on device 0).
 template <typename F>
 void parallel_for(size_t n, F&& f) {
   const int T = (int)std::min<size_t>(n, (size_t)host_threads());
@@ -54,11 +56,17 @@ void parallel_for(size_t n, F&& f) {
     for (size_t i = 0; i < n; ++i) f(i);
     return;
   }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = -1;
+  }
   std::atomic<size_t> next{0};
   std::vector<std::thread> ts;
   ts.reserve(T);
   for (int t = 0; t < T; ++t)
-    ts.emplace_back([&] {
+    ts.emplace_back([&, dev] {
+      if (dev >= 0) cudaSetDevice(dev);
       for (size_t i; (i = next.fetch_add(1)) < n;) f(i);
     });
   for (auto& t : ts) t.join();

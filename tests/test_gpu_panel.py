@@ -1,0 +1,155 @@
+"""The cluster Householder panel QR and the complex64 truncated SVD, through
+the C ABI, against the definitions they implement.
+
+* Panel QR (Sec. 2.3.3 canonical moves and the range orthonormalisation):
+  A = Q R with Q^H Q = I and R upper triangular with a real diagonal, on
+  one-CTA and multi-CTA cluster shapes, ragged row slices, batches, and
+  rank-deficient panels.
+* Truncated SVD of complex64 matrices (Sec. 1.1.1): U Rem equals the best
+  rank-k approximation of Z (Eckart-Young, from numpy's SVD of the same
+  matrix in complex128) within the complex64 accuracy of the path, and U has
+  orthonormal columns.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2603_13304_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build()
+    P.lib()
+
+
+def crandn(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def run_panel(A, c64, with_q=True, with_r=True, batch=1):
+    dt = torch.complex64 if c64 else torch.complex128
+    m, n = A.shape[-2:]
+    Ad = torch.from_numpy(np.ascontiguousarray(A)).to(dt).cuda()
+    Qd = torch.zeros((batch, m, n), dtype=dt, device="cuda") if with_q else None
+    Rd = torch.full((batch, n, n), 7.0, dtype=dt, device="cuda") if with_r else None
+    P.bbp_k_panel_qr(c64, Ad.data_ptr(), m, n, Qd.data_ptr() if with_q else None,
+                     Rd.data_ptr() if with_r else None, batch)
+    torch.cuda.synchronize()
+    return (Qd.cpu().numpy() if with_q else None), (Rd.cpu().numpy() if with_r else None)
+
+
+SHAPES = [(512, 48), (2304, 96), (2300, 96), (517, 50), (1024, 64), (3072, 128), (64, 64), (96, 1)]
+
+
+@pytest.mark.parametrize("c64", [True, False])
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_panel_qr(c64, m, n):
+    if P.bbp_k_panel_cluster(c64, m, n) == 0:
+        pytest.skip("panel does not fit a 16-CTA cluster in this precision")
+    rng = np.random.default_rng(m * 7 + n)
+    # columns with a geometric spread of scales (1 .. 1e-6): rank revealing work
+    A = crandn(rng, m, n) * np.logspace(0, -6, n)[None, :]
+    if c64:
+        A = A.astype(np.complex64).astype(np.complex128)
+    Q, R = run_panel(A, c64)
+    Q, R = Q[0], R[0]
+    eps = 1e-6 if c64 else 1e-14
+    assert np.abs(np.tril(R, -1)).max() == 0.0
+    assert np.abs(np.diag(R).imag).max() == 0.0
+    orth = np.abs(Q.conj().T @ Q - np.eye(n)).max()
+    rec = np.linalg.norm(Q @ R - A) / np.linalg.norm(A)
+    print(f"panel {m}x{n} c64={c64} cluster={P.bbp_k_panel_cluster(c64, m, n)}: |Q^H Q - I| {orth:.2e}, "
+          f"|QR - A|/|A| {rec:.2e}")
+    assert orth < 30 * eps * np.sqrt(m)
+    assert rec < 30 * eps * np.sqrt(m)
+    # R alone equals the R of the full call (same arithmetic)
+    _, R2 = run_panel(A, c64, with_q=False)
+    assert np.array_equal(R2[0], R)
+
+
+@pytest.mark.parametrize("c64", [True, False])
+def test_panel_qr_rank_deficient(c64):
+    """Zero and repeated columns: Q stays orthonormal and Q R = A."""
+    rng = np.random.default_rng(5)
+    m, n = 1500, 40
+    A = crandn(rng, m, n)
+    A[:, 3] = 0
+    A[:, 10] = A[:, 2]
+    A[:, 20] = 2j * A[:, 5]
+    A[:, 39] = 0
+    Q, R = run_panel(A, c64)
+    eps = 1e-6 if c64 else 1e-14
+    assert np.abs(Q[0].conj().T @ Q[0] - np.eye(n)).max() < 30 * eps * np.sqrt(m)
+    assert np.linalg.norm(Q[0] @ R[0] - A) / np.linalg.norm(A) < 30 * eps * np.sqrt(m)
+
+
+def test_panel_qr_batch_equals_single():
+    rng = np.random.default_rng(9)
+    m, n = 2304, 96
+    A = crandn(rng, 2, m, n).astype(np.complex64)
+    Qb, Rb = run_panel(A, True, batch=2)
+    for i in range(2):
+        Qs, Rs = run_panel(A[i], True)
+        assert np.array_equal(Qb[i], Qs[0]) and np.array_equal(Rb[i], Rs[0])
+
+
+def geometric_matrix(rng, m, n, decay):
+    k = min(m, n)
+    U, _ = np.linalg.qr(crandn(rng, m, k))
+    V, _ = np.linalg.qr(crandn(rng, n, k))
+    s = decay ** np.arange(k)
+    return (U * s) @ V.conj().T
+
+
+def run_svd(Z, chi, c64, q):
+    m, n = Z.shape
+    k = min(chi, m, n)
+    dt = torch.complex64 if c64 else torch.complex128
+    Zd = torch.from_numpy(np.ascontiguousarray(Z)).to(dt).cuda()
+    U = torch.zeros((m, k), dtype=dt, device="cuda")
+    Rem = torch.zeros((k, n), dtype=dt, device="cuda")
+    work = torch.zeros(P.bbp_k_svd_work_bytes_rand(c64, m, n, chi), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P.bbp_k_svd_trunc_rand(c64, Zd.data_ptr(), m, n, chi, U.data_ptr(), Rem.data_ptr(), work.data_ptr(),
+                           status.data_ptr(), q)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    return U.cpu().numpy().astype(np.complex128), Rem.cpu().numpy().astype(np.complex128)
+
+
+def check_svd(Z, Uh, Rh, k, tag, err_tol, orth_tol):
+    u, s, vh = np.linalg.svd(Z, full_matrices=False)
+    best = (u[:, :k] * s[:k]) @ vh[:k]
+    err = np.linalg.norm(Uh @ Rh - best) / np.linalg.norm(Z)
+    orth = np.abs(Uh.conj().T @ Uh - np.eye(k)).max()
+    sv = np.sort(np.linalg.norm(Rh, axis=1))[::-1]
+    sig = np.abs(sv - s[:k]).max() / s[0]
+    print(f"{tag}: |U Rem - best_k|/|Z| {err:.2e}, |U^H U - I| {orth:.2e}, sigma rel err {sig:.2e}")
+    assert err < err_tol and orth < orth_tol and sig < err_tol
+
+
+@pytest.mark.parametrize("m,n,chi,decay", [(512, 512, 32, 0.9), (2304, 2304, 64, 0.93), (2304, 1296, 64, 0.9),
+                                           (1296, 64, 64, 0.8), (100, 90, 16, 0.7)])
+def test_svd_trunc_c64(m, n, chi, decay):
+    rng = np.random.default_rng(m + n + chi)
+    Z = geometric_matrix(rng, m, n, decay).astype(np.complex64).astype(np.complex128)
+    k = min(chi, m, n)
+    Uh, Rh = run_svd(Z, chi, True, 1)
+    check_svd(Z, Uh, Rh, k, f"svd c64 {m}x{n} chi {chi}", 2e-5, 1e-4)
+
+
+@pytest.mark.parametrize("m,n,chi,decay", [(512, 512, 32, 0.9), (512, 256, 32, 0.8), (1296, 1296, 64, 0.95),
+                                           (300, 280, 8, 0.6)])
+def test_svd_trunc_rand64(m, n, chi, decay):
+    """complex128 subspace iteration (b = 2 chi, six power steps) against the
+    exact truncation: within 1e-12 of ||Z|| on geometric spectra."""
+    rng = np.random.default_rng(3 * m + n + chi)
+    Z = geometric_matrix(rng, m, n, decay)
+    k = min(chi, m, n)
+    Uh, Rh = run_svd(Z, chi, False, 6)
+    check_svd(Z, Uh, Rh, k, f"svd c128 randomised {m}x{n} chi {chi}", 1e-12, 1e-12)

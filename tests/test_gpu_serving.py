@@ -154,3 +154,31 @@ def test_server_admission_by_footprint():
     wait = [r[0]["wait_s"] for r in res]
     print("latencies", lat, "waits", wait)
     assert wait[1] > 0 and wait[2] >= wait[1] * 0.5
+
+
+def test_kernel_timer_reselect_keeps_captured_graphs_valid():
+    """Selecting a timer class bakes event nodes into the captured iteration
+    graph; selecting another class (or none) afterwards must leave those
+    events alive, so that replaying the graph computes what a context that
+    never used the timer computes."""
+    s = spec("square", 31, 2, 8, P.FP64)
+    ref = make_ctx(s)
+    ctx = make_ctx(s)
+    try:
+        P.bbp_iterate(ref, 0.0, 10)
+        P.bbp_iterate(ctx, 0.0, 3)
+        P.bbp_ktimer_select(P.KT_JACOBI)
+        P.bbp_set_execution(ctx, True, 4)        # recapture with the timer's event nodes
+        P.bbp_iterate(ctx, 0.0, 4)
+        n, ms, _ = P.bbp_ktimer_read()
+        assert n > 0 and ms > 0.0
+        P.bbp_ktimer_select(0)
+        P.bbp_iterate(ctx, 0.0, 3)                # replays the graphs holding those events
+        n2, _, _ = P.bbp_ktimer_read()
+        assert n2 == 0
+        a, b = messages(ref), messages(ctx)
+        assert max(float(np.abs(a[k] - b[k]).max()) for k in a) < 1e-12
+    finally:
+        P.bbp_ktimer_select(0)
+        P.bbp_destroy(ctx)
+        P.bbp_destroy(ref)
