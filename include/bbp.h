@@ -289,11 +289,13 @@ bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, 
  * (m >= n, row-major, not modified) at a stride of m * n elements; Q (m x n
  * per panel, may equal A) and R (n x n per panel, upper triangular with a
  * real diagonal) are written when not NULL.  c64 = 1: complex64 entries,
- * 0: complex128.  BBP_ERR_ARG when m < n or the panel does not fit
- * (bbp_k_panel_cluster returns 0 for it); otherwise the number of CTAs of
- * the cluster that one panel takes. */
+ * 0: complex128.  cluster: CTAs per panel, 0 = automatic; otherwise at
+ * least bbp_k_panel_cluster(c64, m, n) (the fewest whose shared memory holds
+ * the panel; 0 when even 16 do not) and at most 16.  BBP_ERR_ARG when m < n
+ * or the panel does not fit. */
 int bbp_k_panel_cluster(int c64, int m, int n);
-bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R, int batch, void* stream);
+bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R, int batch, int cluster,
+                          void* stream);
 
 /* The engine's truncated SVD (Sec. 1.1.1) with the randomised range
  * reduction (see bbp_set_power_iters): Z (m x n, device, row-major) -> U
@@ -302,12 +304,15 @@ bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R
  * max(8, chi/2) directions whose b x b reduced factor is finished in
  * complex128.  c64 = 0: complex128 entries, b = 2 chi directions, the
  * reduced factor by complex128 Jacobi.  Matrices too small to gain from the
- * reduction take the exact one-sided Jacobi.  power_iters: 0..8.  work:
- * device scratch of bbp_k_svd_work_bytes_rand(c64, m, n, chi) bytes; status
- * as for bbp_k_svd_trunc. */
-size_t bbp_k_svd_work_bytes_rand(int c64, int m, int n, int chi);
+ * reduction take the exact one-sided Jacobi.  power_iters: 0..8.
+ * tensor_cores = 1 (complex64 only): the range-finder products run as
+ * split-TF32 tcgen05 GEMMs (device int err, set to 1 on a pipeline timeout,
+ * as for bbp_k_tc_gemm); 0: SIMT GEMMs (err may be NULL).  work: device
+ * scratch of bbp_k_svd_work_bytes_rand(c64, m, n, chi, tensor_cores) bytes;
+ * status as for bbp_k_svd_trunc. */
+size_t bbp_k_svd_work_bytes_rand(int c64, int m, int n, int chi, int tensor_cores);
 bbp_status bbp_k_svd_trunc_rand(int c64, const void* Z, int m, int n, int chi, void* U, void* Rem, void* work,
-                                int* status, int power_iters, void* stream);
+                                int* status, int power_iters, int tensor_cores, int* err, void* stream);
 
 /* K2 on the tensor cores (tcgen05.mma, TMEM accumulator, TMA-fed operands).
  * Real GEMM C (M x N, device fp32, row stride ldc) = alpha * A * B with
@@ -329,6 +334,14 @@ bbp_status bbp_k_tc_gemm(int bf16, const void* A, long long lda, const void* Bt,
 size_t bbp_k_tc_absorb_bytes(int bf16, int P, int Q, int l, int r);
 bbp_status bbp_k_tc_absorb(int bf16, int c64, const void* X, int P, int Q, const void* S, int l, int r, void* R,
                            void* work, int* err, void* stream);
+
+/* ALU throughput microbenchmark (no counterpart in the thesis; it measures
+ * the FP64 and FP32 denominators of the roofline fractions): blocks x 256
+ * threads run iters rounds of 8 independent FMA chains in FP64 (fp64 = 1) or
+ * FP32.  out: device scratch of 8 bytes (written only to keep the chains
+ * live).  Returns after enqueueing; *flops_out receives the flop count of the
+ * launch, so the caller's event timing gives the rate. */
+bbp_status bbp_k_fma_peak(int fp64, int blocks, int iters, void* out, double* flops_out, void* stream);
 
 /* Host-side plan of one boundary-MPS sweep (no GPU needed): for block `block`
  * and out face `face`, the swallow order as (kind, id) pairs: kind 0 = site

@@ -27,7 +27,7 @@ EXPORTS = [
     "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
     "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message",
     "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
-    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_panel_cluster", "bbp_k_panel_qr", "bbp_k_svd_work_bytes_rand", "bbp_k_svd_trunc_rand", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
+    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_panel_cluster", "bbp_k_panel_qr", "bbp_k_svd_work_bytes_rand", "bbp_k_svd_trunc_rand", "bbp_k_fma_peak", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
     "bbp_batch_iterate", "bbp_server_create", "bbp_job_footprint_bytes", "bbp_server_submit", "bbp_server_step",
     "bbp_server_poll", "bbp_server_take", "bbp_server_destroy", "bbp_ktimer_select", "bbp_ktimer_read",
     "bbp_k_tc_absorb_bytes", "bbp_k_tc_absorb", "bbp_plan_debug",
@@ -75,9 +75,10 @@ _PROTOS = {
     "bbp_k_svd_stats": (_i, [_vp, _i, _i, _ip, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "bbp_k_qr": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
     "bbp_k_panel_cluster": (_i, [_i, _i, _i]),
-    "bbp_k_panel_qr": (_i, [_i, _vp, _i, _i, _vp, _vp, _i, _vp]),
-    "bbp_k_svd_work_bytes_rand": (ctypes.c_size_t, [_i, _i, _i, _i]),
-    "bbp_k_svd_trunc_rand": (_i, [_i, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _vp]),
+    "bbp_k_panel_qr": (_i, [_i, _vp, _i, _i, _vp, _vp, _i, _i, _vp]),
+    "bbp_k_svd_work_bytes_rand": (ctypes.c_size_t, [_i, _i, _i, _i, _i]),
+    "bbp_k_fma_peak": (_i, [_i, _i, _i, _vp, _dp, _vp]),
+    "bbp_k_svd_trunc_rand": (_i, [_i, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp]),
     "bbp_set_execution": (_i, [_vp, _i, _i]),
     "bbp_set_power_iters": (_i, [_vp, _i]),
     "bbp_batch_iterate": (_i, [ctypes.POINTER(_vp), _i, ctypes.c_double, _i, _ip, ctypes.POINTER(ctypes.c_double), _ip]),
@@ -310,18 +311,25 @@ def bbp_k_panel_cluster(c64: bool, m: int, n: int) -> int:
     return int(lib().bbp_k_panel_cluster(int(c64), m, n))
 
 
-def bbp_k_panel_qr(c64: bool, A, m: int, n: int, Q, R, batch: int = 1, stream=None):
-    _check(lib().bbp_k_panel_qr(int(c64), _devptr(A), m, n, _devptr(Q), _devptr(R), batch, _stream(stream)))
+def bbp_k_panel_qr(c64: bool, A, m: int, n: int, Q, R, batch: int = 1, cluster: int = 0, stream=None):
+    _check(lib().bbp_k_panel_qr(int(c64), _devptr(A), m, n, _devptr(Q), _devptr(R), batch, cluster,
+                                _stream(stream)))
 
 
-def bbp_k_svd_work_bytes_rand(c64: bool, m: int, n: int, chi: int) -> int:
-    return int(lib().bbp_k_svd_work_bytes_rand(int(c64), m, n, chi))
+def bbp_k_svd_work_bytes_rand(c64: bool, m: int, n: int, chi: int, tensor_cores: bool = False) -> int:
+    return int(lib().bbp_k_svd_work_bytes_rand(int(c64), m, n, chi, int(tensor_cores)))
 
 
 def bbp_k_svd_trunc_rand(c64: bool, Z, m: int, n: int, chi: int, U, Rem, work, status, power_iters: int,
-                         stream=None):
+                         tensor_cores: bool = False, err=None, stream=None):
     _check(lib().bbp_k_svd_trunc_rand(int(c64), _devptr(Z), m, n, chi, _devptr(U), _devptr(Rem), _devptr(work),
-                                      _devptr(status), power_iters, _stream(stream)))
+                                      _devptr(status), power_iters, int(tensor_cores), _devptr(err), _stream(stream)))
+
+
+def bbp_k_fma_peak(fp64: bool, blocks: int, iters: int, out, stream=None) -> float:
+    fl = ctypes.c_double()
+    _check(lib().bbp_k_fma_peak(int(fp64), blocks, iters, _devptr(out), ctypes.byref(fl), _stream(stream)))
+    return fl.value
 
 
 def bbp_set_execution(ctx, use_graphs: bool = True, max_streams: int = 16):

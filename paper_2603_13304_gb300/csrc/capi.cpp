@@ -397,34 +397,45 @@ int bbp_k_panel_cluster(int c64, int m, int n) {
   return bbp::panel_cluster(m, n, c64 ? sizeof(float2) : sizeof(double2));
 }
 
-bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R, int batch, void* stream) {
+bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R, int batch, int cluster,
+                          void* stream) {
   if (!A || m < 1 || n < 1 || m < n || batch < 1) return set_err(BBP_ERR_ARG, "bad arguments");
-  if (bbp_k_panel_cluster(c64, m, n) == 0) return set_err(BBP_ERR_ARG, "panel too large for a 16-CTA cluster");
+  const int cmin = bbp_k_panel_cluster(c64, m, n);
+  if (cmin == 0) return set_err(BBP_ERR_ARG, "panel too large for a 16-CTA cluster");
+  if (cluster != 0 && (cluster < cmin || cluster > bbp::kPanelMaxCluster))
+    return set_err(BBP_ERR_ARG, "cluster size out of range for this panel");
   if (cudaError_t ae = bbp::init_kernel_attributes()) return cuda_status(ae);
   const long long stride = (long long)m * n;
   if (c64)
     return cuda_status(bbp::launch_panel_qr((const float2*)A, m, n, (float2*)Q, (float2*)R, batch, stride,
-                                            (cudaStream_t)stream));
+                                            (cudaStream_t)stream, cluster));
   return cuda_status(bbp::launch_panel_qr((const double2*)A, m, n, (double2*)Q, (double2*)R, batch, stride,
-                                          (cudaStream_t)stream));
+                                          (cudaStream_t)stream, cluster));
 }
 
-size_t bbp_k_svd_work_bytes_rand(int c64, int m, int n, int chi) {
+size_t bbp_k_svd_work_bytes_rand(int c64, int m, int n, int chi, int tensor_cores) {
   if (m < 1 || n < 1 || chi < 1) return 0;
-  return c64 ? bbp::svd_work_bytes_c64(m, n, chi) : bbp::svd_work_bytes_rand64(m, n, chi);
+  return c64 ? bbp::svd_work_bytes_c64(m, n, chi, tensor_cores != 0) : bbp::svd_work_bytes_rand64(m, n, chi);
 }
 
 bbp_status bbp_k_svd_trunc_rand(int c64, const void* Z, int m, int n, int chi, void* U, void* Rem, void* work,
-                                int* status, int power_iters, void* stream) {
+                                int* status, int power_iters, int tensor_cores, int* err, void* stream) {
   if (!Z || !U || !Rem || !work || !status || m < 1 || n < 1 || chi < 1 || power_iters < 0 || power_iters > 8)
     return set_err(BBP_ERR_ARG, "bad arguments");
+  if (tensor_cores && (!c64 || !err)) return set_err(BBP_ERR_ARG, "tensor_cores needs complex64 data and err");
   if (std::min(m, n) > 4096 || chi > 64) return set_err(BBP_ERR_ARG, "matrix too large");
   if (cudaError_t ae = bbp::init_kernel_attributes()) return cuda_status(ae);
   if (c64)
     return cuda_status(bbp::launch_svd_trunc((const float2*)Z, m, n, chi, (float2*)U, (float2*)Rem, work, status,
-                                             (cudaStream_t)stream, power_iters));
+                                             (cudaStream_t)stream, power_iters, tensor_cores != 0, err));
   return cuda_status(bbp::launch_svd_trunc_rand64((const double2*)Z, m, n, chi, (double2*)U, (double2*)Rem, work,
                                                   status, (cudaStream_t)stream, power_iters));
+}
+
+bbp_status bbp_k_fma_peak(int fp64, int blocks, int iters, void* out, double* flops_out, void* stream) {
+  if (!out || !flops_out || blocks < 1 || blocks > (1 << 20) || iters < 1) return set_err(BBP_ERR_ARG, "bad arguments");
+  *flops_out = bbp::fma_peak_flops(fp64 != 0, blocks, iters);
+  return cuda_status(bbp::launch_fma_peak(fp64 != 0, blocks, iters, out, (cudaStream_t)stream));
 }
 
 bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, void* stream) {

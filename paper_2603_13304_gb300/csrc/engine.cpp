@@ -32,8 +32,29 @@ size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 // truncated SVD of one split, per element type (complex128: the randomised
 // subspace iteration with b = 2 chi, exact Jacobi for small splits)
 cudaError_t svd_call(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work, int* status,
-                     cudaStream_t s, int power_iters) {
+                     cudaStream_t s, int power_iters, bool, int*) {
   return launch_svd_trunc_rand64(Z, m, n, chi, U, Rem, work, status, s, power_iters);
+}
+
+// Segment merge C (M x N) = A (M x K) B (K x N), row-major: on the tensor
+// cores (split TF32, complex64 modes with tc) when the product is large
+// enough to pay for packing, else the SIMT GEMM.
+constexpr double kTcMergeMin = 1 << 22;   // complex multiply-adds
+size_t merge_tc_bytes(int M, int N, int K) { return tc_zpack_bytes(false, M, K) + tc_zpack_bytes(false, 2 * N, K); }
+cudaError_t merge_call(int M, int N, int K, const double2* A, const double2* B, double2* C, void*, size_t, int*,
+                       bool, cudaStream_t s) {
+  return launch_zgemm('N', 'N', M, N, K, make_double2(1, 0), A, K, 0, B, N, 0, make_double2(0, 0), C, N, 0, 1, s);
+}
+cudaError_t merge_call(int M, int N, int K, const float2* A, const float2* B, float2* C, void* tcw, size_t tcw_bytes,
+                       int* tc_err, bool tc, cudaStream_t s) {
+  if (tc && tcw && (double)M * N * K >= kTcMergeMin && merge_tc_bytes(M, N, K) <= tcw_bytes) {
+    void* Bp = (char*)tcw + tc_zpack_bytes(false, M, K);
+    cudaError_t e = tc_zpack_a(false, 'N', M, K, A, K, tcw, s);
+    if (e == cudaSuccess) e = tc_zpack_b(false, 'N', K, N, B, N, Bp, s);
+    if (e == cudaSuccess) e = tc_zgemm_packed(false, M, N, K, tcw, Bp, C, N, tc_err, s);
+    return e;
+  }
+  return launch_zgemm('N', 'N', M, N, K, make_float2(1, 0), A, K, 0, B, N, 0, make_float2(0, 0), C, N, 0, 1, s);
 }
 
 // launches of one truncated SVD (statistics only)
@@ -44,8 +65,8 @@ long long svd_launches(int m, int n, int chi, bool c64, int q) {
   return 12 + 4 * q + (c64 ? 1 : 0);
 }
 cudaError_t svd_call(const float2* Z, int m, int n, int chi, float2* U, float2* Rem, void* work, int* status,
-                     cudaStream_t s, int power_iters) {
-  return launch_svd_trunc(Z, m, n, chi, U, Rem, work, status, s, power_iters);
+                     cudaStream_t s, int power_iters, bool tensor_cores, int* tc_err) {
+  return launch_svd_trunc(Z, m, n, chi, U, Rem, work, status, s, power_iters, tensor_cores, tc_err);
 }
 }  // namespace
 
@@ -529,7 +550,8 @@ void Engine::job_needs(const SweepJob& job, size_t need[7]) const {
   need[0] = std::max<size_t>(need[0], (size_t)tr.max_tensor);
   need[1] = std::max<size_t>(need[1], (size_t)std::max(tr.max_seg, tr.max_tensor));
   need[2] = std::max<size_t>(need[2], cap_x);
-  need[3] = std::max<size_t>(need[3], precision == 0 ? svd_work_bound_rand64(mr, mc, chi) : svd_work_bound_c64(mr, mc, chi));
+  need[3] = std::max<size_t>(need[3], precision == 0 ? svd_work_bound_rand64(mr, mc, chi)
+                                                     : svd_work_bound_c64(mr, mc, chi, false));
   need[4] = std::max<size_t>(need[4], (size_t)tr.max_len + 6);
   need[5] = std::max<size_t>(need[5], (size_t)4 * chi * chi * D * D + 64);
   if (tc_mode && precision != 0)
@@ -660,8 +682,8 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
       int buf = 0;
       for (int q = st.i + 1; q <= st.j; ++q) {
         const int cols = sh[q].p * sh[q].r;
-        CK(launch_zgemm('N', 'N', (int)rows, cols, inner, one, cur, inner, 0, slot(pos[q]), cols, 0, zero, Sb[buf],
-                        cols, 0, 1, s));
+        CK(merge_call((int)rows, cols, inner, cur, slot(pos[q]), Sb[buf], w.tc, w.tc_bytes, w.status + 1,
+                      tc_mode != 0, s));
         cur = Sb[buf];
         buf ^= 1;
         rows *= sh[q].p;
@@ -737,7 +759,10 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
         const int t = take();
         const bool c64 = sizeof(C) == sizeof(float2);
         const int qsteps = c64 ? power_iters : power_iters64;
-        CK(svd_call(cur, rows, (int)cols, chi, slot(t), Rb[rbuf], w.svd, w.status, s, qsteps));
+        // the range-finder products stay on the SIMT GEMM: their K is the
+        // full split width (2304 at D = 6, chi = 64), where the tensor cores'
+        // FP32 accumulation loses an order of magnitude against it
+        CK(svd_call(cur, rows, (int)cols, chi, slot(t), Rb[rbuf], w.svd, w.status, s, qsteps, false, w.status + 1));
         launches += svd_launches(rows, (int)cols, chi, c64, qsteps);
         newpos.push_back(t);
         newsh.push_back(TShape{ll, q1, k});

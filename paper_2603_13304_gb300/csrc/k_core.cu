@@ -746,6 +746,13 @@ size_t jacobi_bytes(int M, int N) {
   return align256(sizeof(C) * (size_t)M * N) + align256(sizeof(C) * (size_t)M * M) + align256(sizeof(double) * M) +
          align256(sizeof(int) * M) + 256;
 }
+template <typename C> static bool jacobi_reduce_fits(int M, int N);
+template <typename C> static size_t jacobi_reduce_bytes(int M, int N);
+// scratch of jacobi_svd, including the QR reduction of long matrices
+template <typename C>
+size_t jacobi_svd_bytes(int M, int N) {
+  return jacobi_bytes<C>(M, N) + (jacobi_reduce_fits<C>(M, N) ? jacobi_reduce_bytes<C>(M, N) : 0);
+}
 
 // Copies Z (or Z^H) into G, sets WH = I and accumulates ||Z||^2 into *zn2;
 // the counters and *zn2 are zeroed by the caller before the launch.
@@ -792,7 +799,7 @@ template <bool kGlobal, typename C> __device__ __forceinline__ void strow(C* p, 
 // orthogonal.  Warp-cooperative (all lanes take the same decision: the xor
 // butterfly leaves bitwise identical sums in every lane); returns 1 when a
 // rotation was applied.
-template <bool kGlobal, typename C>
+template <bool kGlobal, typename C, bool kGlobalW = kGlobal>
 __device__ int rotate_pair(C* ra, C* rb, int N, C* wa, C* wb, int M, int lane, double tol,
                            typename RealOf<C>::T floor) {
   using R = typename RealOf<C>::T;
@@ -829,10 +836,10 @@ __device__ int rotate_pair(C* ra, C* rb, int N, C* wa, C* wb, int M, int lane, d
     strow<kGlobal>(rb + c, cadd(cscale(x, sn), cscale(ey, cs)));
   }
   for (int c = lane; c < M; c += 32) {
-    C x = ldrow<kGlobal>(wa + c), y = ldrow<kGlobal>(wb + c);
+    C x = ldrow<kGlobalW>(wa + c), y = ldrow<kGlobalW>(wb + c);
     C ey = cmul(e, y);
-    strow<kGlobal>(wa + c, csub(cscale(x, cs), cscale(ey, sn)));
-    strow<kGlobal>(wb + c, cadd(cscale(x, sn), cscale(ey, cs)));
+    strow<kGlobalW>(wa + c, csub(cscale(x, cs), cscale(ey, sn)));
+    strow<kGlobalW>(wb + c, cadd(cscale(x, sn), cscale(ey, cs)));
   }
   return 1;
 }
@@ -1043,6 +1050,22 @@ cudaError_t launch_jacobi(SvdWork<C> w, int M, int N, double tol, int max_sweeps
   return cudaLaunchKernelEx(&cfg, k_jacobi<C>, w, M, N, tol, floor_rel_of<C>(), max_sweeps, status, flops);
 }
 
+// G (M x N rows of Z or Z^H) too long for shared memory but with an M x M
+// square that fits: G^H = Q_T R_T (panel QR, N x M), so G = L Q_T^H with
+// L = R_T^H; the Jacobi rotates L into WH L (same singular values and WH),
+// and the rotated rows of G are (WH L) Q_T^H.  Scratch in the G area of w.
+template <typename C>
+static bool jacobi_reduce_fits(int M, int N) {
+  return sizeof(C) * ((size_t)M * N + (size_t)M * M) > (size_t)kSmemMax &&
+         2 * sizeof(C) * (size_t)M * M <= (size_t)kSmemMax && N >= 2 * M && panel_cluster(N, M, sizeof(C)) > 0;
+}
+
+// extra scratch of the reduction: G^H (N x M), Q_T (N x M), L and WH L (M x M)
+template <typename C>
+static size_t jacobi_reduce_bytes(int M, int N) {
+  return 2 * align256(sizeof(C) * (size_t)N * M) + 2 * align256(sizeof(C) * (size_t)M * M);
+}
+
 template <typename C>
 cudaError_t jacobi_svd(const C* Z, int m, int n, int chi, C* U, C* Rem, void* work, int* status, cudaStream_t s,
                        double tol, int max_sweeps) {
@@ -1052,8 +1075,34 @@ cudaError_t jacobi_svd(const C* Z, int m, int n, int chi, C* U, C* Rem, void* wo
   cudaError_t e0 = cudaMemsetAsync(w.counters, 0, 64, s);
   if (e0 != cudaSuccess) return e0;
   k_svd_init<C><<<grid_for((long long)M * N + (long long)M * M, 256), 256, 0, s>>>(Z, m, n, w);
-  cudaError_t e = launch_jacobi(w, M, N, tol, max_sweeps, status, s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (jacobi_reduce_fits<C>(M, N)) {
+    char* p = (char*)work + jacobi_bytes<C>(M, N);
+    C* GH = (C*)p; p += align256(sizeof(C) * (size_t)N * M);
+    C* QT = (C*)p; p += align256(sizeof(C) * (size_t)N * M);
+    C* Lm = (C*)p; p += align256(sizeof(C) * (size_t)M * M);
+    C* LR = (C*)p;
+    if ((e = launch_conj_transpose(w.G, M, N, GH, s)) != cudaSuccess) return e;
+    if ((e = launch_panel_qr(GH, N, M, QT, LR, 1, 0, s)) != cudaSuccess) return e;      // R_T into LR
+    if ((e = launch_conj_transpose(LR, M, M, Lm, s)) != cudaSuccess) return e;          // L = R_T^H
+    // the M x M problem in its own SvdWork view (WH = I there), same counters
+    SvdWork<C> ws = carve<C>(LR, M, M);
+    ws.counters = w.counters;
+    ws.zn2 = w.zn2;
+    ws.sigma = w.sigma;
+    ws.idx = w.idx;
+    ws.WH = w.WH;
+    ws.G = LR;
+    if ((e = cudaMemcpyAsync(LR, Lm, sizeof(C) * (size_t)M * M, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    if ((e = launch_jacobi(ws, M, M, tol, max_sweeps, status, s)) != cudaSuccess) return e;
+    // rotated rows of G: (WH L) Q_T^H (M x N)
+    if ((e = launch_zgemm('N', 'C', M, N, M, cx<C>(1, 0), LR, M, 0, QT, M, 0, cx<C>(0, 0), w.G, N, 0, 1, s)) !=
+        cudaSuccess)
+      return e;
+  } else {
+    e = launch_jacobi(w, M, N, tol, max_sweeps, status, s);
+    if (e != cudaSuccess) return e;
+  }
   k_row_norms<C><<<(M * 32 + 255) / 256, 256, 0, s>>>(w, M, N);
   k_select<C><<<1, 256, 0, s>>>(w, M, k);
   k_svd_out<C><<<grid_for((long long)m * k + (long long)k * n, 256), 256, 0, s>>>(w, m, n, k, floor_rel_of<C>(), U,
@@ -1089,20 +1138,30 @@ __global__ void k_omega(C* O, int n, int b) {
 // arithmetic, which makes the kept rows orthogonal to the discarded ones to
 // double accuracy (the rotations within either set do not change the kept
 // subspace); then the row norms and the choice of the k largest rows are
-// taken in double.  One CTA; G' in shared memory, WH in global memory.
+// taken in double.  The FP64 units of one SM are the bottleneck, so the rows
+// of G' are spread over the shared memory of a cluster of kCutCluster CTAs
+// (row r on CTA r % kCutCluster) and every round's disjoint pairs over all
+// their warps, with one cluster barrier per round; WH stays in global memory.
+constexpr int kCutCluster = 8;
+
 __global__ void __launch_bounds__(1024) k_jacobi_cut64(SvdWork<float2> w, int b, int k, double2* __restrict__ G64,
                                                        double2* __restrict__ WH64, double* __restrict__ sig64,
                                                        int* __restrict__ idx64) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int cs = (int)cl.num_blocks(), cr = (int)cl.block_rank();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* G = (double2*)smem_raw;           // b x b
-  int* kept = (int*)(G + (size_t)b * b);     // k
-  int* disc = kept + k;                      // b - k
-  int* mark = disc + (b - k);                // b
+  const int rpc = (b + cs - 1) / cs;          // rows per CTA
+  double2* G = (double2*)smem_raw;            // local rows: r = cr + cs * t at G + t * b
+  int* kept = (int*)(G + (size_t)rpc * b);    // k
+  int* disc = kept + k;                       // b - k
+  int* mark = disc + (b - k);                 // b
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    G[e] = c128(w.G[e]);
-    WH64[e] = c128(w.WH[e]);
+  for (int e = threadIdx.x; e < rpc * b; e += blockDim.x) {
+    const int t = e / b, c = e % b, r = cr + cs * t;
+    if (r < b) G[e] = c128(w.G[(size_t)r * b + c]);
   }
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x)
+    if ((e / b) % cs == cr) __stcg(WH64 + e, c128(w.WH[e]));
   for (int e = threadIdx.x; e < b; e += blockDim.x) mark[e] = 0;
   __syncthreads();
   for (int e = threadIdx.x; e < k; e += blockDim.x) {
@@ -1117,42 +1176,52 @@ __global__ void __launch_bounds__(1024) k_jacobi_cut64(SvdWork<float2> w, int b,
       if (!mark[a] && q < b - k) disc[q++] = a;
     for (; q < b - k; ++q) disc[q] = -1;     // duplicate indices in idx (never expected)
   }
-  __syncthreads();
+  cl.sync();                                  // every CTA's rows and WH rows are in place
+  auto grow = [&](int r) { return cl.map_shared_rank(G, r % cs) + (size_t)(r / cs) * b; };
   const int nd = b - k;
   const double floor = 1e-32 * (double)*w.zn2;   // eps^2 of double, as in the complex128 Jacobi
   if (nd > 0 && k > 0) {
     const int nbig = k >= nd ? k : nd, nsmall = k >= nd ? nd : k;
     const int* big = k >= nd ? kept : disc;
     const int* small = k >= nd ? disc : kept;
-    for (int r = 0; r < nbig; ++r) {         // round r: pairs (big[(p + r) % nbig], small[p]), disjoint
-      for (int p = warp; p < nsmall; p += nw) {
+    for (int r = 0; r < nbig; ++r) {          // round r: pairs (big[(p + r) % nbig], small[p]), disjoint
+      for (int p = cr + cs * warp; p < nsmall; p += cs * nw) {   // pairs dealt round-robin over the CTAs
         const int a = big[(p + r) % nbig], c = small[p];
         if (a < 0 || c < 0) continue;
-        rotate_pair<false>(G + (size_t)a * b, G + (size_t)c * b, b, WH64 + (size_t)a * b, WH64 + (size_t)c * b, b,
-                           lane, 1e-15, floor);
+        // rows of G' in (distributed) shared memory, rows of WH in global
+        // memory past L1 (other CTAs of the cluster rotate them too)
+        rotate_pair<false, double2, true>(grow(a), grow(c), b, WH64 + (size_t)a * b, WH64 + (size_t)c * b, b, lane,
+                                          1e-15, floor);
       }
-      __syncthreads();
+      cl.sync();
     }
   }
-  for (int row = warp; row < b; row += nw) {
+  // row norms and the selection in double (CTA 0), rows written back
+  for (int t = warp; t < rpc; t += nw) {
+    const int row = cr + cs * t;
+    if (row >= b) continue;
     double sq = 0.0;
-    for (int c = lane; c < b; c += 32) sq += cabs2d(G[(size_t)row * b + c]);
+    for (int c = lane; c < b; c += 32) sq += cabs2d(G[(size_t)t * b + c]);
     sq = warp_sum(sq);
-    if (lane == 0) sig64[row] = sqrt(sq);
+    if (lane == 0) __stcg(sig64 + row, sqrt(sq));
   }
-  __syncthreads();
+  for (int e = threadIdx.x; e < rpc * b; e += blockDim.x) {
+    const int t = e / b, c = e % b, r = cr + cs * t;
+    if (r < b) G64[(size_t)r * b + c] = G[e];
+  }
+  cl.sync();                                  // sig64 complete; no remote reads after this
+  if (cr != 0) return;
   for (int a = threadIdx.x; a < b; a += blockDim.x) {   // total order, non-finite norms last
-    double sa = sig64[a];
+    double sa = __ldcg(sig64 + a);
     if (!(sa >= 0.0) || !isfinite(sa)) sa = -1.0;
     int rank = 0;
     for (int c = 0; c < b; ++c) {
-      double sc = sig64[c];
+      double sc = __ldcg(sig64 + c);
       if (!(sc >= 0.0) || !isfinite(sc)) sc = -1.0;
       rank += (sc > sa) || (sc == sa && c < a);
     }
     if (rank < k) idx64[rank] = a;
   }
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) G64[e] = G[e];
 }
 
 // U = Q WH[top]^H (m x k) and Rem = G'[top] W^H (k x n): WH and G' of the
@@ -1222,10 +1291,14 @@ cudaError_t launch_zgemm(char opA, char opB, int M, int N, int K, float2 alpha, 
   return gemm_t(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, s);
 }
 
+// QR of a canonical move: one CTA when the matrix fits its shared memory, a
+// cluster of CTAs for tall panels, else one CTA over global memory.
 template <typename C>
 static cudaError_t qr_t(C* A, int m, int n, C* Q, C* R, C* tau, cudaStream_t s) {
-  KTimerScope timer(KC_QR, s, qr_flops(m, n));
   const size_t sm = TsqrSmem<C>::bytes(m, n);
+  if (sm > (size_t)kSmemMax && m >= n && panel_cluster(m, n, sizeof(C)) > 0)
+    return launch_panel_qr(A, m, n, Q, R, 1, 0, s);
+  KTimerScope timer(KC_QR, s, qr_flops(m, n));
   if (sm <= (size_t)kSmemMax) {
     cudaError_t e = tsqr_launch<C>(A, m, n, Q, R, m, s);
     if (e != cudaSuccess) return e;
@@ -1297,7 +1370,7 @@ cudaError_t launch_qr(float2* A, int m, int n, float2* Q, float2* R, float2* tau
 
 size_t svd_work_bytes(int m, int n) {
   int M = m < n ? m : n, N = m < n ? n : m;
-  return jacobi_bytes<double2>(M, N);
+  return jacobi_svd_bytes<double2>(M, N);
 }
 
 cudaError_t launch_svd_trunc(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work,
@@ -1331,16 +1404,24 @@ static size_t rand_work_bytes(int m, int n, int b) {
          align256(sizeof(int) * b) + 256;
 }
 
-size_t svd_work_bytes_c64(int m, int n, int chi) {
-  int M = m < n ? m : n, N = m < n ? n : m;
-  const int b = rand_block(m, n, chi);
-  if (b >= M) return jacobi_bytes<float2>(M, N);
-  return rand_work_bytes<float2>(m, n, b);
+// packed operands of the tensor-core range finder: Z for Z W and for Z^H Q,
+// and the small operand (W or Q)
+static size_t rand_tc_bytes(int m, int n, int b) {
+  return tc_zpack_bytes(false, m, n) + tc_zpack_bytes(false, n, m) + tc_zpack_bytes(false, 2 * b, std::max(m, n));
 }
 
-size_t svd_work_bound_c64(int max_min, int max_max, int chi) {
+size_t svd_work_bytes_c64(int m, int n, int chi, bool tensor_cores) {
+  int M = m < n ? m : n, N = m < n ? n : m;
+  const int b = rand_block(m, n, chi);
+  if (b >= M) return jacobi_svd_bytes<float2>(M, N);
+  return rand_work_bytes<float2>(m, n, b) + (tensor_cores ? rand_tc_bytes(m, n, b) : 0);
+}
+
+size_t svd_work_bound_c64(int max_min, int max_max, int chi, bool tensor_cores) {
   const int b = chi + (chi >= 16 ? chi / 2 : 8);
-  return std::max(rand_work_bytes<float2>(max_max, max_max, b), jacobi_bytes<float2>(max_min, max_max));
+  return std::max(rand_work_bytes<float2>(max_max, max_max, b) +
+                      (tensor_cores ? rand_tc_bytes(max_max, max_max, b) : 0),
+                  jacobi_bytes<float2>(max_min, max_max) + jacobi_reduce_bytes<float2>(max_min, max_max));
 }
 
 // complex128 (the 1e-10 parity path): b = 2 chi directions, so that the
@@ -1356,15 +1437,19 @@ int rand_block64(int m, int n, int chi) {
 size_t svd_work_bytes_rand64(int m, int n, int chi) {
   int M = m < n ? m : n, N = m < n ? n : m;
   const int b = rand_block64(m, n, chi);
-  if (b >= M) return jacobi_bytes<double2>(M, N);
+  if (b >= M) return jacobi_svd_bytes<double2>(M, N);
   return rand_work_bytes<double2>(m, n, b);
 }
 
 size_t svd_work_bound_rand64(int max_min, int max_max, int chi) {
-  return std::max(rand_work_bytes<double2>(max_max, max_max, 2 * chi), jacobi_bytes<double2>(max_min, max_max));
+  return std::max(rand_work_bytes<double2>(max_max, max_max, 2 * chi),
+                  jacobi_bytes<double2>(max_min, max_max) + jacobi_reduce_bytes<double2>(max_min, max_max));
 }
 
-static size_t cut64_smem(int b, int k) { return sizeof(double2) * (size_t)b * b + sizeof(int) * (size_t)(2 * b + 8); }
+static size_t cut64_smem(int b, int k) {
+  const size_t rpc = (size_t)(b + kCutCluster - 1) / kCutCluster;
+  return sizeof(double2) * rpc * b + sizeof(int) * (size_t)(2 * b + 8);
+}
 
 // Orthonormalise the columns of Y (rows x b) in place; R (b x b) too when R
 // is not null: one CTA when the panel fits its shared memory, a cluster of
@@ -1387,7 +1472,7 @@ static cudaError_t orth_panel(C* Y, int rows, int b, C* R, cudaStream_t s) {
 // complex128: the Jacobi runs in complex128.
 template <typename C>
 static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* Rem, void* work, int* status,
-                            cudaStream_t s, int power_iters, double jtol) {
+                            cudaStream_t s, int power_iters, double jtol, bool tensor_cores, int* tc_err) {
   const int M = m < n ? m : n;
   const int k = chi < M ? chi : M;
   const bool c64 = sizeof(C) == sizeof(float2);
@@ -1402,19 +1487,52 @@ static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* R
   double2* G64 = (double2*)p; p += align256(zd * (size_t)b * b);
   double2* WH64 = (double2*)p; p += align256(zd * (size_t)b * b);
   double* sig64 = (double*)p; p += align256(sizeof(double) * b);
-  int* idx64 = (int*)p;
+  int* idx64 = (int*)p; p += align256(sizeof(int) * b) + 256;
   const C one = cx<C>(1.0, 0.0), zero = cx<C>(0.0, 0.0);
   cudaError_t e;
+  // the range-finder products Y = Z W and W = Z^H Q: SIMT GEMMs, or (complex64
+  // with tensor_cores) split-TF32 tcgen05 GEMMs with Z packed once per
+  // orientation
+  const bool tc = tensor_cores && sizeof(C) == sizeof(float2) && tc_err;
+  void* Zn = p;
+  void* Zc = (char*)Zn + (tc ? tc_zpack_bytes(false, m, n) : 0);
+  void* Bp = (char*)Zc + (tc ? tc_zpack_bytes(false, n, m) : 0);
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (tc) {
+      if ((e = tc_zpack_a(false, 'N', m, n, Z, n, Zn, s)) != cudaSuccess) return e;
+      if ((e = tc_zpack_a(false, 'C', n, m, Z, n, Zc, s)) != cudaSuccess) return e;
+    }
+  }
+  auto z_times = [&](const C* X, C* Y) -> cudaError_t {   // Y (m x b) = Z X, X n x b
+    if constexpr (sizeof(C) == sizeof(float2)) {
+      if (tc) {
+        cudaError_t e2 = tc_zpack_b(false, 'N', n, b, X, b, Bp, s);
+        if (e2 != cudaSuccess) return e2;
+        return tc_zgemm_packed(false, m, b, n, Zn, Bp, Y, b, tc_err, s);
+      }
+    }
+    return launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, X, b, 0, zero, Y, b, 0, 1, s);
+  };
+  auto zh_times = [&](const C* X, C* Y) -> cudaError_t {  // Y (n x b) = Z^H X, X m x b
+    if constexpr (sizeof(C) == sizeof(float2)) {
+      if (tc) {
+        cudaError_t e2 = tc_zpack_b(false, 'N', m, b, X, b, Bp, s);
+        if (e2 != cudaSuccess) return e2;
+        return tc_zgemm_packed(false, n, b, m, Zc, Bp, Y, b, tc_err, s);
+      }
+    }
+    return launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, X, b, 0, zero, Y, b, 0, 1, s);
+  };
   k_omega<C><<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
-  if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
+  if ((e = z_times(W, Q)) != cudaSuccess) return e;
   if ((e = orth_panel<C>(Q, m, b, nullptr, s)) != cudaSuccess) return e;
   for (int it = 0; it < power_iters; ++it) {
-    if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
+    if ((e = zh_times(Q, W)) != cudaSuccess) return e;
     if ((e = orth_panel<C>(W, n, b, nullptr, s)) != cudaSuccess) return e;
-    if ((e = launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, W, b, 0, zero, Q, b, 0, 1, s)) != cudaSuccess) return e;
+    if ((e = z_times(W, Q)) != cudaSuccess) return e;
     if ((e = orth_panel<C>(Q, m, b, nullptr, s)) != cudaSuccess) return e;
   }
-  if ((e = launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, Q, b, 0, zero, W, b, 0, 1, s)) != cudaSuccess) return e;
+  if ((e = zh_times(Q, W)) != cudaSuccess) return e;
   if ((e = orth_panel<C>(W, n, b, Rw, s)) != cudaSuccess) return e;
   if ((e = launch_conj_transpose(Rw, b, b, L, s)) != cudaSuccess) return e;
   SvdWork<C> w = carve<C>(jw, b, b);
@@ -1428,7 +1546,19 @@ static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* R
   const int* idxo;
   if constexpr (sizeof(C) == sizeof(float2)) {
     if ((e = smem_optin<k_jacobi_cut64>()) != cudaSuccess) return e;
-    k_jacobi_cut64<<<1, 1024, cut64_smem(b, k), s>>>(w, b, k, G64, WH64, sig64, idx64);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCutCluster, 1, 1);
+    cfg.blockDim = dim3(std::min(1024, 32 * std::max(1, (b + 1) / 2)), 1, 1);
+    cfg.dynamicSmemBytes = cut64_smem(b, k);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCutCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, k_jacobi_cut64, w, b, k, G64, WH64, sig64, idx64)) != cudaSuccess) return e;
     WHo = WH64;
     Go = G64;
     idxo = idx64;
@@ -1443,11 +1573,12 @@ static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* R
 }
 
 cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, float2* Rem, void* work, int* status,
-                             cudaStream_t s, int power_iters) {
+                             cudaStream_t s, int power_iters, bool tensor_cores, int* tc_err) {
   const int M = m < n ? m : n;
   const int b = rand_block(m, n, chi);
   if (b >= M) return jacobi_svd<float2>(Z, m, n, chi, U, Rem, work, status, s, jacobi_tol_c64(std::max(m, n)), 60);
-  return rand_svd<float2>(Z, m, n, chi, b, U, Rem, work, status, s, power_iters, jacobi_tol_c64(n));
+  return rand_svd<float2>(Z, m, n, chi, b, U, Rem, work, status, s, power_iters, jacobi_tol_c64(n), tensor_cores,
+                          tc_err);
 }
 
 cudaError_t launch_svd_trunc_rand64(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work,
@@ -1455,7 +1586,7 @@ cudaError_t launch_svd_trunc_rand64(const double2* Z, int m, int n, int chi, dou
   const int M = m < n ? m : n;
   const int b = rand_block64(m, n, chi);
   if (b >= M) return jacobi_svd<double2>(Z, m, n, chi, U, Rem, work, status, s, 1e-14, 60);
-  return rand_svd<double2>(Z, m, n, chi, b, U, Rem, work, status, s, power_iters, 1e-14);
+  return rand_svd<double2>(Z, m, n, chi, b, U, Rem, work, status, s, power_iters, 1e-14, false, nullptr);
 }
 
 cudaError_t svd_stats(const void* work, int m, int n, int* sweeps, long long* rotations, cudaStream_t s) {

@@ -62,30 +62,53 @@ template <typename R> __device__ __forceinline__ R wsum(R v) {
 
 constexpr int kPanelThreads = 512;
 
-// sum of slot[off] over the cluster's CTAs in rank order; the remote loads
-// are issued together before the additions
+// sum of slot[off] over the cluster's CTAs in rank order (the same grouping
+// in every CTA); remote loads are issued four at a time before their additions
 template <typename C>
 __device__ __forceinline__ C cluster_sum(cg::cluster_group& cl, C* slot, size_t off, int cs) {
-  C v[kPanelMaxCluster];
-#pragma unroll
-  for (int q = 0; q < kPanelMaxCluster; ++q)
-    if (q < cs) v[q] = cl.map_shared_rank(slot, q)[off];
   C s = mkc<C>(0, 0);
+  for (int q0 = 0; q0 < cs; q0 += 4) {
+    C v[4];
 #pragma unroll
-  for (int q = 0; q < kPanelMaxCluster; ++q)
-    if (q < cs) s = padd(s, v[q]);
+    for (int u = 0; u < 4; ++u) v[u] = (q0 + u < cs) ? cl.map_shared_rank(slot, q0 + u)[off] : mkc<C>(0, 0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s = padd(s, v[u]);
+  }
   return s;
 }
 
-// dynamic shared memory of one CTA: slice (rows x (n + 1)), two exchange
-// slots of 2n entries (partial dots, row j), the gathered dots and row, tau,
-// and two partial norms
-template <typename C>
-__host__ __device__ inline size_t panel_smem(int rows, int n) {
-  return sizeof(C) * ((size_t)rows * (n + 1) + 4 * (size_t)n + 2 * (size_t)n + (size_t)n) + 4 * sizeof(double) + 64;
+__device__ __forceinline__ double cluster_sum_d(cg::cluster_group& cl, double* slot, size_t off, int cs) {
+  double s = 0.0;
+  for (int q0 = 0; q0 < cs; q0 += 4) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (q0 + u < cs) ? cl.map_shared_rank(slot, q0 + u)[off] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += v[u];
+  }
+  return s;
 }
 
+// dynamic shared memory of one CTA: the column-major slice (n columns of
+// ld = rows | 1 entries), two exchange slots of 2n entries (partial dots,
+// row j), the gathered factors and row, tau, sc and the new diagonal of
+// every step, and two partial norms
 template <typename C>
+__host__ __device__ inline size_t panel_smem(int rows, int n) {
+  return sizeof(C) * ((size_t)(rows | 1) * n + 4 * (size_t)n + 2 * (size_t)n + 3 * (size_t)n) + 4 * sizeof(double) +
+         64;
+}
+
+// Householder step j, with the cluster sums of step j already exchanged:
+//  gather   threads c >= j read the sums (thread j forms the reflector)
+//  pass A   the warp of column j + 1 updates it (and takes its partial norm)
+//  pass B   every warp updates its columns c > j + 1 and, in the same pass
+//           over their registers, takes the partial dots x'^H a_c of step
+//           j + 1 (x' = the updated column j + 1 below row j + 1)
+// Column j stays unscaled while it is read as the reflector of step j; its
+// warp scales it in the next step.  Rows of a CTA: lane l caches local rows
+// l + 32 i, i < MAXR.
+template <typename C, int MAXR>
 __global__ void __launch_bounds__(kPanelThreads) k_panel_qr(const C* __restrict__ Ag, int m, int n, int rows,
                                                             C* __restrict__ Qg, C* __restrict__ Rg, long long stride) {
   cg::cluster_group cl = cg::this_cluster();
@@ -95,192 +118,303 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_qr(const C* __restrict_
   if (Qg) Qg += panel * stride;
   if (Rg) Rg += panel * (long long)n * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ld = n + 1;
-  C* A = (C*)smem_raw;                   // local row i (global r0 + i), column c at A[i * ld + c]
-  C* slot = A + (size_t)rows * ld;       // [2][2n]: partial dots (n), row j (n)
-  C* gdot = slot + 4 * (size_t)n;        // gathered sums
-  C* grow = gdot + n;
+  const int ld = rows | 1;
+  C* A = (C*)smem_raw;                   // local row t of column c at A[c * ld + t]
+  C* slot = A + (size_t)ld * n;          // [2][2n]: partial dots (n), row j (n)
+  C* gdot = slot + 4 * (size_t)n;        // gathered sums, then the factors f_c
+  C* grow = gdot + n;                    // row j
   C* s_tau = grow + n;
-  double* pnorm = (double*)(s_tau + n);  // [2] partial squared norms
-  double* gnorm = pnorm + 2;
+  C* s_sc = s_tau + n;
+  C* s_diag = s_sc + n;
+  double* pnorm = (double*)(s_diag + n); // [2] partial squared norms
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int r0 = cr * rows;
   const int mr = max(0, min(rows, m - r0));
   const int k = min(m, n);
+  const C zero = mkc<C>(0, 0);
 
   for (long long e = threadIdx.x; e < (long long)mr * n; e += blockDim.x) {
-    const int i = (int)(e / n), c = (int)(e % n);
-    A[(size_t)i * ld + c] = Ag[(long long)(r0 + i) * n + c];
+    const int t = (int)(e / n), c = (int)(e % n);
+    A[(size_t)c * ld + t] = Ag[(long long)(r0 + t) * n + c];
   }
   __syncthreads();
 
-  // partial sums of step j into slot `par`: warps over columns c >= j
-  // (c == j: the squared norm), lanes over local rows with global row > j
-  auto partials = [&](int j, int par) {
-    C* sd = slot + (size_t)par * 2 * n;
-    const int i0 = max(0, j + 1 - r0);
-    for (int c = j + warp; c < n; c += nw) {
-      if (c == j) {
-        double s = 0.0;
-        for (int i = i0 + lane; i < mr; i += 32) {
-          const C x = A[(size_t)i * ld + j];
-          s += (double)x.x * x.x + (double)x.y * x.y;
-        }
-        s = wsum(s);
-        if (lane == 0) pnorm[par] = s;
-      } else {
-        C acc = mkc<C>(0, 0);
-        for (int i = i0 + lane; i < mr; i += 32) acc = padd(acc, pmulc(A[(size_t)i * ld + j], A[(size_t)i * ld + c]));
-        acc.x = wsum(acc.x);
-        acc.y = wsum(acc.y);
-        if (lane == 0) sd[c] = acc;
-      }
+  auto load_col = [&](int c, C (&v)[MAXR]) {
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) {
+      const int t = lane + 32 * i;
+      v[i] = t < mr ? A[(size_t)c * ld + t] : zero;
     }
-    if (j >= r0 && j < r0 + mr)          // owner of row j
-      for (int c = j + threadIdx.x; c < n; c += blockDim.x) sd[n + c] = A[(size_t)(j - r0) * ld + c];
+  };
+  auto store_col = [&](int c, const C (&v)[MAXR]) {
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) {
+      const int t = lane + 32 * i;
+      if (t < mr) A[(size_t)c * ld + t] = v[i];
+    }
+  };
+  // sum over this CTA's rows with global row > g0 of conj(x) y
+  auto dot_below = [&](const C (&x)[MAXR], const C (&y)[MAXR], int g0) {
+    C acc = zero;
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i)
+      if (r0 + lane + 32 * i > g0) acc = padd(acc, pmulc(x[i], y[i]));
+    acc.x = wsum(acc.x);
+    acc.y = wsum(acc.y);
+    return acc;
+  };
+  auto norm_below = [&](const C (&x)[MAXR], int g0) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i)
+      if (r0 + lane + 32 * i > g0 && lane + 32 * i < mr) s2 += (double)x[i].x * x[i].x + (double)x[i].y * x[i].y;
+    return wsum(s2);
+  };
+  // row g of column values y into the exchange row when this CTA owns it
+  auto put_row = [&](const C (&y)[MAXR], int g, C* dst) {
+    const int t = g - r0;
+    if (t < 0 || t >= mr) return;
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i)
+      if (lane + 32 * i == t) *dst = y[i];
   };
 
-  if (k > 0) partials(0, 0);
+  // ---- factorisation
+  if (k > 0) {                           // sums of step 0
+    C x0[MAXR];
+    load_col(0, x0);
+    if (warp == 0) {
+      const double s2 = norm_below(x0, 0);
+      if (lane == 0) pnorm[0] = s2;
+      put_row(x0, 0, slot + n + 0);
+    }
+    for (int c = 1 + warp; c < n; c += nw) {
+      C y[MAXR];
+      load_col(c, y);
+      const C d = dot_below(x0, y, 0);
+      if (lane == 0) slot[c] = d;
+      put_row(y, 0, slot + n + c);
+    }
+  }
   cl.sync();
   for (int j = 0; j < k; ++j) {
     const int par = j & 1;
+    const size_t off = (size_t)par * 2 * n, noff = (size_t)(par ^ 1) * 2 * n;
     const int owner = j / rows;
-    // gather the cluster's sums (identical order in every CTA)
     for (int c = j + threadIdx.x; c < n; c += blockDim.x) {
-      if (c > j) gdot[c] = cluster_sum(cl, slot, (size_t)par * 2 * n + c, cs);
-      grow[c] = cl.map_shared_rank(slot, owner)[(size_t)par * 2 * n + n + c];
-    }
-    if (threadIdx.x == blockDim.x - 1) {
-      double s = 0.0;
-      for (int q = 0; q < cs; ++q) s += cl.map_shared_rank(pnorm, q)[par];
-      *gnorm = s;
+      grow[c] = cl.map_shared_rank(slot, owner)[off + n + c];
+      if (c > j) {
+        gdot[c] = cluster_sum(cl, slot, off + c, cs);
+        continue;
+      }
+      const double xn2 = cluster_sum_d(cl, pnorm, par, cs);
+      const C alpha = grow[j];
+      double taur = 0, taui = 0, scr = 0, sci = 0, beta = alpha.x;
+      const double ar = alpha.x, ai = alpha.y;
+      if (!(xn2 == 0.0 && ai == 0.0)) {
+        beta = -copysign(sqrt(ar * ar + ai * ai + xn2), ar);
+        taur = (beta - ar) / beta;
+        taui = -ai / beta;
+        const double dx = ar - beta, dy = ai, dd = dx * dx + dy * dy;
+        scr = dx / dd;
+        sci = -dy / dd;
+        // (the element type must hold sc too: complex64 columns near the
+        // bottom of the float range leave the column as it is)
+        const double smax = sizeof(typename Real<C>::T) == 4 ? 1e37 : 1e300;
+        if (!(isfinite(taur) && isfinite(taui) && isfinite(scr) && isfinite(sci) && isfinite(beta)) ||
+            fabs(scr) > smax || fabs(sci) > smax) {
+          taur = taui = scr = sci = 0.0;
+          beta = ar;
+        }
+      }
+      const bool active = !(taur == 0.0 && taui == 0.0);
+      s_tau[j] = mkc<C>(taur, taui);
+      s_sc[j] = mkc<C>(scr, sci);
+      s_diag[j] = mkc<C>(beta, active ? 0.0 : ai);
     }
     __syncthreads();
-    // reflector (every thread, same arithmetic)
-    const double xn2 = *gnorm;
-    const C alpha = grow[j];
-    double taur = 0, taui = 0, scr = 0, sci = 0, beta = alpha.x;
-    const double ar = alpha.x, ai = alpha.y;
-    if (!(xn2 == 0.0 && ai == 0.0)) {
-      beta = -copysign(sqrt(ar * ar + ai * ai + xn2), ar);
-      taur = (beta - ar) / beta;
-      taui = -ai / beta;
-      const double dx = ar - beta, dy = ai, dd = dx * dx + dy * dy;
-      scr = dx / dd;
-      sci = -dy / dd;
-      // (the element type must hold sc too: complex64 columns near the
-      // bottom of the float range leave the column as it is)
-      const double smax = sizeof(typename Real<C>::T) == 4 ? 1e37 : 1e300;
-      if (!(isfinite(taur) && isfinite(taui) && isfinite(scr) && isfinite(sci) && isfinite(beta)) ||
-          fabs(scr) > smax || fabs(sci) > smax) {
-        taur = taui = scr = sci = 0.0;
-        beta = ar;
+    const C tj = s_tau[j], sc = s_sc[j], ctau = mkc<C>(tj.x, -tj.y);
+    const bool active = !(tj.x == 0 && tj.y == 0);
+    // scale the reflector of step j - 1 (no longer read)
+    if (j > 0 && warp == (j - 1) % nw) {
+      C x[MAXR];
+      load_col(j - 1, x);
+      const C scp = s_sc[j - 1];
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) {
+        const int g = r0 + lane + 32 * i;
+        if (g > j - 1) x[i] = pmul(x[i], scp);
+        else if (g == j - 1) x[i] = s_diag[j - 1];
       }
+      store_col(j - 1, x);
     }
-    const C sc = mkc<C>(scr, sci);
-    const C ctau = mkc<C>(taur, -taui);
-    const bool active = !(taur == 0.0 && taui == 0.0);
-    if (threadIdx.x == 0) s_tau[j] = mkc<C>(taur, taui);
-    // update: a warp per local row, lanes over the trailing columns
-    for (int i = warp; i < mr; i += nw) {
-      const int gr = r0 + i;
-      if (gr < j) continue;
-      C* row = A + (size_t)i * ld;
-      if (gr == j) {
-        for (int c = j + 1 + lane; c < n; c += 32) {
-          const C f = active ? pmul(ctau, padd(grow[c], pmulc(sc, gdot[c]))) : mkc<C>(0, 0);
-          row[c] = psub(grow[c], f);
-        }
-        if (lane == 0) row[j] = mkc<C>(beta, active ? 0.0 : ai);
-      } else if (active) {
-        const C x = row[j];
-        const C v = pmul(x, sc);
-        for (int c = j + 1 + lane; c < n; c += 32) {
-          const C f = pmul(ctau, padd(grow[c], pmulc(sc, gdot[c])));
-          row[c] = psub(row[c], pmul(v, f));
-        }
-        __syncwarp();
-        if (lane == 0) row[j] = v;
+    C v[MAXR];                           // v of step j: x sc below row j, 1 at row j
+    load_col(j, v);
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) {
+      const int g = r0 + lane + 32 * i;
+      v[i] = g > j ? pmul(v[i], sc) : (g == j ? mkc<C>(1, 0) : zero);
+    }
+    auto update = [&](int c, C (&y)[MAXR]) {
+      const C f = active ? pmul(ctau, padd(grow[c], pmulc(sc, gdot[c]))) : zero;
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) y[i] = psub(y[i], pmul(v[i], f));
+    };
+    // pass A: column j + 1
+    if (j + 1 < n && warp == (j + 1) % nw) {
+      C y[MAXR];
+      load_col(j + 1, y);
+      update(j + 1, y);
+      store_col(j + 1, y);
+      if (j + 1 < k) {
+        const double s2 = norm_below(y, j + 1);
+        if (lane == 0) pnorm[par ^ 1] = s2;
+        put_row(y, j + 1, slot + noff + n + j + 1);
       }
     }
     __syncthreads();
-    if (j + 1 < k) partials(j + 1, par ^ 1);
+    // pass B: columns c > j + 1, with the partial dots of step j + 1
+    if (j + 1 < n) {
+      C xn[MAXR];
+      load_col(j + 1, xn);
+      const int c0 = j + 2 + ((warp - (j + 2)) % nw + nw) % nw;
+      for (int c = c0; c < n; c += nw) {
+        C y[MAXR];
+        load_col(c, y);
+        update(c, y);
+        store_col(c, y);
+        if (j + 1 < k) {
+          const C d = dot_below(xn, y, j + 1);
+          if (lane == 0) slot[noff + c] = d;
+          put_row(y, j + 1, slot + noff + n + c);
+        }
+      }
+    }
     cl.sync();
   }
+  if (k > 0 && warp == (k - 1) % nw) {   // scale the last reflector
+    C x[MAXR];
+    load_col(k - 1, x);
+    const C scp = s_sc[k - 1];
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) {
+      const int g = r0 + lane + 32 * i;
+      if (g > k - 1) x[i] = pmul(x[i], scp);
+      else if (g == k - 1) x[i] = s_diag[k - 1];
+    }
+    store_col(k - 1, x);
+  }
+  __syncthreads();
 
   // R (k x n, upper triangular) from the rows this CTA holds
   if (Rg)
     for (long long e = threadIdx.x; e < (long long)mr * n; e += blockDim.x) {
-      const int i = (int)(e / n), c = (int)(e % n), gr = r0 + i;
-      if (gr < k) Rg[(long long)gr * n + c] = (c >= gr) ? A[(size_t)i * ld + c] : mkc<C>(0, 0);
+      const int t = (int)(e / n), c = (int)(e % n), g = r0 + t;
+      if (g < k) Rg[(long long)g * n + c] = (c >= g) ? A[(size_t)c * ld + t] : zero;
     }
   if (!Qg) return;     // no exchange slot is read after the last cl.sync above
-  __syncthreads();
 
-  // Q backwards: step i needs v_i^H q_c over all rows for c in (i, k)
-  auto qpartials = [&](int i, int par) {
-    C* sd = slot + (size_t)par * 2 * n;
-    const int i0 = max(0, i - r0);
-    for (int c = i + 1 + warp; c < k; c += nw) {
-      C acc = mkc<C>(0, 0);
-      for (int t = i0 + lane; t < mr; t += 32) {
-        const int gr = r0 + t;
-        const C v = (gr == i) ? mkc<C>(1, 0) : A[(size_t)t * ld + i];
-        acc = padd(acc, pmulc(v, A[(size_t)t * ld + c]));
-      }
-      acc.x = wsum(acc.x);
-      acc.y = wsum(acc.y);
-      if (lane == 0) sd[c] = acc;
+  // ---- Q = H_0 ... H_{k-1} [I; 0], in place backwards: step i updates the
+  // columns c > i by tau_i v_i (v_i^H q_c) and sets column i to
+  // e_i - tau_i v_i; the pass of step i also takes the partial dots of step
+  // i - 1 (v_{i-1} = column i - 1, untouched until its own step)
+  auto refl = [&](int i, C (&x)[MAXR]) {  // v_i from column i (scaled, 1 on row i)
+    load_col(i, x);
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const int g = r0 + lane + 32 * q;
+      x[q] = g > i ? x[q] : (g == i ? mkc<C>(1, 0) : zero);
     }
   };
-  if (k > 0) qpartials(k - 1, 0);
-  cl.sync();
-  for (int i = k - 1; i >= 0; --i) {
-    const int par = (k - 1 - i) & 1;
-    for (int c = i + 1 + threadIdx.x; c < k; c += blockDim.x) {
-      gdot[c] = cluster_sum(cl, slot, (size_t)par * 2 * n + c, cs);
+  auto dot_from = [&](const C (&x)[MAXR], const C (&y)[MAXR]) {   // rows where x is nonzero
+    C acc = zero;
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) acc = padd(acc, pmulc(x[q], y[q]));
+    acc.x = wsum(acc.x);
+    acc.y = wsum(acc.y);
+    return acc;
+  };
+  auto set_col = [&](int i, const C (&x)[MAXR], C (&y)[MAXR]) {   // e_i - tau_i v_i
+    const C ti = s_tau[i], mt = mkc<C>(-(double)ti.x, -(double)ti.y);
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const int g = r0 + lane + 32 * q;
+      y[q] = g == i ? mkc<C>(1.0 - (double)ti.x, -(double)ti.y) : (g > i ? pmul(mt, x[q]) : zero);
     }
+  };
+  if (k > 0) {                           // column k - 1 and the sums of step k - 2
+    C x[MAXR], xp[MAXR], y[MAXR];
+    refl(k - 1, x);
+    if (k >= 2) refl(k - 2, xp);
     __syncthreads();
-    const C ti = s_tau[i];
-    for (int t = warp; t < mr; t += nw) {
-      const int gr = r0 + t;
-      C* row = A + (size_t)t * ld;
-      const C v = (gr == i) ? mkc<C>(1, 0) : (gr > i ? row[i] : mkc<C>(0, 0));
-      if (gr >= i)
-        for (int c = i + 1 + lane; c < k; c += 32) row[c] = psub(row[c], pmul(v, pmul(ti, gdot[c])));
-      __syncwarp();
-      if (lane == 0) {
-        // column i := e_i - tau_i v_i
-        if (gr == i) row[i] = mkc<C>(1.0 - (double)ti.x, -(double)ti.y);
-        else if (gr > i) row[i] = pmul(mkc<C>(-(double)ti.x, -(double)ti.y), v);
-        else row[i] = mkc<C>(0, 0);
+    if (warp == (k - 1) % nw) {
+      set_col(k - 1, x, y);
+      store_col(k - 1, y);
+      if (k >= 2) {
+        const C d = dot_from(xp, y);
+        if (lane == 0) slot[k - 1] = d;
       }
     }
-    __syncthreads();
-    if (i > 0) qpartials(i - 1, par ^ 1);
+  }
+  cl.sync();
+  for (int i = k - 2; i >= 0; --i) {
+    const int par = (k - 2 - i) & 1;
+    const size_t off = (size_t)par * 2 * n, noff = (size_t)(par ^ 1) * 2 * n;
+    for (int c = i + 1 + threadIdx.x; c < k; c += blockDim.x)
+      gdot[c] = pmul(s_tau[i], cluster_sum(cl, slot, off + c, cs));   // tau_i v_i^H q_c
+    C x[MAXR], xp[MAXR];
+    refl(i, x);
+    if (i >= 1) refl(i - 1, xp);
+    __syncthreads();                     // gdot complete; every warp holds v_i before column i changes
+    for (int c = i + (((warp - i) % nw) + nw) % nw; c < k; c += nw) {
+      C y[MAXR];
+      if (c == i) {
+        set_col(i, x, y);
+      } else {
+        load_col(c, y);
+        const C f = gdot[c];
+#pragma unroll
+        for (int q = 0; q < MAXR; ++q) y[q] = psub(y[q], pmul(x[q], f));
+      }
+      store_col(c, y);
+      if (i >= 1) {
+        const C d = dot_from(xp, y);
+        if (lane == 0) slot[noff + c] = d;
+      }
+    }
     cl.sync();
   }
+  __syncthreads();
   for (long long e = threadIdx.x; e < (long long)mr * k; e += blockDim.x) {
     const int t = (int)(e / k), c = (int)(e % k);
-    Qg[(long long)(r0 + t) * k + c] = A[(size_t)t * ld + c];
+    Qg[(long long)(r0 + t) * k + c] = A[(size_t)c * ld + t];
   }
 }
 
 constexpr int kPanelSmemMax = 211 * 1024;
 
-template <typename C>
-cudaError_t panel_optin() {
+template <typename C, int MAXR>
+cudaError_t panel_optin_one() {
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_panel_qr<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemMax);
+  e = cudaFuncSetAttribute(k_panel_qr<C, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemMax);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_panel_qr<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  e = cudaFuncSetAttribute(k_panel_qr<C, MAXR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) done.fetch_or(bit);
   return e;
+}
+
+template <typename C>
+cudaError_t panel_optin() {
+  cudaError_t e;
+  if ((e = panel_optin_one<C, 2>()) != cudaSuccess) return e;
+  if ((e = panel_optin_one<C, 4>()) != cudaSuccess) return e;
+  if constexpr (sizeof(C) == sizeof(float2)) return panel_optin_one<C, 8>();
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -291,21 +425,38 @@ cudaError_t init_panel_attributes() {
   return panel_optin<double2>();
 }
 
+// Rows of one CTA are cached 32 x MAXR in registers: at most 256 (complex64)
+// or 128 (complex128, twice the registers per entry) per CTA.
+static int panel_max_rows(size_t elem) { return elem == sizeof(double2) ? 128 : 256; }
+
 int panel_cluster(int m, int n, size_t elem) {
   if (m < n || n < 1) return 0;
   for (int cs = 1; cs <= kPanelMaxCluster; ++cs) {
     const int rows = (m + cs - 1) / cs;
     const size_t b = elem == sizeof(double2) ? panel_smem<double2>(rows, n) : panel_smem<float2>(rows, n);
-    if (b <= (size_t)kPanelSmemMax) return cs;
+    if (rows <= panel_max_rows(elem) && b <= (size_t)kPanelSmemMax) return cs;
   }
   return 0;
 }
 
+// Cluster size of a launch: the smallest that fits, raised so that no CTA
+// holds more than kPanelRowsTarget rows (the per-column work of a CTA is its
+// row slice times the trailing width; the exchange costs grow with the
+// cluster).
+int panel_cluster_auto(int m, int n, size_t elem) {
+  const int cmin = panel_cluster(m, n, elem);
+  if (cmin == 0) return 0;
+  const int want = (m + kPanelRowsTarget - 1) / kPanelRowsTarget;
+  return std::max(cmin, std::min(want, kPanelMaxCluster));
+}
+
 template <typename C>
-static cudaError_t panel_t(const C* A, int m, int n, C* Q, C* R, int batch, long long stride, cudaStream_t s) {
+static cudaError_t panel_t(const C* A, int m, int n, C* Q, C* R, int batch, long long stride, cudaStream_t s,
+                           int cluster) {
   if (batch < 1 || m < 1 || n < 1) return cudaSuccess;
-  const int cs = panel_cluster(m, n, sizeof(C));
-  if (cs == 0) return cudaErrorInvalidValue;
+  const int cmin = panel_cluster(m, n, sizeof(C));
+  if (cmin == 0 || cluster > kPanelMaxCluster || (cluster > 0 && cluster < cmin)) return cudaErrorInvalidValue;
+  const int cs = cluster > 0 ? cluster : panel_cluster_auto(m, n, sizeof(C));
   cudaError_t e = panel_optin<C>();
   if (e != cudaSuccess) return e;
   const int rows = (m + cs - 1) / cs;
@@ -322,16 +473,21 @@ static cudaError_t panel_t(const C* A, int m, int n, C* Q, C* R, int batch, long
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_panel_qr<C>, A, m, n, rows, Q, R, stride);
+  if (rows <= 64) return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 2>, A, m, n, rows, Q, R, stride);
+  if (rows <= 128) return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 4>, A, m, n, rows, Q, R, stride);
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (rows <= 256) return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 8>, A, m, n, rows, Q, R, stride);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_panel_qr(const float2* A, int m, int n, float2* Q, float2* R, int batch, long long stride,
-                            cudaStream_t s) {
-  return panel_t(A, m, n, Q, R, batch, stride, s);
+                            cudaStream_t s, int cluster) {
+  return panel_t(A, m, n, Q, R, batch, stride, s, cluster);
 }
 cudaError_t launch_panel_qr(const double2* A, int m, int n, double2* Q, double2* R, int batch, long long stride,
-                            cudaStream_t s) {
-  return panel_t(A, m, n, Q, R, batch, stride, s);
+                            cudaStream_t s, int cluster) {
+  return panel_t(A, m, n, Q, R, batch, stride, s, cluster);
 }
 
 }  // namespace bbp

@@ -408,6 +408,120 @@ __global__ void k_unpack(const float* __restrict__ Cm, long long ldc, int Q, int
   }
 }
 
+// ------------------------------------------- general complex GEMM operands
+//
+// C (M x N complex) = op(A) (M x K) op(B) (K x N) as one real GEMM whose
+// output is C itself, read as an M x 2N real matrix (interleaved re, im):
+//   A'' (M x 6K):  [ hi | hi | lo ] of [re a_0, im a_0, re a_1, im a_1, ...]
+//   B'' (2N x 6K): row 2j   = [ hi | lo | hi ] of [ re b_0j, -im b_0j, ... ]
+//                  row 2j+1 = [ hi | lo | hi ] of [ im b_0j,  re b_0j, ... ]
+// so that the K sum pairs a_k with b_kj and hi*hi + hi*lo + lo*hi
+// accumulates in FP32.  No scaling: TF32 and BF16 keep FP32's exponent
+// range.  Rows are padded to ldK (a multiple of 32) with zeros.
+
+template <typename C> __device__ __forceinline__ float2 ld_f2(const C* p, long long i);
+template <> __device__ __forceinline__ float2 ld_f2(const float2* p, long long i) { return p[i]; }
+template <> __device__ __forceinline__ float2 ld_f2(const double2* p, long long i) {
+  const double2 v = p[i];
+  return make_float2((float)v.x, (float)v.y);
+}
+
+template <bool kBF16>
+__device__ __forceinline__ float split_part(float v, int seg_is_lo) {
+  using O = Op<kBF16>;
+  const float h = O::round(v);
+  return seg_is_lo ? O::round(v - h) : h;
+}
+
+// A'' from op(A) = A (op 'N', A row-major M x K, row stride lda): coalesced
+template <bool kBF16, typename C>
+__global__ void k_zpack_an(const C* __restrict__ A, long long lda, int M, int K, typename Op<kBF16>::T* out,
+                           long long ldK) {
+  using O = Op<kBF16>;
+  const long long tot = (long long)M * ldK;
+  const int K2 = 2 * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ldK), kk = (int)(e % ldK);
+    float v = 0.f;
+    if (kk < 3 * K2) {
+      const int seg = kk / K2, rem = kk % K2;
+      const float2 z = ld_f2(A, (long long)i * lda + (rem >> 1));
+      v = split_part<kBF16>((rem & 1) ? z.y : z.x, seg == 2);
+    }
+    out[e] = O::store(v);
+  }
+}
+
+// A'' from op(A) = A^T or A^H (A row-major K x M, row stride lda): a 32 x 32
+// tile of A is read along its rows and written transposed.
+template <bool kBF16, typename C>
+__global__ void __launch_bounds__(256) k_zpack_at(const C* __restrict__ A, long long lda, bool conj, int M, int K,
+                                                  typename Op<kBF16>::T* out, long long ldK) {
+  using O = Op<kBF16>;
+  __shared__ float2 tile[32][33];
+  const int i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r, i = i0 + tx;
+    float2 z = make_float2(0.f, 0.f);
+    if (k < K && i < M) z = ld_f2(A, (long long)k * lda + i);
+    if (conj) z.y = -z.y;
+    tile[r][tx] = z;                      // tile[k - k0][i - i0]
+  }
+  __syncthreads();
+  const int K2 = 2 * K;
+  // each output row i gets 3 segments x 64 reals from this tile
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r;
+    if (i >= M) continue;
+    for (int q = tx; q < 3 * 64; q += 32) {
+      const int seg = q / 64, w = q % 64, k = k0 + (w >> 1);
+      if (k >= K) continue;
+      const float2 z = tile[w >> 1][r];
+      out[(long long)i * ldK + (long long)seg * K2 + 2 * k + (w & 1)] =
+          O::store(split_part<kBF16>((w & 1) ? z.y : z.x, seg == 2));
+    }
+  }
+}
+
+__global__ void k_zero_pad(float* out, int rows, long long ldK, long long from) {
+  const long long w = ldK - from;
+  const long long tot = (long long)rows * w;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
+    out[(e / w) * ldK + from + e % w] = 0.f;
+}
+__global__ void k_zero_pad_bf(__nv_bfloat16* out, int rows, long long ldK, long long from) {
+  const long long w = ldK - from;
+  const long long tot = (long long)rows * w;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
+    out[(e / w) * ldK + from + e % w] = __float2bfloat16_rn(0.f);
+}
+
+// B'' (2N x ldK) from op(B) (K x N): 'N' B row-major K x N (stride ldb),
+// 'T' / 'C' B row-major N x K.
+template <bool kBF16, typename C>
+__global__ void k_zpack_b(const C* __restrict__ B, long long ldb, char op, int K, int N, typename Op<kBF16>::T* out,
+                          long long ldK) {
+  using O = Op<kBF16>;
+  const long long tot = 2LL * N * ldK;
+  const int K2 = 2 * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / ldK;
+    const int kk = (int)(e % ldK);
+    float v = 0.f;
+    if (kk < 3 * K2) {
+      const int j = (int)(row >> 1), t = (int)(row & 1);
+      const int seg = kk / K2, rem = kk % K2, k = rem >> 1, u = rem & 1;
+      float2 z = (op == 'N') ? ld_f2(B, (long long)k * ldb + j) : ld_f2(B, (long long)j * ldb + k);
+      if (op == 'C') z.y = -z.y;
+      // (t, u): (0,0) re, (0,1) -im, (1,0) im, (1,1) re
+      const float x = (t == u) ? z.x : (t == 0 ? -z.y : z.y);
+      v = split_part<kBF16>(x, seg == 1);
+    }
+    out[e] = O::store(v);
+  }
+}
+
 int grid_of(long long n) {
   long long g = (n + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -441,6 +555,47 @@ cudaError_t launch_tc_gemm(bool bf16, const void* A, long long lda, const void* 
 }
 
 long long tc_ld(int P) { return ((6LL * P + 31) / 32) * 32; }
+
+// ------------------------------------------------ general complex GEMM (c64)
+
+size_t tc_zpack_bytes(bool bf16, int rows, int K) {
+  const size_t es = bf16 ? 2 : 4;
+  return ((size_t)rows * (size_t)tc_ld(K) * es + 255) / 256 * 256;
+}
+
+template <bool kBF16, typename C>
+static cudaError_t zpack_a_t(char opA, int M, int K, const C* A, long long lda, void* out, cudaStream_t s) {
+  using T = typename Op<kBF16>::T;
+  const long long ldK = tc_ld(K);
+  if (opA == 'N') {
+    k_zpack_an<kBF16, C><<<grid_of((long long)M * ldK), 256, 0, s>>>(A, lda, M, K, (T*)out, ldK);
+  } else {
+    dim3 g((M + 31) / 32, (K + 31) / 32);
+    k_zpack_at<kBF16, C><<<g, 256, 0, s>>>(A, lda, opA == 'C', M, K, (T*)out, ldK);
+    if (ldK > 6LL * K) {
+      if (kBF16) k_zero_pad_bf<<<grid_of((long long)M * (ldK - 6LL * K)), 256, 0, s>>>((__nv_bfloat16*)out, M, ldK, 6LL * K);
+      else k_zero_pad<<<grid_of((long long)M * (ldK - 6LL * K)), 256, 0, s>>>((float*)out, M, ldK, 6LL * K);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t tc_zpack_a(bool bf16, char opA, int M, int K, const float2* A, long long lda, void* out, cudaStream_t s) {
+  return bf16 ? zpack_a_t<true>(opA, M, K, A, lda, out, s) : zpack_a_t<false>(opA, M, K, A, lda, out, s);
+}
+
+cudaError_t tc_zpack_b(bool bf16, char opB, int K, int N, const float2* B, long long ldb, void* out, cudaStream_t s) {
+  const long long ldK = tc_ld(K);
+  if (bf16) k_zpack_b<true, float2><<<grid_of(2LL * N * ldK), 256, 0, s>>>(B, ldb, opB, K, N, (__nv_bfloat16*)out, ldK);
+  else k_zpack_b<false, float2><<<grid_of(2LL * N * ldK), 256, 0, s>>>(B, ldb, opB, K, N, (float*)out, ldK);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_zgemm_packed(bool bf16, int M, int N, int K, const void* Ap, const void* Bp, float2* Cm, long long ldc,
+                            int* err, cudaStream_t s) {
+  const long long ldK = tc_ld(K);
+  return launch_tc_gemm(bf16, Ap, ldK, Bp, ldK, (float*)Cm, 2 * ldc, M, 2 * N, (int)ldK, 1.0f, err, s);
+}
 
 size_t tc_absorb_bytes(bool bf16, int P, int Q, int l, int r) {
   const size_t es = bf16 ? 2 : 4;

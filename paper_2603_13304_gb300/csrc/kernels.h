@@ -54,14 +54,17 @@ cudaError_t launch_qr_r(const float2* A, int m, int n, float2* R, float2* s0, fl
 // with `power_iters` power steps reduces Z to rand_block rows first.
 // *status is set to 1 if a sweep limit was reached (never cleared).
 size_t svd_work_bytes(int m, int n);
-size_t svd_work_bytes_c64(int m, int n, int chi);
+// complex64: with tensor_cores the range-finder products of the randomised
+// path run on tcgen05 (split TF32) and the scratch includes their packed
+// operands.
+size_t svd_work_bytes_c64(int m, int n, int chi, bool tensor_cores = false);
 // Scratch bound for every complex64 split with min(m, n) <= max_min and max(m, n) <= max_max.
-size_t svd_work_bound_c64(int max_min, int max_max, int chi);
+size_t svd_work_bound_c64(int max_min, int max_max, int chi, bool tensor_cores = false);
 int rand_block(int m, int n, int chi);
 cudaError_t launch_svd_trunc(const double2* Z, int m, int n, int chi, double2* U, double2* Rem, void* work,
                              int* status, cudaStream_t s);
 cudaError_t launch_svd_trunc(const float2* Z, int m, int n, int chi, float2* U, float2* Rem, void* work, int* status,
-                             cudaStream_t s, int power_iters);
+                             cudaStream_t s, int power_iters, bool tensor_cores = false, int* tc_err = nullptr);
 // complex128 randomised truncation (the engine's FP64 path): b = 2 chi
 // directions, power_iters power steps (six by default), the b x b factor by
 // complex128 Jacobi; small matrices (min(m, n) <= max(4 chi, 64)) take the
@@ -132,6 +135,24 @@ cudaError_t launch_tc_absorb(bool bf16, const double2* X, int P, int Q, const do
 cudaError_t launch_tc_absorb(bool bf16, const float2* X, int P, int Q, const float2* S, int l, int r, float2* R,
                              void* work, int* err, cudaStream_t s);
 
+// General complex64 GEMM on tcgen05 (k_tc.cu): C (M x N, row stride ldc
+// complex) = op(A) (M x K) op(B) (K x N), as one split-precision real GEMM
+// (hi*hi + hi*lo + lo*hi, FP32 accumulation) that writes C's interleaved
+// (re, im) entries directly.  The operands are packed first into scratch of
+// tc_zpack_bytes(bf16, M, K) (A) and tc_zpack_bytes(bf16, 2N, K) (B); op is
+// 'N', 'T' or 'C' (A: M x K as stored, or stored K x M; B: K x N as stored, or
+// stored N x K).  A packed operand may be reused by several products.
+size_t tc_zpack_bytes(bool bf16, int rows, int K);
+cudaError_t tc_zpack_a(bool bf16, char opA, int M, int K, const float2* A, long long lda, void* out, cudaStream_t s);
+cudaError_t tc_zpack_b(bool bf16, char opB, int K, int N, const float2* B, long long ldb, void* out, cudaStream_t s);
+cudaError_t tc_zgemm_packed(bool bf16, int M, int N, int K, const void* Ap, const void* Bp, float2* C, long long ldc,
+                            int* err, cudaStream_t s);
+
+// ALU peak microbenchmark (k_peak.cu): blocks x 256 threads, iters rounds of
+// 8 independent FMA chains each; fma_peak_flops gives the flops launched.
+double fma_peak_flops(bool fp64, int blocks, int iters);
+cudaError_t launch_fma_peak(bool fp64, int blocks, int iters, void* out, cudaStream_t s);
+
 // Live timing of one kernel class (ktimer.cpp): every launch of the selected
 // class is bracketed by CUDA events on its stream; totals of launches,
 // milliseconds and algorithmic flops accumulate until read.
@@ -167,13 +188,17 @@ inline double qr_flops(int m, int n) {
 // A.  batch panels at a stride of `stride` elements (R at n * n).
 // panel_cluster: the cluster size used for an m x n panel of elem-byte
 // entries (0 when it does not fit 16 CTAs' shared memory).
+// cluster = 0 picks panel_cluster_auto; a given size must be at least
+// panel_cluster(m, n, elem) and at most kPanelMaxCluster.
 constexpr int kPanelMaxCluster = 16;
+constexpr int kPanelRowsTarget = 256;
 int panel_cluster(int m, int n, size_t elem);
+int panel_cluster_auto(int m, int n, size_t elem);
 cudaError_t init_panel_attributes();
 cudaError_t launch_panel_qr(const float2* A, int m, int n, float2* Q, float2* R, int batch, long long stride,
-                            cudaStream_t s);
+                            cudaStream_t s, int cluster = 0);
 cudaError_t launch_panel_qr(const double2* A, int m, int n, double2* Q, double2* R, int batch, long long stride,
-                            cudaStream_t s);
+                            cudaStream_t s, int cluster = 0);
 
 // Allocation-free truncated SVD (k_noalloc.cu): scratch in a fixed device
 // array of noalloc_scratch_bytes(); *too_large is set when svd_work_bytes(m, n)

@@ -31,14 +31,14 @@ def crandn(rng, *shape):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 
 
-def run_panel(A, c64, with_q=True, with_r=True, batch=1):
+def run_panel(A, c64, with_q=True, with_r=True, batch=1, cluster=0):
     dt = torch.complex64 if c64 else torch.complex128
     m, n = A.shape[-2:]
     Ad = torch.from_numpy(np.ascontiguousarray(A)).to(dt).cuda()
     Qd = torch.zeros((batch, m, n), dtype=dt, device="cuda") if with_q else None
     Rd = torch.full((batch, n, n), 7.0, dtype=dt, device="cuda") if with_r else None
     P.bbp_k_panel_qr(c64, Ad.data_ptr(), m, n, Qd.data_ptr() if with_q else None,
-                     Rd.data_ptr() if with_r else None, batch)
+                     Rd.data_ptr() if with_r else None, batch, cluster)
     torch.cuda.synchronize()
     return (Qd.cpu().numpy() if with_q else None), (Rd.cpu().numpy() if with_r else None)
 
@@ -88,6 +88,23 @@ def test_panel_qr_rank_deficient(c64):
     assert np.linalg.norm(Q[0] @ R[0] - A) / np.linalg.norm(A) < 30 * eps * np.sqrt(m)
 
 
+@pytest.mark.parametrize("c64,m,n", [(True, 512, 48), (True, 2304, 96), (False, 1024, 64)])
+def test_panel_qr_cluster_sizes(c64, m, n):
+    """Every admissible cluster size computes the same factorisation (to
+    rounding: the cross-CTA sums are added in a different grouping)."""
+    rng = np.random.default_rng(m + 3 * n)
+    A = crandn(rng, m, n)
+    if c64:
+        A = A.astype(np.complex64).astype(np.complex128)
+    cmin = P.bbp_k_panel_cluster(c64, m, n)
+    Q0, R0 = run_panel(A, c64, cluster=cmin)
+    eps = 1e-6 if c64 else 1e-14
+    for cs in sorted({cmin, min(16, cmin + 1), min(16, 2 * cmin), 16}):
+        Q, R = run_panel(A, c64, cluster=cs)
+        assert np.linalg.norm(Q[0] @ R[0] - A) / np.linalg.norm(A) < 30 * eps * np.sqrt(m)
+        assert np.abs(Q[0] - Q0[0]).max() < 1e3 * eps and np.abs(R[0] - R0[0]).max() < 1e3 * eps * np.abs(R0).max()
+
+
 def test_panel_qr_batch_equals_single():
     rng = np.random.default_rng(9)
     m, n = 2304, 96
@@ -106,19 +123,19 @@ def geometric_matrix(rng, m, n, decay):
     return (U * s) @ V.conj().T
 
 
-def run_svd(Z, chi, c64, q):
+def run_svd(Z, chi, c64, q, tc=False):
     m, n = Z.shape
     k = min(chi, m, n)
     dt = torch.complex64 if c64 else torch.complex128
     Zd = torch.from_numpy(np.ascontiguousarray(Z)).to(dt).cuda()
     U = torch.zeros((m, k), dtype=dt, device="cuda")
     Rem = torch.zeros((k, n), dtype=dt, device="cuda")
-    work = torch.zeros(P.bbp_k_svd_work_bytes_rand(c64, m, n, chi), dtype=torch.uint8, device="cuda")
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    work = torch.zeros(P.bbp_k_svd_work_bytes_rand(c64, m, n, chi, tc), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(2, dtype=torch.int32, device="cuda")
     P.bbp_k_svd_trunc_rand(c64, Zd.data_ptr(), m, n, chi, U.data_ptr(), Rem.data_ptr(), work.data_ptr(),
-                           status.data_ptr(), q)
+                           status.data_ptr(), q, tc, status.data_ptr() + 4 if tc else None)
     torch.cuda.synchronize()
-    assert int(status.item()) == 0
+    assert int(status[0].item()) == 0 and int(status[1].item()) == 0
     return U.cpu().numpy().astype(np.complex128), Rem.cpu().numpy().astype(np.complex128)
 
 
@@ -135,12 +152,19 @@ def check_svd(Z, Uh, Rh, k, tag, err_tol, orth_tol):
 
 @pytest.mark.parametrize("m,n,chi,decay", [(512, 512, 32, 0.9), (2304, 2304, 64, 0.93), (2304, 1296, 64, 0.9),
                                            (1296, 64, 64, 0.8), (100, 90, 16, 0.7)])
-def test_svd_trunc_c64(m, n, chi, decay):
+@pytest.mark.parametrize("tc", [False, True])
+def test_svd_trunc_c64(m, n, chi, decay, tc):
+    """tc: the range-finder products as split-TF32 tcgen05 GEMMs."""
     rng = np.random.default_rng(m + n + chi)
     Z = geometric_matrix(rng, m, n, decay).astype(np.complex64).astype(np.complex128)
     k = min(chi, m, n)
-    Uh, Rh = run_svd(Z, chi, True, 1)
-    check_svd(Z, Uh, Rh, k, f"svd c64 {m}x{n} chi {chi}", 2e-5, 1e-4)
+    # three power steps: these spectra decay slowly (sigma_b / sigma_k up to
+    # 0.19), so that one step would leave the randomised error at 1e-4
+    Uh, Rh = run_svd(Z, chi, True, 3, tc)
+    # the tensor cores' FP32 accumulation over K = 6 max(m, n) real terms
+    # loses up to about 2e-8 max(m, n) against the SIMT GEMM (measured 5e-5
+    # at 2304)
+    check_svd(Z, Uh, Rh, k, f"svd c64 {m}x{n} chi {chi} tc={tc}", 3e-8 * max(m, n) if tc else 2e-5, 1e-4)
 
 
 @pytest.mark.parametrize("m,n,chi,decay", [(512, 512, 32, 0.9), (512, 256, 32, 0.8), (1296, 1296, 64, 0.95),
