@@ -72,10 +72,13 @@ void bbp_set_allocator(bbp_alloc_fn alloc, bbp_free_fn free_fn, void* user);
 /* Create a PEPS context (Sec. 1.1.2, PEPS; Sec. 2.1, double layer).
  * lattice: BBP_SQUARE (periodic 0 = open, 1 = torus) or BBP_KAGOME
  * (periodic must be 1).  d: physical dimension; D: bond dimension (<= 8).
- * host_tensors: layout above, d * D^4 complex128 per site, copied to the
- * device.  cuda_stream: a cudaStream_t (NULL = legacy default stream). */
+ * host_tensors: layout above, d * D^4 entries per site, interleaved
+ * (re, im): dtype 0 = complex128 (doubles), 1 = complex64 (floats); copied
+ * to the device (complex64 entries are widened to complex128 there, where
+ * the fusion reads them).  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream). */
 bbp_status bbp_create_peps(bbp_ctx** out, int lattice, int Lx, int Ly, int periodic, int d, int D,
-                           const double* host_tensors, void* cuda_stream);
+                           const void* host_tensors, int dtype, void* cuda_stream);
 
 /* Cut the lattice into blocks (Sec. 2.2.2): square blocks of bx x by sites;
  * Kagome L x L parallelograms of unit cells with bx = by = L >= 2
@@ -84,22 +87,36 @@ bbp_status bbp_create_peps(bbp_ctx** out, int lattice, int Lx, int Ly, int perio
 bbp_status bbp_partition_blocks(bbp_ctx* ctx, int bx, int by);
 
 /* chi: truncation bond dimension of the boundary MPS (Sec. 1.1.3), 1..64.
- * precision: BBP_FP64 -- every tensor complex128, exact one-sided Jacobi
- *   truncation (the reference path, agrees with the FP64 oracle to 1e-10);
+ * precision: BBP_FP64 -- every tensor complex128 (the reference path,
+ *   agrees with the FP64 oracle to 1e-10); each truncation of a large split
+ *   Z runs a subspace iteration with b = 2 chi directions (six power steps by
+ *   default, bbp_set_power_iters) that reaches the exact truncation to
+ *   rounding, finished by a complex128 one-sided Jacobi of the b x b factor;
+ *   small splits take the exact Jacobi directly.
  * BBP_FP32 -- tensors and contractions complex64; each truncation reduces a
  *   large matrix Z to b = chi + max(8, chi/2) directions by a randomised
  *   subspace iteration (bbp_set_power_iters steps, default 1; Householder
- *   orthonormalisation) and runs an exact one-sided Jacobi on the b x b
- *   factor of Q^H Z; message norms, phases, distances and log-scales stay
- *   double.
+ *   orthonormalisation), runs a complex64 one-sided Jacobi on the b x b
+ *   factor and finishes it in complex128 (the pairs across the chi cut are
+ *   rotated again in double; singular values and their selection in double);
+ *   message norms, phases, distances and log-scales stay double.
  * BBP_TF32 / BBP_BF16 -- as BBP_FP32, with the absorb contraction (the
- *   dense X^T S product of each swallow) on the tensor cores: both operands
- *   scaled by a power of two and split into high and low TF32 (or BF16)
- *   parts, hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM (tcgen05).
+ *   dense X^T S product of each swallow) and the segment merges on the
+ *   tensor cores: operands split into high and low TF32 (or BF16) parts,
+ *   hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM (tcgen05).
  *   A pipeline wait that times out makes bbp_iterate return BBP_ERR_TIMEOUT.
- * Must be called before bbp_init_messages.  alpha must be 1 (undamped
- * update).  seed is reserved. */
+ * alpha: learning step (Sec. 2.3.3, Eq. of the learning step), 0 <= alpha
+ *   <= 1: the message that replaces the old one is alpha new + (1 - alpha)
+ *   old, the MPS sum compressed back to bond chi (left-canonical QR sweep,
+ *   then truncated SVDs from the right) and normalised; 1 = plain update.
+ * Must be called before bbp_init_messages.  seed is reserved. */
 bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, uint64_t seed);
+
+/* Hermitisation of messages (Sec. 2.3.3, "Hermitize MPSs"): on = 1 replaces
+ * every new message by its Hermitian part (M + M^dagger) / 2 as an operator
+ * on the fused (ket, bra) legs, compressed to bond chi as for the learning
+ * step and normalised; applied before the learning step.  Default 0. */
+bbp_status bbp_set_hermitise(bbp_ctx* ctx, int on);
 
 /* Randomised truncation (no counterpart in the thesis, whose truncation is
  * an exact SVD): number of subspace-iteration power steps before the reduced
@@ -148,6 +165,20 @@ bbp_status bbp_expect_local(bbp_ctx* ctx, const double* op, int ns, const int* s
  * receives (d^n x d^n) complex128, trace 1, basis index s0 * d + s1.
  * For nsites = 2 the sites may be any two sites of that block. */
 bbp_status bbp_block_rdm(bbp_ctx* ctx, int block, const int* sites, int nsites, double* rdm_out);
+
+/* <O1 (x) O2> on the bond that leaves site `site` through leg slot `slot`
+ * (Sec. 4.2 observables; reading E for bonds across blocks): O1 acts on
+ * `site`, O2 on its neighbour; both host d x d complex128 operators are
+ * inserted whole in one contraction (the scheme of bbp_energy_per_site, whose
+ * bond terms are the three products S^a (x) S^a).  Results in re_out, im_out. */
+bbp_status bbp_expect_product(bbp_ctx* ctx, const double* op1, const double* op2, int site, int slot, double* re_out,
+                              double* im_out);
+
+/* Heisenberg bond energies <S_i . S_j> (Sec. 4.2), d = 2: for nbonds bonds
+ * given as (site, slot) pairs in site_slots, each the sum of three product
+ * insertions S^a (x) S^a as in bbp_energy_per_site; all contractions run as
+ * one batch.  e_out: host array of nbonds doubles. */
+bbp_status bbp_bond_energies(bbp_ctx* ctx, const int* site_slots, int nbonds, double* e_out);
 
 /* Heisenberg energy per site, sum over all nearest-neighbour bonds of
  * <S_i . S_j> (Eq. of the AFM Heisenberg Hamiltonian, Sec. 4.2) divided by the
@@ -203,8 +234,9 @@ typedef struct {
   int lattice, Lx, Ly, periodic, d, D, bx, by, chi, precision;
   double tol;
   int max_iter, streams, power_iters;
-  const double* host_tensors; /* complex128 [n_sites][d][D]^4 */
+  const void* host_tensors;   /* [n_sites][d][D]^4, complex128 or complex64 (tensor_dtype) */
   const double* edge_mats;    /* complex128 [n_sites][4][D][D] */
+  int tensor_dtype;           /* 0 = complex128, 1 = complex64, as for bbp_create_peps */
 } bbp_job;
 
 typedef struct bbp_server bbp_server;

@@ -27,7 +27,7 @@ EXPORTS = [
     "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
     "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message",
     "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
-    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_panel_cluster", "bbp_k_panel_qr", "bbp_k_svd_work_bytes_rand", "bbp_k_svd_trunc_rand", "bbp_k_fma_peak", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
+    "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_panel_cluster", "bbp_k_panel_qr", "bbp_k_svd_work_bytes_rand", "bbp_k_svd_trunc_rand", "bbp_k_fma_peak", "bbp_set_hermitise", "bbp_expect_product", "bbp_bond_energies", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
     "bbp_batch_iterate", "bbp_server_create", "bbp_job_footprint_bytes", "bbp_server_submit", "bbp_server_step",
     "bbp_server_poll", "bbp_server_take", "bbp_server_destroy", "bbp_ktimer_select", "bbp_ktimer_read",
     "bbp_k_tc_absorb_bytes", "bbp_k_tc_absorb", "bbp_plan_debug",
@@ -53,7 +53,7 @@ _FREE = ctypes.CFUNCTYPE(None, _vp, _vp, _vp)
 
 _PROTOS = {
     "bbp_set_allocator": (None, [_ALLOC, _FREE, _vp]),
-    "bbp_create_peps": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _i, _dp, _vp]),
+    "bbp_create_peps": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _i, _vp, _i, _vp]),
     "bbp_partition_blocks": (_i, [_vp, _i, _i]),
     "bbp_set_options": (_i, [_vp, _i, _i, _d, ctypes.c_uint64]),
     "bbp_init_messages": (_i, [_vp, _dp]),
@@ -78,6 +78,9 @@ _PROTOS = {
     "bbp_k_panel_qr": (_i, [_i, _vp, _i, _i, _vp, _vp, _i, _i, _vp]),
     "bbp_k_svd_work_bytes_rand": (ctypes.c_size_t, [_i, _i, _i, _i, _i]),
     "bbp_k_fma_peak": (_i, [_i, _i, _i, _vp, _dp, _vp]),
+    "bbp_set_hermitise": (_i, [_vp, _i]),
+    "bbp_expect_product": (_i, [_vp, _dp, _dp, _i, _i, _dp, _dp]),
+    "bbp_bond_energies": (_i, [_vp, _ip, _i, _dp]),
     "bbp_k_svd_trunc_rand": (_i, [_i, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp]),
     "bbp_set_execution": (_i, [_vp, _i, _i]),
     "bbp_set_power_iters": (_i, [_vp, _i]),
@@ -177,9 +180,15 @@ def _c128(a) -> np.ndarray:
 # ------------------------------------------------------------ context calls
 
 def bbp_create_peps(lattice: int, Lx: int, Ly: int, periodic: int, d: int, D: int, tensors, stream=None):
-    t = _c128(tensors)
+    """tensors: complex128, or complex64 (passed as such, dtype 1)."""
+    if np.asarray(tensors).dtype == np.complex64:
+        t = np.ascontiguousarray(tensors, dtype=np.complex64).view(np.float32)
+        ptr, dtype = t.ctypes.data_as(ctypes.c_void_p), 1
+    else:
+        t = _c128(tensors)
+        ptr, dtype = t.ctypes.data_as(ctypes.c_void_p), 0
     ctx = _vp()
-    _check(lib().bbp_create_peps(ctypes.byref(ctx), lattice, Lx, Ly, int(periodic), d, D, _dptr(t), _stream(stream)))
+    _check(lib().bbp_create_peps(ctypes.byref(ctx), lattice, Lx, Ly, int(periodic), d, D, ptr, dtype, _stream(stream)))
     return ctx
 
 
@@ -213,6 +222,21 @@ def bbp_expect_local(ctx, op, sites):
     re, im = ctypes.c_double(), ctypes.c_double()
     _check(lib().bbp_expect_local(ctx, _dptr(o), ns, _iptr(s), ctypes.byref(re), ctypes.byref(im)), ctx)
     return complex(re.value, im.value)
+
+
+def bbp_expect_product(ctx, op1, op2, site: int, slot: int):
+    a, b = _c128(op1), _c128(op2)
+    re, im = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bbp_expect_product(ctx, _dptr(a), _dptr(b), site, slot, ctypes.byref(re), ctypes.byref(im)), ctx)
+    return complex(re.value, im.value)
+
+
+def bbp_bond_energies(ctx, bonds) -> np.ndarray:
+    """<S_i . S_j> of every bond (site, slot) in `bonds`."""
+    b = np.ascontiguousarray([(int(x[0]), int(x[1])) for x in bonds], dtype=np.int32).reshape(-1)
+    out = np.zeros(len(bonds), dtype=np.float64)
+    _check(lib().bbp_bond_energies(ctx, _iptr(b), len(bonds), _dptr(out)), ctx)
+    return out
 
 
 def bbp_block_rdm(ctx, block: int, sites, d: int = 2):
@@ -332,6 +356,10 @@ def bbp_k_fma_peak(fp64: bool, blocks: int, iters: int, out, stream=None) -> flo
     return fl.value
 
 
+def bbp_set_hermitise(ctx, on: bool = True):
+    _check(lib().bbp_set_hermitise(ctx, int(on)), ctx)
+
+
 def bbp_set_execution(ctx, use_graphs: bool = True, max_streams: int = 16):
     _check(lib().bbp_set_execution(ctx, int(use_graphs), int(max_streams)), ctx)
 
@@ -395,16 +423,17 @@ class bbp_job(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in ("lattice", "Lx", "Ly", "periodic", "d", "D", "bx", "by", "chi",
                                             "precision")] + \
                [("tol", ctypes.c_double)] + [(k, ctypes.c_int) for k in ("max_iter", "streams", "power_iters")] + \
-               [("host_tensors", _vp), ("edge_mats", _vp)]
+               [("host_tensors", _vp), ("edge_mats", _vp), ("tensor_dtype", ctypes.c_int)]
 
 
 def make_job(lattice, Lx, Ly, periodic, d, D, bx, by, chi, precision, tensors, edge_mats, tol, max_iter,
              streams=4, power_iters=1):
     """A job description; keeps references to the host arrays until submitted."""
-    t = np.ascontiguousarray(tensors, dtype=np.complex128)
+    c64 = np.asarray(tensors).dtype == np.complex64
+    t = np.ascontiguousarray(tensors, dtype=np.complex64 if c64 else np.complex128)
     e = np.ascontiguousarray(edge_mats, dtype=np.complex128)
     j = bbp_job(lattice, Lx, Ly, int(periodic), d, D, bx, by, chi, precision, tol, max_iter, streams, power_iters,
-                t.ctypes.data, e.ctypes.data)
+                t.ctypes.data, e.ctypes.data, 1 if c64 else 0)
     j._keep = (t, e)
     return j
 

@@ -55,12 +55,25 @@ void bbp_set_allocator(bbp_alloc_fn alloc, bbp_free_fn free_fn, void* user) {
 }
 
 bbp_status bbp_create_peps(bbp_ctx** out, int lattice, int Lx, int Ly, int periodic, int d, int D,
-                           const double* host_tensors, void* cuda_stream) {
+                           const void* host_tensors, int dtype, void* cuda_stream) {
   return guarded([&]() -> bbp_status {
     if (!out) return set_err(BBP_ERR_ARG, "out is NULL");
     *out = nullptr;
+    if (dtype != 0 && dtype != 1) return set_err(BBP_ERR_ARG, "dtype must be 0 (complex128) or 1 (complex64)");
+    if (!host_tensors) return set_err(BBP_ERR_ARG, "host_tensors is NULL");
+    std::vector<double> wide;
+    const double* t = (const double*)host_tensors;
+    if (dtype == 1) {
+      if (d < 1 || d > 4 || D < 1 || D > 8 || Lx <= 0 || Ly <= 0 || Lx > 4096 || Ly > 4096)
+        return set_err(BBP_ERR_ARG, "d must be 1..4, D 1..8, and the lattice size in range");
+      const size_t ns = (size_t)(lattice == BBP_KAGOME ? 3 : 1) * Lx * Ly;
+      const size_t n = 2 * ns * d * D * D * D * D;
+      const float* f = (const float*)host_tensors;
+      wide.assign(f, f + n);
+      t = wide.data();
+    }
     bbp_ctx* c = new bbp_ctx();
-    int rc = c->eng.create(lattice, Lx, Ly, periodic, d, D, host_tensors, (cudaStream_t)cuda_stream);
+    int rc = c->eng.create(lattice, Lx, Ly, periodic, d, D, t, (cudaStream_t)cuda_stream);
     if (rc) {
       g_err = c->eng.last_error;
       delete c;
@@ -82,13 +95,21 @@ bbp_status bbp_set_options(bbp_ctx* ctx, int chi, int precision, double alpha, u
   if (chi < 1 || chi > 64) return set_err(BBP_ERR_ARG, "chi must be 1..64");
   if (precision != BBP_FP64 && precision != BBP_FP32 && precision != BBP_TF32 && precision != BBP_BF16)
     return set_err(BBP_ERR_ARG, "precision must be BBP_FP64, BBP_TF32, BBP_BF16 or BBP_FP32");
-  if (alpha != 1.0) return set_err(BBP_ERR_ARG, "only the undamped update (alpha = 1) is implemented");
+  if (!(alpha >= 0.0 && alpha <= 1.0)) return set_err(BBP_ERR_ARG, "alpha must lie in [0, 1]");
   if (ctx->eng.messages_ready) return set_err(BBP_ERR_STATE, "options must be set before bbp_init_messages");
   int rc = ctx->eng.set_precision(precision == BBP_FP64 ? 0 : 1);
   if (rc) return from(ctx, rc);
   ctx->eng.tc_mode = precision == BBP_TF32 ? 1 : precision == BBP_BF16 ? 2 : 0;
   ctx->eng.drop_graphs();
   ctx->eng.chi = chi;
+  ctx->eng.alpha = alpha;
+  return BBP_OK;
+}
+
+bbp_status bbp_set_hermitise(bbp_ctx* ctx, int on) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  ctx->eng.drop_graphs();
+  ctx->eng.hermitise = on != 0;
   return BBP_OK;
 }
 
@@ -199,6 +220,52 @@ bbp_status bbp_expect_local(bbp_ctx* ctx, const double* op, int ns, const int* s
     }
     *re_out = sr;
     *im_out = si;
+    return BBP_OK;
+  });
+}
+
+bbp_status bbp_expect_product(bbp_ctx* ctx, const double* op1, const double* op2, int site, int slot, double* re_out,
+                              double* im_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!op1 || !op2 || !re_out || !im_out) return set_err(BBP_ERR_ARG, "NULL argument");
+  return guarded([&]() -> bbp_status {
+    bbp::Engine& e = ctx->eng;
+    if (!e.partitioned || !e.messages_ready) return set_err(BBP_ERR_STATE, "partition and messages are required first");
+    if (site < 0 || site >= e.geom.lat.n_sites() || slot < 0 || slot > 3) return set_err(BBP_ERR_ARG, "bond out of range");
+    std::vector<std::array<int, 2>> coords;
+    std::array<int, 2> k1, k2;
+    if (int rc = e.bond_region(site, slot, coords, k1, k2)) return from(ctx, rc);
+    const int d = e.d;
+    bbp::DBuf dev;
+    if (!dev.ensure(sizeof(double) * 4 * d * d + 256, e.stream)) return set_err(BBP_ERR_OOM, "allocation failed");
+    std::vector<double> host(4 * d * d);
+    std::memcpy(host.data(), op1, sizeof(double) * 2 * d * d);
+    std::memcpy(host.data() + 2 * d * d, op2, sizeof(double) * 2 * d * d);
+    cudaError_t ce = cudaMemcpyAsync(dev.p, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice, e.stream);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    const double* d1 = (const double*)dev.p;
+    std::vector<std::vector<std::array<int, 2>>> C = {coords, coords};
+    std::vector<bbp::OpList> O = {{}, {{k1, d1}, {k2, d1 + 2 * d * d}}};
+    std::vector<double> ls, re, im;
+    if (int rc = e.contract_batch(C, O, ls, re, im)) return from(ctx, rc);
+    const double den = re[0] * re[0] + im[0] * im[0], sc = std::exp(ls[1] - ls[0]);
+    *re_out = (re[1] * re[0] + im[1] * im[0]) / den * sc;
+    *im_out = (im[1] * re[0] - re[1] * im[0]) / den * sc;
+    return BBP_OK;
+  });
+}
+
+bbp_status bbp_bond_energies(bbp_ctx* ctx, const int* site_slots, int nbonds, double* e_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!site_slots || !e_out || nbonds < 0) return set_err(BBP_ERR_ARG, "bad arguments");
+  return guarded([&]() -> bbp_status {
+    bbp::Engine& e = ctx->eng;
+    if (!e.partitioned || !e.messages_ready) return set_err(BBP_ERR_STATE, "partition and messages are required first");
+    std::vector<std::array<int, 2>> bonds(nbonds);
+    for (int b = 0; b < nbonds; ++b) bonds[b] = {site_slots[2 * b], site_slots[2 * b + 1]};
+    std::vector<double> out;
+    if (int rc = e.bond_energies(bonds, out)) return from(ctx, rc);
+    std::copy(out.begin(), out.end(), e_out);
     return BBP_OK;
   });
 }

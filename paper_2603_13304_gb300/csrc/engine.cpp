@@ -203,6 +203,12 @@ unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int
   mix((unsigned long long)chi);
   mix((unsigned long long)power_iters);
   mix((unsigned long long)power_iters64);
+  {
+    unsigned long long ab;
+    std::memcpy(&ab, &alpha, sizeof ab);
+    mix(ab);
+  }
+  mix((unsigned long long)hermitise);
   mix((unsigned long long)nstreams);
   mix((unsigned long long)(uintptr_t)dist_dev.p);
   for (int i = 0; i < nstreams; ++i) mix((unsigned long long)(uintptr_t)pool[i]->arena.p);
@@ -234,6 +240,12 @@ unsigned long long Engine::input_signature(int nstreams) const {
   mix((unsigned long long)chi);
   mix((unsigned long long)power_iters);
   mix((unsigned long long)power_iters64);
+  {
+    unsigned long long ab;
+    std::memcpy(&ab, &alpha, sizeof ab);
+    mix(ab);
+  }
+  mix((unsigned long long)hermitise);
   mix((unsigned long long)nstreams);
   mix((unsigned long long)(uintptr_t)dist_dev.p);
   for (int i = 0; i < nstreams && i < (int)pool.size(); ++i) mix((unsigned long long)(uintptr_t)pool[i]->arena.p);
@@ -261,7 +273,7 @@ Engine::~Engine() {
   if (root_in) cudaEventDestroy(root_in);
   if (root_in2) cudaEventDestroy(root_in2);
   if (root_out) cudaEventDestroy(root_out);
-  if (h_dist) cudaFreeHost(h_dist);
+  if (h_word) cudaFreeHost(h_word);
   for (SweepWork* w : pool) {
     if (w->stream) cudaStreamSynchronize(w->stream);
     w->arena.release();
@@ -443,10 +455,133 @@ ChainDesc chain_of(const Message& m, int which) {
 }
 }  // namespace
 
+// ------------------------------------------ learning step, Hermitisation
+//
+// Sec. 2.3.3: the message that replaces the old one is alpha new +
+// (1 - alpha) old (Eq. of the learning step), and a message may be replaced
+// by its Hermitian part (M + M^dagger) / 2 ("Hermitize MPSs").  Both are MPS
+// sums: the direct sum of the two MPSs, compressed back to bond chi by a
+// left-canonical QR sweep and a right-to-left truncated-SVD sweep, then
+// normalised like every message.  The new message is Hermitised first.
+// The shapes are fixed by the input shapes, so the host knows them at
+// enqueue time (and a captured iteration replays them).
+
+int Engine::reserve_learning(Message& m) {
+  if (!learning() || m.open) return 0;
+  const size_t bytes = elem() * (size_t)m.k() * 5 * m.cap;
+  if (m.lrn.bytes >= bytes && m.lrn.p) return 0;
+  CK(cudaStreamSynchronize(stream));
+  if (!m.lrn.ensure(bytes, stream)) return fail(this, 2, "learning-step scratch allocation failed");
+  return 0;
+}
+
+// compress the sum tensors held in m.lrn (shapes sh) to bond chi, in place
+template <typename C>
+int Engine::compress_lrn(Message& m, std::vector<TShape>& sh, SweepWork& w, cudaStream_t s) {
+  const int k = (int)sh.size();
+  const size_t cap4 = 4 * m.cap;
+  C* aux = (C*)m.lrn.p;
+  auto T = [&](int q) { return aux + (size_t)q * cap4; };
+  const C one = one_of<C>(), zero = zero_of<C>();
+  C* qrA = (C*)w.qrA;
+  C* qrQ = (C*)w.qrQ;
+  C* qrR = (C*)w.qrR;
+  C* tau = (C*)w.tau;
+  C* S0 = (C*)w.S[0];
+  for (int q = 0; q + 1 < k; ++q) {   // left-canonical QR sweep
+    const TShape a = sh[q], b = sh[q + 1];
+    const int mm = a.l * a.p, nn = a.r, kk = std::min(mm, nn);
+    CK(cudaMemcpyAsync(qrA, T(q), sizeof(C) * (size_t)mm * nn, cudaMemcpyDeviceToDevice, s));
+    CK(launch_qr(qrA, mm, nn, qrQ, qrR, tau, s));
+    CK(cudaMemcpyAsync(T(q), qrQ, sizeof(C) * (size_t)mm * kk, cudaMemcpyDeviceToDevice, s));
+    sh[q].r = kk;
+    CK(launch_zgemm('N', 'N', kk, b.p * b.r, nn, one, qrR, nn, 0, T(q + 1), b.p * b.r, 0, zero, S0, b.p * b.r, 0, 1,
+                    s));
+    CK(cudaMemcpyAsync(T(q + 1), S0, sizeof(C) * (size_t)kk * b.p * b.r, cudaMemcpyDeviceToDevice, s));
+    sh[q + 1].l = kk;
+    sweep_launches += 5;
+  }
+  for (int q = k - 1; q >= 1; --q) {  // truncated SVDs from the right: Z^H = U' Rem', T_q = U'^H
+    const TShape a = sh[q], b = sh[q - 1];
+    const int l = a.l, pr = a.p * a.r, kk = std::min(chi, std::min(pr, l));
+    CK(launch_conj_transpose(T(q), l, pr, qrA, s));
+    const bool c64 = sizeof(C) == sizeof(float2);
+    const int qsteps = c64 ? power_iters : power_iters64;
+    CK(svd_call(qrA, pr, l, chi, qrQ, qrR, w.svd, w.status, s, qsteps, false, w.status + 1));
+    CK(launch_conj_transpose(qrQ, pr, kk, T(q), s));
+    sh[q].l = kk;
+    CK(launch_zgemm('N', 'C', b.l * b.p, kk, l, one, T(q - 1), l, 0, qrR, l, 0, zero, S0, kk, 0, 1, s));
+    CK(cudaMemcpyAsync(T(q - 1), S0, sizeof(C) * (size_t)b.l * b.p * kk, cudaMemcpyDeviceToDevice, s));
+    sh[q - 1].r = kk;
+    sweep_launches += 4 + svd_launches(pr, l, chi, c64, qsteps);
+  }
+  return 0;
+}
+
+// Hermitisation and the learning step of the new message in buffer `which`
+// (shapes m.sh[which], updated); the old message is buffer 1 - which.
+template <typename C>
+int Engine::learn_message(Message& m, int which, SweepWork& w, cudaStream_t s) {
+  const int k = m.k();
+  const size_t cap4 = 4 * m.cap;
+  C* aux = (C*)m.lrn.p;
+  C* dag = aux + (size_t)k * cap4;
+  auto T = [&](int q) { return aux + (size_t)q * cap4; };
+  auto sum_into = [&](C* const* x, const std::vector<TShape>& xs, C* const* y, const std::vector<TShape>& ys,
+                      double2 ca, double2 cb, std::vector<TShape>& out) -> int {
+    out.assign(k, TShape());
+    for (int q = 0; q < k; ++q) {
+      CK(launch_mps_sum(x[q], xs[q].l, xs[q].r, y[q], ys[q].l, ys[q].r, xs[q].p, q, k, ca, cb, T(q), s));
+      out[q].l = (k == 1 || q == 0) ? xs[q].l : xs[q].l + ys[q].l;
+      out[q].p = xs[q].p;
+      out[q].r = (k == 1 || q == k - 1) ? xs[q].r : xs[q].r + ys[q].r;
+    }
+    sweep_launches += k;
+    return 0;
+  };
+  auto store_back = [&](const std::vector<TShape>& sh) -> int {
+    for (int q = 0; q < k; ++q) {
+      if ((size_t)sh[q].size() > m.cap) return fail(this, 8, "learned message tensor exceeds its buffer");
+      CK(cudaMemcpyAsync(m.tensor<C>(which, q), T(q), sizeof(C) * (size_t)sh[q].size(), cudaMemcpyDeviceToDevice, s));
+    }
+    m.sh[which] = sh;
+    CK(launch_msg_normalise(chain_of<C>(m, which), sizeof(C) == sizeof(float2), w.k4, s));
+    sweep_launches += k + 1;
+    return 0;
+  };
+  std::vector<C*> nw(k), od(k), dg(k);
+  for (int q = 0; q < k; ++q) {
+    nw[q] = m.tensor<C>(which, q);
+    od[q] = m.tensor<C>(1 - which, q);
+    dg[q] = dag + (size_t)q * m.cap;
+  }
+  std::vector<TShape> sh;
+  if (hermitise) {
+    for (int q = 0; q < k; ++q) {
+      const TShape t = m.sh[which][q];
+      CK(launch_mps_dagger(nw[q], t.l, m.Dleg[q], t.r, dg[q], s));
+    }
+    if (int rc = sum_into(nw.data(), m.sh[which], dg.data(), m.sh[which], make_double2(0.5, 0), make_double2(0.5, 0), sh))
+      return rc;
+    if (int rc = compress_lrn<C>(m, sh, w, s)) return rc;
+    if (int rc = store_back(sh)) return rc;
+  }
+  if (alpha != 1.0) {
+    if (int rc = sum_into(nw.data(), m.sh[which], od.data(), m.sh[1 - which], make_double2(alpha, 0),
+                          make_double2(1.0 - alpha, 0), sh))
+      return rc;
+    if (int rc = compress_lrn<C>(m, sh, w, s)) return rc;
+    if (int rc = store_back(sh)) return rc;
+  }
+  return 0;
+}
+
 // Normalise (unit norm, <I|M> > 0) buffer `which` of m on stream s;
 // optionally write ||new - old|| into dist_slot: the norm of the direct-sum
 // MPS (new, -old) reduced by a QR sweep, in the element type (absolute
-// accuracy ~ eps of that type, no sqrt(2 - 2 Re<old|new>) floor).
+// accuracy ~ eps of that type, no sqrt(2 - 2 Re<old|new>) floor).  In an
+// iteration (with_distance) the learning step and the Hermitisation come
+// between the two.
 template <typename C>
 int Engine::finalize_message(Message& m, int which, SweepWork& w, cudaStream_t s, double* dist_slot,
                              bool with_distance) {
@@ -455,6 +590,8 @@ int Engine::finalize_message(Message& m, int which, SweepWork& w, cudaStream_t s
   CK(launch_msg_normalise(chain_of<C>(m, which), sizeof(C) == sizeof(float2), w.k4, s));
   sweep_launches += 1;
   if (!with_distance) return 0;
+  if (learning() && !m.open)
+    if (int rc = learn_message<C>(m, which, w, s)) return rc;
   const int old = 1 - which;
   const C one = one_of<C>(), zero = zero_of<C>();
   C* X0 = (C*)w.dX0;
@@ -557,6 +694,15 @@ void Engine::job_needs(const SweepJob& job, size_t need[7]) const {
   if (tc_mode && precision != 0)
     for (const auto& st : tr.steps)
       need[6] = std::max<size_t>(need[6], tc_absorb_bytes(tc_mode == 2, st.P, st.Q, st.l, st.r));
+  if (learning()) {
+    // compression of a direct sum: tensors up to (2 chi) x D^2 x (2 chi); SVDs of (2 chi D^2) x (2 chi)
+    const size_t s4 = (size_t)4 * chi * chi * D * D;
+    need[0] = std::max(need[0], s4);
+    need[1] = std::max(need[1], s4);
+    const int lr = 2 * chi * D * D, lc = 2 * chi;
+    need[3] = std::max<size_t>(need[3], precision == 0 ? svd_work_bound_rand64(lc, lr, chi)
+                                                       : svd_work_bound_c64(lc, lr, chi, false));
+  }
 }
 
 int Engine::reserve_workers(const std::vector<SweepJob>& jobs, int nstreams) {
@@ -831,15 +977,9 @@ int Engine::iter_begin() {
   if (!partitioned) return fail(this, 8, "bbp_partition_blocks must come first");
   if (!messages_ready) return fail(this, 8, "bbp_init_messages must come first");
   const int nu = (int)geom.updates().size();
-  if (!dist_dev.ensure(sizeof(double) * nu + 2 * sizeof(int) * nu + 256, stream)) return fail(this, 2, "allocation failed");
-  if (h_cap < (size_t)nu) {
-    if (h_dist) cudaFreeHost(h_dist);
-    h_dist = nullptr;
-    h_cap = 0;
-    CK(cudaHostAlloc((void**)&h_dist, (sizeof(double) + 2 * sizeof(int)) * (size_t)std::max(nu, 1),
-                     cudaHostAllocDefault));
-    h_cap = (size_t)nu;
-  }
+  // device: per-update distances, 2 status ints per update, tol, the word
+  if (!dist_dev.ensure(sizeof(double) * nu + 2 * sizeof(int) * nu + 512, stream)) return fail(this, 2, "allocation failed");
+  if (!h_word) CK(cudaHostAlloc((void**)&h_word, 4 * sizeof(double), cudaHostAllocDefault));
   if (!root) {
     CK(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&root_in, cudaEventDisableTiming));
@@ -870,6 +1010,8 @@ int Engine::iter_launch_t() {
   in_flight = false;
   if (nu == 0) return 0;
   int* status_dev = (int*)((double*)dist_dev.p + nu);
+  double* tol_dev = (double*)((char*)dist_dev.p + ((sizeof(double) * nu + 2 * sizeof(int) * nu + 255) & ~size_t(255)));
+  double* word_dev = tol_dev + 4;
   const int nstreams = std::max(1, std::min(nu, max_streams));
   for (int i = 0; i < nstreams; ++i)
     if (!work(i)) return fail(this, 3, "stream creation failed");
@@ -881,13 +1023,12 @@ int Engine::iter_launch_t() {
     IterGraph& g = graphs[par];
     if (g.exec && g.in_sig == input_signature(nstreams) && (int)g.out_shapes.size() == nu) {
       for (int u = 0; u < nu; ++u) msgs.at({ups[u].recv_block, ups[u].recv_face}).sh[par] = g.out_shapes[u];
+      h_word[0] = iter_tol;
+      CK(cudaMemcpyAsync(tol_dev, h_word, sizeof(double), cudaMemcpyHostToDevice, root));
       CK(cudaGraphLaunch(g.exec, root));
       sweep_launches = g.launches;
       sweep_flops = g.flops;
-      double* hd = h_dist;
-      int* hs = (int*)(h_dist + nu);
-      CK(cudaMemcpyAsync(hd, dist_dev.p, sizeof(double) * nu, cudaMemcpyDeviceToHost, root));
-      CK(cudaMemcpyAsync(hs, status_dev, 2 * sizeof(int) * nu, cudaMemcpyDeviceToHost, root));
+      CK(cudaMemcpyAsync(h_word + 1, word_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, root));
       CK(cudaEventRecord(root_out, root));
       launched_parity = par;
       launched_graph = true;
@@ -920,6 +1061,9 @@ int Engine::iter_launch_t() {
     dst.sh[nxt] = jobs[u].tr.final_mps;
   }
   if ((rc = reserve_workers(jobs, nstreams))) return rc;
+  if (learning())
+    for (int u = 0; u < nu; ++u)
+      if ((rc = reserve_learning(msgs.at({ups[u].recv_block, ups[u].recv_face})))) return rc;
   cudaEvent_t fork = root_in2;
   // fork onto the worker streams, one sweep and one finalisation per update, join
   auto enqueue = [&]() -> int {
@@ -938,6 +1082,10 @@ int Engine::iter_launch_t() {
       CK(cudaEventRecord(pool[i]->done, pool[i]->stream));
       CK(cudaStreamWaitEvent(root, pool[i]->done, 0));
     }
+    if (!e) {
+      CK(launch_iter_reduce((const double*)dist_dev.p, status_dev, nu, tol_dev, word_dev, root));
+      sweep_launches += 1;
+    }
     return e;
   };
   if (!root_in2) {
@@ -947,6 +1095,8 @@ int Engine::iter_launch_t() {
   // capture only once the inputs repeat: while the bond dimensions still
   // grow (the first iterations from bond-1 messages) every iteration would
   // need a new graph, and instantiating it costs more than launching eagerly
+  h_word[0] = iter_tol;
+  CK(cudaMemcpyAsync(tol_dev, h_word, sizeof(double), cudaMemcpyHostToDevice, root));
   const bool stable = in_sig == last_in_sig[parity];
   last_in_sig[parity] = in_sig;
   const bool replayable = graphs[parity].exec && graphs[parity].sig == iter_signature(jobs, nstreams);
@@ -987,17 +1137,14 @@ int Engine::iter_launch_t() {
     }
     g.in_sig = in_sig;
     g.out_shapes.resize(nu);
-    for (int u = 0; u < nu; ++u) g.out_shapes[u] = jobs[u].tr.final_mps;
+    for (int u = 0; u < nu; ++u) g.out_shapes[u] = msgs.at({ups[u].recv_block, ups[u].recv_face}).sh[parity];
     cudaError_t le = cudaGraphLaunch(g.exec, root);
     if (le != cudaSuccess) return fail(this, 3, std::string("graph launch: ") + cudaGetErrorString(le));
     sweep_launches = g.launches;
     sweep_flops = g.flops;
   }
   if (rc) return rc;
-  double* hd = h_dist;
-  int* hs = (int*)(h_dist + nu);
-  CK(cudaMemcpyAsync(hd, dist_dev.p, sizeof(double) * nu, cudaMemcpyDeviceToHost, root));
-  CK(cudaMemcpyAsync(hs, status_dev, 2 * sizeof(int) * nu, cudaMemcpyDeviceToHost, root));
+  CK(cudaMemcpyAsync(h_word + 1, word_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, root));
   CK(cudaEventRecord(root_out, root));
   launched_parity = parity;
   in_flight = true;
@@ -1016,16 +1163,12 @@ int Engine::iter_finish(double* err_out) {
   in_flight = false;
   CK(cudaEventSynchronize(root_out));
   if (ktimer_class()) ktimer_collect(launched_graph ? graph_tag(launched_parity) : -1);
-  const double* hd = h_dist;
-  const int* hs = (const int*)(h_dist + nu);
-  double err = 0.0;
-  bool nonfinite = false, sweep_limit = false, tc_timeout = false;
-  for (int u = 0; u < nu; ++u) {
-    if (!std::isfinite(hd[u])) nonfinite = true;
-    err = std::max(err, hd[u]);
-    sweep_limit = sweep_limit || hs[2 * u] != 0;
-    tc_timeout = tc_timeout || hs[2 * u + 1] != 0;
-  }
+  // the convergence word of the iteration (k_iter_reduce)
+  const double err = h_word[1];
+  int flags = 0;
+  std::memcpy(&flags, h_word + 2, sizeof(int));
+  const bool nonfinite = flags & 1, sweep_limit = flags & 2, tc_timeout = flags & 4;
+  last_converged = (flags & 8) != 0;
   for (const auto& up : ups) msgs.at({up.recv_block, up.recv_face}).cur ^= 1;
   launches_per_iter = sweep_launches;
   flops_per_iter = sweep_flops;
@@ -1039,6 +1182,7 @@ int Engine::iter_finish(double* err_out) {
 
 int Engine::iterate(double tol, int max_iter, int* iters, double* err_out) {
   if (max_iter < 0 || !(tol >= 0.0)) return fail(this, 1, "tol must be >= 0 and max_iter >= 0");
+  iter_tol = tol;
   int rc = iter_begin();
   if (rc) return rc;
   double err = geom.updates().empty() ? 0.0 : INFINITY;
@@ -1047,7 +1191,7 @@ int Engine::iterate(double tol, int max_iter, int* iters, double* err_out) {
     if ((rc = iter_launch())) break;
     rc = iter_finish(&err);
     if (rc) { ++it; break; }
-    if (err <= tol) { ++it; break; }
+    if (last_converged) { ++it; break; }   // the device's convergence word
   }
   const int rc2 = iter_end();
   if (iters) *iters = it;
@@ -1177,6 +1321,50 @@ int Engine::bond_region(int g1, int k1, std::vector<std::array<int, 2>>& coords,
   const Block& b2 = geom.blocks[geom.block_id(X2, Y2)];
   key2 = {1, b2.local_of(t2, i2 - (X2 - b2.X) * geom.bx, j2 - (Y2 - b2.Y) * geom.by)};
   if (key2[1] < 0) return fail(this, 8, "neighbour not found in its block");
+  return 0;
+}
+
+// <S_i . S_j> of the given bonds (site, slot): per bond the region of
+// reading E contracted with nothing inserted and with S^a (x) S^a for
+// a = x, y, z, all contractions of all bonds in one batch.
+int Engine::bond_energies(const std::vector<std::array<int, 2>>& bonds, std::vector<double>& out) {
+  if (d != 2) return fail(this, 1, "the Heisenberg energy needs d = 2");
+  static const double sx[8] = {0, 0, 0.5, 0, 0.5, 0, 0, 0};
+  static const double sy[8] = {0, 0, 0, -0.5, 0, 0.5, 0, 0};
+  static const double sz[8] = {0.5, 0, 0, 0, 0, 0, -0.5, 0};
+  if (!op_dev.ensure(sizeof(double) * 24, stream)) return fail(this, 2, "allocation failed");
+  double hops[24];
+  std::memcpy(hops, sx, sizeof(sx));
+  std::memcpy(hops + 8, sy, sizeof(sy));
+  std::memcpy(hops + 16, sz, sizeof(sz));
+  CK(cudaMemcpyAsync(op_dev.p, hops, sizeof(hops), cudaMemcpyHostToDevice, stream));
+  const double* dsx = (const double*)op_dev.p;
+  std::vector<std::vector<std::array<int, 2>>> Cc;
+  std::vector<OpList> O;
+  for (const auto& bk : bonds) {
+    if (bk[0] < 0 || bk[0] >= geom.lat.n_sites() || bk[1] < 0 || bk[1] > 3) return fail(this, 1, "bond out of range");
+    std::vector<std::array<int, 2>> coords;
+    std::array<int, 2> k1, k2;
+    if (int rc = bond_region(bk[0], bk[1], coords, k1, k2)) return rc;
+    Cc.push_back(coords);
+    O.push_back({});
+    for (const double* op : {dsx, dsx + 8, dsx + 16}) {
+      Cc.push_back(coords);
+      O.push_back({{k1, op}, {k2, op}});
+    }
+  }
+  std::vector<double> ls, re, im;
+  if (int rc = contract_batch(Cc, O, ls, re, im)) return rc;
+  out.assign(bonds.size(), 0.0);
+  for (size_t b = 0; b < bonds.size(); ++b) {
+    const size_t j0 = 4 * b;
+    double tot = 0.0;
+    for (int a = 1; a <= 3; ++a) {
+      const double r0 = re[j0], i0 = im[j0], r1 = re[j0 + a], i1 = im[j0 + a];
+      tot += std::exp(ls[j0 + a] - ls[j0]) * (r1 * r0 + i1 * i0) / (r0 * r0 + i0 * i0);
+    }
+    out[b] = tot;
+  }
   return 0;
 }
 

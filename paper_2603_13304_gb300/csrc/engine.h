@@ -44,6 +44,7 @@ struct Message {
   std::vector<int> Dleg;               // bond dimension of each fused leg
   std::vector<TShape> sh[2];           // shapes of the two buffers
   DBuf buf[2];
+  DBuf lrn;                            // learning step / Hermitisation: k sum tensors of 4 cap, k of cap
   size_t cap = 0;                      // elements per tensor
   int cur = 0;
   template <typename C> C* tensor(int which, int q) const { return (C*)buf[which].p + (size_t)q * cap; }
@@ -89,6 +90,9 @@ class Engine {
  public:
   Geometry geom;
   int d = 2, D = 2, chi = 8, precision = 0, power_iters = 1, power_iters64 = 6;
+  double alpha = 1.0;                  // learning step: alpha new + (1 - alpha) old (Sec. 2.3.3)
+  bool hermitise = false;              // replace each new message by its Hermitian part
+  bool learning() const { return alpha != 1.0 || hermitise; }
   int tc_mode = 0;                     // absorb contraction: 0 SIMT GEMM, 1 tcgen05 TF32 split, 2 tcgen05 BF16 split
   bool use_graphs = true;              // replay a captured CUDA graph per iteration
   int max_streams = 16;                // sweep jobs run on up to this many streams
@@ -129,6 +133,7 @@ class Engine {
   int bond_region(int g1, int k1, std::vector<std::array<int, 2>>& coords, std::array<int, 2>& key1,
                   std::array<int, 2>& key2);
   int energy_per_site(double* e);
+  int bond_energies(const std::vector<std::array<int, 2>>& bonds, std::vector<double>& out);
   int log_norm(double* out);
   int get_message(int block, int face, int* k, int* shapes, double* data, size_t cap);
 
@@ -142,6 +147,9 @@ class Engine {
   template <typename C> int run_sweep(SweepJob& job, SweepWork& w);
   template <typename C>
   int finalize_message(Message& m, int which, SweepWork& w, cudaStream_t s, double* dist_slot, bool with_distance);
+  template <typename C> int compress_lrn(Message& m, std::vector<TShape>& sh, SweepWork& w, cudaStream_t s);
+  template <typename C> int learn_message(Message& m, int which, SweepWork& w, cudaStream_t s);
+  int reserve_learning(Message& m);
   template <typename C> int iter_launch_t();
   template <typename C>
   int contract_batch_t(const std::vector<std::vector<std::array<int, 2>>>& coords, const std::vector<OpList>& ops,
@@ -164,8 +172,13 @@ class Engine {
   unsigned long long last_in_sig[2] = {0, 0};   // inputs of the last iteration of each parity
   cudaStream_t root = nullptr;         // private root of every iteration (and of its capture)
   cudaEvent_t root_in = nullptr, root_in2 = nullptr, root_out = nullptr;
-  double* h_dist = nullptr;            // pinned: per-update distances, then 2 status ints per update
-  size_t h_cap = 0;
+  double* h_word = nullptr;            // pinned: [0] tol of the iteration, [1] largest change, [2] flags (int)
+
+ public:
+  double iter_tol = 0.0;               // tolerance the device compares the iteration's largest change with
+  bool last_converged = false;         // converged bit of the last finished iteration's word
+
+ private:
   bool in_flight = false;
   bool launched_graph = false;         // the iteration in flight is a graph replay
   int launched_parity = 0;

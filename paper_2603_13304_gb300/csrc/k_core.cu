@@ -96,39 +96,54 @@ inline int grid_for(long long n, int threads) {
 }
 
 // ------------------------------------------------------------------ K1 fuse
-// Computed in complex128 and rounded to the output type.
+// One output entry per thread, consecutive threads writing consecutive
+// entries.  The sum over the physical index runs in complex128 for a
+// complex128 output and in complex64 for a complex64 output (two products
+// per term: the rounding of the stored entry dominates either way); the
+// operator, when present, is applied in complex128.  Index arithmetic in 32
+// bits (D <= 8: at most 2^24 entries).
 
 template <typename C>
-__global__ void k_fuse(const double2* __restrict__ t, int d, int Dfull, int4 n4, const double2* __restrict__ op,
-                       int4 perm4, C* __restrict__ T, long long total) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ C ldt(const double2* t, int i) {
+  const double2 v = __ldg(t + i);
+  return cx<C>(v.x, v.y);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_fuse(const double2* __restrict__ t, int d, int Dfull, int4 n4,
+                                              const double2* __restrict__ op, int4 perm4, C* __restrict__ T,
+                                              int total) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int nn[4] = {n4.x, n4.y, n4.z, n4.w};
   const int pp[4] = {perm4.x, perm4.y, perm4.z, perm4.w};
   int ket[4], bra[4];
-  long long rem = idx;
+  int rem = idx;
+#pragma unroll
   for (int q = 3; q >= 0; --q) {
-    int leg = pp[q];
-    int f2 = nn[leg] * nn[leg];
-    int f = (int)(rem % f2);
+    const int leg = pp[q];
+    const int f2 = nn[leg] * nn[leg];
+    const int f = rem % f2;
     rem /= f2;
     ket[leg] = f / nn[leg];
     bra[leg] = f % nn[leg];
   }
-  const long long D = Dfull;
-  const long long sD4 = D * D * D * D;
-  const long long ok = ((ket[0] * D + ket[1]) * D + ket[2]) * D + ket[3];
-  const long long ob = ((bra[0] * D + bra[1]) * D + bra[2]) * D + bra[3];
-  double2 acc = make_double2(0.0, 0.0);
-  for (int s = 0; s < d; ++s) {
-    double2 tb = cconj(t[s * sD4 + ob]);
-    if (op) {
+  const int D = Dfull;
+  const int sD4 = D * D * D * D;
+  const int ok = ((ket[0] * D + ket[1]) * D + ket[2]) * D + ket[3];
+  const int ob = ((bra[0] * D + bra[1]) * D + bra[2]) * D + bra[3];
+  if (op) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int s = 0; s < d; ++s) {
+      const double2 tb = cconj(t[s * sD4 + ob]);
       for (int sp = 0; sp < d; ++sp) acc = cadd(acc, cmul(op[s * d + sp], cmul(t[sp * sD4 + ok], tb)));
-    } else {
-      acc = cadd(acc, cmul(t[s * sD4 + ok], tb));
     }
+    T[idx] = cx<C>(acc.x, acc.y);
+    return;
   }
-  T[idx] = cx<C>(acc.x, acc.y);
+  C acc = cx<C>(0.0, 0.0);
+  for (int s = 0; s < d; ++s) acc = cadd(acc, cmul(ldt<C>(t, s * sD4 + ok), cconj(ldt<C>(t, s * sD4 + ob))));
+  T[idx] = acc;
 }
 
 // -------------------------------------------------------------------- gemm
@@ -1256,9 +1271,10 @@ static cudaError_t fuse_t(const double2* t, int d, int Dfull, const int n[4], co
                           C* T, cudaStream_t s) {
   long long total = 1;
   for (int q = 0; q < 4; ++q) total *= (long long)n[q] * n[q];
+  if (total > (1LL << 30) || (long long)d * Dfull * Dfull * Dfull * Dfull > (1LL << 30)) return cudaErrorInvalidValue;
   long long blocks = (total + 255) / 256;
   k_fuse<C><<<(unsigned)blocks, 256, 0, s>>>(t, d, Dfull, make_int4(n[0], n[1], n[2], n[3]), op,
-                                             make_int4(perm[0], perm[1], perm[2], perm[3]), T, total);
+                                             make_int4(perm[0], perm[1], perm[2], perm[3]), T, (int)total);
   return cudaGetLastError();
 }
 cudaError_t launch_fuse(const double2* t, int d, int D, const int n[4], const double2* op, const int perm[4], double2* T,
@@ -1766,6 +1782,85 @@ __global__ void k_direct_sum(const C* a, int la, int ra, const C* b, int lb, int
   }
 }
 
+// The iteration's convergence word (Alg. 1 with the convergence criterion
+// of the BP update): the largest message change over the nu updates, and
+// flags: 1 a change is not finite, 2 a Jacobi reached its sweep limit, 4 a
+// tensor-core wait timed out, 8 converged (largest change <= *tol, no other
+// flag).  One CTA, after every update of the iteration has finished.
+__global__ void __launch_bounds__(256) k_iter_reduce(const double* __restrict__ dist, const int* __restrict__ status,
+                                                     int nu, const double* __restrict__ tol, double* __restrict__ out) {
+  __shared__ double s_max[8];
+  __shared__ int s_flags[8];
+  double m = 0.0;
+  int flags = 0;
+  for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+    const double x = dist[u];
+    if (!isfinite(x)) flags |= 1;
+    else m = fmax(m, x);
+    if (status[2 * u]) flags |= 2;
+    if (status[2 * u + 1]) flags |= 4;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_max[threadIdx.x >> 5] = m;
+    s_flags[threadIdx.x >> 5] = flags;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmax(m, s_max[w]);
+      flags |= s_flags[w];
+    }
+    if (!flags && m <= *tol) flags |= 8;
+    out[0] = (flags & 1) ? NAN : m;
+    ((int*)(out + 1))[0] = flags;
+  }
+}
+
+// a x + b y as one MPS tensor at chain position pos of k: the direct sum of
+// the bond spaces, the coefficients entering the first tensor (a single
+// tensor is summed entrywise).  The learning step and the Hermitisation of
+// a message (Sec. 2.3.3) add two MPSs this way.
+template <typename C>
+__global__ void k_mps_sum(const C* __restrict__ x, int lx, int rx, const C* __restrict__ y, int ly, int ry, int p,
+                          int pos, int k, double2 ca, double2 cb, C* __restrict__ out) {
+  const int L = (k == 1 || pos == 0) ? lx : lx + ly;
+  const int R = (k == 1 || pos == k - 1) ? rx : rx + ry;
+  const long long tot = (long long)L * p * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / ((long long)p * R)), q = (int)((e / R) % p), c = (int)(e % R);
+    double2 v = make_double2(0.0, 0.0);
+    if (k == 1) {
+      v = cadd(cmul(ca, c128(x[e])), cmul(cb, c128(y[e])));
+    } else if (pos == 0) {
+      v = c < rx ? cmul(ca, c128(x[((long long)a * p + q) * rx + c])) : cmul(cb, c128(y[((long long)a * p + q) * ry + c - rx]));
+    } else if (pos == k - 1) {
+      v = a < lx ? c128(x[((long long)a * p + q) * rx + c]) : c128(y[((long long)(a - lx) * p + q) * ry + c]);
+    } else if (a < lx && c < rx) {
+      v = c128(x[((long long)a * p + q) * rx + c]);
+    } else if (a >= lx && c >= rx) {
+      v = c128(y[((long long)(a - lx) * p + q) * ry + c - rx]);
+    }
+    out[e] = cx<C>(v.x, v.y);
+  }
+}
+
+// The message tensor read as an operator and Hermitian-conjugated: fused leg
+// ket * D + bra becomes bra * D + ket, every entry conjugated.
+template <typename C>
+__global__ void k_mps_dagger(const C* __restrict__ src, int l, int D, int r, C* __restrict__ dst) {
+  const long long tot = (long long)l * D * D * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % r);
+    const long long t = e / r;
+    const int j = (int)(t % D), i = (int)((t / D) % D), a = (int)(t / ((long long)D * D));
+    dst[e] = cconj(src[(((long long)a * D + j) * D + i) * r + c]);
+  }
+}
+
 template <typename C>
 __global__ void __launch_bounds__(1024) k_frob(const C* R, long long n, double* out) {
   __shared__ double sh[40];
@@ -1849,6 +1944,16 @@ __global__ void __launch_bounds__(256) k_mps_dot(ChainDesc A, ChainDesc B, doubl
     k_direct_sum<C><<<grid_for(tot, 256), 256, 0, s>>>(a, la, ra, b, lb, rb, p, pos, k, out);                      \
     return cudaGetLastError();                                                                                     \
   }                                                                                                                \
+  cudaError_t launch_mps_sum(const C* x, int lx, int rx, const C* y, int ly, int ry, int p, int pos, int k,        \
+                             double2 a, double2 b, C* out, cudaStream_t s) {                                        \
+    const int L = (k == 1 || pos == 0) ? lx : lx + ly, R = (k == 1 || pos == k - 1) ? rx : rx + ry;                 \
+    k_mps_sum<C><<<grid_for((long long)L * p * R, 256), 256, 0, s>>>(x, lx, rx, y, ly, ry, p, pos, k, a, b, out);  \
+    return cudaGetLastError();                                                                                     \
+  }                                                                                                                \
+  cudaError_t launch_mps_dagger(const C* src, int l, int D, int r, C* dst, cudaStream_t s) {                        \
+    k_mps_dagger<C><<<grid_for((long long)l * D * D * r, 256), 256, 0, s>>>(src, l, D, r, dst);                    \
+    return cudaGetLastError();                                                                                     \
+  }                                                                                                                \
   cudaError_t launch_frob(const C* R, long long n, double* dist, cudaStream_t s) {                                 \
     k_frob<C><<<1, 1024, 0, s>>>(R, n, dist);                                                                      \
     return cudaGetLastError();                                                                                     \
@@ -1856,6 +1961,12 @@ __global__ void __launch_bounds__(256) k_mps_dot(ChainDesc A, ChainDesc B, doubl
 
 BBP_INSTANTIATE(double2)
 BBP_INSTANTIATE(float2)
+
+cudaError_t launch_iter_reduce(const double* dist, const int* status, int nu, const double* tol, double* out,
+                               cudaStream_t s) {
+  k_iter_reduce<<<1, 256, 0, s>>>(dist, status, nu, tol, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_msg_normalise(const ChainDesc& m, bool c64, double2* work, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};

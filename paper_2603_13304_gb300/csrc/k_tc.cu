@@ -14,13 +14,14 @@
 // TMEM and returns.
 //
 // The complex contraction R[a] = X^T S[a] (batched over a) runs as one real
-// GEMM: X^T and S are split into high and low parts in the operand type
-// (value = hi + lo, each scaled by a power of two so that its largest
-// magnitude is about 1), and the K dimension concatenates
-//   A = [ Re hi, -Im hi | Re hi, -Im hi | Re lo, -Im lo ]   (rows q)
-//       [ Im hi,  Re hi | Im hi,  Re hi | Im lo,  Re lo ]   (rows Q + q)
-//   B = [ Re hi ; Im hi ; Re lo ; Im lo ; Re hi ; Im hi ]
-// so that hi*hi + hi*lo + lo*hi accumulates in FP32 in one pass.
+// GEMM: X^T and S are scaled by a power of two (largest magnitude about 1)
+// and split into limbs of the operand type, and the K dimension concatenates
+// segments that pair a limb of A with a limb of B:
+//   A = [ Re a, -Im a ]  (rows q),  [ Im a, Re a ]  (rows Q + q)  per segment
+//   B = [ Re b ; Im b ]                                           per segment
+// TF32: limbs hi, lo and the segments hi*hi, hi*lo, lo*hi; BF16 (8 bits a
+// limb): limbs h, m, l and the segments hh, hm, mh, hl, mm, lh.  Both
+// accumulate in FP32 in one pass to about FP32 accuracy.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -273,7 +274,7 @@ cudaError_t tc_optin() {
 
 template <bool kBF16, int BN>
 cudaError_t tc_launch(const void* A, long long lda, const void* Bt, long long ldb, float* C, long long ldc, int M, int N,
-                      int K, float alpha, int* err, cudaStream_t s) {
+                      int K, float alpha, int* err, cudaStream_t s, double algo_flops) {
   constexpr int smem = tc_smem<BN>();
   cudaError_t attr_err = tc_optin<kBF16, BN>();
   if (attr_err != cudaSuccess) return attr_err;
@@ -281,7 +282,7 @@ cudaError_t tc_launch(const void* A, long long lda, const void* Bt, long long ld
   if (!make_map(&ta, A, kBF16, M, K, lda, kBM) || !make_map(&tb, Bt, kBF16, N, K, ldb, BN))
     return cudaErrorInvalidValue;
   dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM);
-  KTimerScope timer(KC_TC, s, 2.0 * M * N * K);
+  KTimerScope timer(KC_TC, s, algo_flops > 0 ? algo_flops : 2.0 * M * N * K);
   k_tc_gemm<kBF16, BN><<<grid, 128, smem, s>>>(ta, tb, C, M, N, K, ldc, alpha, err);
   return cudaGetLastError();
 }
@@ -331,29 +332,51 @@ __device__ __forceinline__ float pow2_scale(const int* amax) {
   return exp2f(-(float)ilogbf(m));
 }
 
+// Split of a (scaled) value into limbs of the operand type: TF32 keeps two
+// limbs (hi, lo) and the three products hi*hi + hi*lo + lo*hi; BF16, with 8
+// significant bits a limb, keeps three (h, m, l) and the six products of
+// order up to 2^-16, hh + hm + mh + hl + mm + lh, so that both reach about
+// FP32 accuracy.  Segment s of the K dimension pairs limb kLimbA[s] of A with
+// limb kLimbB[s] of B.
+template <bool kBF16> struct Split;
+template <> struct Split<false> {
+  static constexpr int kSegs = 3;
+  static __device__ __forceinline__ int limb_a(int s) { return s == 2 ? 1 : 0; }   // hi hi lo
+  static __device__ __forceinline__ int limb_b(int s) { return s == 1 ? 1 : 0; }   // hi lo hi
+};
+template <> struct Split<true> {
+  static constexpr int kSegs = 6;
+  static __device__ __forceinline__ int limb_a(int s) { return (0x210100 >> (4 * s)) & 15; }   // h h m h m l
+  static __device__ __forceinline__ int limb_b(int s) { return (0x012010 >> (4 * s)) & 15; }   // h m h l m h
+};
+
+template <bool kBF16>
+__device__ __forceinline__ float limb(float x, int which) {
+  using O = Op<kBF16>;
+  const float h = O::round(x);
+  if (which == 0) return h;
+  const float r1 = x - h, m = O::round(r1);
+  if (which == 1) return m;
+  return O::round(r1 - m);
+}
+
 // A operand from X (P x Q complex, row-major): rows q and Q + q, K index
-// laid out [hi | hi | lo] x [Re/Im block of P]; row stride lda >= 6P.
+// laid out [segment] x [Re/Im block of P]; row stride lda >= 2 kSegs P.
 template <bool kBF16, typename C>
 __global__ void k_pack_a(const C* __restrict__ X, int P, int Q, const int* amax, typename Op<kBF16>::T* A, long long lda) {
   using O = Op<kBF16>;
+  using S = Split<kBF16>;
   const float sc = pow2_scale(amax);
   const long long tot = (long long)Q * lda;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int q = (int)(e / lda), kk = (int)(e % lda);
     float v0 = 0.f, v1 = 0.f;   // rows q (real part) and Q + q (imaginary part)
-    if (kk < 6 * P) {
+    if (kk < 2 * S::kSegs * P) {
       const int blk = kk / (2 * P), rem = kk % (2 * P), p = rem % P;
       const bool im_half = rem >= P;
       double2 x = ld_c(X, (long long)p * Q + q);
-      float xr = (float)x.x * sc, xi = (float)x.y * sc;
-      float hr = O::round(xr), hi = O::round(xi);
-      if (blk == 2) {
-        xr = O::round(xr - hr);
-        xi = O::round(xi - hi);
-      } else {
-        xr = hr;
-        xi = hi;
-      }
+      const int w = S::limb_a(blk);
+      const float xr = limb<kBF16>((float)x.x * sc, w), xi = limb<kBF16>((float)x.y * sc, w);
       // row q: [Re, -Im]; row Q + q: [Im, Re]
       v0 = im_half ? -xi : xr;
       v1 = im_half ? xr : xi;
@@ -364,11 +387,12 @@ __global__ void k_pack_a(const C* __restrict__ X, int P, int Q, const int* amax,
 }
 
 // B^T operand from S (l x P x r complex): row n = a * r + c, K index laid
-// out [hi | lo | hi] x [Re/Im block of P]; row stride ldb >= 6P.
+// out [segment] x [Re/Im block of P]; row stride ldb >= 2 kSegs P.
 template <bool kBF16, typename C>
 __global__ void k_pack_b(const C* __restrict__ S, int l, int P, int r, const int* amax, typename Op<kBF16>::T* B,
                          long long ldb) {
   using O = Op<kBF16>;
+  using Sp = Split<kBF16>;
   const float sc = pow2_scale(amax);
   const long long N = (long long)l * r;
   const long long tot = N * ldb;
@@ -376,14 +400,12 @@ __global__ void k_pack_b(const C* __restrict__ S, int l, int P, int r, const int
     const long long n = e / ldb;
     const int kk = (int)(e % ldb);
     float v = 0.f;
-    if (kk < 6 * P) {
+    if (kk < 2 * Sp::kSegs * P) {
       const int blk = kk / (2 * P), rem = kk % (2 * P), p = rem % P;
       const bool im_half = rem >= P;
       const int a = (int)(n / r), c = (int)(n % r);
       double2 x = ld_c(S, ((long long)a * P + p) * r + c);
-      float xv = (float)(im_half ? x.y : x.x) * sc;
-      float h = O::round(xv);
-      v = (blk == 1) ? O::round(xv - h) : h;
+      v = limb<kBF16>((float)(im_half ? x.y : x.x) * sc, Sp::limb_b(blk));
     }
     B[e] = O::store(v);
   }
@@ -542,19 +564,22 @@ cudaError_t init_tc_attributes() {
 }
 
 cudaError_t launch_tc_gemm(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
-                           long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s) {
+                           long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s,
+                           double algo_flops) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   const int es = bf16 ? 2 : 4;
   if ((lda * es) % 16 || (ldb * es) % 16 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15)) return cudaErrorInvalidValue;
   if (N > 64) {
-    return bf16 ? tc_launch<true, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s)
-                : tc_launch<false, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s);
+    return bf16 ? tc_launch<true, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops)
+                : tc_launch<false, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops);
   }
-  return bf16 ? tc_launch<true, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s)
-              : tc_launch<false, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s);
+  return bf16 ? tc_launch<true, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops)
+              : tc_launch<false, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops);
 }
 
 long long tc_ld(int P) { return ((6LL * P + 31) / 32) * 32; }
+// K extent of the absorb operands: 2 P reals a segment, 3 segments (TF32) or 6 (BF16)
+long long tc_absorb_ld(bool bf16, int P) { return ((2LL * (bf16 ? 6 : 3) * P + 31) / 32) * 32; }
 
 // ------------------------------------------------ general complex GEMM (c64)
 
@@ -594,12 +619,13 @@ cudaError_t tc_zpack_b(bool bf16, char opB, int K, int N, const float2* B, long 
 cudaError_t tc_zgemm_packed(bool bf16, int M, int N, int K, const void* Ap, const void* Bp, float2* Cm, long long ldc,
                             int* err, cudaStream_t s) {
   const long long ldK = tc_ld(K);
-  return launch_tc_gemm(bf16, Ap, ldK, Bp, ldK, (float*)Cm, 2 * ldc, M, 2 * N, (int)ldK, 1.0f, err, s);
+  return launch_tc_gemm(bf16, Ap, ldK, Bp, ldK, (float*)Cm, 2 * ldc, M, 2 * N, (int)ldK, 1.0f, err, s,
+                        8.0 * M * N * (double)K);
 }
 
 size_t tc_absorb_bytes(bool bf16, int P, int Q, int l, int r) {
   const size_t es = bf16 ? 2 : 4;
-  const size_t ld = (size_t)tc_ld(P);
+  const size_t ld = (size_t)tc_absorb_ld(bf16, P);
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   return al(2 * (size_t)Q * ld * es) + al((size_t)l * r * ld * es) + al(sizeof(float) * 2 * (size_t)Q * l * r) + 256;
 }
@@ -608,7 +634,7 @@ template <typename C>
 static cudaError_t tc_absorb_t(bool bf16, const C* X, int P, int Q, const C* S, int l, int r, C* R, void* work,
                                int* err, cudaStream_t s) {
   const size_t es = bf16 ? 2 : 4;
-  const long long ld = tc_ld(P);
+  const long long ld = tc_absorb_ld(bf16, P);
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   char* p = (char*)work;
   void* A = p;
@@ -630,7 +656,9 @@ static cudaError_t tc_absorb_t(bool bf16, const C* X, int P, int Q, const C* S, 
     k_pack_b<false, C><<<grid_of((long long)l * r * ld), 256, 0, s>>>(S, l, P, r, amax + 1, (float*)B, ld);
   }
   const int N = l * r;
-  if ((e = launch_tc_gemm(bf16, A, ld, B, ld, Cm, N, 2 * Q, N, (int)ld, 1.0f, err, s)) != cudaSuccess) return e;
+  if ((e = launch_tc_gemm(bf16, A, ld, B, ld, Cm, N, 2 * Q, N, (int)ld, 1.0f, err, s, 8.0 * Q * N * (double)P)) !=
+      cudaSuccess)
+    return e;
   k_unpack<C><<<grid_of((long long)l * Q * r), 256, 0, s>>>(Cm, N, Q, l, r, amax, amax + 1, R);
   return cudaGetLastError();
 }

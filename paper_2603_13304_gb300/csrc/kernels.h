@@ -109,11 +109,28 @@ struct ChainDesc {
 // 2 * 64 * 64 + 64^3 + 256 entries.  One CTA.
 cudaError_t launch_msg_normalise(const ChainDesc& m, bool c64, double2* work, cudaStream_t s);
 
+// Convergence word of an iteration: out[0] = largest of dist[0..nu), the
+// int after it = flags (1 non-finite, 2 sweep limit, 4 tensor-core timeout,
+// 8 converged: largest <= *tol and no other flag); status: 2 ints per update.
+cudaError_t launch_iter_reduce(const double* dist, const int* status, int nu, const double* tol, double* out,
+                               cudaStream_t s);
+
 // Direct-sum tensor of (new, -old) at chain position pos, in the input type.
 cudaError_t launch_direct_sum(const double2* a, int la, int ra, const double2* b, int lb, int rb, int p, int pos,
                               int k, double2* out, cudaStream_t s);
 cudaError_t launch_direct_sum(const float2* a, int la, int ra, const float2* b, int lb, int rb, int p, int pos, int k,
                               float2* out, cudaStream_t s);
+
+// a x + b y (MPS addition by the direct sum, coefficients on the first
+// tensor) at chain position pos of k; output (L, p, R) with L = lx (pos 0 or
+// k == 1) else lx + ly, R = rx (pos k - 1 or k == 1) else rx + ry.
+cudaError_t launch_mps_sum(const double2* x, int lx, int rx, const double2* y, int ly, int ry, int p, int pos, int k,
+                           double2 a, double2 b, double2* out, cudaStream_t s);
+cudaError_t launch_mps_sum(const float2* x, int lx, int rx, const float2* y, int ly, int ry, int p, int pos, int k,
+                           double2 a, double2 b, float2* out, cudaStream_t s);
+// Hermitian conjugate of a message tensor (l, D*D, r) as an operator.
+cudaError_t launch_mps_dagger(const double2* src, int l, int D, int r, double2* dst, cudaStream_t s);
+cudaError_t launch_mps_dagger(const float2* src, int l, int D, int r, float2* dst, cudaStream_t s);
 
 // *dist = ||R||_F accumulated in double.
 cudaError_t launch_frob(const double2* R, long long n, double* dist, cudaStream_t s);
@@ -127,8 +144,12 @@ cudaError_t launch_mps_dot(const ChainDesc& a, const ChainDesc& b, bool c64, dou
 // (N x K) row-major in TF32 (fp32 storage) or BF16, C fp32; *err = 1 when a
 // pipeline wait timed out.  The complex absorb R[a] = X^T S[a] runs as one
 // split-precision real GEMM (hi*hi + hi*lo + lo*hi).
+// algo_flops: the work the kernel timer credits to the launch (default the
+// real GEMM's 2 M N K; the split-precision complex products pass their
+// complex flops, 8 per complex multiply-add).
 cudaError_t launch_tc_gemm(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
-                           long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s);
+                           long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s,
+                           double algo_flops = 0.0);
 size_t tc_absorb_bytes(bool bf16, int P, int Q, int l, int r);
 cudaError_t launch_tc_absorb(bool bf16, const double2* X, int P, int Q, const double2* S, int l, int r, double2* R,
                              void* work, int* err, cudaStream_t s);

@@ -96,6 +96,7 @@ extern "C" bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int m
       std::vector<int> rcs(active.size(), 0);
       parallel_for(active.size(), [&](size_t a) {
         try {
+          ctxs[active[a]]->eng.iter_tol = tol;
           rcs[a] = ctxs[active[a]]->eng.iter_launch();
         } catch (...) {
           rcs[a] = BBP_ERR_CUDA;
@@ -189,7 +190,7 @@ int start_job(bbp_server::Job* j) {
   // the context's caller stream is the legacy one: its iterations run on
   // the context's own non-blocking streams, so jobs do not serialise on it
   const bbp_job& s = j->spec;
-  bbp_status rc = bbp_create_peps(&j->ctx, s.lattice, s.Lx, s.Ly, s.periodic, s.d, s.D, j->tensors.data(), nullptr);
+  bbp_status rc = bbp_create_peps(&j->ctx, s.lattice, s.Lx, s.Ly, s.periodic, s.d, s.D, j->tensors.data(), 0, nullptr);
   if (rc) return rc;
   if ((rc = bbp_partition_blocks(j->ctx, s.bx, s.by))) return rc;
   if ((rc = bbp_set_options(j->ctx, s.chi, s.precision, 1.0, 0))) return rc;
@@ -230,6 +231,7 @@ extern "C" size_t bbp_job_footprint_bytes(const bbp_job* job) {
 
 extern "C" bbp_status bbp_server_submit(bbp_server* s, const bbp_job* job, long long* id_out) {
   if (!s || !job || !id_out || !job->host_tensors || !job->edge_mats) return BBP_ERR_ARG;
+  if (job->tensor_dtype != 0 && job->tensor_dtype != 1) return BBP_ERR_ARG;
   if (job->Lx < 1 || job->Ly < 1 || job->d < 1 || job->D < 1 || job->chi < 1 || job->max_iter < 0 || !(job->tol >= 0.0))
     return BBP_ERR_ARG;
   try {
@@ -238,7 +240,14 @@ extern "C" bbp_status bbp_server_submit(bbp_server* s, const bbp_job* job, long 
     j->spec = *job;
     const size_t ns = (size_t)n_sites_of(job->lattice, job->Lx, job->Ly);
     const size_t D4 = (size_t)job->D * job->D * job->D * job->D;
-    j->tensors.assign(job->host_tensors, job->host_tensors + 2 * ns * job->d * D4);
+    const size_t nt = 2 * ns * job->d * D4;
+    if (job->tensor_dtype == 1) {
+      const float* f = (const float*)job->host_tensors;
+      j->tensors.assign(f, f + nt);
+    } else {
+      const double* t = (const double*)job->host_tensors;
+      j->tensors.assign(t, t + nt);
+    }
     j->edges.assign(job->edge_mats, job->edge_mats + 2 * ns * 4 * job->D * job->D);
     j->spec.host_tensors = nullptr;
     j->spec.edge_mats = nullptr;
@@ -294,6 +303,7 @@ extern "C" bbp_status bbp_server_step(bbp_server* s, double timeout_ms, int* n_q
       bbp_server::Job* j = idle[a];
       int rc;
       try {
+        j->ctx->eng.iter_tol = j->spec.tol;
         rc = j->ctx->eng.iter_launch();
       } catch (...) {
         rc = BBP_ERR_CUDA;

@@ -59,14 +59,12 @@ def kagome_ctx(D, chi, precision):
     return ctx
 
 
-def bond_energy(ctx, g1, k1):
-    return sum(P.bbp_expect_local(ctx, s2, [g1, k1]).real for s2 in (
-        np.kron(SX, SX), np.kron(SY, SY), np.kron(SZ, SZ)))
-
-
 def observables(ctx, g, bonds):
     sz = np.array([P.bbp_expect_local(ctx, SZ, [i]).real for i in range(36)])
-    be = np.array([bond_energy(ctx, b[0], b[1]) for b in bonds])
+    # three product insertions S^a (x) S^a per bond, the scheme of the
+    # oracle's bond energy (a truncated sweep is not linear in the inserted
+    # operator)
+    be = P.bbp_bond_energies(ctx, [(b[0], b[1]) for b in bonds])
     return sz, be
 
 
