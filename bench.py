@@ -574,6 +574,53 @@ def measure_peaks():
     return res
 
 
+def kernel_case(which: str):
+    """One kernel of the path alone, on the shapes of the D = 6, chi = 64
+    workload, for a profiler capture (`ncu -k ...`): `fuse` K1 at D = 8
+    (output larger than L2), `absorb` the tcgen05 split-TF32 absorb of one
+    bulk swallow (P = Q = 1296, l = r = 64), `panel` the cluster panel QR of
+    one 2304 x 96 range panel.  Each runs three times; prints the CUDA-event
+    time of the last."""
+    import torch
+    import paper_2603_13304_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    if which == "fuse":
+        D, d = 8, 2
+        t = torch.randn(d * D ** 4, dtype=torch.complex128, device="cuda", generator=g)
+        T = torch.empty(D ** 8, dtype=torch.complex128, device="cuda")
+        run = lambda: P.bbp_k_fuse(t.data_ptr(), d, D, [D] * 4, None, [0, 1, 2, 3], T.data_ptr())   # noqa: E731
+        work = f"{D ** 8 * 16 / 1e9:.3f} GB written"
+    elif which == "absorb":
+        Pd, Q, l, r = 1296, 1296, 64, 64
+        X = torch.randn(Pd, Q, dtype=torch.complex64, device="cuda", generator=g)
+        S = torch.randn(l, Pd, r, dtype=torch.complex64, device="cuda", generator=g)
+        R = torch.empty(l, Q, r, dtype=torch.complex64, device="cuda")
+        wk = torch.empty(P.bbp_k_tc_absorb_bytes(0, Pd, Q, l, r), dtype=torch.uint8, device="cuda")
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        run = lambda: P.bbp_k_tc_absorb(0, 1, X.data_ptr(), Pd, Q, S.data_ptr(), l, r, R.data_ptr(), wk.data_ptr(),   # noqa: E731
+                                        err.data_ptr())
+        work = f"{8.0 * l * Pd * Q * r / 1e9:.1f} GFLOP complex"
+    elif which == "panel":
+        m, n = 2304, 96
+        A = torch.randn(m, n, dtype=torch.complex64, device="cuda", generator=g)
+        Qm = torch.empty_like(A)
+        Rm = torch.empty(n, n, dtype=torch.complex64, device="cuda")
+        run = lambda: P.bbp_k_panel_qr(True, A.data_ptr(), m, n, Qm.data_ptr(), Rm.data_ptr(), 1, 0)   # noqa: E731
+        work = f"{m}x{n} complex64 panel, cluster {P.bbp_k_panel_cluster(True, m, n)}+"
+    else:
+        raise SystemExit("kernel case: fuse, absorb or panel")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(3):
+        if i == 2:
+            e0.record()
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": which, "ms": e0.elapsed_time(e1), "work": work}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -590,7 +637,11 @@ def main():
     ap.add_argument("--serve", type=int, default=48, help="jobs in the serving measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--peaks", action="store_true", help="measure the chip's ALU and tensor rates and exit")
+    ap.add_argument("--kernel-case", choices=["fuse", "absorb", "panel"], help="run one kernel alone and exit")
     args = ap.parse_args()
+    if args.kernel_case:
+        kernel_case(args.kernel_case)
+        return
     if args.roofline_kernel is None:
         args.roofline_kernel = "tc" if args.precision in ("tf32", "bf16") else "orth"
     if args.peaks:

@@ -1241,6 +1241,12 @@ __global__ void __launch_bounds__(1024) k_jacobi_cut64(SvdWork<float2> w, int b,
 
 // U = Q WH[top]^H (m x k) and Rem = G'[top] W^H (k x n): WH and G' of the
 // reduced SVD in complex128, Q and W in the path's element type.
+// (products in the element type: Q and W carry its accuracy; for complex64
+// the complex128 factors are rounded once, since FP64 arithmetic here would
+// cost 64x the FP32 rate and add nothing)
+template <typename C>
+__device__ __forceinline__ C as_elem(double2 v) { return cx<C>(v.x, v.y); }
+
 template <typename C>
 __global__ void k_rand_out64(const C* __restrict__ Q, int m, int b, const double2* __restrict__ WH64,
                              const double2* __restrict__ G64, const int* __restrict__ idx64, const C* __restrict__ W,
@@ -1248,16 +1254,16 @@ __global__ void k_rand_out64(const C* __restrict__ Q, int m, int b, const double
   long long totU = (long long)m * k, totR = (long long)k * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < totU + totR;
        e += (long long)gridDim.x * blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
+    C acc = cx<C>(0.0, 0.0);
     if (e < totU) {
       const int i = (int)(e / k), a = min(max(idx64[(int)(e % k)], 0), b - 1);
-      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(c128(Q[(long long)i * b + j]), cconj(WH64[(long long)a * b + j])));
-      U[e] = cx<C>(acc.x, acc.y);
+      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(Q[(long long)i * b + j], cconj(as_elem<C>(WH64[(long long)a * b + j]))));
+      U[e] = acc;
     } else {
       const long long f = e - totU;
       const int a = min(max(idx64[(int)(f / n)], 0), b - 1), c = (int)(f % n);
-      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(G64[(long long)a * b + j], cconj(c128(W[(long long)c * b + j]))));
-      Rem[f] = cx<C>(acc.x, acc.y);
+      for (int j = 0; j < b; ++j) acc = cadd(acc, cmul(as_elem<C>(G64[(long long)a * b + j]), cconj(W[(long long)c * b + j])));
+      Rem[f] = acc;
     }
   }
 }
@@ -1433,11 +1439,14 @@ size_t svd_work_bytes_c64(int m, int n, int chi, bool tensor_cores) {
   return rand_work_bytes<float2>(m, n, b) + (tensor_cores ? rand_tc_bytes(m, n, b) : 0);
 }
 
+// (the exact Jacobi only runs on splits whose smaller side is at most the
+// randomisation threshold, so its scratch is bounded at that size)
 size_t svd_work_bound_c64(int max_min, int max_max, int chi, bool tensor_cores) {
   const int b = chi + (chi >= 16 ? chi / 2 : 8);
+  const int jm = std::min(max_min, std::max(2 * b, 64));
   return std::max(rand_work_bytes<float2>(max_max, max_max, b) +
                       (tensor_cores ? rand_tc_bytes(max_max, max_max, b) : 0),
-                  jacobi_bytes<float2>(max_min, max_max) + jacobi_reduce_bytes<float2>(max_min, max_max));
+                  jacobi_bytes<float2>(jm, max_max) + jacobi_reduce_bytes<float2>(jm, max_max));
 }
 
 // complex128 (the 1e-10 parity path): b = 2 chi directions, so that the
@@ -1458,8 +1467,9 @@ size_t svd_work_bytes_rand64(int m, int n, int chi) {
 }
 
 size_t svd_work_bound_rand64(int max_min, int max_max, int chi) {
+  const int jm = std::min(max_min, std::max(4 * chi, 64));
   return std::max(rand_work_bytes<double2>(max_max, max_max, 2 * chi),
-                  jacobi_bytes<double2>(max_min, max_max) + jacobi_reduce_bytes<double2>(max_min, max_max));
+                  jacobi_bytes<double2>(jm, max_max) + jacobi_reduce_bytes<double2>(jm, max_max));
 }
 
 static size_t cut64_smem(int b, int k) {
@@ -1634,6 +1644,32 @@ __global__ void __launch_bounds__(1024) k_normalise(C* A, long long n, double* l
   } else if (threadIdx.x == 0) {
     *logscale = -INFINITY;
   }
+}
+
+// The same normalisation over many CTAs for large tensors: partial sums of
+// |A|^2 into acc (zeroed before), then every CTA scales its part by
+// 1 / sqrt(acc) and CTA 0 adds log sqrt(acc) to the log-scale.
+template <typename C>
+__global__ void __launch_bounds__(256) k_norm_sum(const C* __restrict__ A, long long n, double* acc) {
+  __shared__ double sh[40];
+  double part = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    part += cabs2d(A[e]);
+  const double s = block_sum(part, sh);
+  if (threadIdx.x == 0) atomicAdd(acc, s);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_norm_apply(C* A, long long n, const double* acc, double* logscale) {
+  const double nrm = sqrt(*acc);
+  if (!(nrm > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *logscale = -INFINITY;
+    return;
+  }
+  const double inv = 1.0 / nrm;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    A[e] = cscale(A[e], inv);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *logscale += log(nrm);
 }
 
 template <typename C>
@@ -1918,7 +1954,16 @@ __global__ void __launch_bounds__(256) k_mps_dot(ChainDesc A, ChainDesc B, doubl
 
 #define BBP_INSTANTIATE(C)                                                                                          \
   cudaError_t launch_normalise(C* A, long long n, double* logscale, cudaStream_t s) {                              \
-    k_normalise<C><<<1, 1024, 0, s>>>(A, n, logscale);                                                             \
+    if (n <= (1 << 15)) {                                                                                          \
+      k_normalise<C><<<1, 1024, 0, s>>>(A, n, logscale);                                                           \
+      return cudaGetLastError();                                                                                   \
+    }                                                                                                              \
+    /* logscale[1]: the accumulator of the many-CTA form */                                                        \
+    cudaError_t e = cudaMemsetAsync(logscale + 1, 0, sizeof(double), s);                                          \
+    if (e != cudaSuccess) return e;                                                                                \
+    const int g = (int)std::min<long long>((n + 2047) / 2048, 304);                                               \
+    k_norm_sum<C><<<g, 256, 0, s>>>(A, n, logscale + 1);                                                           \
+    k_norm_apply<C><<<g, 256, 0, s>>>(A, n, logscale + 1, logscale);                                               \
     return cudaGetLastError();                                                                                     \
   }                                                                                                                \
   cudaError_t launch_copy_tensor(const C* src, C* dst, int l, int p, int r, bool transpose, cudaStream_t s) {       \

@@ -63,28 +63,28 @@ template <typename R> __device__ __forceinline__ R wsum(R v) {
 constexpr int kPanelThreads = 512;
 
 // sum of slot[off] over the cluster's CTAs in rank order (the same grouping
-// in every CTA); remote loads are issued four at a time before their additions
+// in every CTA); remote loads are issued eight at a time before their additions
 template <typename C>
 __device__ __forceinline__ C cluster_sum(cg::cluster_group& cl, C* slot, size_t off, int cs) {
   C s = mkc<C>(0, 0);
-  for (int q0 = 0; q0 < cs; q0 += 4) {
-    C v[4];
+  for (int q0 = 0; q0 < cs; q0 += 8) {
+    C v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = (q0 + u < cs) ? cl.map_shared_rank(slot, q0 + u)[off] : mkc<C>(0, 0);
+    for (int u = 0; u < 8; ++u) v[u] = (q0 + u < cs) ? cl.map_shared_rank(slot, q0 + u)[off] : mkc<C>(0, 0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) s = padd(s, v[u]);
+    for (int u = 0; u < 8; ++u) s = padd(s, v[u]);
   }
   return s;
 }
 
 __device__ __forceinline__ double cluster_sum_d(cg::cluster_group& cl, double* slot, size_t off, int cs) {
   double s = 0.0;
-  for (int q0 = 0; q0 < cs; q0 += 4) {
-    double v[4];
+  for (int q0 = 0; q0 < cs; q0 += 8) {
+    double v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = (q0 + u < cs) ? cl.map_shared_rank(slot, q0 + u)[off] : 0.0;
+    for (int u = 0; u < 8; ++u) v[u] = (q0 + u < cs) ? cl.map_shared_rank(slot, q0 + u)[off] : 0.0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) s += v[u];
+    for (int u = 0; u < 8; ++u) s += v[u];
   }
   return s;
 }
@@ -101,10 +101,12 @@ __host__ __device__ inline size_t panel_smem(int rows, int n) {
 
 // Householder step j, with the cluster sums of step j already exchanged:
 //  gather   threads c >= j read the sums (thread j forms the reflector)
-//  pass A   the warp of column j + 1 updates it (and takes its partial norm)
-//  pass B   every warp updates its columns c > j + 1 and, in the same pass
-//           over their registers, takes the partial dots x'^H a_c of step
-//           j + 1 (x' = the updated column j + 1 below row j + 1)
+//  pass     every warp forms the updated column j + 1 in registers from
+//           the step's reflector and factor (x' = x - v f_{j+1}), updates
+//           its columns c > j + 1 and, from the same registers, takes the
+//           partial dots x'^H a_c of step j + 1; the warp of column j + 1
+//           takes its partial norm and stores it after the cluster barrier
+// (one block barrier and one cluster barrier per step).
 // Column j stays unscaled while it is read as the reflector of step j; its
 // warp scales it in the next step.  Rows of a CTA: lane l caches local rows
 // l + 32 i, i < MAXR.
@@ -212,17 +214,23 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_qr(const C* __restrict_
       double taur = 0, taui = 0, scr = 0, sci = 0, beta = alpha.x;
       const double ar = alpha.x, ai = alpha.y;
       if (!(xn2 == 0.0 && ai == 0.0)) {
+        // beta from the norm accumulated in double; the remaining
+        // parameters in the element's real type, with alpha - beta scaled by
+        // 1 / |beta| (|alpha - beta| >= |beta|), so that nothing underflows
+        using R = typename Real<C>::T;
         beta = -copysign(sqrt(ar * ar + ai * ai + xn2), ar);
-        taur = (beta - ar) / beta;
-        taui = -ai / beta;
-        const double dx = ar - beta, dy = ai, dd = dx * dx + dy * dy;
-        scr = dx / dd;
-        sci = -dy / dd;
-        // (the element type must hold sc too: complex64 columns near the
-        // bottom of the float range leave the column as it is)
-        const double smax = sizeof(typename Real<C>::T) == 4 ? 1e37 : 1e300;
+        const R b = (R)beta, a_r = (R)ar, a_i = (R)ai;
+        const R ib = (R)1 / b, sb = fabs(ib);
+        const R dx = (a_r - b) * sb, dy = a_i * sb, idd = sb / (dx * dx + dy * dy);
+        taur = (double)((b - a_r) * ib);
+        taui = (double)(-a_i * ib);
+        scr = (double)(dx * idd);
+        sci = (double)(-dy * idd);
+        // (the element type must hold sc too: columns near the bottom of its
+        // range leave the column as it is)
+        const double smax = sizeof(R) == 4 ? 1e37 : 1e300;
         if (!(isfinite(taur) && isfinite(taui) && isfinite(scr) && isfinite(sci) && isfinite(beta)) ||
-            fabs(scr) > smax || fabs(sci) > smax) {
+            fabs(scr) > smax || fabs(sci) > smax || b == (R)0) {
           taur = taui = scr = sci = 0.0;
           beta = ar;
         }
@@ -255,33 +263,33 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_qr(const C* __restrict_
       const int g = r0 + lane + 32 * i;
       v[i] = g > j ? pmul(v[i], sc) : (g == j ? mkc<C>(1, 0) : zero);
     }
-    auto update = [&](int c, C (&y)[MAXR]) {
-      const C f = active ? pmul(ctau, padd(grow[c], pmulc(sc, gdot[c]))) : zero;
-#pragma unroll
-      for (int i = 0; i < MAXR; ++i) y[i] = psub(y[i], pmul(v[i], f));
-    };
-    // pass A: column j + 1
-    if (j + 1 < n && warp == (j + 1) % nw) {
-      C y[MAXR];
-      load_col(j + 1, y);
-      update(j + 1, y);
-      store_col(j + 1, y);
-      if (j + 1 < k) {
-        const double s2 = norm_below(y, j + 1);
-        if (lane == 0) pnorm[par ^ 1] = s2;
-        put_row(y, j + 1, slot + noff + n + j + 1);
-      }
-    }
-    __syncthreads();
-    // pass B: columns c > j + 1, with the partial dots of step j + 1
+    auto fac = [&](int c) { return active ? pmul(ctau, padd(grow[c], pmulc(sc, gdot[c]))) : zero; };
+    // one pass: every warp forms the updated column j + 1 in its registers
+    // (x' = x - v f_{j+1}), updates its own columns c > j + 1 and takes the
+    // partial dots x'^H a_c of step j + 1 from the same registers; the warp
+    // of column j + 1 takes its partial norm, and stores it only after the
+    // cluster barrier, when no warp reads the old column any more
+    C xn[MAXR];
+    const bool own_next = j + 1 < n && warp == (j + 1) % nw;
     if (j + 1 < n) {
-      C xn[MAXR];
       load_col(j + 1, xn);
+      const C f1 = fac(j + 1);
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) xn[i] = psub(xn[i], pmul(v[i], f1));
+      if (own_next) {
+        if (j + 1 < k) {
+          const double s2 = norm_below(xn, j + 1);
+          if (lane == 0) pnorm[par ^ 1] = s2;
+          put_row(xn, j + 1, slot + noff + n + j + 1);
+        }
+      }
       const int c0 = j + 2 + ((warp - (j + 2)) % nw + nw) % nw;
       for (int c = c0; c < n; c += nw) {
         C y[MAXR];
         load_col(c, y);
-        update(c, y);
+        const C f = fac(c);
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i) y[i] = psub(y[i], pmul(v[i], f));
         store_col(c, y);
         if (j + 1 < k) {
           const C d = dot_below(xn, y, j + 1);
@@ -291,6 +299,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_qr(const C* __restrict_
       }
     }
     cl.sync();
+    if (own_next) store_col(j + 1, xn);  // ordered before its reads by the next step's block barrier
   }
   if (k > 0 && warp == (k - 1) % nw) {   // scale the last reflector
     C x[MAXR];

@@ -39,7 +39,14 @@ namespace bbp {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kStages = 4;
+// pipeline depth: one stage holds 4 MMAs of 128 x BN x (32 bytes of K), a
+// fraction of a microsecond of tensor work, so enough stages must be in
+// flight to cover the TMA latency from L2: 6 at BN = 128, 8 at BN = 64
+// (about 192 KB of shared memory either way)
+template <int BN> __host__ __device__ constexpr int stages_of() { return BN >= 128 ? 6 : 8; }
+// tile order: groups of kGroupM M tiles sweep the N tiles together, so that
+// a wave of CTAs reuses its A tiles from L2 instead of streaming all of B
+constexpr int kGroupM = 16;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -139,6 +146,7 @@ __global__ void __launch_bounds__(128, 1)
   constexpr int kBKe = 128 / kEs;               // K elements per stage (one 128-byte row)
   constexpr int kUmmaK = 32 / kEs;              // K elements per tcgen05.mma
   constexpr int kABytes = kBM * 128, kBBytes = BN * 128, kStageBytes = kABytes + kBBytes;
+  constexpr int kStages = stages_of<BN>();
   constexpr uint32_t kIdesc = idesc_of<kBF16, BN>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -146,7 +154,14 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM;
+  // grouped rasterisation of the linear block index
+  const int tiles_n = gridDim.x, tiles_m = gridDim.y;
+  const int pid = blockIdx.y * tiles_n + blockIdx.x;
+  const int group = pid / (kGroupM * tiles_n), first_m = group * kGroupM;
+  const int gm = min(kGroupM, tiles_m - first_m);
+  const int in_group = pid - group * kGroupM * tiles_n;
+  const int tm = first_m + in_group % gm, tn = in_group / gm;
+  const int n0 = tn * BN, m0 = tm * kBM;
   const int kt = (K + kBKe - 1) / kBKe;
 
   if (threadIdx.x == 0) {
@@ -256,7 +271,7 @@ bool make_map(CUtensorMap* m, const void* ptr, bool bf16, int rows, int cols, lo
   return r == CUDA_SUCCESS;
 }
 
-template <int BN> constexpr int tc_smem() { return kStages * (kBM + BN) * 128 + 1024; }
+template <int BN> constexpr int tc_smem() { return stages_of<BN>() * (kBM + BN) * 128 + 1024; }
 
 // Dynamic shared memory opt-in, once per kernel and device.
 template <bool kBF16, int BN>
