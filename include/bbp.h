@@ -323,8 +323,12 @@ bbp_status bbp_k_qr(double* A, int m, int n, double* Q, double* R, double* tau, 
  * real diagonal) are written when not NULL.  c64 = 1: complex64 entries,
  * 0: complex128.  cluster: CTAs per panel, 0 = automatic; otherwise at
  * least bbp_k_panel_cluster(c64, m, n) (the fewest whose shared memory holds
- * the panel; 0 when even 16 do not) and at most 16.  BBP_ERR_ARG when m < n
- * or the panel does not fit. */
+ * the panel with Q; 0 when even 16 do not) and at most 16.  A call with
+ * Q = NULL needs a little less shared memory (no reflector scalars), so it
+ * may fit where bbp_k_panel_cluster reports 0.  Each CTA caches 32, 64, ...
+ * rows per warp lane (complex64 up to 256 rows a CTA, complex128 up to 128),
+ * and a CTA beyond the rows a given cluster needs holds none.  BBP_ERR_ARG
+ * when m < n or the panel does not fit. */
 int bbp_k_panel_cluster(int c64, int m, int n);
 bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R, int batch, int cluster,
                           void* stream);

@@ -467,7 +467,7 @@ int bbp_k_panel_cluster(int c64, int m, int n) {
 bbp_status bbp_k_panel_qr(int c64, const void* A, int m, int n, void* Q, void* R, int batch, int cluster,
                           void* stream) {
   if (!A || m < 1 || n < 1 || m < n || batch < 1) return set_err(BBP_ERR_ARG, "bad arguments");
-  const int cmin = bbp_k_panel_cluster(c64, m, n);
+  const int cmin = bbp::panel_cluster(m, n, c64 ? sizeof(float2) : sizeof(double2), Q != nullptr);
   if (cmin == 0) return set_err(BBP_ERR_ARG, "panel too large for a 16-CTA cluster");
   if (cluster != 0 && (cluster < cmin || cluster > bbp::kPanelMaxCluster))
     return set_err(BBP_ERR_ARG, "cluster size out of range for this panel");

@@ -1360,7 +1360,8 @@ static cudaError_t qr_r_t(const C* A, int m, int n, C* R, C* scratch0, C* scratc
   for (int level = 0; level < 16; ++level) {
     // the stacked panel fits one CTA or one cluster: finish there
     if (TsqrSmem<C>::bytes(rows, n) <= (size_t)kSmemMax) return tsqr_launch<C>(src, rows, n, nullptr, R, rows, s);
-    if (rows >= n && panel_cluster(rows, n, sizeof(C)) > 0) return launch_panel_qr(src, rows, n, nullptr, R, 1, 0, s);
+    if (rows >= n && panel_cluster(rows, n, sizeof(C), false) > 0)
+      return launch_panel_qr(src, rows, n, nullptr, R, 1, 0, s);
     if (rb <= n) break;   // stacking row blocks would not shrink the panel
     const int nb = (rows + rb - 1) / rb;
     if ((e = tsqr_launch<C>(src, rows, n, nullptr, bufs[which], rb, s)) != cudaSuccess) return e;

@@ -1,28 +1,34 @@
 // Householder QR of tall panels on a thread-block cluster (Sec. 2.3.3: the
 // canonical moves and the orthonormalisations of the truncation).
 //
-// A panel A (m x n, m >= n, row-major) is cut into cs contiguous row slices,
-// one per CTA of a cluster of cs <= 16 CTAs; each slice stays in that CTA's
-// shared memory for the whole factorisation.  Householder step j needs three
-// sums over all rows below the diagonal: the squared norm of column j, and
-// x^H a_c for every trailing column c (x = column j below row j).  Because
-// the reflector is v = [1; x / (alpha - beta)], v^H a_c = a_jc + conj(sc)
-// x^H a_c follows from those raw sums and row j, so one cluster-wide
-// exchange per column suffices: every CTA writes its partial sums (and the
-// owner of row j writes row j) into a double-buffered slot of its shared
-// memory, the cluster synchronises once, and every CTA reads all slots
-// through distributed shared memory and forms the same reflector in the same
-// order (bitwise identical in every CTA).  Q = H_0 ... H_{k-1} [I; 0] is
-// then formed in place backwards with one exchange per reflector.
+// A panel A (m x n, m >= n, row-major) is cut into row slices of 32 MAXR
+// rows, one per CTA of a cluster of cs <= 16 CTAs; each slice stays in that
+// CTA's shared memory (column-major, zero-padded to 32 MAXR rows) for the
+// whole factorisation, and lane l of a warp caches rows l + 32 i of the
+// columns it works on.  Householder step j needs three sums over all rows
+// below the diagonal: the squared norm of column j, and x^H a_c for every
+// trailing column c (x = column j below row j).  Because the reflector is
+// v = [1; x / (alpha - beta)], v^H a_c = a_jc + conj(sc) x^H a_c follows from
+// those raw sums and row j, so one cluster-wide exchange per column
+// suffices.  The exchange is pushed: every CTA stores its partial sums (and
+// the owner of row j stores row j) straight into every CTA's receive buffer
+// in distributed shared memory before the cluster barrier, so that after it
+// every CTA reads only its own shared memory and forms the same reflector
+// from the same values in the same order (bitwise identical in every CTA).
+// Q = H_0 ... H_{k-1} [I; 0] is then formed in place backwards with one
+// exchange per reflector.
 //
 // Convention (the same as the one-CTA kernels): H = I - tau v v^H, v_j = 1,
-// R has a real diagonal beta_j, the factorisation applies H_j^H.  Norms are
-// accumulated in double in both precisions, so complex64 columns neither
-// underflow nor overflow when squared.
+// R has a real diagonal beta_j, the factorisation applies H_j^H.  Column
+// norms are exchanged as (power-of-two scale, scaled sum of squares) pairs in
+// the element's real type, so complex64 columns neither overflow nor
+// underflow when squared and the complex64 kernel does no FP64 arithmetic.
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <atomic>
+#include <cstdint>
+#include <initializer_list>
 
 #include "kernels.h"
 
@@ -36,9 +42,12 @@ template <typename C> struct Real;
 template <> struct Real<double2> { using T = double; };
 template <> struct Real<float2> { using T = float; };
 
-template <typename C> __device__ __forceinline__ C mkc(double re, double im);
-template <> __device__ __forceinline__ double2 mkc(double re, double im) { return make_double2(re, im); }
-template <> __device__ __forceinline__ float2 mkc(double re, double im) { return make_float2((float)re, (float)im); }
+template <typename C> __device__ __forceinline__ C mkc(typename Real<C>::T re, typename Real<C>::T im) {
+  C r;
+  r.x = re;
+  r.y = im;
+  return r;
+}
 
 template <typename C> __device__ __forceinline__ C pmul(C a, C b) {
   C r;
@@ -59,8 +68,417 @@ template <typename R> __device__ __forceinline__ R wsum(R v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+template <typename R> __device__ __forceinline__ R wmax(R v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// y[q] for a warp-uniform q, by bit masks (a select chain here is turned
+// into an indexed access, which puts the array in local memory)
+template <int MAXR>
+__device__ __forceinline__ float2 pick(const float2 (&y)[MAXR], int q) {
+  unsigned a = 0, b = 0;
+#pragma unroll
+  for (int i = 0; i < MAXR; ++i) {
+    const unsigned msk = q == i ? ~0u : 0u;
+    a |= msk & __float_as_uint(y[i].x);
+    b |= msk & __float_as_uint(y[i].y);
+  }
+  return make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+template <int MAXR>
+__device__ __forceinline__ double2 pick(const double2 (&y)[MAXR], int q) {
+  unsigned long long a = 0, b = 0;
+#pragma unroll
+  for (int i = 0; i < MAXR; ++i) {
+    const unsigned long long msk = q == i ? ~0ull : 0ull;
+    a |= msk & (unsigned long long)__double_as_longlong(y[i].x);
+    b |= msk & (unsigned long long)__double_as_longlong(y[i].y);
+  }
+  return make_double2(__longlong_as_double((long long)a), __longlong_as_double((long long)b));
+}
 
 constexpr int kPanelThreads = 512;
+constexpr int kPanelSmemMax = 227 * 1024;
+
+// distributed shared memory through 32-bit shared-window addresses
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t dsmem_addr(uint32_t a, int rank) {
+  uint32_t r;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_dsmem(uint32_t a, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_dsmem(uint32_t a, double2 v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+
+// Shared memory of one CTA, in elements: the slice (n columns of ld >= 32
+// MAXR entries), the receive buffers of the partial sums ([2][cs][n], by
+// step parity and source CTA), row j ([2][n]), the gathered sums (n, when
+// staged), the partial norms ([2][cs]), tau of every step (n, when Q is
+// formed) and tau, sc and the new diagonal of the last two steps.
+struct PanelLayout {
+  int ld;
+  size_t recv, rowb, gs, pp, tau, ring, bytes;
+};
+template <typename C>
+__host__ __device__ inline PanelLayout panel_layout(int maxr, int n, int cs, bool want_q, bool odd_ld, bool gs) {
+  PanelLayout L;
+  L.ld = 32 * maxr + (odd_ld ? 1 : 0);
+  size_t o = (size_t)L.ld * n;
+  L.recv = o; o += 2 * (size_t)cs * n;
+  L.rowb = o; o += 2 * (size_t)n;
+  L.gs = o; o += gs ? (size_t)n : 0;
+  L.pp = o; o += 2 * (size_t)cs;
+  L.tau = o; o += want_q ? (size_t)n : 0;
+  L.ring = o; o += 6;
+  L.bytes = sizeof(C) * o;
+  return L;
+}
+
+// Householder step j, with the partial sums of step j already received:
+//  gather   threads c > j sum the received partial dots of column c (in
+//           source order); one thread forms the reflector from the partial
+//           norms and row j
+//  pass     every warp forms the updated column j + 1 in registers from the
+//           step's reflector and factor (x' = x - v f_{j+1}), updates its
+//           columns c > j + 1 and, from the same registers, takes the
+//           partial dots x'^H a_c of step j + 1 and pushes them (and row
+//           j + 1, from its owner CTA) to every CTA; the warp of column j + 1
+//           pushes its partial norm and stores the column after the cluster
+//           barrier, when no warp reads the old one any more
+// (one block barrier and one cluster barrier per step).  Column c is always
+// worked on by warp c mod nw, so a warp's own deferred stores and later loads
+// of a column are ordered by program order.  Column j stays unscaled while it
+// is read as the reflector of step j; its warp scales it in the next step.
+template <typename C, int MAXR>
+__global__ void __launch_bounds__(kPanelThreads, 1) k_panel_qr(const C* __restrict__ Ag, int m, int n,
+                                                            C* __restrict__ Qg, C* __restrict__ Rg, long long stride,
+                                                            int ld, int use_gs) {
+  using R = typename Real<C>::T;
+  cg::cluster_group cl = cg::this_cluster();
+  const int cs = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+  const long long panel = blockIdx.x / cs;
+  Ag += panel * stride;
+  if (Qg) Qg += panel * stride;
+  if (Rg) Rg += panel * (long long)n * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PanelLayout L = panel_layout<C>(MAXR, n, cs, Qg != nullptr, (ld & 1) != 0, use_gs != 0);
+  C* A = (C*)smem_raw;                   // local row t of column c at A[c * ld + t]
+  C* recv = A + L.recv;
+  C* rowb = A + L.rowb;
+  C* gs = A + L.gs;
+  C* pp = A + L.pp;                      // (scale, scaled sum of squares)
+  C* s_tau = A + L.tau;
+  C* ring = A + L.ring;                  // [2][3]: tau, sc, diagonal
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int rows = 32 * MAXR;
+  const int r0 = cr * rows;
+  const int mr = max(0, min(rows, m - r0));
+  const int k = min(m, n);
+  const C zero = mkc<C>(0, 0), one = mkc<C>(1, 0);
+  // lane q < cs pushes to CTA q
+  const uint32_t recv_q = lane < cs ? dsmem_addr(smem_addr(recv), lane) : 0u;
+  const uint32_t rowb_q = lane < cs ? dsmem_addr(smem_addr(rowb), lane) : 0u;
+  const uint32_t pp_q = lane < cs ? dsmem_addr(smem_addr(pp), lane) : 0u;
+
+  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+    const int t = e / n, c = e % n;
+    A[(size_t)c * ld + t] = t < mr ? Ag[(long long)(r0 + t) * n + c] : zero;
+  }
+  cl.sync();                             // every CTA of the cluster runs before the first push
+
+  auto load_col = [&](int c, C (&v)[MAXR]) {
+    const C* p = A + (size_t)c * ld + lane;
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) v[i] = p[32 * i];
+  };
+  auto store_col = [&](int c, const C (&v)[MAXR]) {
+    C* p = A + (size_t)c * ld + lane;
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) p[32 * i] = v[i];
+  };
+  auto mask_below = [&](C (&x)[MAXR], int g0) {   // keep global rows > g0
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i)
+      if (r0 + lane + 32 * i <= g0) x[i] = zero;
+  };
+  auto dot = [&](const C (&x)[MAXR], const C (&y)[MAXR]) {   // sum over the slice of conj(x) y
+    C acc = pmulc(x[0], y[0]);
+#pragma unroll
+    for (int i = 1; i < MAXR; ++i) acc = padd(acc, pmulc(x[i], y[i]));
+    acc.x = wsum(acc.x);
+    acc.y = wsum(acc.y);
+    return acc;
+  };
+  // (scale, sum of squares / scale^2) of the slice; complex128: (1, sum)
+  auto norm_part = [&](const C (&x)[MAXR]) {
+    if constexpr (sizeof(R) == 8) {
+      R s2 = 0;
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) s2 += x[i].x * x[i].x + x[i].y * x[i].y;
+      return mkc<C>(1, wsum(s2));
+    } else {
+      R amax = 0;
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) amax = fmaxf(amax, fmaxf(fabsf(x[i].x), fabsf(x[i].y)));
+      amax = wmax(amax);
+      if (amax == 0) return zero;
+      int ex;
+      frexpf(amax, &ex);                 // amax < 2^ex; 2^-ex in two in-range factors
+      const R s1 = ldexpf(1.f, -(ex / 2)), s2 = ldexpf(1.f, -(ex - ex / 2));
+      R ss = 0;
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) {
+        const R a = x[i].x * s1 * s2, b = x[i].y * s1 * s2;
+        ss += a * a + b * b;
+      }
+      return mkc<C>(ldexpf(1.f, ex), wsum(ss));
+    }
+  };
+  auto push_recv = [&](int par, int c, C d) {
+    if (lane < cs) st_dsmem(recv_q + (uint32_t)(sizeof(C) * ((size_t)(par * cs + cr) * n + c)), d);
+  };
+  auto push_norm = [&](int par, C np) {
+    if (lane < cs) st_dsmem(pp_q + (uint32_t)(sizeof(C) * (size_t)(par * cs + cr)), np);
+  };
+  // row g of column values y, from the CTA that holds it, into every CTA
+  auto push_row = [&](const C (&y)[MAXR], int g, int par, int c) {
+    const int t = g - r0;
+    if (t < 0 || t >= mr) return;        // uniform over the CTA
+    C val = pick(y, t >> 5);
+    val.x = __shfl_sync(0xffffffffu, val.x, t & 31);
+    val.y = __shfl_sync(0xffffffffu, val.y, t & 31);
+    if (lane < cs) st_dsmem(rowb_q + (uint32_t)(sizeof(C) * ((size_t)par * n + c)), val);
+  };
+  auto sum_recv = [&](int par, int c) {   // the cluster sum of column c, in source order
+    C s = zero;
+    for (int q = 0; q < cs; ++q) s = padd(s, recv[(size_t)(par * cs + q) * n + c]);
+    return s;
+  };
+
+  // ---- factorisation
+  if (k > 0) {                           // sums of step 0
+    C x[MAXR];
+    load_col(0, x);
+    if (warp == 0) push_row(x, 0, 0, 0);
+    mask_below(x, 0);
+    if (warp == 0) push_norm(0, norm_part(x));
+    for (int c = warp == 0 ? nw : warp; c < n; c += nw) {
+      C y[MAXR];
+      load_col(c, y);
+      push_recv(0, c, dot(x, y));
+      push_row(y, 0, 0, c);
+    }
+  }
+  cl.sync();
+  for (int j = 0; j < k; ++j) {
+    const int par = j & 1;
+    if (use_gs)
+      for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) gs[c] = sum_recv(par, c);
+    if (threadIdx.x == blockDim.x - 1) {
+      // the reflector of step j from the norm of x and alpha = A[j][j]
+      R M = 0, S = 0;
+      for (int q = 0; q < cs; ++q) M = fmax(M, pp[par * cs + q].x);
+      if (M > 0)
+        for (int q = 0; q < cs; ++q) {
+          const C np = pp[par * cs + q];
+          const R rq = np.x / M;
+          S += np.y * rq * rq;
+        }
+      const R xnorm = M * sqrt(S);
+      const C alpha = rowb[(size_t)par * n + j];
+      const R ar = alpha.x, ai = alpha.y;
+      R taur = 0, taui = 0, scr = 0, sci = 0, beta = ar;
+      if (!(xnorm == 0 && ai == 0)) {
+        // beta = -sign(ar) |(alpha, x)| from scaled terms; alpha - beta
+        // scaled by 1 / |beta| (|alpha - beta| >= |beta|), so that nothing
+        // overflows or underflows
+        const R mx = fmax(fmax(fabs(ar), fabs(ai)), xnorm);
+        const R u = ar / mx, w = ai / mx, z = xnorm / mx;
+        beta = -copysign(mx * sqrt(u * u + w * w + z * z), ar);
+        const R ib = (R)1 / beta, sb = fabs(ib);
+        const R dx = (ar - beta) * sb, dy = ai * sb, idd = sb / (dx * dx + dy * dy);
+        taur = (beta - ar) * ib;
+        taui = -ai * ib;
+        scr = dx * idd;
+        sci = -dy * idd;
+        // (the element type must hold sc too: columns near the bottom of its
+        // range leave the column as it is)
+        const R smax = sizeof(R) == 4 ? (R)1e37 : (R)1e300;
+        if (!(isfinite(taur) && isfinite(taui) && isfinite(scr) && isfinite(sci) && isfinite(beta)) ||
+            fabs(scr) > smax || fabs(sci) > smax || beta == (R)0) {
+          taur = taui = scr = sci = 0;
+          beta = ar;
+        }
+      }
+      const bool act = !(taur == 0 && taui == 0);
+      ring[par * 3 + 0] = mkc<C>(taur, taui);
+      ring[par * 3 + 1] = mkc<C>(scr, sci);
+      ring[par * 3 + 2] = mkc<C>(beta, act ? (R)0 : ai);
+      if (Qg) s_tau[j] = mkc<C>(taur, taui);
+    }
+    __syncthreads();
+    const C tj = ring[par * 3 + 0], sc = ring[par * 3 + 1], ctau = mkc<C>(tj.x, -tj.y);
+    const bool active = !(tj.x == 0 && tj.y == 0);
+    // scale the reflector of step j - 1 (no longer read)
+    if (j > 0 && warp == (j - 1) % nw) {
+      C x[MAXR];
+      load_col(j - 1, x);
+      const C scp = ring[(par ^ 1) * 3 + 1], dg = ring[(par ^ 1) * 3 + 2];
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) {
+        const int g = r0 + lane + 32 * i;
+        if (g > j - 1) x[i] = pmul(x[i], scp);
+        else if (g == j - 1) x[i] = dg;
+      }
+      store_col(j - 1, x);
+    }
+    C v[MAXR];                           // v of step j: x sc below row j, 1 at row j
+    load_col(j, v);
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) {
+      const int g = r0 + lane + 32 * i;
+      v[i] = g > j ? pmul(v[i], sc) : (g == j ? one : zero);
+    }
+    auto fac = [&](int c) {
+      const C s = use_gs ? gs[c] : sum_recv(par, c);
+      return active ? pmul(ctau, padd(rowb[(size_t)par * n + c], pmulc(sc, s))) : zero;
+    };
+    const bool own = j + 1 < n && warp == (j + 1) % nw;
+    C xm[MAXR];                          // column j + 1 after step j, then its rows > j + 1
+    C keep_j = zero, keep_j1 = zero;     // (owner) its rows j and j + 1, in the lanes that hold them
+    if (j + 1 < n) {
+      load_col(j + 1, xm);
+      const C f1 = fac(j + 1);
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) xm[i] = psub(xm[i], pmul(v[i], f1));
+      if (own) {
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i) {
+          const int g = r0 + lane + 32 * i;
+          if (g == j) keep_j = xm[i];
+          if (g == j + 1) keep_j1 = xm[i];
+        }
+        if (j + 1 < k) push_row(xm, j + 1, par ^ 1, j + 1);
+      }
+      mask_below(xm, j + 1);
+      if (own && j + 1 < k) push_norm(par ^ 1, norm_part(xm));
+      for (int c = j + 2 + ((warp - (j + 2)) % nw + nw) % nw; c < n; c += nw) {
+        C y[MAXR];
+        load_col(c, y);
+        const C f = fac(c);
+#pragma unroll
+        for (int i = 0; i < MAXR; ++i) y[i] = psub(y[i], pmul(v[i], f));
+        store_col(c, y);
+        if (j + 1 < k) {
+          push_recv(par ^ 1, c, dot(xm, y));
+          push_row(y, j + 1, par ^ 1, c);
+        }
+      }
+    }
+    cl.sync();
+    if (own) {                           // column j + 1, rows >= j (rows above are unchanged)
+      C* p = A + (size_t)(j + 1) * ld + lane;
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) {
+        const int g = r0 + lane + 32 * i;
+        if (g > j + 1) p[32 * i] = xm[i];
+        else if (g == j + 1) p[32 * i] = keep_j1;
+        else if (g == j) p[32 * i] = keep_j;
+      }
+    }
+  }
+  if (k > 0 && warp == (k - 1) % nw) {   // scale the last reflector
+    C x[MAXR];
+    load_col(k - 1, x);
+    const C scp = ring[((k - 1) & 1) * 3 + 1], dg = ring[((k - 1) & 1) * 3 + 2];
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) {
+      const int g = r0 + lane + 32 * i;
+      if (g > k - 1) x[i] = pmul(x[i], scp);
+      else if (g == k - 1) x[i] = dg;
+    }
+    store_col(k - 1, x);
+  }
+  __syncthreads();
+
+  // R (k x n, upper triangular) from the rows this CTA holds
+  if (Rg)
+    for (int e = threadIdx.x; e < mr * n; e += blockDim.x) {
+      const int t = e / n, c = e % n, g = r0 + t;
+      if (g < k) Rg[(long long)g * n + c] = (c >= g) ? A[(size_t)c * ld + t] : zero;
+    }
+  if (!Qg) return;     // nothing is pushed after the last cluster barrier above
+
+  // ---- Q = H_0 ... H_{k-1} [I; 0], in place backwards: step i updates the
+  // columns c > i by tau_i v_i (v_i^H q_c) and sets column i to
+  // e_i - tau_i v_i (stored after the cluster barrier, when no warp reads v_i
+  // any more); the pass of step i also pushes the partial dots of step i - 1
+  // (v_{i-1} = column i - 1, untouched until its own step)
+  auto refl = [&](int i, C (&x)[MAXR]) {  // v_i from column i (scaled, 1 on row i)
+    load_col(i, x);
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const int g = r0 + lane + 32 * q;
+      x[q] = g > i ? x[q] : (g == i ? one : zero);
+    }
+  };
+  auto set_col = [&](int i, const C (&x)[MAXR], C (&y)[MAXR]) {   // e_i - tau_i v_i
+    const C ti = s_tau[i], mt = mkc<C>(-ti.x, -ti.y), d0 = mkc<C>((R)1 - ti.x, -ti.y);
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const int g = r0 + lane + 32 * q;
+      y[q] = g == i ? d0 : (g > i ? pmul(mt, x[q]) : zero);
+    }
+  };
+  C y[MAXR];                             // the owner's column i, stored after the barrier
+  if (k > 0 && warp == (k - 1) % nw) {   // column k - 1 and the sums of step k - 2
+    C x[MAXR];
+    refl(k - 1, x);
+    set_col(k - 1, x, y);
+    if (k >= 2) {
+      refl(k - 2, x);
+      push_recv(0, k - 1, dot(x, y));
+    }
+  }
+  cl.sync();
+  if (k > 0 && warp == (k - 1) % nw) store_col(k - 1, y);
+  for (int i = k - 2; i >= 0; --i) {
+    const int par = (k - 2 - i) & 1;
+    if (use_gs)
+      for (int c = i + 1 + threadIdx.x; c < k; c += blockDim.x) gs[c] = pmul(s_tau[i], sum_recv(par, c));
+    __syncthreads();
+    C x[MAXR], xp[MAXR];
+    refl(i, x);
+    if (i >= 1) refl(i - 1, xp);
+    int c0 = i + ((warp - i) % nw + nw) % nw;
+    if (c0 == i) c0 += nw;               // the owner of column i takes it last
+    for (int c = c0; c < k; c += nw) {
+      load_col(c, y);
+      const C f = use_gs ? gs[c] : pmul(s_tau[i], sum_recv(par, c));
+#pragma unroll
+      for (int q = 0; q < MAXR; ++q) y[q] = psub(y[q], pmul(x[q], f));
+      store_col(c, y);
+      if (i >= 1) push_recv(par ^ 1, c, dot(xp, y));
+    }
+    const bool own = warp == i % nw;
+    if (own) {
+      set_col(i, x, y);
+      if (i >= 1) push_recv(par ^ 1, i, dot(xp, y));
+    }
+    cl.sync();
+    if (own) store_col(i, y);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < mr * k; e += blockDim.x) {
+    const int t = e / k, c = e % k;
+    Qg[(long long)(r0 + t) * k + c] = A[(size_t)c * ld + t];
+  }
+}
 
 // sum of slot[off] over the cluster's CTAs in rank order (the same grouping
 // in every CTA); remote loads are issued eight at a time before their additions
@@ -94,11 +512,14 @@ __device__ __forceinline__ double cluster_sum_d(cg::cluster_group& cl, double* s
 // row j), the gathered factors and row, tau, sc and the new diagonal of
 // every step, and two partial norms
 template <typename C>
-__host__ __device__ inline size_t panel_smem(int rows, int n) {
+__host__ __device__ inline size_t panel_smem_pull(int rows, int n) {
   return sizeof(C) * ((size_t)(rows | 1) * n + 4 * (size_t)n + 2 * (size_t)n + 3 * (size_t)n) + 4 * sizeof(double) +
          64;
 }
 
+// The pulled form, for panels whose push buffers do not fit: every CTA
+// writes its partial sums into a double-buffered slot of its own shared
+// memory and, after the cluster barrier, reads every CTA's slot remotely.
 // Householder step j, with the cluster sums of step j already exchanged:
 //  gather   threads c >= j read the sums (thread j forms the reflector)
 //  pass     every warp forms the updated column j + 1 in registers from
@@ -111,7 +532,7 @@ __host__ __device__ inline size_t panel_smem(int rows, int n) {
 // warp scales it in the next step.  Rows of a CTA: lane l caches local rows
 // l + 32 i, i < MAXR.
 template <typename C, int MAXR>
-__global__ void __launch_bounds__(kPanelThreads) k_panel_qr(const C* __restrict__ Ag, int m, int n, int rows,
+__global__ void __launch_bounds__(kPanelThreads, 1) k_panel_qr_pull(const C* __restrict__ Ag, int m, int n, int rows,
                                                             C* __restrict__ Qg, C* __restrict__ Rg, long long stride) {
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks(), cr = (int)cl.block_rank();
@@ -400,7 +821,9 @@ __global__ void __launch_bounds__(kPanelThreads) k_panel_qr(const C* __restrict_
   }
 }
 
-constexpr int kPanelSmemMax = 211 * 1024;
+// rows a CTA caches per lane: 32 x MAXR rows per CTA
+constexpr int kMaxrF[] = {1, 2, 3, 4, 5, 6, 8};   // complex64
+constexpr int kMaxrD[] = {1, 2, 3, 4};            // complex128 (twice the registers per entry)
 
 template <typename C, int MAXR>
 cudaError_t panel_optin_one() {
@@ -417,13 +840,153 @@ cudaError_t panel_optin_one() {
   return e;
 }
 
+template <typename C, int MAXR>
+cudaError_t panel_optin_pull() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_panel_qr_pull<C, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemMax);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_panel_qr_pull<C, MAXR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 template <typename C>
 cudaError_t panel_optin() {
   cudaError_t e;
+  if ((e = panel_optin_pull<C, 2>()) != cudaSuccess) return e;
+  if ((e = panel_optin_pull<C, 4>()) != cudaSuccess) return e;
+  if constexpr (sizeof(C) == sizeof(float2))
+    if ((e = panel_optin_pull<C, 8>()) != cudaSuccess) return e;
+  if ((e = panel_optin_one<C, 1>()) != cudaSuccess) return e;
   if ((e = panel_optin_one<C, 2>()) != cudaSuccess) return e;
+  if ((e = panel_optin_one<C, 3>()) != cudaSuccess) return e;
   if ((e = panel_optin_one<C, 4>()) != cudaSuccess) return e;
-  if constexpr (sizeof(C) == sizeof(float2)) return panel_optin_one<C, 8>();
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if ((e = panel_optin_one<C, 5>()) != cudaSuccess) return e;
+    if ((e = panel_optin_one<C, 6>()) != cudaSuccess) return e;
+    return panel_optin_one<C, 8>();
+  }
   return cudaSuccess;
+}
+
+struct PanelPlan {
+  bool pull = false;
+  int maxr = 0, cs = 0, ld = 0, rows = 0;
+  bool gs = true;
+  size_t bytes = 0;
+};
+
+// the first layout that fits: odd column stride (no bank conflicts in the
+// row-major copies) with staged sums, even stride, then sums taken in place
+template <typename C>
+bool panel_fit(int n, int maxr, int cs, bool want_q, PanelPlan& p) {
+  for (int v = 0; v < 3; ++v) {
+    const PanelLayout L = panel_layout<C>(maxr, n, cs, want_q, v == 0, v < 2);
+    if (L.bytes <= (size_t)kPanelSmemMax) {
+      p.pull = false;
+      p.maxr = maxr;
+      p.cs = cs;
+      p.ld = L.ld;
+      p.rows = 32 * maxr;
+      p.gs = v < 2;
+      p.bytes = L.bytes;
+      return true;
+    }
+  }
+  return false;
+}
+
+// the pulled form: rows = ceil(m / cs) a CTA, at most 256 (complex64) or
+// 128 (complex128)
+template <typename C>
+bool panel_fit_pull(int m, int n, int cs, PanelPlan& p) {
+  const int rows = (m + cs - 1) / cs;
+  const int max_rows = sizeof(C) == sizeof(double2) ? 128 : 256;
+  if (rows > max_rows) return false;
+  const size_t b = panel_smem_pull<C>(rows, n);
+  if (b > (size_t)kPanelSmemMax) return false;
+  p.pull = true;
+  p.maxr = rows <= 64 ? 2 : (rows <= 128 ? 4 : 8);
+  p.cs = cs;
+  p.rows = rows;
+  p.ld = rows | 1;
+  p.bytes = b;
+  return true;
+}
+
+template <typename C>
+void maxr_list(const int*& list, int& nl) {
+  if (sizeof(C) == sizeof(float2)) {
+    list = kMaxrF;
+    nl = (int)(sizeof(kMaxrF) / sizeof(int));
+  } else {
+    list = kMaxrD;
+    nl = (int)(sizeof(kMaxrD) / sizeof(int));
+  }
+}
+
+// Launch plan of an m x n panel.  A given cluster size takes the fewest rows
+// per CTA that cover m; otherwise the fewest rows per CTA whose cluster has
+// at most 9 CTAs (complex64: two such clusters share one GPC's SMs, so
+// concurrent panels of different streams still place; the complex128 kernel
+// is bound by the FP64 rate of its SMs and spreads over up to 16), else up
+// to 16 CTAs.  Panels whose push buffers do not fit take the pulled form.
+template <typename C>
+bool panel_plan(int m, int n, bool want_q, int cluster, PanelPlan& p) {
+  if (m < n || n < 1) return false;
+  const int* list;
+  int nl;
+  maxr_list<C>(list, nl);
+  if (cluster > 0) {
+    if (cluster > kPanelMaxCluster) return false;
+    const int need = ((m + cluster - 1) / cluster + 31) / 32;
+    for (int a = 0; a < nl; ++a)
+      if (list[a] >= need) {
+        if (panel_fit<C>(n, list[a], cluster, want_q, p)) return true;
+        break;
+      }
+    return panel_fit_pull<C>(m, n, cluster, p);
+  }
+  const int pref = sizeof(C) == sizeof(float2) ? 9 : kPanelMaxCluster;
+  for (int lim : {pref, kPanelMaxCluster})
+    for (int a = 0; a < nl; ++a) {
+      const int cs = (m + 32 * list[a] - 1) / (32 * list[a]);
+      if (cs <= lim && panel_fit<C>(n, list[a], cs, want_q, p)) return true;
+    }
+  // pulled: the fewest CTAs that fit, raised to about 256 (complex64) or
+  // 64 (complex128) rows a CTA
+  for (int cs = 1; cs <= kPanelMaxCluster; ++cs)
+    if (panel_fit_pull<C>(m, n, cs, p)) {
+      const int target = sizeof(C) == sizeof(float2) ? 256 : 64;
+      const int want = std::min(kPanelMaxCluster, std::max(cs, (m + target - 1) / target));
+      return panel_fit_pull<C>(m, n, want, p) || panel_fit_pull<C>(m, n, cs, p);
+    }
+  return false;
+}
+
+template <typename C>
+int panel_min_cluster(int m, int n, bool want_q) {
+  if (m < n || n < 1) return 0;
+  const int* list;
+  int nl;
+  maxr_list<C>(list, nl);
+  int best = 0;
+  PanelPlan p;
+  for (int a = nl - 1; a >= 0; --a) {
+    const int cs = (m + 32 * list[a] - 1) / (32 * list[a]);
+    if (cs <= kPanelMaxCluster && panel_fit<C>(n, list[a], cs, want_q, p) && (best == 0 || cs < best)) best = cs;
+  }
+  for (int cs = 1; cs <= kPanelMaxCluster && (best == 0 || cs < best); ++cs)
+    if (panel_fit_pull<C>(m, n, cs, p)) {
+      best = cs;
+      break;
+    }
+  return best;
 }
 
 }  // namespace
@@ -434,58 +997,60 @@ cudaError_t init_panel_attributes() {
   return panel_optin<double2>();
 }
 
-// Rows of one CTA are cached 32 x MAXR in registers: at most 256 (complex64)
-// or 128 (complex128, twice the registers per entry) per CTA.
-static int panel_max_rows(size_t elem) { return elem == sizeof(double2) ? 128 : 256; }
-
-int panel_cluster(int m, int n, size_t elem) {
-  if (m < n || n < 1) return 0;
-  for (int cs = 1; cs <= kPanelMaxCluster; ++cs) {
-    const int rows = (m + cs - 1) / cs;
-    const size_t b = elem == sizeof(double2) ? panel_smem<double2>(rows, n) : panel_smem<float2>(rows, n);
-    if (rows <= panel_max_rows(elem) && b <= (size_t)kPanelSmemMax) return cs;
-  }
-  return 0;
+int panel_cluster(int m, int n, size_t elem, bool want_q) {
+  return elem == sizeof(double2) ? panel_min_cluster<double2>(m, n, want_q) : panel_min_cluster<float2>(m, n, want_q);
 }
 
-// Cluster size of a launch: the smallest that fits, raised so that no CTA
-// holds more than kPanelRowsTarget rows (the per-column work of a CTA is its
-// row slice times the trailing width; the exchange costs grow with the
-// cluster).
-int panel_cluster_auto(int m, int n, size_t elem) {
-  const int cmin = panel_cluster(m, n, elem);
-  if (cmin == 0) return 0;
-  const int want = (m + kPanelRowsTarget - 1) / kPanelRowsTarget;
-  return std::max(cmin, std::min(want, kPanelMaxCluster));
+int panel_cluster_auto(int m, int n, size_t elem, bool want_q) {
+  PanelPlan p;
+  const bool ok = elem == sizeof(double2) ? panel_plan<double2>(m, n, want_q, 0, p)
+                                          : panel_plan<float2>(m, n, want_q, 0, p);
+  return ok ? p.cs : 0;
 }
 
 template <typename C>
 static cudaError_t panel_t(const C* A, int m, int n, C* Q, C* R, int batch, long long stride, cudaStream_t s,
                            int cluster) {
   if (batch < 1 || m < 1 || n < 1) return cudaSuccess;
-  const int cmin = panel_cluster(m, n, sizeof(C));
-  if (cmin == 0 || cluster > kPanelMaxCluster || (cluster > 0 && cluster < cmin)) return cudaErrorInvalidValue;
-  const int cs = cluster > 0 ? cluster : panel_cluster_auto(m, n, sizeof(C));
+  PanelPlan p;
+  if (!panel_plan<C>(m, n, Q != nullptr, cluster, p)) return cudaErrorInvalidValue;
   cudaError_t e = panel_optin<C>();
   if (e != cudaSuccess) return e;
-  const int rows = (m + cs - 1) / cs;
   KTimerScope timer(KC_ORTH, s, batch * qr_flops(m, n));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cs * batch, 1, 1);
+  cfg.gridDim = dim3(p.cs * batch, 1, 1);
   cfg.blockDim = dim3(kPanelThreads, 1, 1);
-  cfg.dynamicSmemBytes = panel_smem<C>(rows, n);
+  cfg.dynamicSmemBytes = p.bytes;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.x = p.cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (rows <= 64) return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 2>, A, m, n, rows, Q, R, stride);
-  if (rows <= 128) return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 4>, A, m, n, rows, Q, R, stride);
+  if (p.pull) {
+    if (p.maxr == 2) return cudaLaunchKernelEx(&cfg, k_panel_qr_pull<C, 2>, A, m, n, p.rows, Q, R, stride);
+    if (p.maxr == 4) return cudaLaunchKernelEx(&cfg, k_panel_qr_pull<C, 4>, A, m, n, p.rows, Q, R, stride);
+    if constexpr (sizeof(C) == sizeof(float2))
+      if (p.maxr == 8) return cudaLaunchKernelEx(&cfg, k_panel_qr_pull<C, 8>, A, m, n, p.rows, Q, R, stride);
+    return cudaErrorInvalidValue;
+  }
+  const int gsf = p.gs ? 1 : 0;
+  switch (p.maxr) {
+    case 1: return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 1>, A, m, n, Q, R, stride, p.ld, gsf);
+    case 2: return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 2>, A, m, n, Q, R, stride, p.ld, gsf);
+    case 3: return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 3>, A, m, n, Q, R, stride, p.ld, gsf);
+    case 4: return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 4>, A, m, n, Q, R, stride, p.ld, gsf);
+    default: break;
+  }
   if constexpr (sizeof(C) == sizeof(float2)) {
-    if (rows <= 256) return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 8>, A, m, n, rows, Q, R, stride);
+    switch (p.maxr) {
+      case 5: return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 5>, A, m, n, Q, R, stride, p.ld, gsf);
+      case 6: return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 6>, A, m, n, Q, R, stride, p.ld, gsf);
+      case 8: return cudaLaunchKernelEx(&cfg, k_panel_qr<C, 8>, A, m, n, Q, R, stride, p.ld, gsf);
+      default: break;
+    }
   }
   return cudaErrorInvalidValue;
 }

@@ -207,14 +207,14 @@ inline double qr_flops(int m, int n) {
 // (k_panel.cu): A (m x n, m >= n, row-major, not modified) = Q (m x n) R
 // (n x n, upper triangular, real diagonal); Q or R may be null.  Q may alias
 // A.  batch panels at a stride of `stride` elements (R at n * n).
-// panel_cluster: the cluster size used for an m x n panel of elem-byte
-// entries (0 when it does not fit 16 CTAs' shared memory).
-// cluster = 0 picks panel_cluster_auto; a given size must be at least
+// panel_cluster: the fewest CTAs whose shared memory holds an m x n panel of
+// elem-byte entries (with the reflector scalars Q needs when want_q; 0 when
+// even 16 do not); panel_cluster_auto: the cluster size of an automatic
+// launch.  cluster = 0 picks it; a given size must be at least
 // panel_cluster(m, n, elem) and at most kPanelMaxCluster.
 constexpr int kPanelMaxCluster = 16;
-constexpr int kPanelRowsTarget = 256;
-int panel_cluster(int m, int n, size_t elem);
-int panel_cluster_auto(int m, int n, size_t elem);
+int panel_cluster(int m, int n, size_t elem, bool want_q = true);
+int panel_cluster_auto(int m, int n, size_t elem, bool want_q = true);
 cudaError_t init_panel_attributes();
 cudaError_t launch_panel_qr(const float2* A, int m, int n, float2* Q, float2* R, int batch, long long stride,
                             cudaStream_t s, int cluster = 0);

@@ -49,16 +49,29 @@ SHAPES = [(512, 48), (2304, 96), (2300, 96), (517, 50), (1024, 64), (3072, 128),
 @pytest.mark.parametrize("c64", [True, False])
 @pytest.mark.parametrize("m,n", SHAPES)
 def test_panel_qr(c64, m, n):
-    if P.bbp_k_panel_cluster(c64, m, n) == 0:
-        pytest.skip("panel does not fit a 16-CTA cluster in this precision")
     rng = np.random.default_rng(m * 7 + n)
     # columns with a geometric spread of scales (1 .. 1e-6): rank revealing work
     A = crandn(rng, m, n) * np.logspace(0, -6, n)[None, :]
     if c64:
         A = A.astype(np.complex64).astype(np.complex128)
+    eps = 1e-6 if c64 else 1e-14
+    if P.bbp_k_panel_cluster(c64, m, n) == 0:
+        # the R factor alone (the direct-sum distances) needs less shared
+        # memory than Q and R: R^H R = A^H A, upper triangular, real diagonal
+        try:
+            _, R = run_panel(A, c64, with_q=False)
+        except P.BBPError:
+            pytest.skip("panel does not fit a 16-CTA cluster in this precision")
+        R = R[0]
+        assert np.abs(np.tril(R, -1)).max() == 0.0
+        assert np.abs(np.diag(R).imag).max() == 0.0
+        G = A.conj().T @ A
+        gram = np.abs(R.conj().T @ R - G).max() / np.abs(G).max()
+        print(f"panel {m}x{n} c64={c64} R only: |R^H R - A^H A| / max|A^H A| {gram:.2e}")
+        assert gram < 30 * eps * np.sqrt(m)
+        return
     Q, R = run_panel(A, c64)
     Q, R = Q[0], R[0]
-    eps = 1e-6 if c64 else 1e-14
     assert np.abs(np.tril(R, -1)).max() == 0.0
     assert np.abs(np.diag(R).imag).max() == 0.0
     orth = np.abs(Q.conj().T @ Q - np.eye(n)).max()
@@ -67,9 +80,11 @@ def test_panel_qr(c64, m, n):
           f"|QR - A|/|A| {rec:.2e}")
     assert orth < 30 * eps * np.sqrt(m)
     assert rec < 30 * eps * np.sqrt(m)
-    # R alone equals the R of the full call (same arithmetic)
+    # R alone: the same factorisation (bitwise when both calls take the same
+    # launch plan; a panel whose Q does not fit the pushed form takes the
+    # pulled one, which groups the cross-CTA sums differently)
     _, R2 = run_panel(A, c64, with_q=False)
-    assert np.array_equal(R2[0], R)
+    assert np.abs(R2[0] - R).max() <= 1e3 * eps * np.abs(R).max()
 
 
 @pytest.mark.parametrize("c64", [True, False])
