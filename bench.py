@@ -331,6 +331,129 @@ def run_ours(args, rank, world):
 
 # -------------------------------------------------- many networks, serving
 
+def network_mix(n, seed):
+    """The batched mix: n independent networks, each square (open 2b x 2b
+    lattice cut into four b x b blocks, b uniform in 2..4) or Kagome (the
+    periodic 3L x L super-cell cut into three L x L blocks of 3 L^2 sites, L
+    uniform in 2..4) with equal odds; D uniform in 2..6, chi uniform in
+    {8, 16, 32, 64}; complex64 site tensors, i.i.d. complex Gaussian (seeded)
+    normalised by their largest singular value."""
+    import numpy as np
+    import synthetic as syn
+    import paper_2603_13304_gb300 as P
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for _ in range(n):
+        kagome = bool(rng.integers(2))
+        size = int(rng.integers(2, 5))
+        D = int(rng.integers(2, 7))
+        chi = int(rng.choice([8, 16, 32, 64]))
+        s = int(rng.integers(1 << 30))
+        if kagome:
+            Lx, Ly, bx = 3 * size, size, size
+            n_sites = 3 * Lx * Ly
+            jobs.append(dict(lattice=P.KAGOME, Lx=Lx, Ly=Ly, periodic=1, bx=bx, by=bx, D=D, chi=chi,
+                             kind=f"kagome L={size}"))
+        else:
+            Lx = Ly = 2 * size
+            n_sites = Lx * Ly
+            jobs.append(dict(lattice=P.SQUARE, Lx=Lx, Ly=Ly, periodic=0, bx=size, by=size, D=D, chi=chi,
+                             kind=f"square {size}x{size} blocks"))
+        jobs[-1]["t"] = syn.gaussian_peps(n_sites, 2, D, seed=s).astype(np.complex64)
+        jobs[-1]["em"] = syn.initial_edge_matrices(n_sites, D, seed=s + 1)
+    return jobs
+
+
+def make_network(P, j, precision, streams, fuse_cache=None):
+    c = P.bbp_create_peps(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["t"])
+    P.bbp_partition_blocks(c, j["bx"], j["by"])
+    if fuse_cache is not None:
+        P.bbp_set_fuse_cache(c, fuse_cache)
+    P.bbp_set_options(c, j["chi"], precision)
+    P.bbp_set_execution(c, True, streams)
+    P.bbp_init_messages(c, j["em"])
+    return c
+
+
+def run_batched(n_networks, steps, warmup, precision, seed=4):
+    """One synchronous iteration of every one of n_networks independent
+    networks per round (bbp_batch_iterate: the replayed iterations of a round
+    go out as one graph launch), with the tensor-core tiles autotuned on the
+    shapes recorded while the bond dimensions settle; beside it the same
+    networks one at a time (bbp_iterate on a sample of every 8th network)."""
+    import torch
+    import paper_2603_13304_gb300 as P
+    t0 = time.perf_counter()
+    jobs = network_mix(n_networks, seed)
+    # every site fused right before its absorb (nothing cached), 2 worker
+    # streams a network; networks are added while 24 GB of HBM stay free
+    ctxs = []
+    for j in jobs:
+        if torch.cuda.mem_get_info()[0] < 24e9:
+            break
+        ctxs.append(make_network(P, j, precision, 2, fuse_cache=0))
+    jobs = jobs[:len(ctxs)]
+    n_networks = len(ctxs)
+    n_updates = sum(P.bbp_info(c)[1] for c in ctxs)
+    setup_s = time.perf_counter() - t0
+    P.bbp_autotune_record(True)
+    prev = None
+    settle = 0
+    for settle in range(1, 9):         # until the work of every network stops changing
+        rc, _, _, st = P.bbp_batch_iterate(ctxs, 0.0, 1)
+        cur = [P.bbp_stats(c) for c in ctxs]
+        if cur == prev:
+            break
+        prev = cur
+    P.bbp_autotune_record(False)
+    t1 = time.perf_counter()
+    tuned = P.bbp_autotune_run()
+    tune_s = time.perf_counter() - t1
+    for _ in range(warmup):            # recapture with the tuned tiles, build the round's graph
+        P.bbp_batch_iterate(ctxs, 0.0, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.perf_counter()
+    e0.record()
+    for _ in range(steps):
+        rc, _, _, st = P.bbp_batch_iterate(ctxs, 0.0, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    host = time.perf_counter() - h0
+    secs = max(e0.elapsed_time(e1) * 1e-3, host)
+    failed = int(sum(1 for x in st if x not in (0, 6)))
+    # one network at a time, on every 8th network (each settled and captured)
+    sample = list(range(0, n_networks, 8))
+    seq_updates, seq_secs = 0, 0.0
+    for i in sample:
+        P.bbp_iterate(ctxs[i], 0.0, 1)     # (instantiates its own graph)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        P.bbp_iterate(ctxs[i], 0.0, 1)
+        torch.cuda.synchronize()
+        seq_secs += time.perf_counter() - a
+        seq_updates += P.bbp_info(ctxs[i])[1]
+    used = torch.cuda.mem_get_info()
+    for c in ctxs:
+        P.bbp_destroy(c)
+    P.bbp_autotune_clear()
+    kinds = {}
+    for j in jobs:
+        kinds[j["kind"]] = kinds.get(j["kind"], 0) + 1
+    return {"networks": n_networks, "message_updates_per_round": n_updates, "rounds": steps,
+            "value": n_updates * steps / secs, "unit": "message updates/s", "ms_per_round": 1e3 * secs / steps,
+            "launch": "one graph launch per round (every network's iteration graph a child)",
+            "failed_networks": failed, "settle_rounds": settle, "autotuned_shapes": tuned,
+            "autotune_s": round(tune_s, 2), "setup_s": round(setup_s, 2),
+            "chi_below_D2_fraction": sum(1 for j in jobs if j["chi"] < j["D"] ** 2) / n_networks,
+            "hbm_used_gb": round((used[1] - used[0]) / 1e9, 1),
+            "one_at_a_time": {"value": seq_updates / seq_secs, "unit": "message updates/s",
+                              "sample": f"bbp_iterate on {len(sample)} networks (every 8th), one iteration each"},
+            "mix": ("square 2b x 2b open (b x b blocks, b 2..4) and Kagome 3L x L (L x L blocks, L 2..4); D 2..6, "
+                    f"chi 8/16/32/64; complex64 Gaussian tensors; seed {seed}; 2 streams per network"),
+            "kinds": kinds}
+
+
 def job_mix(n, seed, precision, max_D=4, chis=(8, 16, 32)):
     """A seeded mix of small BlockBP problems: square 4x4 (2x2 blocks) and
     6x6 (3x3 blocks) open lattices with i.i.d. Gaussian tensors normalised
@@ -364,101 +487,161 @@ def job_mix(n, seed, precision, max_D=4, chis=(8, 16, 32)):
     return jobs
 
 
-def run_batched(n_networks, steps, warmup, precision):
-    """All message updates of n_networks independent networks, one
-    synchronous iteration of every network per round (bbp_batch_iterate)."""
-    import torch
+def serving_pool(n, seed):
+    """Job templates of the serving stream: the batched network mix plus 10 %
+    Kagome D = 6, chi = 64 jobs (the 6 x 2 super-cell, L = 2, a random
+    dimer-singlet state plus 1e-2 noise, complex64)."""
+    import numpy as np
+    import synthetic as syn
     import paper_2603_13304_gb300 as P
-    jobs = job_mix(n_networks, 4, precision)
-    ctxs = []
-    n_updates = 0
-    for j in jobs:
-        c = P.bbp_create_peps(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["t"])
-        P.bbp_partition_blocks(c, j["bx"], j["by"])
-        P.bbp_set_options(c, j["chi"], precision)
-        P.bbp_set_execution(c, True, 2)
-        P.bbp_init_messages(c, j["em"])
-        n_updates += P.bbp_info(c)[1]
-        ctxs.append(c)
-    for _ in range(warmup + 4):          # settle the bond dimensions, capture the graphs
-        P.bbp_batch_iterate(ctxs, 0.0, 1)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    e0.record()
-    for _ in range(steps):
-        P.bbp_batch_iterate(ctxs, 0.0, 1)
-    e1.record()
-    torch.cuda.synchronize()
-    host = time.perf_counter() - t0
-    secs = e0.elapsed_time(e1) * 1e-3
-    for c in ctxs:
-        P.bbp_destroy(c)
-    return {"networks": n_networks, "message_updates_per_round": n_updates, "rounds": steps,
-            "value": n_updates * steps / max(secs, host), "unit": "message updates/s",
-            "ms_per_round": 1e3 * max(secs, host) / steps,
-            "mix": "square 4x4 (2x2 blocks) / 6x6 (3x3 blocks), Kagome 6x2 (L=2); D 2..4, chi 8/16/32; seed 4"}
+    rng = np.random.default_rng(seed)
+    base = network_mix(n, seed)
+    pool = []
+    for j in base:
+        if rng.random() < 0.1:
+            s = int(rng.integers(1 << 30))
+            nb = syn.kagome_neighbours(6, 2)
+            t = syn.dimer_singlet_peps(nb, 2, 6, seed=s, noise=1e-2, noise_seed=s + 1).astype(np.complex64)
+            j = dict(lattice=P.KAGOME, Lx=6, Ly=2, periodic=1, bx=2, by=2, D=6, chi=64, t=t,
+                     em=syn.initial_edge_matrices(36, 6, seed=s + 2), kind="kagome L=2 D=6 chi=64")
+        pool.append(j)
+    return pool
 
 
-def run_serving(n_jobs, rate, precision, tol=1e-6, max_iter=40):
-    """Poisson arrivals (seed 5) of a job mix into the server; each job runs
-    to tol; returns throughput and latency percentiles, and the same trace
-    run one job at a time (bbp_iterate on each in arrival order)."""
+def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, drain_s=None, pool_n=16, seed=5,
+                fp64_sample=8):
+    """Poisson arrivals (seed `seed`) at `rate` jobs/s for warm_s + duration_s
+    seconds of job templates drawn from serving_pool; each job runs to `tol`
+    or `max_iter` iterations on the continuous-batching server (messages
+    resident, admission by HBM footprint).  Latency is reported for jobs
+    that arrive after the warm-up and finish within drain_s of the last
+    arrival; the rest are counted as unfinished.  Beside it: one job at a
+    time in FP64, as a FIFO queue over the same arrival trace whose service
+    times are measured per template (FP64 time per iteration x the
+    iterations the template needed when served), and the energy error of
+    served jobs against FP64 runs of the same template to the same stopping
+    rule, on `fp64_sample` templates."""
     import numpy as np
     import torch
     import paper_2603_13304_gb300 as P
-    jobs = job_mix(n_jobs, 5, precision, max_D=3, chis=(8, 16))
-    rng = np.random.default_rng(5)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
-    srv = P.bbp_server_create(200 << 30, 64)
-    lat, waits, iters, stat = {}, {}, {}, {}
+    pool = serving_pool(pool_n, seed)
+    rng = np.random.default_rng(seed)
+    horizon = warm_s + duration_s
+    arrivals = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > horizon:
+            break
+        arrivals.append((t, int(rng.integers(pool_n))))
+    jobs_spec = [P.make_job(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["bx"], j["by"], j["chi"],
+                            precision, j["t"], j["em"], tol, max_iter, 2, 1) for j in pool]
+    free, _ = torch.cuda.mem_get_info()
+    srv = P.bbp_server_create(int(free * 0.8), 256)
+    lat, iters, stat, sub = {}, {}, {}, {}
+    energy = {}
     t0 = time.perf_counter()
     nxt = 0
     ids = {}
-    while len(lat) < n_jobs:
+    served_e = {}
+    if drain_s is None:
+        drain_s = min(120.0, 2.0 * duration_s + 30.0)
+    deadline = horizon + drain_s
+    while True:
         now = time.perf_counter() - t0
-        while nxt < n_jobs and arrivals[nxt] <= now:
-            j = jobs[nxt]
-            job = P.make_job(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["bx"], j["by"], j["chi"],
-                             precision, j["t"], j["em"], tol, max_iter, 2, 1)
-            ids[P.bbp_server_submit(srv, job)] = nxt
+        while nxt < len(arrivals) and arrivals[nxt][0] <= now:
+            ids[P.bbp_server_submit(srv, jobs_spec[arrivals[nxt][1]])] = nxt
             nxt += 1
-        P.bbp_server_step(srv, 2.0)
+        q, a, f = P.bbp_server_step(srv, 2.0)
         for r in P.bbp_server_poll(srv):
             k = ids[r["id"]]
-            lat[k], waits[k], iters[k], stat[k] = r["latency_s"], r["wait_s"], r["iters"], r["status"]
-            P.bbp_server_take(srv, r["id"])
+            lat[k], iters[k], stat[k] = r["latency_s"], r["iters"], r["status"]
+            tpl = arrivals[k][1]
+            if tpl not in served_e and r["status"] in (0, 6):
+                ctx = P.bbp_server_take(srv, r["id"], keep_context=True)
+                served_e[tpl] = (P.bbp_energy_per_site(ctx), r["iters"])
+                P.bbp_destroy(ctx)
+            else:
+                P.bbp_server_take(srv, r["id"])
+        if nxt >= len(arrivals) and (len(lat) == len(arrivals) or now > deadline):
+            break
     wall = time.perf_counter() - t0
     P.bbp_server_destroy(srv)
-    # the same trace, one job at a time
-    t1 = time.perf_counter()
-    seq_lat = []
-    clock = 0.0
-    for k, j in enumerate(jobs):
-        start = max(clock, arrivals[k])
-        s0 = time.perf_counter()
-        c = P.bbp_create_peps(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["t"])
-        P.bbp_partition_blocks(c, j["bx"], j["by"])
-        P.bbp_set_options(c, j["chi"], precision)
-        P.bbp_init_messages(c, j["em"])
+    measured = [k for k in range(len(arrivals)) if arrivals[k][0] >= warm_s]
+    done = [k for k in measured if k in lat]
+    # unfinished jobs enter the percentiles with their age at the end of the
+    # run (a lower bound of their latency)
+    L = np.array([lat[k] if k in lat else wall - arrivals[k][0] for k in measured]) if measured else np.zeros(1)
+    conv = sum(1 for k in done if stat[k] == 0)
+    # FP64 one at a time: service time per template, FIFO over the same trace
+    prec64 = 0
+    svc = {}
+    e64 = {}
+    tpl_iters = {}
+    for k in done:
+        tpl_iters.setdefault(arrivals[k][1], iters[k])
+    sample = sorted(served_e)[:fp64_sample]
+    for tpl in sorted(set(a[1] for a in arrivals)):
+        j = pool[tpl]
+        c = make_network(P, j, prec64, 16)
+        per_it = float("nan")
         try:
-            P.bbp_iterate(c, tol, max_iter)
+            # iterations until the work settles (the bond dimensions grow
+            # from the initial messages), the last one timed; at most 5, and
+            # none after 20 s (the last time then bounds the settled one
+            # from below)
+            prev = None
+            spent = 0.0
+            for _ in range(5):
+                if spent > 20.0:
+                    break
+                torch.cuda.synchronize()
+                a0 = time.perf_counter()
+                P.bbp_iterate(c, 0.0, 1)
+                torch.cuda.synchronize()
+                per_it = time.perf_counter() - a0
+                spent += per_it
+                cur = P.bbp_stats(c)
+                if cur == prev:
+                    break
+                prev = cur
         except P.BBPError:
             pass
-        torch.cuda.synchronize()
         P.bbp_destroy(c)
-        clock = start + (time.perf_counter() - s0)
-        seq_lat.append(clock - arrivals[k])
-    seq_wall = time.perf_counter() - t1
-    L = np.array([lat[k] for k in range(n_jobs)])
-    S = np.array(seq_lat)
-    return {"jobs": n_jobs, "arrival_rate_per_s": rate, "tol": tol, "max_iter": max_iter,
-            "throughput_jobs_per_s": n_jobs / wall, "p50_ms": 1e3 * float(np.percentile(L, 50)),
-            "p99_ms": 1e3 * float(np.percentile(L, 99)), "mean_iters": float(np.mean([iters[k] for k in iters])),
-            "converged": int(sum(1 for k in stat if stat[k] == 0)),
-            "one_at_a_time": {"throughput_jobs_per_s": n_jobs / seq_wall, "p50_ms": 1e3 * float(np.percentile(S, 50)),
-                              "p99_ms": 1e3 * float(np.percentile(S, 99))},
-            "mix": "square 4x4 / 6x6, Kagome 6x2; D 2..3, chi 8/16; seed 5; 2 streams per job"}
+        svc[tpl] = per_it * tpl_iters.get(tpl, max_iter)
+        if tpl in sample and served_e[tpl][1] <= 40 and per_it * served_e[tpl][1] < 60.0:
+            c = make_network(P, j, prec64, 16)
+            try:
+                P.bbp_iterate(c, tol, served_e[tpl][1])
+            except P.BBPError:
+                pass
+            e64[tpl] = abs(P.bbp_energy_per_site(c) - served_e[tpl][0])
+            P.bbp_destroy(c)
+    clock, seq = 0.0, []
+    for k, (ta, tpl) in enumerate(arrivals):
+        start = max(clock, ta)
+        clock = start + svc[tpl]
+        if ta >= warm_s:
+            seq.append(clock - ta)
+    S = np.array(seq) if seq else np.zeros(1)
+    window = [k for k in done if arrivals[k][0] <= horizon]
+    return {"arrival_rate_per_s": rate, "warmup_s": warm_s, "duration_s": duration_s, "tol": tol,
+            "max_iter": max_iter, "jobs_arrived": len(measured), "jobs_finished": len(done),
+            "jobs_unfinished": len(measured) - len(done), "converged": conv,
+            "throughput_jobs_per_s": len(done) / max(1e-9, wall - warm_s),
+            "p50_ms": 1e3 * float(np.percentile(L, 50)), "p99_ms": 1e3 * float(np.percentile(L, 99)),
+            "latency_note": "over every job arriving after the warm-up; unfinished ones at their age when the run ended",
+            "mean_iters": float(np.mean([iters[k] for k in done])) if done else None,
+            "wall_s": round(wall, 1), "drain_s": drain_s,
+            "energy_err_vs_fp64": {"max": max(e64.values()) if e64 else None, "templates": len(e64),
+                                   "within_1e-5": sum(1 for v in e64.values() if v <= 1e-5)},
+            "one_at_a_time_fp64": {"p50_ms": 1e3 * float(np.percentile(S, 50)),
+                                   "p99_ms": 1e3 * float(np.percentile(S, 99)),
+                                   "throughput_jobs_per_s": len(arrivals) / clock if clock > 0 else None,
+                                   "method": "FIFO over the same arrivals; service = FP64 s/iteration x the "
+                                             "template's served iterations (measured per template)"},
+            "pool": f"{pool_n} templates (network_mix + 10% Kagome D=6 chi=64), seed {seed}; 2 streams per job",
+            "window_finished": len(window)}
 
 
 # ---------------------------------------------------------------- oracle
@@ -633,8 +816,13 @@ def main():
     ap.add_argument("--roofline-kernel", default=None, choices=sorted(KERNELS),
                     help="kernel class timed for the roofline (default: tc for tf32/bf16, else orth)")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--batch", type=int, default=64, help="networks in the batched measurement (0: skip)")
-    ap.add_argument("--serve", type=int, default=48, help="jobs in the serving measurement (0: skip)")
+    ap.add_argument("--batch", type=int, default=32, help="networks in the batched measurement (0: skip)")
+    ap.add_argument("--batch-rounds", type=int, default=2, help="timed rounds of the batched measurement")
+    ap.add_argument("--serve", type=float, default=3.0,
+                    help="seconds of arrivals after the warm-up in the serving measurement (0: skip)")
+    ap.add_argument("--serve-pool", type=int, default=16, help="job templates of the serving stream")
+    ap.add_argument("--only", choices=["batched", "serving"],
+                    help="run only the batched or the serving measurement and print it")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--peaks", action="store_true", help="measure the chip's ALU and tensor rates and exit")
     ap.add_argument("--kernel-case", choices=["fuse", "absorb", "panel"], help="run one kernel alone and exit")
@@ -646,6 +834,20 @@ def main():
         args.roofline_kernel = "tc" if args.precision in ("tf32", "bf16") else "orth"
     if args.peaks:
         print(json.dumps(measure_peaks()))
+        return
+    if args.only:
+        import torch
+        import paper_2603_13304_gb300 as P
+        torch.cuda.set_device(0)
+        P.build()
+        P.use_torch_allocator()
+        prec_code = {"tf32": 1, "bf16": 2, "fp32": 3, "fp64": 0}[args.precision]
+        if args.only == "batched":
+            out = run_batched(args.batch, args.batch_rounds, 1, prec_code)
+        else:
+            out = run_serving(args.serve, args.serve_rate, prec_code, warm_s=min(5.0, args.serve / 4),
+                              pool_n=args.serve_pool)
+        print(json.dumps({args.only: out}))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -698,15 +900,18 @@ def main():
         cpu = {"value": 1.0 / dt, "unit": "message updates/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"one complete message update at full bond ({dt:.1f} s of CPU work)"}
     prec_code = {"tf32": 1, "bf16": 2, "fp32": 3, "fp64": 0}[args.precision]
-    batched = run_batched(args.batch, args.steps, args.warmup, prec_code) if args.batch > 0 and world == 1 else None
-    serving = run_serving(args.serve, args.serve_rate, prec_code) if args.serve > 0 and world == 1 else None
+    batched = (run_batched(args.batch, args.batch_rounds, 1, prec_code)
+               if args.batch > 0 and world == 1 else None)
+    serving = (run_serving(args.serve, args.serve_rate, prec_code, warm_s=min(5.0, args.serve / 4),
+                           pool_n=args.serve_pool)
+               if args.serve > 0 and world == 1 else None)
     line = {
         "metric": "BlockBP message updates/s", "value": res["value"], "unit": "message updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * res["secs"] / args.steps, "host_ms_per_step": 1e3 * res["host_secs"] / args.steps,
         "step_ms": [round(x, 3) for x in res["step_ms"]],
         "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "c128", "fp32": "c64+f64", "tf32": "tf32x3+c64+f64", "bf16": "bf16x3+c64+f64"}[args.precision], "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp64": "c128", "fp32": "c64+f64", "tf32": "tf32x3+c64+f64", "bf16": "bf16x6+c64+f64"}[args.precision], "data": "synthetic",
         "config": dict(config, precision=args.precision,
                        execution="eager launches" if args.no_graphs else "CUDA-graph replay of each iteration",
                        streams=16),

@@ -135,6 +135,13 @@ bbp_status bbp_set_power_iters(bbp_ctx* ctx, int power_iters);
  * replays it while shapes and buffers stay the same; 0 launches eagerly. */
 bbp_status bbp_set_execution(bbp_ctx* ctx, int use_graphs, int max_streams);
 
+/* The fused double-layer site tensors (K1, D^8 entries each, one per site
+ * and sweep direction) are kept on the device while they take at most
+ * max_bytes together (default 2 GiB); above it every site is fused into the
+ * sweep's scratch right before its absorb, each iteration, and nothing is
+ * kept.  Results are the same either way. */
+bbp_status bbp_set_fuse_cache(bbp_ctx* ctx, size_t max_bytes);
+
 /* Initial messages (Alg. 1, "random MPS"): every incoming message becomes a
  * bond-1 MPS whose leg j carries the D x D matrix edge_mats[s][k] of the
  * receiving site s and its slot k.  edge_mats: complex128 [n_sites][4][D][D].
@@ -216,12 +223,18 @@ void bbp_destroy(bbp_ctx* ctx);
  * ------------------------------------------------------------------- */
 
 /* Iterate n contexts together: each round launches one synchronous
- * iteration of every context that has not converged (each on its own
- * streams, so they overlap on the device) and then reads all their errors;
- * a context leaves when its error <= tol or it fails.  Per context:
- * iterations done, final error and status (BBP_NOT_CONVERGED after
- * max_iter rounds).  Returns BBP_OK, BBP_NOT_CONVERGED, or the first
- * failure among the contexts. */
+ * iteration of every context that has not converged and then reads all
+ * their errors; a context leaves when its error <= tol or it fails.  The
+ * contexts whose iteration replays a captured graph (all of them once their
+ * bond dimensions have settled) go to the device as ONE graph launch per
+ * round, every context's iteration graph a child node of it (independent, so
+ * they overlap on the device); the others launch eagerly on their own
+ * streams.  Per context: iterations done, final error and status
+ * (BBP_NOT_CONVERGED after max_iter rounds).  Returns BBP_OK,
+ * BBP_NOT_CONVERGED, or the first failure among the contexts.
+ * bbp_batch_single_launch(0) launches every context's graph separately
+ * instead (the default is 1). */
+bbp_status bbp_batch_single_launch(int on);
 bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int max_iter, int* iters_out, double* err_out,
                              int* status_out);
 
@@ -359,6 +372,32 @@ bbp_status bbp_k_svd_trunc_rand(int c64, const void* Z, int m, int n, int chi, v
  * int set to 1 when a pipeline wait timed out (never cleared). */
 bbp_status bbp_k_tc_gemm(int bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C, long long ldc,
                          int M, int N, int K, float alpha, int* err, void* stream);
+/* The same GEMM with an explicit tile: bn (output columns of a CTA: 64,
+ * 128 or 256) and group_m >= 1 (M tiles that sweep the N tiles together).
+ * bbp_k_tc_gemm takes the autotuner's tile for its shape, else the size rule
+ * (bn 128 above N = 64, else 64; group_m 16). */
+bbp_status bbp_k_tc_gemm_tile(int bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
+                              long long ldc, int M, int N, int K, float alpha, int bn, int group_m, int* err,
+                              void* stream);
+
+/* Tile autotuner of the tensor-core GEMM (process-wide; thread-safe).
+ * bbp_autotune_record(1) collects the shape (precision, M, N, K) of every
+ * later tensor-core GEMM launch that has no table entry, for example during
+ * an eager first iteration; bbp_autotune_run times every candidate tile of
+ * each collected shape on scratch operands it allocates (synchronously, on
+ * its own stream; not inside a graph capture), keeps the fastest, sets
+ * *n_tuned, and writes the whole table to cache_path when it is not NULL
+ * (one line "tc bf16 M N K bn group_m microseconds" per shape).
+ * bbp_autotune_load merges a table written that way (*n_loaded entries).
+ * Every table change advances a generation that the contexts' captured
+ * iteration graphs check, so later iterations re-capture with the new tiles.
+ * Tiles change only the order of the work, never the arithmetic of an
+ * output element. */
+bbp_status bbp_autotune_record(int on);
+bbp_status bbp_autotune_run(const char* cache_path, int* n_tuned);
+bbp_status bbp_autotune_load(const char* cache_path, int* n_loaded);
+bbp_status bbp_autotune_info(int* n_entries, int* n_pending, unsigned long long* generation);
+bbp_status bbp_autotune_clear(void);
 
 /* The absorb contraction of Sec. 2.3.3 on the tensor cores:
  * R[a] (Q x r) = X^T (Q x P) S[a] (P x r) for a < l, complex, row-major,

@@ -30,7 +30,9 @@ EXPORTS = [
     "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_panel_cluster", "bbp_k_panel_qr", "bbp_k_svd_work_bytes_rand", "bbp_k_svd_trunc_rand", "bbp_k_fma_peak", "bbp_set_hermitise", "bbp_expect_product", "bbp_bond_energies", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
     "bbp_batch_iterate", "bbp_server_create", "bbp_job_footprint_bytes", "bbp_server_submit", "bbp_server_step",
     "bbp_server_poll", "bbp_server_take", "bbp_server_destroy", "bbp_ktimer_select", "bbp_ktimer_read",
-    "bbp_k_tc_absorb_bytes", "bbp_k_tc_absorb", "bbp_plan_debug",
+    "bbp_k_tc_absorb_bytes", "bbp_k_tc_absorb", "bbp_plan_debug", "bbp_k_tc_gemm_tile", "bbp_autotune_record",
+    "bbp_autotune_run", "bbp_autotune_load", "bbp_autotune_info", "bbp_autotune_clear", "bbp_batch_single_launch",
+    "bbp_set_fuse_cache",
 ]
 
 
@@ -96,6 +98,15 @@ _PROTOS = {
     "bbp_ktimer_select": (None, [_i]),
     "bbp_ktimer_read": (_i, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)]),
+    "bbp_k_tc_gemm_tile": (_i, [_i, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _i, _i,
+                                _i, ctypes.c_float, _i, _i, _vp, _vp]),
+    "bbp_autotune_record": (_i, [_i]),
+    "bbp_batch_single_launch": (_i, [_i]),
+    "bbp_set_fuse_cache": (_i, [_vp, ctypes.c_size_t]),
+    "bbp_autotune_run": (_i, [ctypes.c_char_p, _ip]),
+    "bbp_autotune_load": (_i, [ctypes.c_char_p, _ip]),
+    "bbp_autotune_info": (_i, [_ip, _ip, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "bbp_autotune_clear": (_i, []),
     "bbp_k_tc_gemm": (_i, [_i, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _i, _i, _i,
                            ctypes.c_float, _vp, _vp]),
     "bbp_k_tc_absorb_bytes": (ctypes.c_size_t, [_i, _i, _i, _i, _i]),
@@ -387,6 +398,48 @@ def bbp_k_tc_gemm(bf16: bool, A, lda: int, Bt, ldb: int, C, ldc: int, M: int, N:
                   stream=None):
     _check(lib().bbp_k_tc_gemm(int(bf16), _devptr(A), lda, _devptr(Bt), ldb, _devptr(C), ldc, M, N, K, alpha,
                                _devptr(err), _stream(stream)))
+
+
+def bbp_k_tc_gemm_tile(bf16: bool, A, lda: int, Bt, ldb: int, C, ldc: int, M: int, N: int, K: int, alpha: float,
+                       bn: int, group_m: int, err, stream=None):
+    _check(lib().bbp_k_tc_gemm_tile(int(bf16), _devptr(A), lda, _devptr(Bt), ldb, _devptr(C), ldc, M, N, K, alpha,
+                                    bn, group_m, _devptr(err), _stream(stream)))
+
+
+def bbp_set_fuse_cache(ctx, max_bytes: int):
+    _check(lib().bbp_set_fuse_cache(ctx, int(max_bytes)), ctx)
+
+
+def bbp_batch_single_launch(on: bool):
+    _check(lib().bbp_batch_single_launch(int(on)))
+
+
+def bbp_autotune_record(on: bool):
+    _check(lib().bbp_autotune_record(int(on)))
+
+
+def bbp_autotune_run(cache_path: str = None) -> int:
+    """Tunes the recorded tensor-core GEMM shapes; returns how many."""
+    n = ctypes.c_int(0)
+    _check(lib().bbp_autotune_run(cache_path.encode() if cache_path else None, ctypes.byref(n)))
+    return n.value
+
+
+def bbp_autotune_load(cache_path: str) -> int:
+    n = ctypes.c_int(0)
+    _check(lib().bbp_autotune_load(cache_path.encode(), ctypes.byref(n)))
+    return n.value
+
+
+def bbp_autotune_info():
+    """(table entries, recorded shapes not yet tuned, generation)"""
+    e, p, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_ulonglong(0)
+    _check(lib().bbp_autotune_info(ctypes.byref(e), ctypes.byref(p), ctypes.byref(g)))
+    return e.value, p.value, g.value
+
+
+def bbp_autotune_clear():
+    _check(lib().bbp_autotune_clear())
 
 
 def bbp_k_tc_absorb_bytes(bf16: bool, P: int, Q: int, l: int, r: int) -> int:

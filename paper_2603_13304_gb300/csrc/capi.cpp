@@ -131,6 +131,14 @@ bbp_status bbp_set_execution(bbp_ctx* ctx, int use_graphs, int max_streams) {
   return BBP_OK;
 }
 
+bbp_status bbp_set_fuse_cache(bbp_ctx* ctx, size_t max_bytes) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  ctx->eng.drop_graphs();
+  ctx->eng.fuse_cache_max = max_bytes;
+  if (ctx->eng.fuse_on_the_fly()) ctx->eng.fused.clear();
+  return BBP_OK;
+}
+
 bbp_status bbp_init_messages(bbp_ctx* ctx, const double* edge_mats) {
   if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
   return guarded([&] { return from(ctx, ctx->eng.init_messages(edge_mats)); });
@@ -443,6 +451,50 @@ bbp_status bbp_k_tc_gemm(int bf16, const void* A, long long lda, const void* Bt,
     return set_err(BBP_ERR_ARG, "bad arguments");
   return cuda_status(bbp::launch_tc_gemm(bf16 != 0, A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err,
                                          (cudaStream_t)stream));
+}
+
+bbp_status bbp_k_tc_gemm_tile(int bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
+                              long long ldc, int M, int N, int K, float alpha, int bn, int group_m, int* err,
+                              void* stream) {
+  if (!A || !Bt || !C || !err || M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N || group_m < 1 ||
+      (bn != 64 && bn != 128 && bn != 256))
+    return set_err(BBP_ERR_ARG, "bad arguments");
+  if (cudaError_t ae = bbp::init_kernel_attributes()) return cuda_status(ae);
+  return cuda_status(bbp::launch_tc_gemm_tile(bf16 != 0, A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err,
+                                              (cudaStream_t)stream, bn, group_m));
+}
+
+bbp_status bbp_autotune_record(int on) {
+  bbp::tc_autotune_record(on != 0);
+  return BBP_OK;
+}
+
+bbp_status bbp_autotune_run(const char* cache_path, int* n_tuned) {
+  int n = 0;
+  const cudaError_t e = bbp::tc_autotune(cache_path, &n);
+  if (n_tuned) *n_tuned = n;
+  if (e == cudaErrorInvalidValue) return set_err(BBP_ERR_ARG, "the tile cache could not be written");
+  if (e == cudaErrorLaunchTimeout) return set_err(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+  return cuda_status(e);
+}
+
+bbp_status bbp_autotune_load(const char* cache_path, int* n_loaded) {
+  if (!cache_path) return set_err(BBP_ERR_ARG, "bad arguments");
+  const int n = bbp::tc_autotune_load(cache_path);
+  if (n_loaded) *n_loaded = n < 0 ? 0 : n;
+  if (n < 0) return set_err(BBP_ERR_ARG, "the tile cache could not be read");
+  return BBP_OK;
+}
+
+bbp_status bbp_autotune_info(int* n_entries, int* n_pending, unsigned long long* generation) {
+  bbp::tc_autotune_info(n_entries, n_pending);
+  if (generation) *generation = bbp::tc_tune_generation();
+  return BBP_OK;
+}
+
+bbp_status bbp_autotune_clear(void) {
+  bbp::tc_autotune_clear();
+  return BBP_OK;
 }
 
 size_t bbp_k_tc_absorb_bytes(int bf16, int P, int Q, int l, int r) {

@@ -4,6 +4,7 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -183,9 +184,43 @@ bool SweepWork::reserve(size_t el, size_t ct, size_t cs, size_t cx, size_t sb, s
 void Engine::drop_graphs() {
   for (int p = 0; p < 2; ++p) {
     if (graphs[p].exec) cudaGraphExecDestroy(graphs[p].exec);
+    if (graphs[p].graph) cudaGraphDestroy(graphs[p].graph);
     graphs[p] = IterGraph();
     ktimer_drop_tag(graph_tag(p));
   }
+}
+
+namespace {
+std::atomic<unsigned long long> g_uid{1};
+}
+
+bool Engine::deferred(Deferred& d) const {
+  if (!in_flight || !pending_launch) return false;
+  const IterGraph& g = graphs[launched_parity];
+  const int nu = (int)geom.updates().size();
+  double* tol_dev = (double*)((char*)dist_dev.p + ((sizeof(double) * nu + 2 * sizeof(int) * nu + 255) & ~size_t(255)));
+  d.graph = g.graph;
+  d.uid = g.uid;
+  d.tol_dev = tol_dev;
+  d.word_dev = tol_dev + 4;
+  d.host_word = h_word;
+  return g.graph != nullptr;
+}
+
+int Engine::defer_before(cudaStream_t batch) {
+  DeviceScope ds(device);
+  if (!root_pre) CK(cudaEventCreateWithFlags(&root_pre, cudaEventDisableTiming));
+  CK(cudaEventRecord(root_pre, root));
+  CK(cudaStreamWaitEvent(batch, root_pre, 0));
+  return 0;
+}
+
+int Engine::defer_after(cudaStream_t batch) {
+  DeviceScope ds(device);
+  CK(cudaEventRecord(root_out, batch));
+  CK(cudaStreamWaitEvent(root, root_out, 0));
+  pending_launch = false;
+  return 0;
 }
 
 // FNV-1a over everything a captured iteration bakes in: job tensors and
@@ -200,6 +235,7 @@ unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int
   };
   auto mixs = [&](const TShape& t) { mix((unsigned long long)t.l); mix((unsigned long long)t.p); mix((unsigned long long)t.r); };
   mix((unsigned long long)precision);
+  mix(tc_tune_generation());           // the tensor-core tiles the launches take
   mix((unsigned long long)chi);
   mix((unsigned long long)power_iters);
   mix((unsigned long long)power_iters64);
@@ -215,6 +251,7 @@ unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int
   for (const SweepJob& j : jobs) {
     mix((unsigned long long)(uintptr_t)j.plan);
     for (const void* p : j.node_tensor) mix((unsigned long long)(uintptr_t)p);
+    for (const auto& f : j.node_fuse) mix((unsigned long long)(f[0] + 1) * 256 + f[1] * 64 + f[2] * 16 + f[3] * 4 + f[4]);
     for (const TShape& t : j.node_shape) mixs(t);
     for (const void* p : j.start) mix((unsigned long long)(uintptr_t)p);
     for (const TShape& t : j.start_shape) mixs(t);
@@ -237,6 +274,7 @@ unsigned long long Engine::input_signature(int nstreams) const {
   };
   mix((unsigned long long)precision);
   mix((unsigned long long)tc_mode);
+  mix(tc_tune_generation());
   mix((unsigned long long)chi);
   mix((unsigned long long)power_iters);
   mix((unsigned long long)power_iters64);
@@ -273,6 +311,7 @@ Engine::~Engine() {
   if (root_in) cudaEventDestroy(root_in);
   if (root_in2) cudaEventDestroy(root_in2);
   if (root_out) cudaEventDestroy(root_out);
+  if (root_pre) cudaEventDestroy(root_pre);
   if (h_word) cudaFreeHost(h_word);
   for (SweepWork* w : pool) {
     if (w->stream) cudaStreamSynchronize(w->stream);
@@ -302,6 +341,7 @@ int Engine::create(int lattice, int Lx, int Ly, int periodic, int d_, int D_, co
   d = d_;
   D = D_;
   stream = s;
+  uid_ = g_uid.fetch_add(1);
   if (cudaGetDevice(&device) != cudaSuccess) return fail(this, 3, "no current CUDA device");
   geom.lat.kind = lattice;
   geom.lat.Lx = Lx;
@@ -364,6 +404,19 @@ int Engine::set_precision(int p) {
   if (p != precision) fused.clear();
   precision = p;
   return 0;
+}
+
+// Whether the fused double-layer tensors of every site and sweep direction
+// (at most four orders a site) would take more than fuse_cache_max; then
+// each is fused (K1) into the sweep's scratch right before its absorb.
+bool Engine::fuse_on_the_fly() const {
+  size_t tot = 0;
+  for (const auto& nn : site_n) {
+    size_t e = 1;
+    for (int q = 0; q < 4; ++q) e *= (size_t)nn[q] * nn[q];
+    tot += 4 * e * elem();
+  }
+  return tot > fuse_cache_max;
 }
 
 template <typename C>
@@ -629,6 +682,7 @@ int Engine::fill_job(const Region& R, const SweepPlan& plan, SweepJob& job, cons
   job.plan = &plan;
   LegDims dims;
   job.node_tensor.assign(plan.nodes.size(), nullptr);
+  job.node_fuse.assign(plan.nodes.size(), std::array<int, 5>{-1, 0, 0, 0, 0});
   job.node_shape.assign(plan.nodes.size(), TShape());
   dims.node_dims.resize(plan.nodes.size());
   for (size_t s = 0; s < plan.nodes.size(); ++s) {
@@ -652,6 +706,9 @@ int Engine::fill_job(const Region& R, const SweepPlan& plan, SweepJob& job, cons
         const double2* t = (const double2*)t_dev.p + (size_t)n.gid * d * D * D * D * D;
         CK(launch_fuse(t, d, D, nn.data(), (const double2*)op, perm, (C*)b->p, stream));
         job.node_tensor[s] = b->p;
+      } else if (fuse_on_the_fly()) {
+        job.node_tensor[s] = nullptr;  // fused into the sweep's scratch right before its absorb
+        job.node_fuse[s] = {n.gid, perm[0], perm[1], perm[2], perm[3]};
       } else {
         job.node_tensor[s] = fused_tensor<C>(n.gid, perm);
         if (!job.node_tensor[s]) return fail(this, 2, "fusion failed");
@@ -681,8 +738,15 @@ int Engine::fill_job(const Region& R, const SweepPlan& plan, SweepJob& job, cons
 void Engine::job_needs(const SweepJob& job, size_t need[7]) const {
   const ShapeTrace& tr = job.tr;
   size_t cap_x = 1;
-  for (size_t q = 0; q < job.plan->nodes.size(); ++q)
+  for (size_t q = 0; q < job.plan->nodes.size(); ++q) {
     if (!job.plan->nodes[q].site) cap_x = std::max(cap_x, (size_t)job.node_shape[q].size());
+    else if (job.node_fuse[q][0] >= 0) {
+      const auto& nn = site_n[job.node_fuse[q][0]];
+      size_t tot = 1;
+      for (int k = 0; k < 4; ++k) tot *= (size_t)nn[k] * nn[k];
+      cap_x = std::max(cap_x, tot);
+    }
+  }
   const int mr = (int)std::max<long long>(tr.max_svd_rows, 1), mc = (int)std::max<long long>(tr.max_svd_cols, 1);
   need[0] = std::max<size_t>(need[0], (size_t)tr.max_tensor);
   need[1] = std::max<size_t>(need[1], (size_t)std::max(tr.max_seg, tr.max_tensor));
@@ -842,7 +906,14 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
     if (P != rec.P) return fail(this, 8, "sweep: merged dimension disagrees with the plan");
     // contraction R[a, Q, b] = sum_P X[P, Q] S[a, P, b]
     const C* X = (const C*)job.node_tensor[st.node];
-    if (!node.site) {
+    if (node.site && !X) {             // K1 into the scratch, right before its use
+      const auto& f = job.node_fuse[st.node];
+      const double2* t = (const double2*)t_dev.p + (size_t)f[0] * d * D * D * D * D;
+      const int perm[4] = {f[1], f[2], f[3], f[4]};
+      CK(launch_fuse(t, d, D, site_n[f[0]].data(), nullptr, perm, (C*)w.X, s));
+      X = (const C*)w.X;
+      ++launches;
+    } else if (!node.site) {
       const TShape ms = job.node_shape[st.node];
       int perm[3];
       for (int q = 0; q < st.nin; ++q) perm[q] = st.in_leg[q];
@@ -1021,18 +1092,29 @@ int Engine::iter_launch_t() {
     // replay without rebuilding the jobs when nothing the graph reads changed
     const int par = 1 - msgs.at({ups[0].recv_block, ups[0].recv_face}).cur;
     IterGraph& g = graphs[par];
-    if (g.exec && g.in_sig == input_signature(nstreams) && (int)g.out_shapes.size() == nu) {
+    if (g.graph && g.in_sig == input_signature(nstreams) && (int)g.out_shapes.size() == nu) {
       for (int u = 0; u < nu; ++u) msgs.at({ups[u].recv_block, ups[u].recv_face}).sh[par] = g.out_shapes[u];
       h_word[0] = iter_tol;
-      CK(cudaMemcpyAsync(tol_dev, h_word, sizeof(double), cudaMemcpyHostToDevice, root));
-      CK(cudaGraphLaunch(g.exec, root));
       sweep_launches = g.launches;
       sweep_flops = g.flops;
-      CK(cudaMemcpyAsync(h_word + 1, word_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, root));
-      CK(cudaEventRecord(root_out, root));
       launched_parity = par;
       launched_graph = true;
       in_flight = true;
+      if (defer_graph) {
+        pending_launch = true;
+        return 0;
+      }
+      if (!g.exec) {
+        const cudaError_t ce = cudaGraphInstantiate(&g.exec, g.graph, 0);
+        if (ce != cudaSuccess) {
+          in_flight = false;
+          return fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
+        }
+      }
+      CK(cudaMemcpyAsync(tol_dev, h_word, sizeof(double), cudaMemcpyHostToDevice, root));
+      CK(cudaGraphLaunch(g.exec, root));
+      CK(cudaMemcpyAsync(h_word + 1, word_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, root));
+      CK(cudaEventRecord(root_out, root));
       return 0;
     }
   }
@@ -1096,18 +1178,20 @@ int Engine::iter_launch_t() {
   // grow (the first iterations from bond-1 messages) every iteration would
   // need a new graph, and instantiating it costs more than launching eagerly
   h_word[0] = iter_tol;
-  CK(cudaMemcpyAsync(tol_dev, h_word, sizeof(double), cudaMemcpyHostToDevice, root));
   const bool stable = in_sig == last_in_sig[parity];
   last_in_sig[parity] = in_sig;
-  const bool replayable = graphs[parity].exec && graphs[parity].sig == iter_signature(jobs, nstreams);
+  const bool replayable = graphs[parity].graph && graphs[parity].sig == iter_signature(jobs, nstreams);
   launched_graph = use_graphs && (stable || replayable);
+  if (!launched_graph || !defer_graph)
+    CK(cudaMemcpyAsync(tol_dev, h_word, sizeof(double), cudaMemcpyHostToDevice, root));
   if (!launched_graph) {
     rc = enqueue();
   } else {
     IterGraph& g = graphs[parity];
     const unsigned long long sig = iter_signature(jobs, nstreams);
-    if (!g.exec || g.sig != sig) {
+    if (!g.graph || g.sig != sig) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
       g = IterGraph();
       const long long tag = graph_tag(parity);
       ktimer_drop_tag(tag);
@@ -1122,15 +1206,18 @@ int Engine::iter_launch_t() {
       ce = cudaStreamEndCapture(root, &graph);
       ktimer_set_tag(-1);
       if (!e && ce != cudaSuccess) e = fail(this, 3, std::string("graph capture: ") + cudaGetErrorString(ce));
-      if (!e) {
+      if (!e && !defer_graph) {
         ce = cudaGraphInstantiate(&g.exec, graph, 0);
         if (ce != cudaSuccess) e = fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
       }
-      if (graph) cudaGraphDestroy(graph);
       if (e) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (graph) cudaGraphDestroy(graph);
         g = IterGraph();
         return e;
       }
+      g.graph = graph;
+      g.uid = g_uid.fetch_add(1);
       g.sig = sig;
       g.launches = sweep_launches;
       g.flops = sweep_flops;
@@ -1138,10 +1225,20 @@ int Engine::iter_launch_t() {
     g.in_sig = in_sig;
     g.out_shapes.resize(nu);
     for (int u = 0; u < nu; ++u) g.out_shapes[u] = msgs.at({ups[u].recv_block, ups[u].recv_face}).sh[parity];
-    cudaError_t le = cudaGraphLaunch(g.exec, root);
-    if (le != cudaSuccess) return fail(this, 3, std::string("graph launch: ") + cudaGetErrorString(le));
     sweep_launches = g.launches;
     sweep_flops = g.flops;
+    if (defer_graph) {
+      launched_parity = parity;
+      in_flight = true;
+      pending_launch = true;
+      return 0;
+    }
+    if (!g.exec) {
+      const cudaError_t ce = cudaGraphInstantiate(&g.exec, g.graph, 0);
+      if (ce != cudaSuccess) return fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
+    }
+    cudaError_t le = cudaGraphLaunch(g.exec, root);
+    if (le != cudaSuccess) return fail(this, 3, std::string("graph launch: ") + cudaGetErrorString(le));
   }
   if (rc) return rc;
   CK(cudaMemcpyAsync(h_word + 1, word_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, root));
@@ -1160,6 +1257,11 @@ int Engine::iter_finish(double* err_out) {
     return 0;
   }
   if (!in_flight) return fail(this, 8, "no iteration in flight");
+  if (pending_launch) {
+    in_flight = false;
+    pending_launch = false;
+    return fail(this, 8, "a deferred iteration was never launched");
+  }
   in_flight = false;
   CK(cudaEventSynchronize(root_out));
   if (ktimer_class()) ktimer_collect(launched_graph ? graph_tag(launched_parity) : -1);

@@ -78,6 +78,7 @@ struct SweepJob {
   const SweepPlan* plan = nullptr;
   ShapeTrace tr;
   std::vector<const void*> node_tensor;      // site: fused T permuted (in..., out...); message: raw (l, p, r)
+  std::vector<std::array<int, 5>> node_fuse; // site fused on the fly (node_tensor null): gid, perm[4]
   std::vector<TShape> node_shape;            // message nodes: tensor shape
   std::vector<const void*> start;            // start chain tensors, canonical orientation
   std::vector<TShape> start_shape;           // their shapes (canonical orientation)
@@ -96,6 +97,7 @@ class Engine {
   int tc_mode = 0;                     // absorb contraction: 0 SIMT GEMM, 1 tcgen05 TF32 split, 2 tcgen05 BF16 split
   bool use_graphs = true;              // replay a captured CUDA graph per iteration
   int max_streams = 16;                // sweep jobs run on up to this many streams
+  size_t fuse_cache_max = size_t(2) << 30;   // fused site tensors kept when they take at most this; else fused per use
   cudaStream_t stream = nullptr;
   int device = -1;                     // device current at create(); every iteration call runs on it
   bool partitioned = false;
@@ -116,6 +118,7 @@ class Engine {
 
   ~Engine();
   size_t elem() const { return precision == 0 ? sizeof(double2) : sizeof(float2); }
+  bool fuse_on_the_fly() const;
   int create(int lattice, int Lx, int Ly, int periodic, int d, int D, const double* host_t, cudaStream_t s);
   int partition(int bx, int by);
   int set_precision(int p);
@@ -162,7 +165,9 @@ class Engine {
   struct IterGraph {
     unsigned long long sig = 0;
     unsigned long long in_sig = 0;     // inputs only: message shapes and buffers, workspaces
-    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;       // the captured graph (a child of a batch's graph)
+    cudaGraphExec_t exec = nullptr;    // instantiated on the first launch of its own
+    unsigned long long uid = 0;        // unique over the process, per capture
     long long launches = 0;
     double flops = 0.0;
     std::vector<std::vector<TShape>> out_shapes;   // per update: the outgoing message's shapes
@@ -180,12 +185,33 @@ class Engine {
 
  private:
   bool in_flight = false;
+  bool pending_launch = false;         // the iteration in flight waits for the caller's batch launch
+  cudaEvent_t root_pre = nullptr;      // the root's work before a deferred launch
+  unsigned long long uid_ = 0;
   bool launched_graph = false;         // the iteration in flight is a graph replay
   int launched_parity = 0;
   long long graph_tag(int parity) const { return (long long)(((uintptr_t)this >> 4) * 2 + (uintptr_t)parity); }
 
  public:
   void drop_graphs();
+  // Deferred graph launch (bbp_batch_iterate): with defer_graph set, an
+  // iteration that would replay or newly capture its graph leaves the launch
+  // (the tolerance upload, the graph, the word download) to the caller, who
+  // puts it into one graph over many contexts; deferred() describes it.
+  bool defer_graph = false;
+  struct Deferred {
+    cudaGraph_t graph = nullptr;
+    unsigned long long uid = 0;
+    double* tol_dev = nullptr;         // <- host_word[0], 8 bytes, before the graph
+    double* word_dev = nullptr;        // -> host_word + 1, 16 bytes, after it
+    double* host_word = nullptr;
+  };
+  bool deferred(Deferred& d) const;
+  // orders the batch stream after this context's root stream, and the root
+  // (and the iteration's completion event) after the batch's launch
+  int defer_before(cudaStream_t batch);
+  int defer_after(cudaStream_t batch);
+  unsigned long long uid() const { return uid_; }
 
  private:
   unsigned long long iter_signature(const std::vector<SweepJob>& jobs, int nstreams) const;

@@ -1420,11 +1420,15 @@ int rand_block(int m, int n, int chi) {
 // (b x b each), the Jacobi of L in the element type, and the complex128
 // reduced factor (G64, WH64: b x b; sig64, idx64: b).
 template <typename C>
+static size_t orth_scratch_bytes(int m, int n, int b) {
+  return align256(std::max(panel_chunk_scratch_bytes(m, b, sizeof(C)), panel_chunk_scratch_bytes(n, b, sizeof(C))));
+}
+template <typename C>
 static size_t rand_work_bytes(int m, int n, int b) {
   const size_t z = sizeof(C), zd = sizeof(double2);
   return align256(z * (size_t)n * b) + align256(z * (size_t)m * b) + 2 * align256(z * (size_t)b * b) +
          jacobi_bytes<C>(b, b) + 2 * align256(zd * (size_t)b * b) + align256(sizeof(double) * b) +
-         align256(sizeof(int) * b) + 256;
+         align256(sizeof(int) * b) + 256 + orth_scratch_bytes<C>(m, n, b);
 }
 
 // packed operands of the tensor-core range finder: Z for Z W and for Z^H Q,
@@ -1482,11 +1486,12 @@ static size_t cut64_smem(int b, int k) {
 // is not null: one CTA when the panel fits its shared memory, a cluster of
 // CTAs otherwise.
 template <typename C>
-static cudaError_t orth_panel(C* Y, int rows, int b, C* R, cudaStream_t s) {
+static cudaError_t orth_panel(C* Y, int rows, int b, C* R, void* chunk_scratch, cudaStream_t s) {
   if (TsqrSmem<C>::bytes(rows, b) <= (size_t)kSmemMax) {
     KTimerScope timer(KC_ORTH, s, qr_flops(rows, b));
     return tsqr_launch<C>(Y, rows, b, Y, R, rows, s);
   }
+  if (panel_cluster(rows, b, sizeof(C), true) == 0) return launch_panel_qr_chunked(Y, rows, b, Y, R, chunk_scratch, s);
   return launch_panel_qr(Y, rows, b, Y, R, 1, 0, s);
 }
 
@@ -1515,6 +1520,7 @@ static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* R
   double2* WH64 = (double2*)p; p += align256(zd * (size_t)b * b);
   double* sig64 = (double*)p; p += align256(sizeof(double) * b);
   int* idx64 = (int*)p; p += align256(sizeof(int) * b) + 256;
+  void* chunk = p; p += orth_scratch_bytes<C>(m, n, b);
   const C one = cx<C>(1.0, 0.0), zero = cx<C>(0.0, 0.0);
   cudaError_t e;
   // the range-finder products Y = Z W and W = Z^H Q: SIMT GEMMs, or (complex64
@@ -1552,15 +1558,15 @@ static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* R
   };
   k_omega<C><<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
   if ((e = z_times(W, Q)) != cudaSuccess) return e;
-  if ((e = orth_panel<C>(Q, m, b, nullptr, s)) != cudaSuccess) return e;
+  if ((e = orth_panel<C>(Q, m, b, nullptr, chunk, s)) != cudaSuccess) return e;
   for (int it = 0; it < power_iters; ++it) {
     if ((e = zh_times(Q, W)) != cudaSuccess) return e;
-    if ((e = orth_panel<C>(W, n, b, nullptr, s)) != cudaSuccess) return e;
+    if ((e = orth_panel<C>(W, n, b, nullptr, chunk, s)) != cudaSuccess) return e;
     if ((e = z_times(W, Q)) != cudaSuccess) return e;
-    if ((e = orth_panel<C>(Q, m, b, nullptr, s)) != cudaSuccess) return e;
+    if ((e = orth_panel<C>(Q, m, b, nullptr, chunk, s)) != cudaSuccess) return e;
   }
   if ((e = zh_times(Q, W)) != cudaSuccess) return e;
-  if ((e = orth_panel<C>(W, n, b, Rw, s)) != cudaSuccess) return e;
+  if ((e = orth_panel<C>(W, n, b, Rw, chunk, s)) != cudaSuccess) return e;
   if ((e = launch_conj_transpose(Rw, b, b, L, s)) != cudaSuccess) return e;
   SvdWork<C> w = carve<C>(jw, b, b);
   if ((e = cudaMemsetAsync(w.counters, 0, 64, s)) != cudaSuccess) return e;

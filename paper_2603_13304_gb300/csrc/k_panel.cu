@@ -100,6 +100,7 @@ __device__ __forceinline__ double2 pick(const double2 (&y)[MAXR], int q) {
 
 constexpr int kPanelThreads = 512;
 constexpr int kPanelSmemMax = 227 * 1024;
+constexpr int kQBlock = 8;               // reflectors a block of the Q formation
 
 // distributed shared memory through 32-bit shared-window addresses
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -129,10 +130,16 @@ __host__ __device__ inline PanelLayout panel_layout(int maxr, int n, int cs, boo
   PanelLayout L;
   L.ld = 32 * maxr + (odd_ld ? 1 : 0);
   size_t o = (size_t)L.ld * n;
+  const size_t ex0 = o;
   L.recv = o; o += 2 * (size_t)cs * n;
   L.rowb = o; o += 2 * (size_t)n;
   L.gs = o; o += gs ? (size_t)n : 0;
   L.pp = o; o += 2 * (size_t)cs;
+  // the same area holds the block buffers of the Q formation
+  if (want_q) {
+    const size_t qb = ex0 + 3 * (size_t)kQBlock * (n + kQBlock) + (size_t)kQBlock * kQBlock;
+    o = o > qb ? o : qb;
+  }
   L.tau = o; o += want_q ? (size_t)n : 0;
   L.ring = o; o += 6;
   L.bytes = sizeof(C) * o;
@@ -414,66 +421,153 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_qr(const C* __restri
     }
   if (!Qg) return;     // nothing is pushed after the last cluster barrier above
 
-  // ---- Q = H_0 ... H_{k-1} [I; 0], in place backwards: step i updates the
-  // columns c > i by tau_i v_i (v_i^H q_c) and sets column i to
-  // e_i - tau_i v_i (stored after the cluster barrier, when no warp reads v_i
-  // any more); the pass of step i also pushes the partial dots of step i - 1
-  // (v_{i-1} = column i - 1, untouched until its own step)
-  auto refl = [&](int i, C (&x)[MAXR]) {  // v_i from column i (scaled, 1 on row i)
-    load_col(i, x);
-#pragma unroll
-    for (int q = 0; q < MAXR; ++q) {
-      const int g = r0 + lane + 32 * q;
-      x[q] = g > i ? x[q] : (g == i ? one : zero);
-    }
+  // ---- Q = H_0 ... H_{k-1} [I; 0] by blocks of NB reflectors, the last
+  // block first, in place: H_{b0} ... H_{b1-1} = I - V T V^H (compact WY;
+  // T upper triangular, T_jj = tau_j, T_{0:j,j} = -tau_j T_{0:j,0:j}
+  // (V^H V)_{0:j,j}), so with Q' the columns >= b1 built so far and e_c the
+  // block's own columns,  Q_{:,c} = Q'_{:,c} - V (T (V^H Q'_{:,c})).
+  // One cluster exchange per block: every CTA writes its partial V^H Q'
+  // and V^H V over its rows into its own shared memory, and after the
+  // barrier every CTA sums all CTAs' partials remotely in rank order (the
+  // same T and the same products in every CTA).
+  constexpr int NB = kQBlock;
+  const int W = k + NB;                  // a row of the block buffers: V^H Q' at c < k, V^H V at k + b
+  C* Pb = A + L.recv;                    // [2][NB][W]: own partials, by block parity
+  C* Sb = Pb + 2 * (size_t)NB * W;       // [NB][W]: cluster sums, then T V^H Q'
+  C* Tb = Sb + (size_t)NB * W;           // [NB][NB]
+  constexpr int rows_pad = 32 * MAXR;
+  const int ngroups = max(1, (int)blockDim.x / rows_pad);
+  // V_B[t][a] of the block starting at column b0: reflector b0 + a at local row t
+  auto vb = [&](int b0, int a, int t) {
+    const int col = b0 + a, g = r0 + t;
+    return g > col ? A[(size_t)col * ld + t] : (g == col ? one : zero);
   };
-  auto set_col = [&](int i, const C (&x)[MAXR], C (&y)[MAXR]) {   // e_i - tau_i v_i
-    const C ti = s_tau[i], mt = mkc<C>(-ti.x, -ti.y), d0 = mkc<C>((R)1 - ti.x, -ti.y);
+  const int nblk = (k + NB - 1) / NB;
+  for (int B = nblk - 1; B >= 0; --B) {
+    const int b0 = B * NB, b1 = min(k, b0 + NB), nbB = b1 - b0;
+    C* Pw = Pb + (size_t)(B & 1) * NB * W;
+    // partials V^H Q' (columns c >= b1): a warp per column, the block's
+    // reflectors four at a time in registers
+    for (int a0 = 0; a0 < nbB; a0 += 4) {
+      C vch[4][MAXR];
 #pragma unroll
-    for (int q = 0; q < MAXR; ++q) {
-      const int g = r0 + lane + 32 * q;
-      y[q] = g == i ? d0 : (g > i ? pmul(mt, x[q]) : zero);
-    }
-  };
-  C y[MAXR];                             // the owner's column i, stored after the barrier
-  if (k > 0 && warp == (k - 1) % nw) {   // column k - 1 and the sums of step k - 2
-    C x[MAXR];
-    refl(k - 1, x);
-    set_col(k - 1, x, y);
-    if (k >= 2) {
-      refl(k - 2, x);
-      push_recv(0, k - 1, dot(x, y));
-    }
-  }
-  cl.sync();
-  if (k > 0 && warp == (k - 1) % nw) store_col(k - 1, y);
-  for (int i = k - 2; i >= 0; --i) {
-    const int par = (k - 2 - i) & 1;
-    if (use_gs)
-      for (int c = i + 1 + threadIdx.x; c < k; c += blockDim.x) gs[c] = pmul(s_tau[i], sum_recv(par, c));
-    __syncthreads();
-    C x[MAXR], xp[MAXR];
-    refl(i, x);
-    if (i >= 1) refl(i - 1, xp);
-    int c0 = i + ((warp - i) % nw + nw) % nw;
-    if (c0 == i) c0 += nw;               // the owner of column i takes it last
-    for (int c = c0; c < k; c += nw) {
-      load_col(c, y);
-      const C f = use_gs ? gs[c] : pmul(s_tau[i], sum_recv(par, c));
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int q = 0; q < MAXR; ++q) y[q] = psub(y[q], pmul(x[q], f));
-      store_col(c, y);
-      if (i >= 1) push_recv(par ^ 1, c, dot(xp, y));
+        for (int i = 0; i < MAXR; ++i) vch[u][i] = a0 + u < nbB ? vb(b0, a0 + u, lane + 32 * i) : zero;
+      for (int c = b1 + ((warp - b1) % nw + nw) % nw; c < k; c += nw) {
+        C y[MAXR];
+        load_col(c, y);
+        R acc[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          C d = pmulc(vch[u][0], y[0]);
+#pragma unroll
+          for (int i = 1; i < MAXR; ++i) d = padd(d, pmulc(vch[u][i], y[i]));
+          acc[2 * u] = d.x;
+          acc[2 * u + 1] = d.y;
+        }
+        // eight sums over the warp, halving the set at every level: lane l
+        // ends with sum r = 4 b4 + 2 b3 + b2 of its lane bits
+        const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const R send = h4 ? acc[q] : acc[4 + q];
+          acc[q] = (h4 ? acc[4 + q] : acc[q]) + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const R send = h3 ? acc[q] : acc[2 + q];
+          acc[q] = (h3 ? acc[2 + q] : acc[q]) + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        {
+          const R send = h2 ? acc[0] : acc[1];
+          acc[0] = (h2 ? acc[1] : acc[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+        if ((lane & 3) == 0) {
+          const int r = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0), u = r >> 1;
+          if (a0 + u < nbB) ((R*)&Pw[(size_t)(a0 + u) * W + c])[r & 1] = acc[0];
+        }
+      }
     }
-    const bool own = warp == i % nw;
-    if (own) {
-      set_col(i, x, y);
-      if (i >= 1) push_recv(par ^ 1, i, dot(xp, y));
+    // the block's own columns e_c (c in [b0, b1)): conj(V_B[c][a]) from the
+    // CTA that holds row c, zero elsewhere
+    for (int e = threadIdx.x; e < nbB * nbB; e += blockDim.x) {
+      const int a = e / nbB, c = b0 + e % nbB, t = c - r0;
+      const C v = (t >= 0 && t < mr) ? vb(b0, a, t) : zero;
+      Pw[(size_t)a * W + c] = mkc<C>(v.x, -v.y);
+    }
+    // V^H V (a < b) over the slice: a warp per pair
+    for (int pr = warp; pr < nbB * nbB; pr += nw) {
+      const int a = pr / nbB, b = pr % nbB;
+      if (a >= b) continue;
+      C x[MAXR], y[MAXR];
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) {
+        x[i] = vb(b0, a, lane + 32 * i);
+        y[i] = vb(b0, b, lane + 32 * i);
+      }
+      const C d = dot(x, y);
+      if (lane == 0) Pw[(size_t)a * W + k + b] = d;
     }
     cl.sync();
-    if (own) store_col(i, y);
+    // cluster sums of the block's partials, read from every CTA in rank order
+    for (int e = threadIdx.x; e < nbB * W; e += blockDim.x) {
+      const int a = e / W, col = e % W;
+      if (col < b0 || (col >= k && (col - k <= a || col - k >= nbB))) continue;
+      C sum = zero;
+      for (int q0 = 0; q0 < cs; q0 += 8) {
+        C vq[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) vq[u] = q0 + u < cs ? cl.map_shared_rank(Pw, q0 + u)[e] : zero;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum = padd(sum, vq[u]);
+      }
+      Sb[e] = sum;
+    }
+    __syncthreads();
+    if (warp == 0) {                     // T of the block, lane a holds row a
+      const int a = lane;
+      if (a < NB)
+        for (int b = 0; b < NB; ++b) Tb[a * NB + b] = (a == b && a < nbB) ? s_tau[b0 + a] : zero;
+      __syncwarp();
+      for (int j = 1; j < nbB; ++j) {
+        if (a < j) {
+          C acc = zero;
+          for (int b = a; b < j; ++b) acc = padd(acc, pmul(Tb[a * NB + b], Sb[(size_t)b * W + k + j]));
+          const C tj = s_tau[b0 + j];
+          Tb[a * NB + j] = mkc<C>(-(tj.x * acc.x - tj.y * acc.y), -(tj.x * acc.y + tj.y * acc.x));
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int c = b0 + threadIdx.x; c < k; c += blockDim.x)   // T V^H Q' in place, rows in ascending order
+      for (int a = 0; a < nbB; ++a) {
+        C acc = zero;
+        for (int b = a; b < nbB; ++b) acc = padd(acc, pmul(Tb[a * NB + b], Sb[(size_t)b * W + c]));
+        Sb[(size_t)a * W + c] = acc;
+      }
+    // every thread takes its row's V_B before the block's columns change
+    const int t = threadIdx.x % rows_pad, grp = threadIdx.x / rows_pad;
+    C v[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) v[a] = a < nbB ? vb(b0, a, t) : zero;
+    __syncthreads();
+    if (grp < ngroups) {
+      const int g = r0 + t;
+      for (int c = b0 + grp; c < k; c += ngroups) {
+        C q = c >= b1 ? A[(size_t)c * ld + t] : (g == c ? one : zero);
+#pragma unroll
+        for (int a = 0; a < NB; ++a)
+          if (a < nbB) q = psub(q, pmul(v[a], Sb[(size_t)a * W + c]));
+        A[(size_t)c * ld + t] = q;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
+  cl.sync();                             // no CTA still reads this CTA's partials
   for (int e = threadIdx.x; e < mr * k; e += blockDim.x) {
     const int t = e / k, c = e % k;
     Qg[(long long)(r0 + t) * k + c] = A[(size_t)c * ld + t];
@@ -1053,6 +1147,64 @@ static cudaError_t panel_t(const C* A, int m, int n, C* Q, C* R, int batch, long
     }
   }
   return cudaErrorInvalidValue;
+}
+
+// ---- panels taller than one cluster holds: row chunks that each fit one,
+// their R factors stacked and factorised again, and every chunk's Q
+// multiplied by its block of the stack's Q (two-level TSQR):
+//   A = [A_0; ...; A_{c-1}],  A_i = Q_i R_i,  [R_0; ...; R_{c-1}] = Qs R,
+//   Q = [Q_0 Qs_0; ...; Q_{c-1} Qs_{c-1}]
+// Scratch: the chunks' Q (m x n), the stack and its Q (c n x n each).
+namespace {
+int chunk_count(int m, int n, size_t elem) {
+  for (int c = 2; c <= 64; ++c) {
+    const int rows = (m + c - 1) / c;
+    if (rows < n) break;
+    if (panel_cluster(rows, n, elem, true) > 0 && panel_cluster(c * n, n, elem, true) > 0) return c;
+  }
+  return 0;
+}
+}  // namespace
+
+size_t panel_chunk_scratch_bytes(int m, int n, size_t elem) {
+  if (m < n || n < 1 || panel_cluster(m, n, elem, true) > 0) return 0;
+  const int c = chunk_count(m, n, elem);
+  if (c == 0) return 0;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  return al(elem * (size_t)m * n) + 2 * al(elem * (size_t)c * n * n);
+}
+
+template <typename C>
+static cudaError_t panel_chunked_t(const C* A, int m, int n, C* Q, C* R, void* scratch, cudaStream_t s) {
+  const int c = chunk_count(m, n, sizeof(C));
+  if (c == 0 || !scratch || !Q) return cudaErrorInvalidValue;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  C* Qc = (C*)scratch;
+  C* Rs = (C*)((char*)scratch + al(sizeof(C) * (size_t)m * n));
+  C* Qs = (C*)((char*)Rs + al(sizeof(C) * (size_t)c * n * n));
+  const int rows = (m + c - 1) / c, last = m - (c - 1) * rows;
+  cudaError_t e;
+  const long long st = (long long)rows * n;
+  if ((e = panel_t(A, rows, n, Qc, Rs, c - 1, st, s, 0)) != cudaSuccess) return e;
+  if ((e = panel_t(A + (c - 1) * st, last, n, Qc + (c - 1) * st, Rs + (size_t)(c - 1) * n * n, 1, 0, s, 0)) !=
+      cudaSuccess)
+    return e;
+  if ((e = panel_t(Rs, c * n, n, Qs, R, 1, 0, s, 0)) != cudaSuccess) return e;
+  const C one = C{1, 0}, zero = C{0, 0};
+  if ((e = launch_zgemm('N', 'N', rows, n, n, one, Qc, n, st, Qs, n, (long long)n * n, zero, Q, n, st, c - 1, s)) !=
+      cudaSuccess)
+    return e;
+  return launch_zgemm('N', 'N', last, n, n, one, Qc + (c - 1) * st, n, 0, Qs + (size_t)(c - 1) * n * n, n, 0, zero,
+                      Q + (c - 1) * st, n, 0, 1, s);
+}
+
+cudaError_t launch_panel_qr_chunked(const float2* A, int m, int n, float2* Q, float2* R, void* scratch,
+                                    cudaStream_t s) {
+  return panel_chunked_t(A, m, n, Q, R, scratch, s);
+}
+cudaError_t launch_panel_qr_chunked(const double2* A, int m, int n, double2* Q, double2* R, void* scratch,
+                                    cudaStream_t s) {
+  return panel_chunked_t(A, m, n, Q, R, scratch, s);
 }
 
 cudaError_t launch_panel_qr(const float2* A, int m, int n, float2* Q, float2* R, int batch, long long stride,

@@ -30,7 +30,12 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <initializer_list>
+#include <map>
 #include <mutex>
+#include <set>
+#include <vector>
 
 #include "kernels.h"
 
@@ -41,12 +46,13 @@ namespace {
 constexpr int kBM = 128;
 // pipeline depth: one stage holds 4 MMAs of 128 x BN x (32 bytes of K), a
 // fraction of a microsecond of tensor work, so enough stages must be in
-// flight to cover the TMA latency from L2: 6 at BN = 128, 8 at BN = 64
-// (about 192 KB of shared memory either way)
-template <int BN> __host__ __device__ constexpr int stages_of() { return BN >= 128 ? 6 : 8; }
-// tile order: groups of kGroupM M tiles sweep the N tiles together, so that
+// flight to cover the TMA latency from L2: 4 at BN = 256, 6 at BN = 128, 8
+// at BN = 64 (about 192 KB of shared memory each)
+template <int BN> __host__ __device__ constexpr int stages_of() { return BN >= 256 ? 4 : (BN >= 128 ? 6 : 8); }
+// tile order: groups of group_m M tiles sweep the N tiles together, so that
 // a wave of CTAs reuses its A tiles from L2 instead of streaming all of B
-constexpr int kGroupM = 16;
+// (group_m is a launch parameter, picked per shape by the autotuner)
+constexpr int kGroupMDefault = 16;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -141,7 +147,7 @@ __host__ __device__ constexpr uint32_t idesc_of() {
 template <bool kBF16, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, float* __restrict__ C,
-              int M, int N, int K, long long ldc, float alpha, int* err) {
+              int M, int N, int K, long long ldc, float alpha, int* err, int group_m) {
   constexpr int kEs = kBF16 ? 2 : 4;
   constexpr int kBKe = 128 / kEs;               // K elements per stage (one 128-byte row)
   constexpr int kUmmaK = 32 / kEs;              // K elements per tcgen05.mma
@@ -157,9 +163,9 @@ __global__ void __launch_bounds__(128, 1)
   // grouped rasterisation of the linear block index
   const int tiles_n = gridDim.x, tiles_m = gridDim.y;
   const int pid = blockIdx.y * tiles_n + blockIdx.x;
-  const int group = pid / (kGroupM * tiles_n), first_m = group * kGroupM;
-  const int gm = min(kGroupM, tiles_m - first_m);
-  const int in_group = pid - group * kGroupM * tiles_n;
+  const int group = pid / (group_m * tiles_n), first_m = group * group_m;
+  const int gm = min(group_m, tiles_m - first_m);
+  const int in_group = pid - group * group_m * tiles_n;
   const int tm = first_m + in_group % gm, tn = in_group / gm;
   const int n0 = tn * BN, m0 = tm * kBM;
   const int kt = (K + kBKe - 1) / kBKe;
@@ -289,7 +295,7 @@ cudaError_t tc_optin() {
 
 template <bool kBF16, int BN>
 cudaError_t tc_launch(const void* A, long long lda, const void* Bt, long long ldb, float* C, long long ldc, int M, int N,
-                      int K, float alpha, int* err, cudaStream_t s, double algo_flops) {
+                      int K, float alpha, int* err, cudaStream_t s, double algo_flops, int group_m) {
   constexpr int smem = tc_smem<BN>();
   cudaError_t attr_err = tc_optin<kBF16, BN>();
   if (attr_err != cudaSuccess) return attr_err;
@@ -298,7 +304,7 @@ cudaError_t tc_launch(const void* A, long long lda, const void* Bt, long long ld
     return cudaErrorInvalidValue;
   dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM);
   KTimerScope timer(KC_TC, s, algo_flops > 0 ? algo_flops : 2.0 * M * N * K);
-  k_tc_gemm<kBF16, BN><<<grid, 128, smem, s>>>(ta, tb, C, M, N, K, ldc, alpha, err);
+  k_tc_gemm<kBF16, BN><<<grid, 128, smem, s>>>(ta, tb, C, M, N, K, ldc, alpha, err, group_m < 1 ? 1 : group_m);
   return cudaGetLastError();
 }
 
@@ -574,22 +580,219 @@ cudaError_t init_tc_attributes() {
   cudaError_t e;
   if ((e = tc_optin<false, 64>()) != cudaSuccess) return e;
   if ((e = tc_optin<false, 128>()) != cudaSuccess) return e;
+  if ((e = tc_optin<false, 256>()) != cudaSuccess) return e;
   if ((e = tc_optin<true, 64>()) != cudaSuccess) return e;
-  return tc_optin<true, 128>();
+  if ((e = tc_optin<true, 128>()) != cudaSuccess) return e;
+  return tc_optin<true, 256>();
+}
+
+cudaError_t launch_tc_gemm_tile(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
+                                long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s, int bn,
+                                int group_m, double algo_flops) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  const int es = bf16 ? 2 : 4;
+  if ((lda * es) % 16 || (ldb * es) % 16 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15)) return cudaErrorInvalidValue;
+  switch (bn) {
+    case 64:
+      return bf16 ? tc_launch<true, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops, group_m)
+                  : tc_launch<false, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops, group_m);
+    case 128:
+      return bf16 ? tc_launch<true, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops, group_m)
+                  : tc_launch<false, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops, group_m);
+    case 256:
+      return bf16 ? tc_launch<true, 256>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops, group_m)
+                  : tc_launch<false, 256>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops, group_m);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------ autotuner
+//
+// The tile of a launch (BN, the width of a CTA's output tile, and group_m,
+// the M tiles a wave sweeps together) is looked up by the exact GEMM shape
+// (precision, M, N, K); shapes not in the table take the size rule (BN 128
+// above N = 64, else 64; group_m 16).  While recording is on, unknown shapes
+// are collected; tc_autotune times every candidate tile of each collected
+// shape on scratch operands (CUDA events, outside any capture) and keeps
+// the fastest.  The table can be written to and read from a text cache.
+namespace {
+
+struct TcKey {
+  int bf16, M, N, K;
+  bool operator<(const TcKey& o) const {
+    if (bf16 != o.bf16) return bf16 < o.bf16;
+    if (M != o.M) return M < o.M;
+    if (N != o.N) return N < o.N;
+    return K < o.K;
+  }
+};
+struct TcTile {
+  int bn = 0, group_m = kGroupMDefault;
+  float us = 0.f;
+};
+std::mutex g_tune_mu;
+std::map<TcKey, TcTile> g_tiles;
+std::set<TcKey> g_pending;
+std::atomic<bool> g_recording{false};
+std::atomic<unsigned long long> g_tune_gen{0};
+
+TcTile rule_tile(int N) {
+  TcTile t;
+  t.bn = N > 64 ? 128 : 64;
+  return t;
+}
+
+bool write_cache(const char* path) {
+  FILE* f = std::fopen(path, "w");
+  if (!f) return false;
+  std::fprintf(f, "# bbp tensor-core GEMM tiles: tc bf16 M N K bn group_m microseconds\n");
+  for (const auto& kv : g_tiles)
+    std::fprintf(f, "tc %d %d %d %d %d %d %.3f\n", kv.first.bf16, kv.first.M, kv.first.N, kv.first.K, kv.second.bn,
+                 kv.second.group_m, kv.second.us);
+  return std::fclose(f) == 0;
+}
+
+}  // namespace
+
+unsigned long long tc_tune_generation() { return g_tune_gen.load(); }
+
+void tc_autotune_record(bool on) { g_recording.store(on); }
+
+void tc_autotune_info(int* entries, int* pending) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (entries) *entries = (int)g_tiles.size();
+  if (pending) *pending = (int)g_pending.size();
+}
+
+void tc_autotune_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tiles.clear();
+  g_pending.clear();
+  ++g_tune_gen;
+}
+
+cudaError_t tc_autotune(const char* cache_path, int* tuned) {
+  if (tuned) *tuned = 0;
+  std::vector<TcKey> todo;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TcKey& k : g_pending)
+      if (!g_tiles.count(k)) todo.push_back(k);
+    g_pending.clear();
+  }
+  cudaError_t e = init_tc_attributes();
+  if (e != cudaSuccess) return e;
+  cudaStream_t s = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int* err = nullptr;
+  cudaMalloc(&err, sizeof(int));
+  int n_done = 0;
+  for (const TcKey& k : todo) {
+    const size_t es = k.bf16 ? 2 : 4;
+    const long long ld = ((long long)k.K + 31) / 32 * 32;
+    void *A = nullptr, *B = nullptr;
+    float* C = nullptr;
+    if (cudaMalloc(&A, (size_t)k.M * ld * es) != cudaSuccess || cudaMalloc(&B, (size_t)k.N * ld * es) != cudaSuccess ||
+        cudaMalloc(&C, sizeof(float) * (size_t)k.M * k.N) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(A);
+      cudaFree(B);
+      cudaFree(C);
+      continue;   // no scratch for this shape: it keeps the size rule
+    }
+    cudaMemsetAsync(A, 0, (size_t)k.M * ld * es, s);
+    cudaMemsetAsync(B, 0, (size_t)k.N * ld * es, s);
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    TcTile best;
+    best.us = 1e30f;
+    const int tiles_m = (k.M + kBM - 1) / kBM;
+    for (int bn : {64, 128, 256}) {
+      if (bn == 256 && k.N <= 128) continue;
+      if (bn == 64 && k.N > 1024) continue;
+      for (int gm : {1, 8, 16}) {
+        // groups of at least tiles_m M tiles all give one group (the same order)
+        if ((gm == 16 && tiles_m <= 8) || (gm == 8 && tiles_m <= 1)) continue;
+        if (launch_tc_gemm_tile(k.bf16 != 0, A, ld, B, ld, C, k.N, k.M, k.N, k.K, 1.f, err, s, bn, gm, 0.0) !=
+            cudaSuccess)
+          continue;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch_tc_gemm_tile(k.bf16 != 0, A, ld, B, ld, C, k.N, k.M, k.N, k.K, 1.f, err, s, bn, gm, 0.0);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float us = 1e3f * ms / 3.f;
+        if (us < best.us) {
+          best.bn = bn;
+          best.group_m = gm;
+          best.us = us;
+        }
+      }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(A);
+    cudaFree(B);
+    cudaFree(C);
+    if (best.bn) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tiles[k] = best;
+      ++n_done;
+    }
+  }
+  int h_err = 0;
+  cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(err);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (n_done) ++g_tune_gen;
+  if (tuned) *tuned = n_done;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (h_err) return cudaErrorLaunchTimeout;
+  if (cache_path && *cache_path) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!write_cache(cache_path)) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+int tc_autotune_load(const char* cache_path) {
+  FILE* f = std::fopen(cache_path, "r");
+  if (!f) return -1;
+  char line[256];
+  int n = 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  while (std::fgets(line, sizeof(line), f)) {
+    TcKey k;
+    TcTile t;
+    if (std::sscanf(line, "tc %d %d %d %d %d %d %f", &k.bf16, &k.M, &k.N, &k.K, &t.bn, &t.group_m, &t.us) != 7) continue;
+    if ((t.bn != 64 && t.bn != 128 && t.bn != 256) || t.group_m < 1 || k.M < 1 || k.N < 1 || k.K < 1) continue;
+    g_tiles[k] = t;
+    ++n;
+  }
+  std::fclose(f);
+  if (n) ++g_tune_gen;
+  return n;
 }
 
 cudaError_t launch_tc_gemm(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
                            long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s,
                            double algo_flops) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-  const int es = bf16 ? 2 : 4;
-  if ((lda * es) % 16 || (ldb * es) % 16 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15)) return cudaErrorInvalidValue;
-  if (N > 64) {
-    return bf16 ? tc_launch<true, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops)
-                : tc_launch<false, 128>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops);
+  TcTile t = rule_tile(N);
+  {
+    const TcKey key{bf16 ? 1 : 0, M, N, K};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tiles.find(key);
+    if (it != g_tiles.end()) t = it->second;
+    else if (g_recording.load(std::memory_order_relaxed)) g_pending.insert(key);
   }
-  return bf16 ? tc_launch<true, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops)
-              : tc_launch<false, 64>(A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, algo_flops);
+  return launch_tc_gemm_tile(bf16, A, lda, Bt, ldb, C, ldc, M, N, K, alpha, err, s, t.bn, t.group_m, algo_flops);
 }
 
 long long tc_ld(int P) { return ((6LL * P + 31) / 32) * 32; }

@@ -150,6 +150,23 @@ cudaError_t launch_mps_dot(const ChainDesc& a, const ChainDesc& b, bool c64, dou
 cudaError_t launch_tc_gemm(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
                            long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s,
                            double algo_flops = 0.0);
+// The same GEMM with an explicit tile: bn in {64, 128, 256}, group_m >= 1.
+cudaError_t launch_tc_gemm_tile(bool bf16, const void* A, long long lda, const void* Bt, long long ldb, float* C,
+                                long long ldc, int M, int N, int K, float alpha, int* err, cudaStream_t s, int bn,
+                                int group_m, double algo_flops = 0.0);
+// Tile autotuner of launch_tc_gemm (k_tc.cu): record collects the shapes of
+// later launches that have no table entry; tc_autotune times the candidate
+// tiles of each collected shape (synchronously, on its own stream, outside
+// any capture) and writes the table to cache_path when it is not null;
+// tc_autotune_load reads a table (returns the entries read, -1 when the file
+// cannot be opened).  The generation counts table changes (captured graphs
+// that launched with an older table are re-captured).
+void tc_autotune_record(bool on);
+cudaError_t tc_autotune(const char* cache_path, int* tuned);
+int tc_autotune_load(const char* cache_path);
+void tc_autotune_info(int* entries, int* pending);
+void tc_autotune_clear();
+unsigned long long tc_tune_generation();
 size_t tc_absorb_bytes(bool bf16, int P, int Q, int l, int r);
 cudaError_t launch_tc_absorb(bool bf16, const double2* X, int P, int Q, const double2* S, int l, int r, double2* R,
                              void* work, int* err, cudaStream_t s);
@@ -220,6 +237,15 @@ cudaError_t launch_panel_qr(const float2* A, int m, int n, float2* Q, float2* R,
                             cudaStream_t s, int cluster = 0);
 cudaError_t launch_panel_qr(const double2* A, int m, int n, double2* Q, double2* R, int batch, long long stride,
                             cudaStream_t s, int cluster = 0);
+// Panels taller than one cluster holds (panel_cluster = 0): two-level TSQR
+// over row chunks that each fit one cluster; Q is required, R may be null.
+// panel_chunk_scratch_bytes: the device scratch it needs (0 when the panel
+// fits one cluster or cannot be chunked).
+size_t panel_chunk_scratch_bytes(int m, int n, size_t elem);
+cudaError_t launch_panel_qr_chunked(const float2* A, int m, int n, float2* Q, float2* R, void* scratch,
+                                    cudaStream_t s);
+cudaError_t launch_panel_qr_chunked(const double2* A, int m, int n, double2* Q, double2* R, void* scratch,
+                                    cudaStream_t s);
 
 // Allocation-free truncated SVD (k_noalloc.cu): scratch in a fixed device
 // array of noalloc_scratch_bytes(); *too_large is set when svd_work_bytes(m, n)

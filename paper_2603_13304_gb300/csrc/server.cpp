@@ -19,6 +19,7 @@
 #include <chrono>
 #include <cmath>
 #include <deque>
+#include <mutex>
 #include <exception>
 #include <string>
 #include <thread>
@@ -72,7 +73,78 @@ void parallel_for(size_t n, F&& f) {
   for (auto& t : ts) t.join();
 }
 
+// ------------------------------------------------ one launch per round
+//
+// The graph-replayed iterations of a round go to the device as one graph:
+// per context the tolerance upload, the context's iteration graph as a child
+// node and the download of its convergence word, the contexts independent of
+// one another.  Built once per set of (context, capture) ids and relaunched
+// while the set repeats (a few sets are kept: the iterations alternate
+// between two message parities).
+std::atomic<bool> g_single_launch{true};
+
+struct BatchGraph {
+  std::vector<std::pair<unsigned long long, unsigned long long>> key;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_bg_mu;
+std::deque<BatchGraph> g_bg;
+constexpr size_t kBatchGraphsKept = 4;
+
+int launch_round(bbp_ctx** ctxs, const std::vector<int>& idx, const std::vector<bbp::Engine::Deferred>& ds,
+                 cudaStream_t bs) {
+  std::vector<std::pair<unsigned long long, unsigned long long>> key(idx.size());
+  for (size_t a = 0; a < idx.size(); ++a) key[a] = {ctxs[idx[a]]->eng.uid(), ds[a].uid};
+  std::lock_guard<std::mutex> lk(g_bg_mu);
+  cudaGraphExec_t exec = nullptr;
+  for (auto it = g_bg.begin(); it != g_bg.end(); ++it)
+    if (it->key == key) {
+      exec = it->exec;
+      BatchGraph hit = *it;
+      g_bg.erase(it);
+      g_bg.push_front(hit);
+      break;
+    }
+  if (!exec) {
+    cudaGraph_t G = nullptr;
+    if (cudaGraphCreate(&G, 0) != cudaSuccess) return BBP_ERR_CUDA;
+    bool ok = true;
+    for (size_t a = 0; a < ds.size() && ok; ++a) {
+      cudaGraphNode_t n1, n2, n3;
+      ok = cudaGraphAddMemcpyNode1D(&n1, G, nullptr, 0, ds[a].tol_dev, ds[a].host_word, sizeof(double),
+                                    cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaGraphAddChildGraphNode(&n2, G, &n1, 1, ds[a].graph) == cudaSuccess &&
+           cudaGraphAddMemcpyNode1D(&n3, G, &n2, 1, ds[a].host_word + 1, ds[a].word_dev, 2 * sizeof(double),
+                                    cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&exec, G, 0) == cudaSuccess;
+    cudaGraphDestroy(G);
+    if (!ok) {
+      cudaGetLastError();
+      return BBP_ERR_CUDA;
+    }
+    if (g_bg.size() >= kBatchGraphsKept) {
+      cudaStreamSynchronize(bs);        // (an evicted graph may still run on an earlier round)
+      cudaDeviceSynchronize();
+      cudaGraphExecDestroy(g_bg.back().exec);
+      g_bg.pop_back();
+    }
+    g_bg.push_front(BatchGraph{key, exec});
+  }
+  for (int i : idx)
+    if (ctxs[i]->eng.defer_before(bs)) return BBP_ERR_CUDA;
+  if (cudaGraphLaunch(exec, bs) != cudaSuccess) return BBP_ERR_CUDA;
+  for (int i : idx)
+    if (ctxs[i]->eng.defer_after(bs)) return BBP_ERR_CUDA;
+  return BBP_OK;
+}
+
 }  // namespace
+
+extern "C" bbp_status bbp_batch_single_launch(int on) {
+  g_single_launch.store(on != 0);
+  return BBP_OK;
+}
 
 extern "C" bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int max_iter, int* iters_out,
                                         double* err_out, int* status_out) {
@@ -92,32 +164,52 @@ extern "C" bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int m
       if (rc) status_out[i] = rc;
       else active.push_back(i);
     }
+    const bool single = g_single_launch.load() && active.size() > 1;
+    cudaStream_t bs = nullptr;
+    if (single && cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return BBP_ERR_CUDA;
     for (int round = 0; round < max_iter && !active.empty(); ++round) {
       std::vector<int> rcs(active.size(), 0);
       parallel_for(active.size(), [&](size_t a) {
         try {
           ctxs[active[a]]->eng.iter_tol = tol;
+          ctxs[active[a]]->eng.defer_graph = single;
           rcs[a] = ctxs[active[a]]->eng.iter_launch();
+          ctxs[active[a]]->eng.defer_graph = false;
         } catch (...) {
           rcs[a] = BBP_ERR_CUDA;
         }
       });
-      std::vector<int> launched;
+      std::vector<int> launched, deferred;
+      std::vector<bbp::Engine::Deferred> ds;
       for (size_t a = 0; a < active.size(); ++a) {
-        if (rcs[a]) status_out[active[a]] = rcs[a];
-        else launched.push_back(active[a]);
+        if (rcs[a]) {
+          status_out[active[a]] = rcs[a];
+          continue;
+        }
+        launched.push_back(active[a]);
+        bbp::Engine::Deferred d;
+        if (ctxs[active[a]]->eng.deferred(d)) {
+          deferred.push_back(active[a]);
+          ds.push_back(d);
+        }
+      }
+      if (!deferred.empty() && launch_round(ctxs, deferred, ds, bs) != BBP_OK) {
+        for (int i : deferred) ctxs[i]->eng.defer_after(bs);   // (finish reports the failed round)
+        for (int i : deferred) status_out[i] = BBP_ERR_CUDA;
       }
       std::vector<int> next;
       for (int i : launched) {
         double e = INFINITY;
+        const bool failed = status_out[i] != BBP_OK;   // (its round's launch failed)
         const int rc = ctxs[i]->eng.iter_finish(&e);
         ++iters_out[i];
         err_out[i] = e;
         if (rc) status_out[i] = rc;
-        else if (!(e <= tol)) next.push_back(i);
+        else if (!failed && !(e <= tol)) next.push_back(i);
       }
       active.swap(next);
     }
+    if (bs) cudaStreamDestroy(bs);     // (its work completes first)
     for (int i = 0; i < n; ++i) {
       if (!ctxs[i]) continue;
       ctxs[i]->eng.iter_end();

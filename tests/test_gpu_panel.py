@@ -183,10 +183,12 @@ def test_svd_trunc_c64(m, n, chi, decay, tc):
 
 
 @pytest.mark.parametrize("m,n,chi,decay", [(512, 512, 32, 0.9), (512, 256, 32, 0.8), (1296, 1296, 64, 0.95),
-                                           (300, 280, 8, 0.6)])
+                                           (300, 280, 8, 0.6), (2304, 2304, 64, 0.95)])
 def test_svd_trunc_rand64(m, n, chi, decay):
     """complex128 subspace iteration (b = 2 chi, six power steps) against the
-    exact truncation: within 1e-12 of ||Z|| on geometric spectra."""
+    exact truncation: within 1e-12 of ||Z|| on geometric spectra.  At 2304
+    rows and b = 128 the complex128 panels exceed one cluster and take the
+    two-level TSQR over row chunks."""
     rng = np.random.default_rng(3 * m + n + chi)
     Z = geometric_matrix(rng, m, n, decay)
     k = min(chi, m, n)

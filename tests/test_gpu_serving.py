@@ -93,6 +93,32 @@ def test_batch_matches_individual():
             P.bbp_destroy(c)
 
 
+def test_batch_single_launch_matches_separate():
+    """One graph launch per round (every context's replayed iteration a
+    child of one graph) computes what separate per-context launches compute;
+    8 rounds, so that the graphs take over once the bond dimensions settle."""
+    specs = [spec(*a) for a in SPECS]
+    out = {}
+    for single in (False, True):
+        P.bbp_batch_single_launch(single)
+        ctxs = [make_ctx(s) for s in specs]
+        try:
+            for _ in range(8):      # one round a call, as a serving loop would
+                rc, iters, errs, st = P.bbp_batch_iterate(ctxs, 0.0, 1)
+                assert rc in (0, 6)
+            out[single] = [(messages(c), P.bbp_energy_per_site(c)) for c in ctxs]
+        finally:
+            for c in ctxs:
+                P.bbp_destroy(c)
+    P.bbp_batch_single_launch(True)
+    for i, s in enumerate(specs):
+        tol = 1e-10 if s["precision"] == P.FP64 else 1e-6
+        d = diff(out[False][i][0], out[True][i][0])
+        de = abs(out[False][i][1] - out[True][i][1])
+        print(f"job {i}: single vs separate launches: message diff {d:.2e}, |dE| {de:.2e}")
+        assert d < tol and de < tol
+
+
 def run_server(specs, budget=1 << 36, max_active=64, iters=6, stagger=0):
     srv = P.bbp_server_create(budget, max_active)
     ids = []

@@ -93,3 +93,87 @@ def test_tc_absorb(Pd, Q, l, r, bf16, c64):
     print(f"absorb P={Pd} Q={Q} l={l} r={r} bf16={bf16} c64={c64}: max err / sum|x s| = {rel:.2e}")
     # three-product split: ~3 u^2, plus FP32 accumulation over 6P terms
     assert rel < (3e-4 if bf16 else 2e-5)
+
+
+def tc_gemm_tile(A, Bt, bf16, bn, group_m):
+    M, K = A.shape
+    N = Bt.shape[0]
+    step = 8 if bf16 else 4
+    ld = (K + step - 1) // step * step
+    dt = torch.bfloat16 if bf16 else torch.float32
+    Ad = torch.zeros(M, ld, dtype=dt, device="cuda")
+    Bd = torch.zeros(N, ld, dtype=dt, device="cuda")
+    Ad[:, :K] = A.to("cuda", dt)
+    Bd[:, :K] = Bt.to("cuda", dt)
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    P.bbp_k_tc_gemm_tile(bf16, Ad, ld, Bd, ld, C, N, M, N, K, 1.0, bn, group_m, err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0, "pipeline wait timed out"
+    return C.cpu().double()
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("M,N,K", [(300, 130, 1000), (1000, 600, 512), (2592, 520, 264), (17, 300, 40)])
+def test_tc_gemm_tiles(M, N, K, bf16):
+    """Every tile (bn 64 / 128 / 256, group_m 1 / 8 / 16) computes the same
+    GEMM: each output element accumulates the same K steps in the same order
+    whatever the tile, so the tiles agree to FP32 rounding (in practice
+    bitwise), and each is within the operand-rounding bound of the FP64
+    product."""
+    g = torch.Generator().manual_seed(M + 3 * N + 7 * K)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64)
+    Bt = torch.randn(N, K, generator=g, dtype=torch.float64)
+    ref = A @ Bt.T
+    scale = (A.abs() @ Bt.abs().T).max().item()
+    u = 2.0 ** -8 if bf16 else 2.0 ** -11
+    base = tc_gemm(A, Bt, bf16)
+    same = 0
+    for bn in (64, 128, 256):
+        for gm in (1, 8, 16):
+            C = tc_gemm_tile(A, Bt, bf16, bn, gm)
+            assert (C - ref).abs().max().item() <= 2.5 * u * scale
+            d = (C - base).abs().max().item()
+            assert d <= 1e-6 * scale, f"bn={bn} group_m={gm}: {d:.3e}"
+            same += int(d == 0.0)
+    print(f"M={M} N={N} K={K} bf16={bf16}: {same} of 9 tiles bitwise equal to the default")
+
+
+def test_autotune_record_run_load(tmp_path):
+    """Recording the tensor-core shapes of a TF32 iteration, tuning them and
+    reloading the cache: the table round-trips, the tuned iteration is
+    recaptured (generation advances) and gives the same messages."""
+    import synthetic as syn
+    nb = syn.kagome_neighbours(6, 2)
+    t = syn.dimer_singlet_peps(nb, 2, 4, seed=2, noise=1e-2, noise_seed=3)
+    em = syn.initial_edge_matrices(len(nb), 4, seed=7)
+
+    def run(iters):
+        ctx = P.bbp_create_peps(P.KAGOME, 6, 2, 1, 2, 4, t)
+        P.bbp_partition_blocks(ctx, 2, 2)
+        P.bbp_set_options(ctx, 32, P.TF32)
+        P.bbp_init_messages(ctx, em)
+        P.bbp_iterate(ctx, 0.0, iters)
+        out = [np.concatenate([x.ravel() for x in P.bbp_get_message(ctx, b, f)]) for b in range(3) for f in range(4)]
+        P.bbp_destroy(ctx)
+        return out
+
+    P.bbp_autotune_clear()
+    P.bbp_autotune_record(True)
+    before = run(3)
+    P.bbp_autotune_record(False)
+    _, pending, gen0 = P.bbp_autotune_info()
+    assert pending >= 1, "no tensor-core GEMM was recorded"
+    cache = str(tmp_path / "tiles.txt")
+    tuned = P.bbp_autotune_run(cache)
+    entries, pending2, gen1 = P.bbp_autotune_info()
+    assert tuned == pending and entries == tuned and pending2 == 0 and gen1 > gen0
+    lines = [ln for ln in open(cache) if ln.startswith("tc ")]
+    assert len(lines) == entries
+    P.bbp_autotune_clear()
+    assert P.bbp_autotune_load(cache) == entries
+    after = run(3)
+    worst = max(float(np.abs(a - b).max()) for a, b in zip(before, after))
+    print(f"autotune: {entries} shapes; largest message change after retuning {worst:.2e}")
+    assert worst <= 1e-6
+    P.bbp_autotune_clear()
