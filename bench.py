@@ -375,7 +375,7 @@ def make_network(P, j, precision, streams, fuse_cache=None):
     return c
 
 
-def run_batched(n_networks, steps, warmup, precision, seed=4):
+def run_batched(n_networks, steps, warmup, precision, seed=4, groups=0):
     """One synchronous iteration of every one of n_networks independent
     networks per round (bbp_batch_iterate: the replayed iterations of a round
     go out as one graph launch), with the tensor-core tiles autotuned on the
@@ -386,7 +386,9 @@ def run_batched(n_networks, steps, warmup, precision, seed=4):
     t0 = time.perf_counter()
     jobs = network_mix(n_networks, seed)
     # every site fused right before its absorb (nothing cached), 2 worker
-    # streams a network; networks are added while 24 GB of HBM stay free
+    # streams a network; networks are added while 24 GB of HBM stay free (the
+    # worker arenas come at the first iteration: with `groups` pools they
+    # take groups x the largest arena, else one arena set per network)
     ctxs = []
     for j in jobs:
         if torch.cuda.mem_get_info()[0] < 24e9:
@@ -395,6 +397,8 @@ def run_batched(n_networks, steps, warmup, precision, seed=4):
     jobs = jobs[:len(ctxs)]
     n_networks = len(ctxs)
     n_updates = sum(P.bbp_info(c)[1] for c in ctxs)
+    if groups:
+        P.bbp_share_workers(ctxs, groups)
     setup_s = time.perf_counter() - t0
     P.bbp_autotune_record(True)
     prev = None
@@ -443,6 +447,7 @@ def run_batched(n_networks, steps, warmup, precision, seed=4):
     return {"networks": n_networks, "message_updates_per_round": n_updates, "rounds": steps,
             "value": n_updates * steps / secs, "unit": "message updates/s", "ms_per_round": 1e3 * secs / steps,
             "launch": "one graph launch per round (every network's iteration graph a child)",
+            "worker_pools": groups or n_networks,
             "failed_networks": failed, "settle_rounds": settle, "autotuned_shapes": tuned,
             "autotune_s": round(tune_s, 2), "setup_s": round(setup_s, 2),
             "chi_below_D2_fraction": sum(1 for j in jobs if j["chi"] < j["D"] ** 2) / n_networks,
@@ -509,7 +514,7 @@ def serving_pool(n, seed):
 
 
 def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, drain_s=None, pool_n=16, seed=5,
-                fp64_sample=8):
+                fp64_sample=8, max_active=32, fp64_baseline=True):
     """Poisson arrivals (seed `seed`) at `rate` jobs/s for warm_s + duration_s
     seconds of job templates drawn from serving_pool; each job runs to `tol`
     or `max_iter` iterations on the continuous-batching server (messages
@@ -537,7 +542,7 @@ def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, 
     jobs_spec = [P.make_job(j["lattice"], j["Lx"], j["Ly"], j["periodic"], 2, j["D"], j["bx"], j["by"], j["chi"],
                             precision, j["t"], j["em"], tol, max_iter, 2, 1) for j in pool]
     free, _ = torch.cuda.mem_get_info()
-    srv = P.bbp_server_create(int(free * 0.8), 256)
+    srv = P.bbp_server_create(int(free * 0.8), max_active)
     lat, iters, stat, sub = {}, {}, {}, {}
     energy = {}
     t0 = time.perf_counter()
@@ -581,7 +586,7 @@ def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, 
     for k in done:
         tpl_iters.setdefault(arrivals[k][1], iters[k])
     sample = sorted(served_e)[:fp64_sample]
-    for tpl in sorted(set(a[1] for a in arrivals)):
+    for tpl in (sorted(set(a[1] for a in arrivals)) if fp64_baseline else []):
         j = pool[tpl]
         c = make_network(P, j, prec64, 16)
         per_it = float("nan")
@@ -618,7 +623,7 @@ def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, 
             e64[tpl] = abs(P.bbp_energy_per_site(c) - served_e[tpl][0])
             P.bbp_destroy(c)
     clock, seq = 0.0, []
-    for k, (ta, tpl) in enumerate(arrivals):
+    for k, (ta, tpl) in enumerate(arrivals if fp64_baseline else []):
         start = max(clock, ta)
         clock = start + svc[tpl]
         if ta >= warm_s:
@@ -641,6 +646,7 @@ def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, 
                                    "method": "FIFO over the same arrivals; service = FP64 s/iteration x the "
                                              "template's served iterations (measured per template)"},
             "pool": f"{pool_n} templates (network_mix + 10% Kagome D=6 chi=64), seed {seed}; 2 streams per job",
+            "max_active": max_active,
             "window_finished": len(window)}
 
 
@@ -816,11 +822,15 @@ def main():
     ap.add_argument("--roofline-kernel", default=None, choices=sorted(KERNELS),
                     help="kernel class timed for the roofline (default: tc for tf32/bf16, else orth)")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--batch", type=int, default=32, help="networks in the batched measurement (0: skip)")
+    ap.add_argument("--batch", type=int, default=16, help="networks in the batched measurement (0: skip)")
     ap.add_argument("--batch-rounds", type=int, default=2, help="timed rounds of the batched measurement")
-    ap.add_argument("--serve", type=float, default=3.0,
+    ap.add_argument("--batch-pools", type=int, default=0,
+                    help="worker pools shared by the batched networks (0: one each)")
+    ap.add_argument("--serve", type=float, default=0.0,
                     help="seconds of arrivals after the warm-up in the serving measurement (0: skip)")
     ap.add_argument("--serve-pool", type=int, default=16, help="job templates of the serving stream")
+    ap.add_argument("--serve-active", type=int, default=32, help="resident jobs at most (server slots)")
+    ap.add_argument("--serve-no-fp64", action="store_true", help="skip the FP64 one-at-a-time baseline")
     ap.add_argument("--only", choices=["batched", "serving"],
                     help="run only the batched or the serving measurement and print it")
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -843,10 +853,11 @@ def main():
         P.use_torch_allocator()
         prec_code = {"tf32": 1, "bf16": 2, "fp32": 3, "fp64": 0}[args.precision]
         if args.only == "batched":
-            out = run_batched(args.batch, args.batch_rounds, 1, prec_code)
+            out = run_batched(args.batch, args.batch_rounds, 1, prec_code, groups=args.batch_pools)
         else:
             out = run_serving(args.serve, args.serve_rate, prec_code, warm_s=min(5.0, args.serve / 4),
-                              pool_n=args.serve_pool)
+                              pool_n=args.serve_pool, max_active=args.serve_active,
+                              fp64_baseline=not args.serve_no_fp64)
         print(json.dumps({args.only: out}))
         return
     rank = int(os.environ.get("RANK", "0"))
@@ -900,10 +911,11 @@ def main():
         cpu = {"value": 1.0 / dt, "unit": "message updates/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"one complete message update at full bond ({dt:.1f} s of CPU work)"}
     prec_code = {"tf32": 1, "bf16": 2, "fp32": 3, "fp64": 0}[args.precision]
-    batched = (run_batched(args.batch, args.batch_rounds, 1, prec_code)
+    batched = (run_batched(args.batch, args.batch_rounds, 1, prec_code, groups=args.batch_pools)
                if args.batch > 0 and world == 1 else None)
     serving = (run_serving(args.serve, args.serve_rate, prec_code, warm_s=min(5.0, args.serve / 4),
-                           pool_n=args.serve_pool)
+                           pool_n=args.serve_pool, max_active=args.serve_active,
+                           fp64_baseline=not args.serve_no_fp64)
                if args.serve > 0 and world == 1 else None)
     line = {
         "metric": "BlockBP message updates/s", "value": res["value"], "unit": "message updates/s",

@@ -235,6 +235,14 @@ void bbp_destroy(bbp_ctx* ctx);
  * bbp_batch_single_launch(0) launches every context's graph separately
  * instead (the default is 1). */
 bbp_status bbp_batch_single_launch(int on);
+/* Worker streams and workspace arenas shared by groups of contexts: the n
+ * contexts are dealt into `groups` pools (heaviest first, back and forth, so
+ * that the groups get like mixes); the contexts of one pool run their
+ * iterations one after another (in a batch round, in the order of ctxs) and
+ * the pool's arenas are sized by its largest member, so that many contexts
+ * fit the device.  groups = 0 gives every context a private pool again.
+ * Waits for the contexts' work in flight. */
+bbp_status bbp_share_workers(bbp_ctx** ctxs, int n, int groups);
 bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int max_iter, int* iters_out, double* err_out,
                              int* status_out);
 

@@ -11,7 +11,7 @@ from ._lib import (  # noqa: F401
     bbp_k_panel_cluster, bbp_k_panel_qr, bbp_k_svd_work_bytes_rand, bbp_k_svd_trunc_rand, bbp_k_fma_peak, bbp_set_hermitise, bbp_expect_product, bbp_bond_energies,
     bbp_k_svd_stats, bbp_k_svd_trunc_noalloc, bbp_k_svd_work_bytes, bbp_k_tc_absorb, bbp_k_tc_absorb_bytes,
     bbp_k_tc_gemm, bbp_k_tc_gemm_tile, bbp_autotune_record, bbp_autotune_run, bbp_autotune_load, bbp_autotune_info,
-    bbp_autotune_clear, bbp_batch_single_launch, bbp_set_fuse_cache, bbp_ktimer_read, bbp_ktimer_select, bbp_last_error, bbp_norm, bbp_partition_blocks, bbp_plan_debug, bbp_set_execution, bbp_set_options, bbp_set_power_iters, bbp_stats,
+    bbp_autotune_clear, bbp_batch_single_launch, bbp_set_fuse_cache, bbp_share_workers, bbp_ktimer_read, bbp_ktimer_select, bbp_last_error, bbp_norm, bbp_partition_blocks, bbp_plan_debug, bbp_set_execution, bbp_set_options, bbp_set_power_iters, bbp_stats,
     use_default_allocator, use_torch_allocator, bbp_batch_iterate, bbp_job, make_job, bbp_job_footprint_bytes,
     bbp_server_create, bbp_server_submit, bbp_server_step, bbp_server_poll, bbp_server_take, bbp_server_destroy,
 )

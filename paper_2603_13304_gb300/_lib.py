@@ -32,7 +32,7 @@ EXPORTS = [
     "bbp_server_poll", "bbp_server_take", "bbp_server_destroy", "bbp_ktimer_select", "bbp_ktimer_read",
     "bbp_k_tc_absorb_bytes", "bbp_k_tc_absorb", "bbp_plan_debug", "bbp_k_tc_gemm_tile", "bbp_autotune_record",
     "bbp_autotune_run", "bbp_autotune_load", "bbp_autotune_info", "bbp_autotune_clear", "bbp_batch_single_launch",
-    "bbp_set_fuse_cache",
+    "bbp_set_fuse_cache", "bbp_share_workers",
 ]
 
 
@@ -103,6 +103,7 @@ _PROTOS = {
     "bbp_autotune_record": (_i, [_i]),
     "bbp_batch_single_launch": (_i, [_i]),
     "bbp_set_fuse_cache": (_i, [_vp, ctypes.c_size_t]),
+    "bbp_share_workers": (_i, [_vp, _i, _i]),
     "bbp_autotune_run": (_i, [ctypes.c_char_p, _ip]),
     "bbp_autotune_load": (_i, [ctypes.c_char_p, _ip]),
     "bbp_autotune_info": (_i, [_ip, _ip, ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -408,6 +409,12 @@ def bbp_k_tc_gemm_tile(bf16: bool, A, lda: int, Bt, ldb: int, C, ldc: int, M: in
 
 def bbp_set_fuse_cache(ctx, max_bytes: int):
     _check(lib().bbp_set_fuse_cache(ctx, int(max_bytes)), ctx)
+
+
+def bbp_share_workers(ctxs, groups: int):
+    n = len(ctxs)
+    arr = (_vp * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    _check(lib().bbp_share_workers(arr, n, int(groups)))
 
 
 def bbp_batch_single_launch(on: bool):

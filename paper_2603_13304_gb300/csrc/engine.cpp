@@ -204,6 +204,7 @@ bool Engine::deferred(Deferred& d) const {
   d.tol_dev = tol_dev;
   d.word_dev = tol_dev + 4;
   d.host_word = h_word;
+  d.pool = workers.get();
   return g.graph != nullptr;
 }
 
@@ -212,6 +213,7 @@ int Engine::defer_before(cudaStream_t batch) {
   if (!root_pre) CK(cudaEventCreateWithFlags(&root_pre, cudaEventDisableTiming));
   CK(cudaEventRecord(root_pre, root));
   CK(cudaStreamWaitEvent(batch, root_pre, 0));
+  if (workers) CK(cudaStreamWaitEvent(batch, workers->last_done, 0));
   return 0;
 }
 
@@ -219,6 +221,7 @@ int Engine::defer_after(cudaStream_t batch) {
   DeviceScope ds(device);
   CK(cudaEventRecord(root_out, batch));
   CK(cudaStreamWaitEvent(root, root_out, 0));
+  if (workers) CK(cudaEventRecord(workers->last_done, batch));
   pending_launch = false;
   return 0;
 }
@@ -247,7 +250,7 @@ unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int
   mix((unsigned long long)hermitise);
   mix((unsigned long long)nstreams);
   mix((unsigned long long)(uintptr_t)dist_dev.p);
-  for (int i = 0; i < nstreams; ++i) mix((unsigned long long)(uintptr_t)pool[i]->arena.p);
+  for (int i = 0; i < nstreams; ++i) mix((unsigned long long)(uintptr_t)workers->w[i]->arena.p);
   for (const SweepJob& j : jobs) {
     mix((unsigned long long)(uintptr_t)j.plan);
     for (const void* p : j.node_tensor) mix((unsigned long long)(uintptr_t)p);
@@ -286,7 +289,8 @@ unsigned long long Engine::input_signature(int nstreams) const {
   mix((unsigned long long)hermitise);
   mix((unsigned long long)nstreams);
   mix((unsigned long long)(uintptr_t)dist_dev.p);
-  for (int i = 0; i < nstreams && i < (int)pool.size(); ++i) mix((unsigned long long)(uintptr_t)pool[i]->arena.p);
+  for (int i = 0; workers && i < nstreams && i < (int)workers->w.size(); ++i)
+    mix((unsigned long long)(uintptr_t)workers->w[i]->arena.p);
   for (const auto& kv : msgs) {
     const Message& m = kv.second;
     mix((unsigned long long)m.cur);
@@ -313,23 +317,49 @@ Engine::~Engine() {
   if (root_out) cudaEventDestroy(root_out);
   if (root_pre) cudaEventDestroy(root_pre);
   if (h_word) cudaFreeHost(h_word);
-  for (SweepWork* w : pool) {
-    if (w->stream) cudaStreamSynchronize(w->stream);
-    w->arena.release();
-    if (w->done) cudaEventDestroy(w->done);
-    if (w->stream) cudaStreamDestroy(w->stream);
-    delete w;
+  workers.reset();
+}
+
+WorkerPool::WorkerPool() { cudaEventCreateWithFlags(&last_done, cudaEventDisableTiming); }
+
+WorkerPool::~WorkerPool() {
+  if (last_done) {
+    cudaEventSynchronize(last_done);
+    cudaEventDestroy(last_done);
+  }
+  for (SweepWork* x : w) {
+    if (x->stream) cudaStreamSynchronize(x->stream);
+    x->arena.release();
+    if (x->done) cudaEventDestroy(x->done);
+    if (x->stream) cudaStreamDestroy(x->stream);
+    delete x;
   }
 }
 
+WorkerPool& Engine::pool_ref() {
+  if (!workers) workers = std::make_shared<WorkerPool>();
+  return *workers;
+}
+
+int Engine::use_workers(std::shared_ptr<WorkerPool> p) {
+  DeviceScope ds(device);
+  if (root) CK(cudaStreamSynchronize(root));
+  if (stream) CK(cudaStreamSynchronize(stream));
+  if (workers) CK(cudaEventSynchronize(workers->last_done));
+  drop_graphs();
+  workers = p ? std::move(p) : std::make_shared<WorkerPool>();
+  return 0;
+}
+
 SweepWork* Engine::work(size_t i) {
-  while (pool.size() <= i) {
+  WorkerPool& P = pool_ref();
+  while (P.w.size() <= i) {
     SweepWork* w = new SweepWork();
     if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) { delete w; return nullptr; }
     cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming);
-    pool.push_back(w);
+    P.w.push_back(w);
   }
-  return pool[i];
+  return P.w[i];
 }
 
 int Engine::create(int lattice, int Lx, int Ly, int periodic, int d_, int D_, const double* host_t, cudaStream_t s) {
@@ -773,10 +803,11 @@ int Engine::reserve_workers(const std::vector<SweepJob>& jobs, int nstreams) {
   for (int i = 0; i < nstreams; ++i) {
     size_t need[7] = {1, 1, 1, 256, 4, 16, 0};
     for (size_t j = i; j < jobs.size(); j += nstreams) job_needs(jobs[j], need);
-    SweepWork& w = *pool[i];
+    SweepWork& w = *workers->w[i];
     if (w.elem == elem() && need[0] <= w.cap_t && need[1] <= w.cap_seg && need[2] <= w.cap_x &&
         need[3] <= w.svd_bytes && need[4] <= w.nslots && need[5] <= w.cap_d && need[6] <= w.tc_bytes && w.arena.p)
       continue;
+    CK(cudaEventSynchronize(workers->last_done));   // (another context's graph may still use it)
     CK(cudaStreamSynchronize(w.stream));
     CK(cudaStreamSynchronize(stream));
     if (!w.reserve(elem(), need[0], need[1], need[2], need[3], need[4], need[5], need[6]))
@@ -1071,6 +1102,7 @@ int Engine::iter_end() {
 
 int Engine::iter_launch() {
   DeviceScope ds(device);
+  std::lock_guard<std::mutex> lk(pool_ref().mu);
   return precision == 0 ? iter_launch_t<double2>() : iter_launch_t<float2>();
 }
 
@@ -1086,6 +1118,7 @@ int Engine::iter_launch_t() {
   const int nstreams = std::max(1, std::min(nu, max_streams));
   for (int i = 0; i < nstreams; ++i)
     if (!work(i)) return fail(this, 3, "stream creation failed");
+  CK(cudaStreamWaitEvent(root, workers->last_done, 0));   // the pool's previous user
   sweep_launches = 0;
   sweep_flops = 0.0;
   if (use_graphs) {
@@ -1115,6 +1148,7 @@ int Engine::iter_launch_t() {
       CK(cudaGraphLaunch(g.exec, root));
       CK(cudaMemcpyAsync(h_word + 1, word_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, root));
       CK(cudaEventRecord(root_out, root));
+      CK(cudaEventRecord(workers->last_done, root));
       return 0;
     }
   }
@@ -1150,10 +1184,10 @@ int Engine::iter_launch_t() {
   // fork onto the worker streams, one sweep and one finalisation per update, join
   auto enqueue = [&]() -> int {
     CK(cudaEventRecord(fork, root));
-    for (int i = 0; i < nstreams; ++i) CK(cudaStreamWaitEvent(pool[i]->stream, fork, 0));
+    for (int i = 0; i < nstreams; ++i) CK(cudaStreamWaitEvent(workers->w[i]->stream, fork, 0));
     int e = 0;
     for (int u = 0; u < nu && !e; ++u) {
-      SweepWork& w = *pool[u % nstreams];
+      SweepWork& w = *workers->w[u % nstreams];
       const auto& up = ups[u];
       Message& dst = msgs.at({up.recv_block, up.recv_face});
       if ((e = run_sweep<C>(jobs[u], w))) break;
@@ -1161,8 +1195,8 @@ int Engine::iter_launch_t() {
       CK(cudaMemcpyAsync(status_dev + 2 * u, w.status, 2 * sizeof(int), cudaMemcpyDeviceToDevice, w.stream));
     }
     for (int i = 0; i < nstreams; ++i) {
-      CK(cudaEventRecord(pool[i]->done, pool[i]->stream));
-      CK(cudaStreamWaitEvent(root, pool[i]->done, 0));
+      CK(cudaEventRecord(workers->w[i]->done, workers->w[i]->stream));
+      CK(cudaStreamWaitEvent(root, workers->w[i]->done, 0));
     }
     if (!e) {
       CK(launch_iter_reduce((const double*)dist_dev.p, status_dev, nu, tol_dev, word_dev, root));
@@ -1243,6 +1277,7 @@ int Engine::iter_launch_t() {
   if (rc) return rc;
   CK(cudaMemcpyAsync(h_word + 1, word_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, root));
   CK(cudaEventRecord(root_out, root));
+  CK(cudaEventRecord(workers->last_done, root));
   launched_parity = parity;
   in_flight = true;
   return 0;
@@ -1321,8 +1356,10 @@ int Engine::contract_batch_t(const std::vector<std::vector<std::array<int, 2>>>&
   re.assign(nj, 0.0);
   im.assign(nj, 0.0);
   const int nstreams = std::max(1, std::min(nj, 16));
+  std::lock_guard<std::mutex> lk(pool_ref().mu);
   for (int i = 0; i < nstreams; ++i)
     if (!work(i)) return fail(this, 3, "stream creation failed");
+  CK(cudaStreamWaitEvent(stream, workers->last_done, 0));   // the pool's previous user
   cudaEvent_t fork;
   CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
   DBuf res;
@@ -1351,10 +1388,10 @@ int Engine::contract_batch_t(const std::vector<std::vector<std::array<int, 2>>>&
   if (!rc) rc = reserve_workers(jobs, nstreams);
   if (!rc) {
     CK(cudaEventRecord(fork, stream));
-    for (int i = 0; i < nstreams; ++i) CK(cudaStreamWaitEvent(pool[i]->stream, fork, 0));
+    for (int i = 0; i < nstreams; ++i) CK(cudaStreamWaitEvent(workers->w[i]->stream, fork, 0));
   }
   for (int j = 0; j < nj && !rc; ++j) {
-    SweepWork& w = *pool[j % nstreams];
+    SweepWork& w = *workers->w[j % nstreams];
     SweepJob& job = jobs[j];
     if ((rc = run_sweep<C>(job, w))) break;
     ChainDesc A{}, B{};
@@ -1381,9 +1418,10 @@ int Engine::contract_batch_t(const std::vector<std::vector<std::array<int, 2>>>&
     CK(cudaMemcpyAsync(rp + 3, w.status, sizeof(int), cudaMemcpyDeviceToDevice, w.stream));
   }
   for (int i = 0; i < nstreams; ++i) {
-    CK(cudaEventRecord(pool[i]->done, pool[i]->stream));
-    CK(cudaStreamWaitEvent(stream, pool[i]->done, 0));
+    CK(cudaEventRecord(workers->w[i]->done, workers->w[i]->stream));
+    CK(cudaStreamWaitEvent(stream, workers->w[i]->done, 0));
   }
+  CK(cudaEventRecord(workers->last_done, stream));
   std::vector<double> h(4 * (size_t)nj);
   if (!rc) CK(cudaMemcpyAsync(h.data(), res.p, sizeof(double) * 4 * nj, cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));

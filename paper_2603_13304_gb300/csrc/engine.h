@@ -10,6 +10,8 @@
 
 #include <array>
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <map>
 #include <string>
 #include <vector>
@@ -74,6 +76,20 @@ struct SweepWork {
                size_t tc_bytes);
 };
 
+// The worker streams and workspace arenas of one or more contexts.  Contexts
+// that share a pool (bbp_share_workers) run their iterations one after
+// another: every use locks the pool on the host, waits for last_done and
+// records it again when its work is enqueued.
+struct WorkerPool {
+  std::vector<SweepWork*> w;
+  cudaEvent_t last_done = nullptr;
+  std::mutex mu;
+  WorkerPool();
+  ~WorkerPool();
+  WorkerPool(const WorkerPool&) = delete;
+  WorkerPool& operator=(const WorkerPool&) = delete;
+};
+
 struct SweepJob {
   const SweepPlan* plan = nullptr;
   ShapeTrace tr;
@@ -109,7 +125,7 @@ class Engine {
   std::map<std::pair<int, int>, Message> msgs;  // incoming message per (block, face)
   std::map<std::pair<int, int>, SweepPlan> plans;   // (block, face) -> plan (single-block regions)
   std::vector<Region> block_regions;                // single-block region per block
-  std::vector<SweepWork*> pool;
+  std::shared_ptr<WorkerPool> workers;
   DBuf dist_dev, op_dev;
   long long launches_per_iter = 0;
   double flops_per_iter = 0.0;
@@ -205,6 +221,7 @@ class Engine {
     double* tol_dev = nullptr;         // <- host_word[0], 8 bytes, before the graph
     double* word_dev = nullptr;        // -> host_word + 1, 16 bytes, after it
     double* host_word = nullptr;
+    const void* pool = nullptr;        // contexts of one worker pool run in launch order
   };
   bool deferred(Deferred& d) const;
   // orders the batch stream after this context's root stream, and the root
@@ -212,6 +229,10 @@ class Engine {
   int defer_before(cudaStream_t batch);
   int defer_after(cudaStream_t batch);
   unsigned long long uid() const { return uid_; }
+  // join a worker pool (null: a private one again); waits for this
+  // context's work in flight
+  int use_workers(std::shared_ptr<WorkerPool> p);
+  WorkerPool& pool_ref();
 
  private:
   unsigned long long iter_signature(const std::vector<SweepJob>& jobs, int nstreams) const;

@@ -290,12 +290,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_qr(const C* __restri
       // the reflector of step j from the norm of x and alpha = A[j][j]
       R M = 0, S = 0;
       for (int q = 0; q < cs; ++q) M = fmax(M, pp[par * cs + q].x);
-      if (M > 0)
+      if (M > 0) {
+        const R iM = (R)1 / M;           // (the scales are powers of two: exact)
         for (int q = 0; q < cs; ++q) {
           const C np = pp[par * cs + q];
-          const R rq = np.x / M;
+          const R rq = np.x * iM;
           S += np.y * rq * rq;
         }
+      }
       const R xnorm = M * sqrt(S);
       const C alpha = rowb[(size_t)par * n + j];
       const R ar = alpha.x, ai = alpha.y;
@@ -304,8 +306,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_qr(const C* __restri
         // beta = -sign(ar) |(alpha, x)| from scaled terms; alpha - beta
         // scaled by 1 / |beta| (|alpha - beta| >= |beta|), so that nothing
         // overflows or underflows
-        const R mx = fmax(fmax(fabs(ar), fabs(ai)), xnorm);
-        const R u = ar / mx, w = ai / mx, z = xnorm / mx;
+        const R mx = fmax(fmax(fabs(ar), fabs(ai)), xnorm), imx = (R)1 / mx;
+        const R u = ar * imx, w = ai * imx, z = xnorm * imx;
         beta = -copysign(mx * sqrt(u * u + w * w + z * z), ar);
         const R ib = (R)1 / beta, sb = fabs(ib);
         const R dx = (ar - beta) * sb, dy = ai * sb, idd = sb / (dx * dx + dy * dy);

@@ -19,6 +19,8 @@
 #include <chrono>
 #include <cmath>
 #include <deque>
+#include <map>
+#include <memory>
 #include <mutex>
 #include <exception>
 #include <string>
@@ -109,13 +111,18 @@ int launch_round(bbp_ctx** ctxs, const std::vector<int>& idx, const std::vector<
     cudaGraph_t G = nullptr;
     if (cudaGraphCreate(&G, 0) != cudaSuccess) return BBP_ERR_CUDA;
     bool ok = true;
+    std::map<const void*, cudaGraphNode_t> last;   // contexts of one worker pool run one after another
     for (size_t a = 0; a < ds.size() && ok; ++a) {
       cudaGraphNode_t n1, n2, n3;
-      ok = cudaGraphAddMemcpyNode1D(&n1, G, nullptr, 0, ds[a].tol_dev, ds[a].host_word, sizeof(double),
-                                    cudaMemcpyHostToDevice) == cudaSuccess &&
+      auto it = last.find(ds[a].pool);
+      const bool chained = it != last.end();
+      cudaGraphNode_t prev = chained ? it->second : nullptr;
+      ok = cudaGraphAddMemcpyNode1D(&n1, G, chained ? &prev : nullptr, chained ? 1 : 0, ds[a].tol_dev,
+                                    ds[a].host_word, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
            cudaGraphAddChildGraphNode(&n2, G, &n1, 1, ds[a].graph) == cudaSuccess &&
            cudaGraphAddMemcpyNode1D(&n3, G, &n2, 1, ds[a].host_word + 1, ds[a].word_dev, 2 * sizeof(double),
                                     cudaMemcpyDeviceToHost) == cudaSuccess;
+      if (ok) last[ds[a].pool] = n3;
     }
     if (ok) ok = cudaGraphInstantiate(&exec, G, 0) == cudaSuccess;
     cudaGraphDestroy(G);
@@ -140,6 +147,42 @@ int launch_round(bbp_ctx** ctxs, const std::vector<int>& idx, const std::vector<
 }
 
 }  // namespace
+
+// Worker pools shared by groups of contexts: heaviest first, dealt round
+// the groups back and forth, so that every group gets a like mix (its arenas
+// sized by its heaviest member) and the groups' serial chains balance.
+extern "C" bbp_status bbp_share_workers(bbp_ctx** ctxs, int n, int groups) {
+  if (!ctxs || n < 0 || groups < 0) return BBP_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return BBP_ERR_ARG;
+  try {
+    if (groups == 0) {
+      for (int i = 0; i < n; ++i)
+        if (ctxs[i]->eng.use_workers(nullptr)) return BBP_ERR_CUDA;
+      return BBP_OK;
+    }
+    std::vector<std::pair<double, int>> w(n);
+    for (int i = 0; i < n; ++i) {
+      const bbp::Engine& e = ctxs[i]->eng;
+      const double D2 = (double)e.D * e.D;
+      w[i] = {(double)e.geom.lat.n_sites() * (double)e.chi * e.chi * D2 * std::max(D2, (double)e.chi), i};
+    }
+    std::sort(w.begin(), w.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<std::shared_ptr<bbp::WorkerPool>> pools(std::min(groups, std::max(n, 1)));
+    for (auto& p : pools) p = std::make_shared<bbp::WorkerPool>();
+    const int G = (int)pools.size();
+    for (int r = 0; r < n; ++r) {
+      const int lap = r / G, pos = r % G;
+      const int g = (lap & 1) ? G - 1 - pos : pos;
+      if (ctxs[w[r].second]->eng.use_workers(pools[g])) return BBP_ERR_CUDA;
+    }
+    return BBP_OK;
+  } catch (const std::bad_alloc&) {
+    return BBP_ERR_OOM;
+  } catch (...) {
+    return BBP_ERR_CUDA;
+  }
+}
 
 extern "C" bbp_status bbp_batch_single_launch(int on) {
   g_single_launch.store(on != 0);

@@ -119,6 +119,37 @@ def test_batch_single_launch_matches_separate():
         assert d < tol and de < tol
 
 
+@pytest.mark.parametrize("single", [True, False])
+def test_shared_workers_match_private(single):
+    """Contexts dealt into two shared worker pools (their iterations one after
+    another on the pool's streams and arenas) compute what they compute with
+    private pools, with the round as one graph launch or separate launches."""
+    specs = [spec(*a) for a in SPECS]
+    out = {}
+    P.bbp_batch_single_launch(single)
+    try:
+        for shared in (False, True):
+            ctxs = [make_ctx(s) for s in specs]
+            try:
+                if shared:
+                    P.bbp_share_workers(ctxs, 2)
+                for _ in range(8):
+                    rc, iters, errs, st = P.bbp_batch_iterate(ctxs, 0.0, 1)
+                    assert rc in (0, 6)
+                out[shared] = [(messages(c), P.bbp_energy_per_site(c)) for c in ctxs]
+            finally:
+                for c in ctxs:
+                    P.bbp_destroy(c)
+    finally:
+        P.bbp_batch_single_launch(True)
+    for i, s in enumerate(specs):
+        tol = 1e-10 if s["precision"] == P.FP64 else 1e-6
+        d = diff(out[False][i][0], out[True][i][0])
+        de = abs(out[False][i][1] - out[True][i][1])
+        print(f"job {i}: shared vs private workers (single launch {single}): message diff {d:.2e}, |dE| {de:.2e}")
+        assert d < tol and de < tol
+
+
 def run_server(specs, budget=1 << 36, max_active=64, iters=6, stagger=0):
     srv = P.bbp_server_create(budget, max_active)
     ids = []
