@@ -122,6 +122,11 @@ KERNELS = {
     "gemm": (6, "every SIMT complex GEMM (k_gemm)"),
 }
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu captures summarised under profiles/, keyed by (kernel class,
+# workload, precision); an entry is removed when its kernel changes.
+TRAFFIC = {}
+
 # TF32 / BF16 dense tensor rates of the part, nominal (for the ratio only)
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 
@@ -255,19 +260,26 @@ def run_ours(args, rank, world):
     # second pass, same steps, with the dominant kernel class bracketed by
     # CUDA events on its own streams (events in the graph perturb the step,
     # so the headline value above is taken without them)
-    P.bbp_ktimer_select(cls)
-    P.bbp_set_execution(ctx, not args.no_graphs, 16)   # recapture with the event nodes
-    P.bbp_iterate(ctx, 0.0, 1)
-    P.bbp_ktimer_read()
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
+    def timer_pass(c):
+        P.bbp_ktimer_select(c)
+        P.bbp_set_execution(ctx, not args.no_graphs, 16)   # recapture with the event nodes
         P.bbp_iterate(ctx, 0.0, 1)
-    torch.cuda.synchronize()
-    timer_pass_secs = time.perf_counter() - t1
-    k_n, k_ms, k_flops = P.bbp_ktimer_read()
-    P.bbp_ktimer_select(0)
+        P.bbp_ktimer_read()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            P.bbp_iterate(ctx, 0.0, 1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        out = P.bbp_ktimer_read() + (dt,)
+        P.bbp_ktimer_select(0)
+        return out
+
+    k_n, k_ms, k_flops, timer_pass_secs = timer_pass(cls)
+    # the tensor-core GEMM beside the dominant kernel, in the tensor modes
+    tc_pass = timer_pass(KERNELS["tc"][0]) if (args.precision in ("tf32", "bf16") and args.roofline_kernel != "tc") \
+        else None
     secs = max_over_ranks(secs, world)
     value = world * n_updates * args.steps / secs
     energy = P.bbp_energy_per_site(ctx) if rank == 0 else None
@@ -298,34 +310,40 @@ def run_ours(args, rank, world):
 
     acc = accuracy_vs_oracle(P, w, prec) if rank == 0 else None
 
-    roof = None
-    if rank == 0 and k_n > 0:
+    def roofline(kname, k_n, k_ms, k_flops, pass_secs):
         pk = peaks()
-        tensor = args.roofline_kernel == "tc"
+        tensor = kname == "tc"
         bound, unit = ("tensor", "TFLOP/s") if tensor else ("alu", "TFLOP/s")
         key = (args.precision if args.precision in ("tf32", "bf16") else "tf32") if tensor else (
             "fp64" if args.precision == "fp64" else "fp32")
         per_launch_s = k_ms * 1e-3 / k_n
-        # the library credits each tensor-core launch with its algorithmic
-        # complex flops; the split operands execute three real products per
+        # the library credits each launch with its algorithmic complex flops;
+        # the split tensor-core operands execute three real products per
         # complex product in TF32 (six in BF16)
         split = (6.0 if args.precision == "bf16" else 3.0) if tensor else 1.0
         achieved = k_flops / k_n / per_launch_s / 1e12
-        roof = {"bound": bound, "achieved": achieved, "peak": pk[key], "unit": unit, "frac": achieved / pk[key],
-                "traffic": None, "kernel": kdesc,
-                "peak_kind": (key + " dense, of measured (bf16 burst x nominal tf32/bf16 ratio)" if key == "tf32"
-                              else "bf16 dense burst, of measured") if tensor else key + ", " + pk[key + "_kind"],
-                "flops_kind": "algorithmic complex flops (8 per complex multiply-add)",
-                "executed_tensor_frac": achieved * split / pk[key] if tensor else None,
-                "launches_per_step": k_n / args.steps, "launch_us": per_launch_s * 1e6,
-                "kernel_ms_per_step_all_streams": k_ms / args.steps,
-                "timer_pass_ms_per_step": 1e3 * timer_pass_secs / args.steps}
+        tr = TRAFFIC.get((kname, args.workload, args.precision))
+        r = {"bound": bound, "achieved": achieved, "peak": pk[key], "unit": unit, "frac": achieved / pk[key],
+             "traffic": tr["bytes"] if tr else None, "kernel": KERNELS[kname][1],
+             "peak_kind": (key + " dense, of measured (bf16 burst x nominal tf32/bf16 ratio)" if key == "tf32"
+                           else "bf16 dense burst, of measured") if tensor else key + ", " + pk[key + "_kind"],
+             "flops_kind": "algorithmic complex flops (8 per complex multiply-add)",
+             "executed_tensor_frac": achieved * split / pk[key] if tensor else None,
+             "launches_per_step": k_n / args.steps, "launch_us": per_launch_s * 1e6,
+             "kernel_ms_per_step_all_streams": k_ms / args.steps,
+             "timer_pass_ms_per_step": 1e3 * pass_secs / args.steps}
+        if tr:
+            r["traffic_note"] = tr["note"]
         if not tensor:
-            roof["frac_of_one_sm"] = achieved / (pk[key] / 152)
+            r["frac_of_one_sm"] = achieved / (pk[key] / 152)
+        return r
+
+    roof = roofline(args.roofline_kernel, k_n, k_ms, k_flops, timer_pass_secs) if rank == 0 and k_n > 0 else None
+    roof_tc = roofline("tc", *tc_pass) if rank == 0 and tc_pass and tc_pass[0] > 0 else None
     return {
         "value": value, "secs": secs, "host_secs": host_secs, "step_ms": step_ms, "n_updates": n_updates, "n_sites": n_sites, "energy": energy,
         "clocks": clk.summary(), "launches": launches, "flops_iter": flops_iter, "e2e": e2e, "roofline": roof,
-        "accuracy": acc,
+        "roofline_tc": roof_tc, "accuracy": acc,
     }
 
 
@@ -564,7 +582,7 @@ def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, 
             tpl = arrivals[k][1]
             if tpl not in served_e and r["status"] in (0, 6):
                 ctx = P.bbp_server_take(srv, r["id"], keep_context=True)
-                served_e[tpl] = (P.bbp_energy_per_site(ctx), r["iters"])
+                served_e[tpl] = (P.bbp_energy_per_site(ctx), r["iters"], r["err"])
                 P.bbp_destroy(ctx)
             else:
                 P.bbp_server_take(srv, r["id"])
@@ -582,6 +600,7 @@ def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, 
     prec64 = 0
     svc = {}
     e64 = {}
+    e64_detail = []
     tpl_iters = {}
     for k in done:
         tpl_iters.setdefault(arrivals[k][1], iters[k])
@@ -616,11 +635,16 @@ def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, 
         svc[tpl] = per_it * tpl_iters.get(tpl, max_iter)
         if tpl in sample and served_e[tpl][1] <= 40 and per_it * served_e[tpl][1] < 60.0:
             c = make_network(P, j, prec64, 16)
+            it64, err64 = 0, float("nan")
             try:
-                P.bbp_iterate(c, tol, served_e[tpl][1])
+                it64, err64, _ = P.bbp_iterate(c, tol, served_e[tpl][1])
             except P.BBPError:
                 pass
-            e64[tpl] = abs(P.bbp_energy_per_site(c) - served_e[tpl][0])
+            e_fp64 = P.bbp_energy_per_site(c)
+            e64[tpl] = abs(e_fp64 - served_e[tpl][0])
+            e64_detail.append({"template": j["kind"] + f" D={j['D']} chi={j['chi']}", "served_iters": served_e[tpl][1],
+                               "served_err": served_e[tpl][2], "fp64_iters": int(it64), "fp64_err": float(err64),
+                               "abs_d_energy": e64[tpl]})
             P.bbp_destroy(c)
     clock, seq = 0.0, []
     for k, (ta, tpl) in enumerate(arrivals if fp64_baseline else []):
@@ -639,7 +663,9 @@ def run_serving(duration_s, rate, precision, tol=1e-8, max_iter=30, warm_s=5.0, 
             "mean_iters": float(np.mean([iters[k] for k in done])) if done else None,
             "wall_s": round(wall, 1), "drain_s": drain_s,
             "energy_err_vs_fp64": {"max": max(e64.values()) if e64 else None, "templates": len(e64),
-                                   "within_1e-5": sum(1 for v in e64.values() if v <= 1e-5)},
+                                   "within_1e-5": sum(1 for v in e64.values() if v <= 1e-5),
+                                   "detail": e64_detail},
+            "jobs_finished_all": len(lat),
             "one_at_a_time_fp64": {"p50_ms": 1e3 * float(np.percentile(S, 50)),
                                    "p99_ms": 1e3 * float(np.percentile(S, 99)),
                                    "throughput_jobs_per_s": len(arrivals) / clock if clock > 0 else None,
@@ -791,15 +817,27 @@ def kernel_case(which: str):
         run = lambda: P.bbp_k_tc_absorb(0, 1, X.data_ptr(), Pd, Q, S.data_ptr(), l, r, R.data_ptr(), wk.data_ptr(),   # noqa: E731
                                         err.data_ptr())
         work = f"{8.0 * l * Pd * Q * r / 1e9:.1f} GFLOP complex"
-    elif which == "panel":
+    elif which in ("panel", "panel_r"):
         m, n = 2304, 96
         A = torch.randn(m, n, dtype=torch.complex64, device="cuda", generator=g)
-        Qm = torch.empty_like(A)
+        Qm = torch.empty_like(A) if which == "panel" else None
         Rm = torch.empty(n, n, dtype=torch.complex64, device="cuda")
-        run = lambda: P.bbp_k_panel_qr(True, A.data_ptr(), m, n, Qm.data_ptr(), Rm.data_ptr(), 1, 0)   # noqa: E731
-        work = f"{m}x{n} complex64 panel, cluster {P.bbp_k_panel_cluster(True, m, n)}+"
+        qp = Qm.data_ptr() if Qm is not None else None
+        run = lambda: P.bbp_k_panel_qr(True, A.data_ptr(), m, n, qp, Rm.data_ptr(), 1, 0)   # noqa: E731
+        work = f"{m}x{n} complex64 panel ({'Q and R' if Qm is not None else 'R only'})"
+    elif which == "svd":
+        m = n = 2304
+        chi = 64
+        A = torch.randn(m, n, dtype=torch.complex64, device="cuda", generator=g)
+        U = torch.empty(m, chi, dtype=torch.complex64, device="cuda")
+        Rm = torch.empty(chi, n, dtype=torch.complex64, device="cuda")
+        wk = torch.empty(P.bbp_k_svd_work_bytes_rand(True, m, n, chi, False), dtype=torch.uint8, device="cuda")
+        st = torch.zeros(4, dtype=torch.int32, device="cuda")
+        run = lambda: P.bbp_k_svd_trunc_rand(True, A.data_ptr(), m, n, chi, U.data_ptr(), Rm.data_ptr(),   # noqa: E731
+                                             wk.data_ptr(), st.data_ptr(), 1, False, None)
+        work = f"complex64 randomised truncation of a {m}x{n} split to chi = {chi} (b = 96, one power step)"
     else:
-        raise SystemExit("kernel case: fuse, absorb or panel")
+        raise SystemExit("kernel case: fuse, absorb, panel, panel_r or svd")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for i in range(3):
         if i == 2:
@@ -820,7 +858,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16", "fp32", "fp64"])
     ap.add_argument("--roofline-kernel", default=None, choices=sorted(KERNELS),
-                    help="kernel class timed for the roofline (default: tc for tf32/bf16, else orth)")
+                    help="kernel class timed for the roofline (default: orth, the cluster panel QR)")
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="networks in the batched measurement (0: skip)")
     ap.add_argument("--batch-rounds", type=int, default=2, help="timed rounds of the batched measurement")
@@ -835,13 +873,14 @@ def main():
                     help="run only the batched or the serving measurement and print it")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--peaks", action="store_true", help="measure the chip's ALU and tensor rates and exit")
-    ap.add_argument("--kernel-case", choices=["fuse", "absorb", "panel"], help="run one kernel alone and exit")
+    ap.add_argument("--kernel-case", choices=["fuse", "absorb", "panel", "panel_r", "svd"],
+                    help="run one kernel alone and exit")
     args = ap.parse_args()
     if args.kernel_case:
         kernel_case(args.kernel_case)
         return
     if args.roofline_kernel is None:
-        args.roofline_kernel = "tc" if args.precision in ("tf32", "bf16") else "orth"
+        args.roofline_kernel = "orth"     # the cluster panel QR: the largest share of every step
     if args.peaks:
         print(json.dumps(measure_peaks()))
         return
@@ -928,7 +967,8 @@ def main():
                        execution="eager launches" if args.no_graphs else "CUDA-graph replay of each iteration",
                        streams=16),
         "clocks": res["clocks"], "e2e": res["e2e"], "gpu_launches": res["launches"] * args.steps,
-        "roofline": res["roofline"], "cpu_baseline": cpu, "accuracy_vs_oracle": res["accuracy"],
+        "roofline": res["roofline"], "roofline_tensor_gemm": res["roofline_tc"], "cpu_baseline": cpu,
+        "accuracy_vs_oracle": res["accuracy"],
         "energy_per_site": res["energy"], "absorb_tflop_per_step": res["flops_iter"] / 1e12,
         "batched": batched, "serving": serving,
     }

@@ -221,7 +221,33 @@ int Engine::defer_after(cudaStream_t batch) {
   DeviceScope ds(device);
   CK(cudaEventRecord(root_out, batch));
   CK(cudaStreamWaitEvent(root, root_out, 0));
-  if (workers) CK(cudaEventRecord(workers->last_done, batch));
+  if (workers) {
+    std::lock_guard<std::mutex> lk(workers->mu);
+    CK(cudaEventRecord(workers->last_done, batch));
+    auto& pv = workers->pending;
+    pv.erase(std::remove(pv.begin(), pv.end(), this), pv.end());
+  }
+  pending_launch = false;
+  return 0;
+}
+
+int Engine::launch_deferred_now() {
+  DeviceScope ds(device);
+  if (!pending_launch) return 0;
+  IterGraph& g = graphs[launched_parity];
+  const int nu = (int)geom.updates().size();
+  double* tol_dev = (double*)((char*)dist_dev.p + ((sizeof(double) * nu + 2 * sizeof(int) * nu + 255) & ~size_t(255)));
+  double* word_dev = tol_dev + 4;
+  if (!g.exec) {
+    const cudaError_t ce = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (ce != cudaSuccess) return fail(this, 3, std::string("graph instantiation: ") + cudaGetErrorString(ce));
+  }
+  CK(cudaStreamWaitEvent(root, workers->last_done, 0));
+  CK(cudaMemcpyAsync(tol_dev, h_word, sizeof(double), cudaMemcpyHostToDevice, root));
+  CK(cudaGraphLaunch(g.exec, root));
+  CK(cudaMemcpyAsync(h_word + 1, word_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, root));
+  CK(cudaEventRecord(root_out, root));
+  CK(cudaEventRecord(workers->last_done, root));
   pending_launch = false;
   return 0;
 }
@@ -307,6 +333,11 @@ unsigned long long Engine::input_signature(int nstreams) const {
 }
 
 Engine::~Engine() {
+  if (workers) {
+    std::lock_guard<std::mutex> lk(workers->mu);
+    auto& pv = workers->pending;
+    pv.erase(std::remove(pv.begin(), pv.end(), this), pv.end());
+  }
   drop_graphs();
   if (root) {
     cudaStreamSynchronize(root);
@@ -807,7 +838,16 @@ int Engine::reserve_workers(const std::vector<SweepJob>& jobs, int nstreams) {
     if (w.elem == elem() && need[0] <= w.cap_t && need[1] <= w.cap_seg && need[2] <= w.cap_x &&
         need[3] <= w.svd_bytes && need[4] <= w.nslots && need[5] <= w.cap_d && need[6] <= w.tc_bytes && w.arena.p)
       continue;
-    CK(cudaEventSynchronize(workers->last_done));   // (another context's graph may still use it)
+    // the arenas move: iterations of the pool's other members that are
+    // bound to them and still wait for a batch launch run now, and every
+    // use of the old arenas completes first
+    for (Engine* e : workers->pending)
+      if (e != this)
+        if (int rc = e->launch_deferred_now()) return rc;
+    workers->pending.erase(std::remove_if(workers->pending.begin(), workers->pending.end(),
+                                          [this](Engine* e) { return e != this; }),
+                           workers->pending.end());
+    CK(cudaEventSynchronize(workers->last_done));
     CK(cudaStreamSynchronize(w.stream));
     CK(cudaStreamSynchronize(stream));
     if (!w.reserve(elem(), need[0], need[1], need[2], need[3], need[4], need[5], need[6]))
@@ -1135,6 +1175,7 @@ int Engine::iter_launch_t() {
       in_flight = true;
       if (defer_graph) {
         pending_launch = true;
+        workers->pending.push_back(this);
         return 0;
       }
       if (!g.exec) {
@@ -1265,6 +1306,7 @@ int Engine::iter_launch_t() {
       launched_parity = parity;
       in_flight = true;
       pending_launch = true;
+      workers->pending.push_back(this);
       return 0;
     }
     if (!g.exec) {
@@ -1295,6 +1337,11 @@ int Engine::iter_finish(double* err_out) {
   if (pending_launch) {
     in_flight = false;
     pending_launch = false;
+    if (workers) {
+      std::lock_guard<std::mutex> lk(workers->mu);
+      auto& pv = workers->pending;
+      pv.erase(std::remove(pv.begin(), pv.end(), this), pv.end());
+    }
     return fail(this, 8, "a deferred iteration was never launched");
   }
   in_flight = false;

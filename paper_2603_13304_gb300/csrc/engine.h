@@ -80,10 +80,12 @@ struct SweepWork {
 // that share a pool (bbp_share_workers) run their iterations one after
 // another: every use locks the pool on the host, waits for last_done and
 // records it again when its work is enqueued.
+class Engine;
 struct WorkerPool {
   std::vector<SweepWork*> w;
   cudaEvent_t last_done = nullptr;
   std::mutex mu;
+  std::vector<Engine*> pending;        // members whose deferred graph (bound to the arenas) awaits its launch
   WorkerPool();
   ~WorkerPool();
   WorkerPool(const WorkerPool&) = delete;
@@ -228,6 +230,9 @@ class Engine {
   // (and the iteration's completion event) after the batch's launch
   int defer_before(cudaStream_t batch);
   int defer_after(cudaStream_t batch);
+  // launches a deferred iteration on this context's own root stream now
+  // (the pool's lock held by the caller)
+  int launch_deferred_now();
   unsigned long long uid() const { return uid_; }
   // join a worker pool (null: a private one again); waits for this
   // context's work in flight

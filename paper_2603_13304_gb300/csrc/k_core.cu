@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <atomic>
 #include <cmath>
 
@@ -1730,7 +1731,7 @@ __global__ void k_permute3(const C* __restrict__ src, int d0, int d1, int d2, in
 // outputs over the cluster's threads and ends at a cluster barrier (the
 // intermediates live in the global work buffer), so the complex128 work of
 // one message runs on kK4Cluster SMs' FP64 units.
-constexpr int kK4Cluster = 8;
+constexpr int kK4Cluster = 16;   // (a non-portable cluster size, opted in per kernel)
 constexpr int kK4Split = 4;   // lanes per output of the r x r phase (divides 32)
 
 template <typename C>
@@ -2065,6 +2066,9 @@ cudaError_t init_kernel_attributes() {
   if ((e = smem_optin<k_jacobi_smem<double2>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_smem<float2>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_cut64>()) != cudaSuccess) return e;
+  for (const void* f : {(const void*)k_msg_normalise<double2>, (const void*)k_msg_normalise<float2>,
+                        (const void*)k_mps_dot<double2>, (const void*)k_mps_dot<float2>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
   if ((e = init_panel_attributes()) != cudaSuccess) return e;
   return init_tc_attributes();
 }

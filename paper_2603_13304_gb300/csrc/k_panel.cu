@@ -376,7 +376,49 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_qr(const C* __restri
       }
       mask_below(xm, j + 1);
       if (own && j + 1 < k) push_norm(par ^ 1, norm_part(xm));
-      for (int c = j + 2 + ((warp - (j + 2)) % nw + nw) % nw; c < n; c += nw) {
+      int c = j + 2 + ((warp - (j + 2)) % nw + nw) % nw;
+      if constexpr ((sizeof(R) == 4 && MAXR <= 6) || (sizeof(R) == 8 && MAXR <= 2)) {
+        // two columns at a time (two independent chains, one reduction
+        // tree for both dots: lanes 0-7 end with the first real part, 8-15
+        // its imaginary part, 16-31 the second column's)
+        for (; c + nw < n; c += 2 * nw) {
+          const int c2 = c + nw;
+          C y[MAXR], y2[MAXR];
+          load_col(c, y);
+          load_col(c2, y2);
+          const C f = fac(c), f2 = fac(c2);
+#pragma unroll
+          for (int i = 0; i < MAXR; ++i) {
+            y[i] = psub(y[i], pmul(v[i], f));
+            y2[i] = psub(y2[i], pmul(v[i], f2));
+          }
+          store_col(c, y);
+          store_col(c2, y2);
+          if (j + 1 < k) {
+            C d = pmulc(xm[0], y[0]), d2 = pmulc(xm[0], y2[0]);
+#pragma unroll
+            for (int i = 1; i < MAXR; ++i) {
+              d = padd(d, pmulc(xm[i], y[i]));
+              d2 = padd(d2, pmulc(xm[i], y2[i]));
+            }
+            const bool h4 = lane & 16, h3 = lane & 8;
+            R a0 = h4 ? d2.x : d.x, a1 = h4 ? d2.y : d.y;     // kept halves
+            a0 += __shfl_xor_sync(0xffffffffu, h4 ? d.x : d2.x, 16);
+            a1 += __shfl_xor_sync(0xffffffffu, h4 ? d.y : d2.y, 16);
+            R b = (h3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, h3 ? a0 : a1, 8);
+            b += __shfl_xor_sync(0xffffffffu, b, 4);
+            b += __shfl_xor_sync(0xffffffffu, b, 2);
+            b += __shfl_xor_sync(0xffffffffu, b, 1);
+            const C s1 = mkc<C>(__shfl_sync(0xffffffffu, b, 0), __shfl_sync(0xffffffffu, b, 8));
+            const C s2 = mkc<C>(__shfl_sync(0xffffffffu, b, 16), __shfl_sync(0xffffffffu, b, 24));
+            push_recv(par ^ 1, c, s1);
+            push_recv(par ^ 1, c2, s2);
+            push_row(y, j + 1, par ^ 1, c);
+            push_row(y2, j + 1, par ^ 1, c2);
+          }
+        }
+      }
+      for (; c < n; c += nw) {
         C y[MAXR];
         load_col(c, y);
         const C f = fac(c);

@@ -119,12 +119,15 @@ def test_batch_single_launch_matches_separate():
         assert d < tol and de < tol
 
 
-@pytest.mark.parametrize("single", [True, False])
-def test_shared_workers_match_private(single):
-    """Contexts dealt into two shared worker pools (their iterations one after
+@pytest.mark.parametrize("single,groups", [(True, 2), (False, 2), (True, 1)])
+def test_shared_workers_match_private(single, groups):
+    """Contexts dealt into shared worker pools (their iterations one after
     another on the pool's streams and arenas) compute what they compute with
-    private pools, with the round as one graph launch or separate launches."""
-    specs = [spec(*a) for a in SPECS]
+    private pools, with the round as one graph launch or separate launches.
+    With one pool, the small networks settle (and defer their replayed
+    iterations to the round's launch) while the larger ones still grow the
+    pool's arenas in the same round."""
+    specs = [spec(*a) for a in SPECS] + [spec("kagome", 7, 3, 16, P.TF32)]
     out = {}
     P.bbp_batch_single_launch(single)
     try:
@@ -132,7 +135,7 @@ def test_shared_workers_match_private(single):
             ctxs = [make_ctx(s) for s in specs]
             try:
                 if shared:
-                    P.bbp_share_workers(ctxs, 2)
+                    P.bbp_share_workers(ctxs, groups)
                 for _ in range(8):
                     rc, iters, errs, st = P.bbp_batch_iterate(ctxs, 0.0, 1)
                     assert rc in (0, 6)
@@ -146,7 +149,8 @@ def test_shared_workers_match_private(single):
         tol = 1e-10 if s["precision"] == P.FP64 else 1e-6
         d = diff(out[False][i][0], out[True][i][0])
         de = abs(out[False][i][1] - out[True][i][1])
-        print(f"job {i}: shared vs private workers (single launch {single}): message diff {d:.2e}, |dE| {de:.2e}")
+        print(f"job {i}: shared vs private workers ({groups} pools, single launch {single}): message diff {d:.2e}, "
+              f"|dE| {de:.2e}")
         assert d < tol and de < tol
 
 
