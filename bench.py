@@ -418,12 +418,17 @@ def run_batched(n_networks, steps, warmup, precision, seed=4, groups=0):
     if groups:
         P.bbp_share_workers(ctxs, groups)
     setup_s = time.perf_counter() - t0
+    def note(msg):                     # progress on stderr (the JSON line goes to stdout)
+        print(f"[batched] {time.perf_counter() - t0:7.1f} s  {msg}", file=sys.stderr, flush=True)
+
+    note(f"{n_networks} networks created, {groups or n_networks} worker pools")
     P.bbp_autotune_record(True)
     prev = None
     settle = 0
     for settle in range(1, 9):         # until the work of every network stops changing
         rc, _, _, st = P.bbp_batch_iterate(ctxs, 0.0, 1)
         cur = [P.bbp_stats(c) for c in ctxs]
+        note(f"settle round {settle}: status {rc}, {sum(1 for x in st if x not in (0, 6))} failed")
         if cur == prev:
             break
         prev = cur
@@ -431,8 +436,10 @@ def run_batched(n_networks, steps, warmup, precision, seed=4, groups=0):
     t1 = time.perf_counter()
     tuned = P.bbp_autotune_run()
     tune_s = time.perf_counter() - t1
-    for _ in range(warmup):            # recapture with the tuned tiles, build the round's graph
+    note(f"autotuned {tuned} shapes in {tune_s:.1f} s")
+    for w in range(warmup):            # recapture with the tuned tiles, build the round's graph
         P.bbp_batch_iterate(ctxs, 0.0, 1)
+        note(f"warm-up round {w + 1}")
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     h0 = time.perf_counter()
@@ -444,6 +451,7 @@ def run_batched(n_networks, steps, warmup, precision, seed=4, groups=0):
     host = time.perf_counter() - h0
     secs = max(e0.elapsed_time(e1) * 1e-3, host)
     failed = int(sum(1 for x in st if x not in (0, 6)))
+    note(f"{steps} timed rounds: {secs:.1f} s")
     # one network at a time, on every 8th network (each settled and captured)
     sample = list(range(0, n_networks, 8))
     seq_updates, seq_secs = 0, 0.0

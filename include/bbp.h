@@ -226,10 +226,11 @@ void bbp_destroy(bbp_ctx* ctx);
  * iteration of every context that has not converged and then reads all
  * their errors; a context leaves when its error <= tol or it fails.  The
  * contexts whose iteration replays a captured graph (all of them once their
- * bond dimensions have settled) go to the device as ONE graph launch per
- * round, every context's iteration graph a child node of it (independent, so
- * they overlap on the device); the others launch eagerly on their own
- * streams.  Per context: iterations done, final error and status
+ * bond dimensions have settled) go to the device as one graph launch per
+ * round for every 128 or so of them (whole worker pools per graph, each
+ * graph on its own stream), every context's iteration graph a child node
+ * (independent, so they overlap on the device); the others launch eagerly
+ * on their own streams.  Per context: iterations done, final error and status
  * (BBP_NOT_CONVERGED after max_iter rounds).  Returns BBP_OK,
  * BBP_NOT_CONVERGED, or the first failure among the contexts.
  * bbp_batch_single_launch(0) launches every context's graph separately

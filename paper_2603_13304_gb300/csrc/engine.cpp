@@ -138,6 +138,7 @@ bool SweepWork::reserve(size_t el, size_t ct, size_t cs, size_t cx, size_t sb, s
       tb <= tc_bytes && arena.p)
     return true;
   if (el != elem) { cap_t = cap_seg = cap_x = svd_bytes = nslots = cap_d = tc_bytes = 0; }
+  ++gen;                               // the layout changes (even when the base address comes back)
   tc_bytes = std::max(tb, tc_bytes);
   elem = el;
   cap_t = std::max(ct, cap_t);
@@ -276,7 +277,10 @@ unsigned long long Engine::iter_signature(const std::vector<SweepJob>& jobs, int
   mix((unsigned long long)hermitise);
   mix((unsigned long long)nstreams);
   mix((unsigned long long)(uintptr_t)dist_dev.p);
-  for (int i = 0; i < nstreams; ++i) mix((unsigned long long)(uintptr_t)workers->w[i]->arena.p);
+  for (int i = 0; i < nstreams; ++i) {
+    mix((unsigned long long)(uintptr_t)workers->w[i]->arena.p);
+    mix(workers->w[i]->gen);
+  }
   for (const SweepJob& j : jobs) {
     mix((unsigned long long)(uintptr_t)j.plan);
     for (const void* p : j.node_tensor) mix((unsigned long long)(uintptr_t)p);
@@ -315,8 +319,10 @@ unsigned long long Engine::input_signature(int nstreams) const {
   mix((unsigned long long)hermitise);
   mix((unsigned long long)nstreams);
   mix((unsigned long long)(uintptr_t)dist_dev.p);
-  for (int i = 0; workers && i < nstreams && i < (int)workers->w.size(); ++i)
+  for (int i = 0; workers && i < nstreams && i < (int)workers->w.size(); ++i) {
     mix((unsigned long long)(uintptr_t)workers->w[i]->arena.p);
+    mix(workers->w[i]->gen);
+  }
   for (const auto& kv : msgs) {
     const Message& m = kv.second;
     mix((unsigned long long)m.cur);

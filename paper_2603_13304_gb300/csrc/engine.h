@@ -60,6 +60,7 @@ struct SweepWork {
   cudaEvent_t done = nullptr;
   DBuf arena;
   size_t elem = 0, cap_t = 0, cap_seg = 0, cap_x = 0, svd_bytes = 0, nslots = 0, cap_d = 0, tc_bytes = 0;
+  unsigned long long gen = 0;          // advances with every new layout of the arena
   std::vector<void*> slot;
   void *S[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr};
   void *qrA = nullptr, *qrQ = nullptr, *qrR = nullptr, *tau = nullptr, *X = nullptr;

@@ -84,6 +84,7 @@ void parallel_for(size_t n, F&& f) {
 // while the set repeats (a few sets are kept: the iterations alternate
 // between two message parities).
 std::atomic<bool> g_single_launch{true};
+constexpr size_t kBatchGraphChildren = 128;
 
 struct BatchGraph {
   std::vector<std::pair<unsigned long long, unsigned long long>> key;
@@ -91,7 +92,7 @@ struct BatchGraph {
 };
 std::mutex g_bg_mu;
 std::deque<BatchGraph> g_bg;
-constexpr size_t kBatchGraphsKept = 4;
+constexpr size_t kBatchGraphsKept = 32;   // (chunks x two message parities)
 
 int launch_round(bbp_ctx** ctxs, const std::vector<int>& idx, const std::vector<bbp::Engine::Deferred>& ds,
                  cudaStream_t bs) {
@@ -208,8 +209,7 @@ extern "C" bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int m
       else active.push_back(i);
     }
     const bool single = g_single_launch.load() && active.size() > 1;
-    cudaStream_t bs = nullptr;
-    if (single && cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return BBP_ERR_CUDA;
+    std::vector<cudaStream_t> chunk_streams;
     for (int round = 0; round < max_iter && !active.empty(); ++round) {
       std::vector<int> rcs(active.size(), 0);
       parallel_for(active.size(), [&](size_t a) {
@@ -236,9 +236,34 @@ extern "C" bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int m
           ds.push_back(d);
         }
       }
-      if (!deferred.empty() && launch_round(ctxs, deferred, ds, bs) != BBP_OK) {
-        for (int i : deferred) ctxs[i]->eng.defer_after(bs);   // (finish reports the failed round)
-        for (int i : deferred) status_out[i] = BBP_ERR_CUDA;
+      // the round's graph in chunks of whole worker pools, about
+      // kBatchGraphChildren contexts each, every chunk on its own stream
+      // (the contexts of one pool stay in one chunk, in launch order)
+      if (!deferred.empty()) {
+        std::vector<size_t> ord(deferred.size());
+        for (size_t a = 0; a < ord.size(); ++a) ord[a] = a;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return ds[x].pool < ds[y].pool; });
+        size_t chunk = 0;
+        for (size_t a0 = 0; a0 < ord.size(); ++chunk) {
+          size_t a1 = a0;
+          while (a1 < ord.size() && (a1 - a0 < kBatchGraphChildren || ds[ord[a1]].pool == ds[ord[a1 - 1]].pool)) ++a1;
+          std::vector<int> ci;
+          std::vector<bbp::Engine::Deferred> cd;
+          for (size_t a = a0; a < a1; ++a) {
+            ci.push_back(deferred[ord[a]]);
+            cd.push_back(ds[ord[a]]);
+          }
+          while (chunk_streams.size() <= chunk) {
+            cudaStream_t cs = nullptr;
+            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return BBP_ERR_CUDA;
+            chunk_streams.push_back(cs);
+          }
+          if (launch_round(ctxs, ci, cd, chunk_streams[chunk]) != BBP_OK) {
+            for (int i : ci) ctxs[i]->eng.defer_after(chunk_streams[chunk]);   // (finish reports the failed round)
+            for (int i : ci) status_out[i] = BBP_ERR_CUDA;
+          }
+          a0 = a1;
+        }
       }
       std::vector<int> next;
       for (int i : launched) {
@@ -252,7 +277,7 @@ extern "C" bbp_status bbp_batch_iterate(bbp_ctx** ctxs, int n, double tol, int m
       }
       active.swap(next);
     }
-    if (bs) cudaStreamDestroy(bs);     // (its work completes first)
+    for (cudaStream_t cs : chunk_streams) cudaStreamDestroy(cs);   // (their work completes first)
     for (int i = 0; i < n; ++i) {
       if (!ctxs[i]) continue;
       ctxs[i]->eng.iter_end();
