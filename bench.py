@@ -125,7 +125,16 @@ KERNELS = {
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # the ncu captures summarised under profiles/, keyed by (kernel class,
 # workload, precision); an entry is removed when its kernel changes.
-TRAFFIC = {}
+TRAFFIC = {
+    ("orth", "kagome-6x2-L2-D6-chi64", "tf32"): {
+        "bytes": 1.84e6,
+        "note": "one 2304 x 96 complex64 panel with Q (bench.py --kernel-case panel): DRAM read 1.84 MB, write 0 "
+                "(the 1.8 MB of Q stays in L2); profiles/k_panel_qr_2304x96-c64.md"},
+    ("tc", "kagome-6x2-L2-D6-chi64", "tf32"): {
+        "bytes": 588.3e6,
+        "note": "one absorb GEMM at P = Q = 1296, l = r = 64 (bench.py --kernel-case absorb): DRAM read 549.5 MB + "
+                "write 38.9 MB against 250.5 MB of operands and output; profiles/k_tc_gemm_absorb-P1296-l64-r64_tf32.md"},
+}
 
 # TF32 / BF16 dense tensor rates of the part, nominal (for the ratio only)
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25

@@ -860,6 +860,53 @@ __device__ int rotate_pair(C* ra, C* rb, int N, C* wa, C* wb, int M, int lane, d
   return 1;
 }
 
+// The same rotation by a half warp (16 lanes: lane l of the half handles
+// entries l, l + 16, ...): two pairs a warp.  Both halves always run the
+// sums (an invalid pair on zeros), so the shuffles see the whole warp.
+template <typename C>
+__device__ int rotate_pair_half(C* ra, C* rb, int N, C* wa, C* wb, int M, int hl, bool valid, double tol,
+                                typename RealOf<C>::T floor) {
+  using R = typename RealOf<C>::T;
+  R al = 0, be = 0, gx = 0, gy = 0;
+  if (valid)
+    for (int c = hl; c < N; c += 16) {
+      const C x = ra[c], y = rb[c];
+      al += cabs2(x);
+      be += cabs2(y);
+      gx += x.x * y.x + x.y * y.y;
+      gy += x.y * y.x - x.x * y.y;
+    }
+  for (int o = 8; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    gx += __shfl_xor_sync(0xffffffffu, gx, o);
+    gy += __shfl_xor_sync(0xffffffffu, gy, o);
+  }
+  if (!valid) return 0;
+  R g = sqrt(gx * gx + gy * gy);
+  if (g == 0 || g <= (R)tol * sqrt(al) * sqrt(be)) return 0;
+  if (fmin(al, be) <= floor) return 0;
+  const R far = sizeof(R) == 8 ? (R)1e-60 : (R)1e-30;
+  if (fmin(al, be) <= far * fmax(al, be)) return 0;
+  C e = cx<C>(gx / g, gy / g);
+  R zeta = (be - al) / (2 * g);
+  R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+  R cs = (R)1 / sqrt((R)1 + t * t), sn = cs * t;
+  for (int c = hl; c < N; c += 16) {
+    const C x = ra[c], y = rb[c];
+    const C ey = cmul(e, y);
+    ra[c] = csub(cscale(x, cs), cscale(ey, sn));
+    rb[c] = cadd(cscale(x, sn), cscale(ey, cs));
+  }
+  for (int c = hl; c < M; c += 16) {
+    const C x = wa[c], y = wb[c];
+    const C ey = cmul(e, y);
+    wa[c] = csub(cscale(x, cs), cscale(ey, sn));
+    wb[c] = cadd(cscale(x, sn), cscale(ey, cs));
+  }
+  return 1;
+}
+
 // Algorithmic flops of a one-sided Jacobi run: every sweep tests M(M-1)/2
 // pairs (two squared norms and one complex inner product over N: 16 N), every
 // applied rotation updates two rows of G and two of WH (18 per element pair).
@@ -935,18 +982,35 @@ __global__ void __launch_bounds__(1024) k_jacobi_smem(SvdWork<C> w, int M, int N
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     int rot = 0;
+    const bool halves = npairs > nw;     // more pairs than warps: a pair per half warp
     for (int r = 0; r < Mp - 1; ++r) {
-      for (int q = warp; q < npairs; q += nw) {
-        int a, b;
-        if (q == 0) { a = Mp - 1; b = r; }
-        else { a = (r + q) % (Mp - 1); b = (r - q + Mp - 1) % (Mp - 1); }
-        if (a >= M || b >= M) continue;
-        rot += rotate_pair<false>(G + (long long)a * N, G + (long long)b * N, N, WH + (long long)a * M,
-                             WH + (long long)b * M, M, lane, tol, floor);
+      if (halves) {
+        const int hl = lane & 15, hw = 2 * warp + (lane >> 4);
+        for (int q0 = 2 * warp; q0 < npairs; q0 += 2 * nw) {
+          const int q = hw + (q0 - 2 * warp);   // this half's pair
+          int a = 0, b = 0;
+          if (q < npairs) {
+            if (q == 0) { a = Mp - 1; b = r; }
+            else { a = (r + q) % (Mp - 1); b = (r - q + Mp - 1) % (Mp - 1); }
+          }
+          const bool valid = q < npairs && a < M && b < M;
+          const int aa = valid ? a : 0, bb = valid ? b : 0;
+          rot += rotate_pair_half(G + (long long)aa * N, G + (long long)bb * N, N, WH + (long long)aa * M,
+                                  WH + (long long)bb * M, M, hl, valid, tol, floor);
+        }
+      } else {
+        for (int q = warp; q < npairs; q += nw) {
+          int a, b;
+          if (q == 0) { a = Mp - 1; b = r; }
+          else { a = (r + q) % (Mp - 1); b = (r - q + Mp - 1) % (Mp - 1); }
+          if (a >= M || b >= M) continue;
+          rot += rotate_pair<false>(G + (long long)a * N, G + (long long)b * N, N, WH + (long long)a * M,
+                               WH + (long long)b * M, M, lane, tol, floor);
+        }
       }
       __syncthreads();
     }
-    if (lane == 0 && rot) atomicAdd(&s_rot, rot);
+    if ((halves ? (lane & 15) : lane) == 0 && rot) atomicAdd(&s_rot, rot);
     __syncthreads();
     const int total = s_rot;
     ++sweeps;
@@ -1158,7 +1222,7 @@ __global__ void k_omega(C* O, int n, int b) {
 // of G' are spread over the shared memory of a cluster of kCutCluster CTAs
 // (row r on CTA r % kCutCluster) and every round's disjoint pairs over all
 // their warps, with one cluster barrier per round; WH stays in global memory.
-constexpr int kCutCluster = 8;
+constexpr int kCutCluster = 16;   // (a non-portable cluster size, opted in)
 
 __global__ void __launch_bounds__(1024) k_jacobi_cut64(SvdWork<float2> w, int b, int k, double2* __restrict__ G64,
                                                        double2* __restrict__ WH64, double* __restrict__ sig64,
@@ -2067,7 +2131,8 @@ cudaError_t init_kernel_attributes() {
   if ((e = smem_optin<k_jacobi_smem<float2>>()) != cudaSuccess) return e;
   if ((e = smem_optin<k_jacobi_cut64>()) != cudaSuccess) return e;
   for (const void* f : {(const void*)k_msg_normalise<double2>, (const void*)k_msg_normalise<float2>,
-                        (const void*)k_mps_dot<double2>, (const void*)k_mps_dot<float2>})
+                        (const void*)k_mps_dot<double2>, (const void*)k_mps_dot<float2>,
+                        (const void*)k_jacobi_cut64})
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
   if ((e = init_panel_attributes()) != cudaSuccess) return e;
   return init_tc_attributes();
