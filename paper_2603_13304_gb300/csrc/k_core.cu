@@ -175,14 +175,28 @@ __global__ void __launch_bounds__(256) k_gemm(char opA, char opB, int M, int N, 
   C acc[2][2];
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) acc[i][j] = cx<C>(0, 0);
+  // the next k tile is loaded into registers while the current one is
+  // multiplied (GT * GK / 256 = 2 entries of A and 2 of B a thread)
+  constexpr int kPer = GT * GK / 256;
+  C pa[kPer], pb[kPer];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      pa[u] = load_op(A, lda, opA, row0 + e / GK, k0 + e % GK, M, K);
+      pb[u] = load_op(B, ldb, opB, k0 + e / GT, col0 + e % GT, K, N);
+    }
+  };
+  if (K > 0) fetch(0);
   for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = threadIdx.x; e < GT * GK; e += 256) {
-      int i = e / GK, kk = e % GK;
-      As[i][kk] = load_op(A, lda, opA, row0 + i, k0 + kk, M, K);
-      int kb = e / GT, j = e % GT;
-      Bs[kb][j] = load_op(B, ldb, opB, k0 + kb, col0 + j, K, N);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      As[e / GK][e % GK] = pa[u];
+      Bs[e / GT][e % GT] = pb[u];
     }
     __syncthreads();
+    if (k0 + GK < K) fetch(k0 + GK);
 #pragma unroll 4
     for (int kk = 0; kk < GK; ++kk) {
       C a0 = As[ty][kk], a1 = As[ty + 16][kk];
