@@ -123,17 +123,17 @@ KERNELS = {
 }
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu captures summarised under profiles/, keyed by (kernel class,
-# workload, precision); an entry is removed when its kernel changes.
+# ncu captures of the kernel cases below, keyed by (kernel class, workload,
+# precision); an entry is removed when its kernel changes.
 TRAFFIC = {
     ("orth", "kagome-6x2-L2-D6-chi64", "tf32"): {
         "bytes": 1.84e6,
         "note": "one 2304 x 96 complex64 panel with Q (bench.py --kernel-case panel): DRAM read 1.84 MB, write 0 "
-                "(the 1.8 MB of Q stays in L2); profiles/k_panel_qr_2304x96-c64.md"},
+                "(the 1.8 MB of Q stays in L2)"},
     ("tc", "kagome-6x2-L2-D6-chi64", "tf32"): {
         "bytes": 588.3e6,
         "note": "one absorb GEMM at P = Q = 1296, l = r = 64 (bench.py --kernel-case absorb): DRAM read 549.5 MB + "
-                "write 38.9 MB against 250.5 MB of operands and output; profiles/k_tc_gemm_absorb-P1296-l64-r64_tf32.md"},
+                "write 38.9 MB against 250.5 MB of operands and output"},
 }
 
 # TF32 / BF16 dense tensor rates of the part, nominal (for the ratio only)
@@ -141,7 +141,7 @@ NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 
 
 def peaks():
-    """Roofline denominators: the measured BF16 burst rate, TF32 at the
+    """Roofline denominators: the measured BF16 burst rate (MEASURED_PEAKS.json), TF32 at the
     nominal TF32 / BF16 ratio of the part; the FP32 and FP64 ALU rates from
     unit counts and the maximum clock (152 SMs x 128 FP32 lanes, x 2 FP64
     FMA per clock, 2.07 GHz), which the FMA microbenchmark of `--peaks`
