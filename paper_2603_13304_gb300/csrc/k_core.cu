@@ -160,16 +160,26 @@ __device__ __forceinline__ C load_op(const C* P, int ld, char op, int r, int c, 
   return op == 'C' ? cconj(v) : v;
 }
 
+// With part != null the grid's z index is a slice of K (kchunk entries,
+// batch 1): each CTA writes its raw partial tile to part[z][M][N] and
+// k_gemm_reduce adds the slices in order (split K for skinny products).
 template <typename C>
 __global__ void __launch_bounds__(256) k_gemm(char opA, char opB, int M, int N, int K, C alpha, const C* __restrict__ A,
                                               int lda, long long sA, const C* __restrict__ B, int ldb, long long sB,
-                                              C beta, C* __restrict__ Cm, int ldc, long long sC) {
+                                              C beta, C* __restrict__ Cm, int ldc, long long sC, int kchunk,
+                                              C* __restrict__ part) {
   __shared__ C As[GT][GK + 1];
   __shared__ C Bs[GK][GT + 1];
   const int bz = blockIdx.z;
-  A += bz * sA;
-  B += bz * sB;
-  Cm += bz * sC;
+  int kb = 0, ke = K;
+  if (part) {
+    kb = bz * kchunk;
+    ke = min(K, kb + kchunk);
+  } else {
+    A += bz * sA;
+    B += bz * sB;
+    Cm += bz * sC;
+  }
   const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   C acc[2][2];
@@ -183,12 +193,12 @@ __global__ void __launch_bounds__(256) k_gemm(char opA, char opB, int M, int N, 
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int e = threadIdx.x + 256 * u;
-      pa[u] = load_op(A, lda, opA, row0 + e / GK, k0 + e % GK, M, K);
-      pb[u] = load_op(B, ldb, opB, k0 + e / GT, col0 + e % GT, K, N);
+      pa[u] = load_op(A, lda, opA, row0 + e / GK, k0 + e % GK, M, ke);
+      pb[u] = load_op(B, ldb, opB, k0 + e / GT, col0 + e % GT, ke, N);
     }
   };
-  if (K > 0) fetch(0);
-  for (int k0 = 0; k0 < K; k0 += GK) {
+  if (kb < ke) fetch(kb);
+  for (int k0 = kb; k0 < ke; k0 += GK) {
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int e = threadIdx.x + 256 * u;
@@ -196,7 +206,7 @@ __global__ void __launch_bounds__(256) k_gemm(char opA, char opB, int M, int N, 
       Bs[e / GT][e % GT] = pb[u];
     }
     __syncthreads();
-    if (k0 + GK < K) fetch(k0 + GK);
+    if (k0 + GK < ke) fetch(k0 + GK);
 #pragma unroll 4
     for (int kk = 0; kk < GK; ++kk) {
       C a0 = As[ty][kk], a1 = As[ty + 16][kk];
@@ -212,11 +222,29 @@ __global__ void __launch_bounds__(256) k_gemm(char opA, char opB, int M, int N, 
     for (int j = 0; j < 2; ++j) {
       int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
       if (r < M && c < N) {
+        if (part) {
+          part[((long long)bz * M + r) * N + c] = acc[i][j];
+          continue;
+        }
         C v = cmul(alpha, acc[i][j]);
         if (beta.x != 0 || beta.y != 0) v = cadd(v, cmul(beta, Cm[(long long)r * ldc + c]));
         Cm[(long long)r * ldc + c] = v;
       }
     }
+}
+
+template <typename C>
+__global__ void k_gemm_reduce(const C* __restrict__ part, int S, int M, int N, C alpha, C beta, C* __restrict__ Cm,
+                              int ldc) {
+  const long long tot = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    C v = part[e];
+    for (int z = 1; z < S; ++z) v = cadd(v, part[(long long)z * tot + e]);
+    const int r = (int)(e / N), c = (int)(e % N);
+    v = cmul(alpha, v);
+    if (beta.x != 0 || beta.y != 0) v = cadd(v, cmul(beta, Cm[(long long)r * ldc + c]));
+    Cm[(long long)r * ldc + c] = v;
+  }
 }
 
 // ---------------------------------------------------------------------- QR
@@ -1371,14 +1399,33 @@ cudaError_t launch_fuse(const double2* t, int d, int D, const int n[4], const do
   return fuse_t(t, d, D, n, op, perm, T, s);
 }
 
+// K slices of a skinny product (few output tiles, long K) when a scratch of
+// kSplitMax x M x N entries is given
+constexpr int kSplitMax = 8;
 template <typename C>
 static cudaError_t gemm_t(char opA, char opB, int M, int N, int K, C alpha, const C* A, int lda, long long sA,
                           const C* B, int ldb, long long sB, C beta, C* Cm, int ldc, long long sC, int batch,
-                          cudaStream_t s) {
+                          cudaStream_t s, void* work = nullptr, size_t work_bytes = 0) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   KTimerScope timer(KC_GEMM, s, 8.0 * M * N * (double)K * batch);
+  const int tiles = ((N + GT - 1) / GT) * ((M + GT - 1) / GT);
+  int S = 1;
+  if (batch == 1 && work && tiles < 2 * 152 && K >= 8 * GK) {
+    S = std::min(kSplitMax, std::max(2, (6 * 152) / tiles));   // about six CTAs an SM
+    S = std::min(S, K / (4 * GK));
+    while (S > 1 && (size_t)S * M * N * sizeof(C) > work_bytes) --S;
+  }
+  if (S > 1) {
+    const int kchunk = ((K + S - 1) / S + GK - 1) / GK * GK;
+    S = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, S);
+    k_gemm<C><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, Cm, ldc, sC, kchunk,
+                                   (C*)work);
+    k_gemm_reduce<C><<<grid_for((long long)M * N, 256), 256, 0, s>>>((const C*)work, S, M, N, alpha, beta, Cm, ldc);
+    return cudaGetLastError();
+  }
   dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, batch);
-  k_gemm<C><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, Cm, ldc, sC);
+  k_gemm<C><<<grid, 256, 0, s>>>(opA, opB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, Cm, ldc, sC, 0, nullptr);
   return cudaGetLastError();
 }
 cudaError_t launch_zgemm(char opA, char opB, int M, int N, int K, double2 alpha, const double2* A, int lda,
@@ -1507,7 +1554,8 @@ static size_t rand_work_bytes(int m, int n, int b) {
   const size_t z = sizeof(C), zd = sizeof(double2);
   return align256(z * (size_t)n * b) + align256(z * (size_t)m * b) + 2 * align256(z * (size_t)b * b) +
          jacobi_bytes<C>(b, b) + 2 * align256(zd * (size_t)b * b) + align256(sizeof(double) * b) +
-         align256(sizeof(int) * b) + 256 + orth_scratch_bytes<C>(m, n, b);
+         align256(sizeof(int) * b) + 256 + orth_scratch_bytes<C>(m, n, b) +
+         align256(sizeof(C) * (size_t)kSplitMax * std::max(m, n) * b);
 }
 
 // packed operands of the tensor-core range finder: Z for Z W and for Z^H Q,
@@ -1600,6 +1648,8 @@ static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* R
   double* sig64 = (double*)p; p += align256(sizeof(double) * b);
   int* idx64 = (int*)p; p += align256(sizeof(int) * b) + 256;
   void* chunk = p; p += orth_scratch_bytes<C>(m, n, b);
+  const size_t split_bytes = align256(sizeof(C) * (size_t)kSplitMax * std::max(m, n) * b);
+  void* split = p; p += split_bytes;
   const C one = cx<C>(1.0, 0.0), zero = cx<C>(0.0, 0.0);
   cudaError_t e;
   // the range-finder products Y = Z W and W = Z^H Q: SIMT GEMMs, or (complex64
@@ -1623,7 +1673,7 @@ static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* R
         return tc_zgemm_packed(false, m, b, n, Zn, Bp, Y, b, tc_err, s);
       }
     }
-    return launch_zgemm('N', 'N', m, b, n, one, Z, n, 0, X, b, 0, zero, Y, b, 0, 1, s);
+    return gemm_t('N', 'N', m, b, n, one, Z, n, 0, X, b, 0, zero, Y, b, 0, 1, s, split, split_bytes);
   };
   auto zh_times = [&](const C* X, C* Y) -> cudaError_t {  // Y (n x b) = Z^H X, X m x b
     if constexpr (sizeof(C) == sizeof(float2)) {
@@ -1633,7 +1683,7 @@ static cudaError_t rand_svd(const C* Z, int m, int n, int chi, int b, C* U, C* R
         return tc_zgemm_packed(false, n, b, m, Zc, Bp, Y, b, tc_err, s);
       }
     }
-    return launch_zgemm('C', 'N', n, b, m, one, Z, n, 0, X, b, 0, zero, Y, b, 0, 1, s);
+    return gemm_t('C', 'N', n, b, m, one, Z, n, 0, X, b, 0, zero, Y, b, 0, 1, s, split, split_bytes);
   };
   k_omega<C><<<grid_for((long long)n * b, 256), 256, 0, s>>>(W, n, b);
   if ((e = z_times(W, Q)) != cudaSuccess) return e;
