@@ -317,7 +317,9 @@ bbp_status bbp_k_svd_trunc(const double* Z, int m, int n, int chi, double* U, do
 
 /* Allocation-free variant of bbp_k_svd_trunc (the thesis has no counterpart;
  * this serves callers that cannot allocate device memory when they need the
- * SVD, e.g. inside a stream capture or an allocator-free real-time loop).
+ * SVD: real-time loops that must not enter the allocator, since cudaMalloc
+ * can synchronise the device, and hosts whose device memory is owned by
+ * another runtime with a budget fixed at start-up).
  * Same inputs, outputs and status as bbp_k_svd_trunc, without `work`: the
  * scratch is a fixed device array of 8 MiB + 64 KiB that every GPU loading
  * the library holds until exit, enough for bbp_k_svd_work_bytes(m, n) up to

@@ -1,9 +1,9 @@
 // Allocation-free variant of the truncated-SVD entry point.
 //
 // Some callers cannot allocate device memory at the moment they need an SVD:
-// code running inside a CUDA-graph capture of someone else's stream, real-time
-// loops that must not enter the allocator (cudaMalloc synchronises the
-// device), or hosts whose allocator is owned by another runtime.  For them
+// real-time loops that must not enter the allocator (cudaMalloc can
+// synchronise the device), or hosts whose device memory is owned by another
+// runtime with a budget fixed at start-up.  For them
 // this file keeps the SVD scratch in a fixed device array, so a call needs no
 // allocation of its own.
 //

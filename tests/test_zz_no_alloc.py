@@ -1,7 +1,8 @@
 """The allocation-free SVD entry point (bbp_k_svd_trunc_noalloc).
 
 It exists for callers that cannot allocate device memory when they need the
-SVD (inside a stream capture, allocator-free loops).  It must give the same
+SVD (real-time loops that must not enter the allocator, hosts whose device
+memory belongs to another runtime).  It must give the same
 result as bbp_k_svd_trunc, which takes caller-allocated scratch, on two calls
 in a row (the second one reusing the shared device array), and reject sizes
 beyond its fixed scratch.  This file is collected last on purpose.
