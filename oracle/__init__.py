@@ -16,6 +16,10 @@ tn        double-layer fusion, MPS helpers, boundary-MPS sweep (Sec. 1.1.3)
 blockbp   the BlockBP iteration and local observables (Sec. 2.2, Alg. 1)
 bp        site-level BP (Eq. of BP) used as a pin: 1x1 blocks reduce to it
 exact     brute-force exact contraction of small finite lattices
+core      core extraction: two opposing bubbles, the zipper into a pMPS, the
+          Edge TN of a bond (Sec. 2.3, "Core", "Edge")
+ite       imaginary time evolution: two-site gate, ALS on the Edge TN, full
+          ITE over a block (Ch. 3, Alg. 2)
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
 the loopy configurations themselves, which have no closed form: the BlockBP

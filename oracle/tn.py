@@ -125,13 +125,21 @@ class SweepError(RuntimeError):
     pass
 
 
-def sweep(region: Region, out_dir: int, T: dict, msgs: dict, chi: int, trace: list | None = None):
+def sweep(region: Region, out_dir: int, T: dict, msgs: dict, chi: int, trace: list | None = None,
+          skip=None, stop=None, raw: bool = False):
     """Contract a region with the incoming messages of all sides but ``out_dir``.
 
     T[(inst, local)]   fused site tensor, legs in slot order (dims D^2, or 1 open)
     msgs[(inst, dir)]  incoming MPS on that face, canonical order, tensors (l, p, r)
     Returns (mps, logscale): the MPS over the out side's edges in canonical
     order, and the natural log of the scale factored out along the way.
+
+    A bubble that must leave a core unswallowed (Sec. 2.3, "Core"): ``skip``
+    holds the (inst, local) keys of sites that are never swallowed (their
+    legs stay open on the boundary), ``stop`` a sweep key at which the bubble
+    halts (nodes whose key is >= stop are left), and ``raw`` returns the
+    boundary as it stands: (tensors incl. the two end-bond tensors, their leg
+    labels in boundary order, logscale).
     """
     lat = region.geom.lattice
     start = (out_dir + 2) % 4
@@ -149,6 +157,8 @@ def sweep(region: Region, out_dir: int, T: dict, msgs: dict, chi: int, trace: li
     nodes = []
     node_ident = {}
     for rs in region.sites:
+        if skip and (rs.inst, rs.local) in skip:
+            continue
         legs = []
         for k in range(4):
             legs.append((rs.labels[k], _angle(lat, rs.pos4, rs.nbr_pos4[k])))
@@ -211,6 +221,8 @@ def sweep(region: Region, out_dir: int, T: dict, msgs: dict, chi: int, trace: li
     normalise()
 
     for key, kind, payload in nodes:
+        if stop is not None and key >= stop:
+            break
         if kind == "site":
             rs, legs = payload
             X = T[(rs.inst, rs.local)]
@@ -283,6 +295,8 @@ def sweep(region: Region, out_dir: int, T: dict, msgs: dict, chi: int, trace: li
             c = i + nout - 1
         normalise()
 
+    if raw:
+        return A, labels, logscale
     # finish: [end(lo), out legs..., end(hi)]
     out_labels = [e.label for e in region.sides[out_dir]]
     exp_lateral = out_labels if chain_forward else list(reversed(out_labels))

@@ -1,0 +1,253 @@
+"""Pins of the oracle's core extraction (pMPS, Edge TN) and its ITE step with ALS.
+
+No GPU.  Sec. 2.3 (Core, Edge) and Ch. 3 (ITE update step, Full ITE).  Every
+test ties the two modules to something other than themselves: brute-force
+contraction, the one-bubble contraction of the message update, a direct
+contraction of the two bubbles without the zipper, a library matrix
+exponential and eigensolver, Eckart-Young, and closed-form ground states.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import core as C
+from oracle import exact, ite
+from oracle.blockbp import BlockBP
+from oracle.geometry import Geometry
+
+SX, SY, SZ = ite.SX, ite.SY, ite.SZ
+
+
+def _bbp(geom, D, chi, seed, iters, tol=1e-13):
+    n = geom.n_sites
+    t = syn.gaussian_peps(n, 2, D, seed=seed)
+    bb = BlockBP(geom, t, chi=chi)
+    bb.init_messages(syn.initial_edge_matrices(n, D, seed=seed + 1))
+    bb.run(tol, iters)
+    return bb, t
+
+
+# ------------------------------------------------------------------- core --
+
+def test_core_on_a_tree_of_blocks_is_exact():
+    """Two blocks in a row have no loop between them, so the converged
+    messages are exact; the core route must then give the exact <S^z>, bond
+    energy and two-site RDM of the core (brute force over the whole lattice)."""
+    geom = Geometry.square(6, 3, 3, 3)
+    bb, t = _bbp(geom, 2, 512, 41, 12)
+    b = geom.blocks[0]
+    core = [(0, 4), (0, 5)]                      # centre of the 3x3 block and its right neighbour
+    env = C.CoreEnv(bb, [(b.X, b.Y)], core)
+    g = [b.gids[k[1]] for k in core]
+    for k, gg in zip(core, g):
+        assert abs(env.expect({k: SZ}) - exact.expect(geom.lattice, t, {gg: SZ})) < 1e-12
+    e_core = sum(env.expect({core[0]: S, core[1]: S}) for S in (SX, SY, SZ))
+    e_ref = sum(exact.expect(geom.lattice, t, {g[0]: S, g[1]: S}) for S in (SX, SY, SZ))
+    assert abs(e_core - e_ref) < 1e-12
+    rho = env.rdm(core)
+    assert np.abs(rho - exact.rdm(geom.lattice, t, g)).max() < 1e-12
+
+
+@pytest.mark.parametrize("core", [[(0, 4)], [(0, 3), (0, 4)], [(0, 4), (0, 7)], [(0, 1), (0, 4), (0, 5)]])
+def test_core_equals_one_bubble_contraction(core):
+    """On a loopy network, with chi above every rank of the bubbles, the core
+    route and the one-bubble contraction of the block with its incoming
+    messages are both exact contractions of the same network."""
+    geom = Geometry.square(6, 6, 3, 3)
+    bb, _ = _bbp(geom, 2, 256, 5, 2)
+    b = geom.blocks[0]
+    env = C.CoreEnv(bb, [(b.X, b.Y)], core)
+    for k in core:
+        assert abs(env.expect({k: SZ}) - bb.expect({k: SZ}, [(b.X, b.Y)])) < 1e-13
+
+
+def test_kagome_unit_cell_core():
+    """The Kagome unit cell (the up-triangle A, B, C) as the core of an L = 2
+    parallelogram block: with messages of bond 16 and chi = 64 nothing is
+    truncated, so every site of the cell matches the one-bubble contraction;
+    the cell's six outer legs give a six-tensor pMPS."""
+    geom = Geometry.kagome(6, 2, 2)
+    bb, _ = _bbp(geom, 2, 16, 7, 2)
+    bb.chi = 64
+    b = geom.blocks[0]
+    cell = [b.sites.index((0, 0, 0)), b.sites.index((1, 0, 0)), b.sites.index((2, 0, 0))]
+    core = [(0, q) for q in cell]
+    env = C.CoreEnv(bb, [(b.X, b.Y)], core)
+    assert len(env.pmps) == 6
+    for k in core:
+        assert abs(env.expect({k: SZ}) - bb.expect({k: SZ}, [(b.X, b.Y)])) < 1e-13
+
+
+def test_zipper_equals_direct_contraction_of_the_bubbles():
+    """The zipper only reorders an exact contraction: the core closed with the
+    pMPS equals the core contracted with the two bubbles' raw MPSs directly,
+    with truncation inside the bubbles (chi below the ranks)."""
+    geom = Geometry.square(6, 6, 3, 3)
+    bb, _ = _bbp(geom, 2, 6, 9, 2)
+    b = geom.blocks[0]
+    core = [(0, 4), (0, 5)]
+    env = C.CoreEnv(bb, [(b.X, b.Y)], core)
+    B, LB, Tt, LT = env.parts
+    items = []
+    for name, A, L in (("B", B, LB), ("T", Tt, LT)):
+        for q, X in enumerate(A):
+            lab = [(name, q), L[q], (name, q + 1)]
+            if q == 0:
+                X, lab = X[0], lab[1:]
+            if q == len(A) - 1:
+                X, lab = X[..., 0], lab[:-1]
+            items.append((X, lab))
+    for ops in (None, {core[0]: SZ}, {core[0]: SX, core[1]: SY}):
+        direct = exact.contract_network(items + env.core_items(ops))
+        assert abs(env.value(ops)[1] - direct) < 1e-12 * abs(direct)
+
+
+def test_edge_tn_rdm_matches_insertions_and_is_physical():
+    """The Edge TN of a bond (every other core site contracted into the pMPS)
+    gives the bond's RDM as a dense environment; it must equal the RDM from
+    operator insertions on the full core, be Hermitian with unit trace, and
+    be positive on a tree of blocks (exact messages)."""
+    geom = Geometry.square(6, 3, 3, 3)
+    bb, t = _bbp(geom, 2, 512, 43, 12)
+    b = geom.blocks[0]
+    core = [(0, 3), (0, 4), (0, 5)]
+    env = C.CoreEnv(bb, [(b.X, b.Y)], core)
+    k1, k2 = (0, 4), (0, 5)
+    N, labels, slots = env.edge(k1, k2)
+    rs1, rs2 = env.sites[k1], env.sites[k2]
+    s1 = rs1.labels.index(next(iter(set(rs1.labels) & set(rs2.labels))))
+    s2 = rs2.labels.index(next(iter(set(rs1.labels) & set(rs2.labels))))
+    rho = C.edge_rdm(N, slots, 2, 2, 2, bb.tc[rs1.gid], bb.tc[rs2.gid], s1, s2)
+    ref = env.rdm([k1, k2])
+    assert np.abs(rho - ref).max() < 1e-12
+    assert np.abs(rho - rho.conj().T).max() < 1e-13
+    assert abs(np.trace(rho) - 1) < 1e-13
+    assert np.linalg.eigvalsh(0.5 * (rho + rho.conj().T)).min() > -1e-12
+    assert np.abs(rho - exact.rdm(geom.lattice, t, [rs1.gid, rs2.gid])).max() < 1e-12
+
+
+def test_zipper_rejects_mismatched_front_lines():
+    """A bubble pair whose shared legs do not meet end to end is refused."""
+    A = [np.ones((1, 1, 2)), np.ones((2, 1, 1))]
+    with pytest.raises(C.ZipError):
+        C.zipper(A, ["a", "b"], A, ["c", "d"])
+
+
+# -------------------------------------------------------------------- ITE --
+
+def test_gate_is_the_matrix_exponential():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    h = ite.heisenberg_h()
+    for dt in (0.0, 0.01, 0.3):
+        assert np.abs(ite.gate(h, dt) - scipy_linalg.expm(-dt * h)).max() < 1e-13
+    # S.S has the singlet at -3/4 and the triplet at 1/4
+    assert np.allclose(np.linalg.eigvalsh(h), [-0.75, 0.25, 0.25, 0.25], atol=1e-14)
+
+
+def _random_bond(D, seed):
+    rng = np.random.default_rng(seed)
+    g = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    return g(2, D, D, D, D), g(2, D, D, D, D)
+
+
+def test_als_with_identity_environment_is_eckart_young():
+    """With the identity environment Phi is the plain Frobenius distance, whose
+    minimum over a bond of D is the sum of the discarded squared singular
+    values of the evolved tensor across the bond; the SVD start already
+    reaches it and ALS cannot go below it."""
+    D = 2
+    t1, t2 = _random_bond(D, 3)
+    s1, s2 = 1, 3
+    dims = [D] * 3
+    G = ite.gate(ite.heisenberg_h(), 0.7)
+    # N[K, B] = delta(K, B), written over fused legs (ket * D + bra)
+    Nkb = np.eye(D ** 6)
+    Nf = Nkb.reshape([D] * 12).transpose([q // 2 + 6 * (q % 2) for q in range(12)]).reshape([D * D] * 6)
+    a, b, hist = ite.als(t1, t2, s1, s2, Nf, dims, dims, G, D, max_sweeps=10)
+    Theta = ite.evolve(t1, t2, s1, s2, G)
+    M = np.transpose(Theta, (0, 2, 3, 4, 1, 5, 6, 7)).reshape(2 * D ** 3, 2 * D ** 3)
+    s = np.linalg.svd(M, compute_uv=False)
+    tail = float(np.sum(s[D:] ** 2))
+    assert abs(hist[0] - tail) < 1e-10 * tail
+    assert min(hist) > tail * (1 - 1e-10)
+    assert abs(hist[-1] - tail) < 1e-9 * tail
+
+
+def test_als_decreases_phi_and_is_exact_when_the_bond_suffices():
+    """Each half-step minimises Phi exactly, so Phi never increases; with a
+    random positive environment ALS improves on the SVD start.  With dt = 0
+    the evolved state still has bond D, and Phi reaches zero."""
+    D = 2
+    t1, t2 = _random_bond(D, 5)
+    s1, s2 = 0, 2
+    dims = [D] * 3
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((D ** 6, D ** 6)) + 1j * rng.standard_normal((D ** 6, D ** 6))
+    Nkb = X @ X.conj().T / D ** 6 + np.eye(D ** 6)
+    Nf = Nkb.reshape([D] * 12).transpose([q // 2 + 6 * (q % 2) for q in range(12)]).reshape([D * D] * 6)
+    assert np.abs(ite.env_matrix(Nf, dims, dims) - Nkb).max() < 1e-12
+    G = ite.gate(ite.heisenberg_h(), 0.5)
+    _, _, hist = ite.als(t1, t2, s1, s2, Nf, dims, dims, G, D, max_sweeps=30)
+    assert all(h >= -1e-12 for h in hist)
+    assert all(hist[q + 1] <= hist[q] * (1 + 1e-10) + 1e-14 for q in range(len(hist) - 1))
+    assert hist[-1] < hist[0]
+    _, _, hist0 = ite.als(t1, t2, s1, s2, Nf, dims, dims, ite.gate(ite.heisenberg_h(), 0.0), D)
+    norm2 = ite.phi(np.zeros_like(t1), t2, s1, s2, Nkb, ite.evolve(t1, t2, s1, s2, np.eye(4)))
+    assert hist0[-1] < 1e-20 * norm2
+
+
+def test_ite_two_spins_reach_the_singlet():
+    """Two spins with D = 2 can hold the singlet exactly; ITE from a random
+    state converges to it: <S_1 . S_2> = -3/4, i.e. -3/8 per site."""
+    geom = Geometry.square(2, 1, 2, 1)
+    t = syn.gaussian_peps(2, 2, 2, seed=13)
+    _, E = ite.full_ite(geom, t, 16, [0.5] * 40, syn.initial_edge_matrices(2, 2, seed=14))
+    assert abs(E[-1] - (-0.375)) < 1e-8
+
+
+def _ed_ground(bonds, n):
+    H = np.zeros((2 ** n, 2 ** n), dtype=np.complex128)
+    for (a, b) in bonds:
+        for S in (SX, SY, SZ):
+            ops = [np.eye(2)] * n
+            ops[a], ops[b] = S, S
+            M = ops[0]
+            for o in ops[1:]:
+                M = np.kron(M, o)
+            H += M
+    return float(np.linalg.eigvalsh(H)[0])
+
+
+def test_ite_three_site_chain_ground_energy():
+    """An open chain of three spins: every cut has Schmidt rank <= 2, so D = 2
+    is exact; ITE with shrinking steps reaches the exact ground energy (-1,
+    from an eigensolver) up to the splitting error of the last step."""
+    geom = Geometry.square(3, 1, 3, 1)
+    bonds = [(g1, g2) for (g1, _, g2, _) in geom.bonds()]
+    E0 = _ed_ground(bonds, 3)
+    assert abs(E0 - (-1.0)) < 1e-12
+    t = syn.gaussian_peps(3, 2, 2, seed=3)
+    _, E = ite.full_ite(geom, t, 16, [0.2] * 20 + [0.05] * 20 + [0.01] * 20, syn.initial_edge_matrices(3, 2, seed=4))
+    assert E[-1].real * 3 > E0 - 1e-12
+    assert abs(E[-1].real * 3 - E0) < 2e-4
+
+
+def test_ite_on_a_tree_of_blocks_matches_one_block():
+    """Full ITE on the 2 x 2 plaquette: two 2 x 1 blocks form a tree, so their
+    converged messages give the exact environment and every update equals
+    the one-block run; the energy stays above the exact ground energy
+    (eigensolver) and falls with imaginary time."""
+    dts = [0.2] * 6 + [0.05] * 4
+    runs = []
+    for (bx, by) in ((2, 2), (2, 1)):
+        geom = Geometry.square(2, 2, bx, by)
+        t = syn.gaussian_peps(4, 2, 2, seed=3)
+        runs.append(ite.full_ite(geom, t, 64, dts, syn.initial_edge_matrices(4, 2, seed=4)))
+    (t1, E1), (t2, E2) = runs
+    assert max(abs(a - b) for a, b in zip(E1, E2)) < 1e-9
+    bonds = [(g1, g2) for (g1, _, g2, _) in Geometry.square(2, 2, 2, 2).bonds()]
+    E0 = _ed_ground(bonds, 4) / 4
+    assert all(e.real > E0 - 1e-12 for e in E1)
+    assert E1[-1].real < E1[0].real < 0

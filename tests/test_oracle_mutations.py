@@ -59,3 +59,31 @@ def test_truncation_off_by_one_is_caught(monkeypatch):
     monkeypatch.setattr(tn, "svd_split", bad_split)
     assert _single_block_error() > 1e-8
     monkeypatch.setattr(tn, "svd_split", real)
+
+
+def test_zipper_front_line_transposed_is_caught(monkeypatch):
+    """Plant a transposed left front-line matrix in the core's zipper: the
+    core route on a tree of blocks must then miss the brute-force <S^z>."""
+    from oracle import core as C
+    geom = Geometry.square(6, 3, 3, 3)
+    t = syn.gaussian_peps(18, 2, 2, seed=41)
+    bb = BlockBP(geom, t, chi=512)
+    bb.init_messages(syn.initial_edge_matrices(18, 2, seed=42))
+    bb.run(1e-13, 12)
+    sz = np.diag([0.5, -0.5]).astype(np.complex128)
+    b = geom.blocks[0]
+    ref = exact.expect(geom.lattice, t, {b.gids[4]: sz})
+    env = C.CoreEnv(bb, [(b.X, b.Y)], [(0, 4)])
+    assert abs(env.expect({(0, 4): sz}) - ref) < 1e-12
+    real_einsum = C.np.einsum
+
+    def bad_einsum(spec, *ops, **kw):
+        if spec == "xy,xpz,wpy->zw":
+            spec = "xy,xpz,wpy->wz"
+        return real_einsum(spec, *ops, **kw)
+    monkeypatch.setattr(C.np, "einsum", bad_einsum)
+    try:
+        err = abs(C.CoreEnv(bb, [(b.X, b.Y)], [(0, 4)]).expect({(0, 4): sz}) - ref)
+    except Exception:
+        err = math.inf
+    assert err > 1e-6
