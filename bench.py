@@ -356,6 +356,52 @@ def run_ours(args, rank, world):
     }
 
 
+def run_core(workload: str, precision: int, reps: int = 3):
+    """Core extraction (Sec. 2.3) at a Kagome workload: once the messages have
+    settled, the pMPS around the unit cell (up-triangle A, B, C of the
+    block's first cell) of every block, each timed over `reps` calls of
+    bbp_core_pmps (two bubbles, the zipper, the copy of the pMPS to the host)
+    with CUDA events on the context's stream."""
+    import torch
+    import paper_2603_13304_gb300 as P
+    w = WORKLOADS[workload]
+    t, em = make_inputs(w)
+    ctx = P.bbp_create_peps(P.KAGOME, w["Lx"], w["Ly"], 1, w["d"], w["D"], t)
+    P.bbp_partition_blocks(ctx, w["L"], w["L"])
+    P.bbp_set_options(ctx, w["chi"], precision)
+    P.bbp_init_messages(ctx, em)
+    prev = None
+    for _ in range(12):                # until the work per iteration stops changing
+        P.bbp_iterate(ctx, 0.0, 1)
+        cur = P.bbp_stats(ctx)
+        if cur == prev:
+            break
+        prev = cur
+    n_blocks = P.bbp_info(ctx)[0]
+    cells = [[3 * (b * w["L"]) + k for k in range(3)] for b in range(n_blocks)]   # cell (b L, 0): A, B, C
+    for b, c in enumerate(cells):      # warm-up (first use of the raw plans and scratch)
+        P.bbp_core_pmps(ctx, b, c)
+    stream = torch.cuda.current_stream()
+    ms, ring_len, bonds = [], 0, 0
+    for b, c in enumerate(cells):
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ring, legs, _ = P.bbp_core_pmps(ctx, b, c)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ring_len = len(ring)
+        bonds = max(bonds, max(x.shape[0] for x in ring))
+    P.bbp_destroy(ctx)
+    ms.sort()
+    return {"workload": workload, "core": "unit cell (up-triangle A, B, C) of each block",
+            "cores_timed": len(cells), "calls": len(ms), "ms_per_core_median": ms[len(ms) // 2],
+            "ms_per_core_min": ms[0], "pmps_tensors": ring_len, "pmps_bond_max": bonds,
+            "note": "two bubbles from the bottom and top faces, zipper into the pMPS, copy to host memory"}
+
+
 # -------------------------------------------------- many networks, serving
 
 def network_mix(n, seed):
@@ -886,8 +932,8 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=16, help="job templates of the serving stream")
     ap.add_argument("--serve-active", type=int, default=32, help="resident jobs at most (server slots)")
     ap.add_argument("--serve-no-fp64", action="store_true", help="skip the FP64 one-at-a-time baseline")
-    ap.add_argument("--only", choices=["batched", "serving"],
-                    help="run only the batched or the serving measurement and print it")
+    ap.add_argument("--only", choices=["batched", "serving", "core"],
+                    help="run only the batched, the serving or the core-extraction measurement and print it")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--peaks", action="store_true", help="measure the chip's ALU and tensor rates and exit")
     ap.add_argument("--kernel-case", choices=["fuse", "absorb", "panel", "panel_r", "svd"],
@@ -910,6 +956,8 @@ def main():
         prec_code = {"tf32": 1, "bf16": 2, "fp32": 3, "fp64": 0}[args.precision]
         if args.only == "batched":
             out = run_batched(args.batch, args.batch_rounds, 1, prec_code, groups=args.batch_pools)
+        elif args.only == "core":
+            out = run_core(args.workload, prec_code)
         else:
             out = run_serving(args.serve, args.serve_rate, prec_code, warm_s=min(5.0, args.serve / 4),
                               pool_n=args.serve_pool, max_active=args.serve_active,

@@ -202,6 +202,31 @@ bbp_status bbp_norm(bbp_ctx* ctx, double* log_norm_out);
 bbp_status bbp_get_message(bbp_ctx* ctx, int block, int face, int* k_out, int* shapes_out, double* data_out,
                            size_t cap);
 
+/* Core extraction (Sec. 2.3, "Core"): with the current messages, two
+ * boundary-MPS sweeps start from the bottom and top faces of `block`,
+ * truncate to chi like the message update, and leave the core sites open;
+ * the bottom bubble swallows every node before the core's last site in the
+ * bottom-up order, the top bubble every node after it.  They meet at two
+ * front lines, which the zipper contracts exactly, leaving a periodic MPS
+ * (pMPS) around the core, one tensor per open leg of the core.
+ * core_sites: ncore distinct global site ids of `block`.  Outputs, in
+ * caller-owned host buffers:
+ *   len_out       L, the number of pMPS tensors (at most cap_len);
+ *   shapes_out    3 L ints, (l, p, r) of each tensor in cyclic order; the r
+ *                 of tensor L-1 equals the l of tensor 0;
+ *   legs_out      2 L ints, (position in core_sites, leg slot 0..3) of the
+ *                 core leg that each tensor's index p joins;
+ *   data_out      the tensors back to back, row-major (l, p, r), complex128
+ *                 interleaved, at most cap doubles;
+ *   logscale_out  natural log of the scale the two bubbles factored out.
+ * The core's value with operators inserted is the exact contraction of its
+ * fused tensors with the pMPS.  Errors: BBP_ERR_ARG (block or site out of
+ * range, a core whose open legs do not face both bubbles, buffers too
+ * small), BBP_ERR_STATE (no partition or messages), BBP_ERR_NUMERIC (an
+ * SVD of a bubble reached its sweep limit). */
+bbp_status bbp_core_pmps(bbp_ctx* ctx, int block, const int* core_sites, int ncore, int cap_len, int* len_out,
+                         int* shapes_out, int* legs_out, double* data_out, size_t cap, double* logscale_out);
+
 /* Device bytes the context would hold for the given problem (estimate). */
 size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int by, int precision);
 
@@ -436,6 +461,18 @@ bbp_status bbp_k_fma_peak(int fp64, int blocks, int iters, void* out, double* fl
  * 4 ints per step: kind, id, nin, nout.  n_steps_out receives the count. */
 bbp_status bbp_plan_debug(int lattice, int Lx, int Ly, int periodic, int bx, int by, int block, int face, int* out,
                           int cap, int* n_steps_out);
+
+/* Host-side plan of a core extraction (no GPU needed; see bbp_core_pmps):
+ * for the core sites core_sites (global ids) of `block`, steps_out receives
+ * the swallow order of the bottom bubble and then of the top bubble, 4 ints
+ * per step as in bbp_plan_debug (capacity cap ints); info_out 7 ints: steps
+ * of the bottom bubble, steps of the top bubble, boundary lengths n and m of
+ * the two bubbles, the shared end runs a and c of the zipper, and the number
+ * L of pMPS tensors; legs_out 2 L ints (capacity 2 * cap_len): the (position
+ * in core_sites, slot) of each pMPS tensor's physical leg. */
+bbp_status bbp_core_plan_debug(int lattice, int Lx, int Ly, int periodic, int bx, int by, int block,
+                               const int* core_sites, int ncore, int* steps_out, int cap, int* info_out, int* legs_out,
+                               int cap_len);
 
 #ifdef __cplusplus
 }

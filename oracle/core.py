@@ -45,11 +45,12 @@ class ZipError(RuntimeError):
     pass
 
 
-def bubbles(bbp, coords, core: set):
+def bubbles(bbp, coords, core: set, traces: list | None = None):
     """The two bubbles of step 1 around the core sites ``core`` ((inst, local)
     keys) of the region ``coords``.  Returns (B, LB, lsB), (Tt, LT, lsT): the
     bottom-up and top-down boundary MPSs with their leg labels in boundary
-    order and their log scales."""
+    order and their log scales.  ``traces``, if given, receives the swallow
+    records of the two sweeps (see tn.sweep)."""
     region = build_region(bbp.geom, coords)
     keys = {(rs.inst, rs.local): rs for rs in region.sites}
     if not core or any(k not in keys for k in core):
@@ -58,8 +59,12 @@ def bubbles(bbp, coords, core: set):
     msgs = bbp.region_msgs(region)
     last = max(core, key=lambda k: tn.sweep_key(TOP, keys[k].pos4))
     p4 = keys[last].pos4
-    B, LB, lsB = tn.sweep(region, TOP, T, msgs, bbp.chi, skip=core, stop=tn.sweep_key(TOP, p4), raw=True)
-    Tt, LT, lsT = tn.sweep(region, BOTTOM, T, msgs, bbp.chi, skip=core, stop=tn.sweep_key(BOTTOM, p4), raw=True)
+    tb, tt = ([], []) if traces is not None else (None, None)
+    B, LB, lsB = tn.sweep(region, TOP, T, msgs, bbp.chi, trace=tb, skip=core, stop=tn.sweep_key(TOP, p4), raw=True)
+    Tt, LT, lsT = tn.sweep(region, BOTTOM, T, msgs, bbp.chi, trace=tt, skip=core, stop=tn.sweep_key(BOTTOM, p4),
+                           raw=True)
+    if traces is not None:
+        traces.extend([tb, tt])
     return region, (B, LB, lsB), (Tt, LT, lsT)
 
 

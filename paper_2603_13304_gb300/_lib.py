@@ -25,7 +25,7 @@ BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
 
 EXPORTS = [
     "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
-    "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message",
+    "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message", "bbp_core_pmps", "bbp_core_plan_debug",
     "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
     "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_panel_cluster", "bbp_k_panel_qr", "bbp_k_svd_work_bytes_rand", "bbp_k_svd_trunc_rand", "bbp_k_fma_peak", "bbp_set_hermitise", "bbp_expect_product", "bbp_bond_energies", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
     "bbp_batch_iterate", "bbp_server_create", "bbp_job_footprint_bytes", "bbp_server_submit", "bbp_server_step",
@@ -65,6 +65,8 @@ _PROTOS = {
     "bbp_energy_per_site": (_i, [_vp, _dp]),
     "bbp_norm": (_i, [_vp, _dp]),
     "bbp_get_message": (_i, [_vp, _i, _i, _ip, _ip, _dp, ctypes.c_size_t]),
+    "bbp_core_pmps": (_i, [_vp, _i, _ip, _i, _i, _ip, _ip, _ip, _dp, ctypes.c_size_t, _dp]),
+    "bbp_core_plan_debug": (_i, [_i, _i, _i, _i, _i, _i, _i, _ip, _i, _ip, _i, _ip, _ip, _i]),
     "bbp_footprint_bytes": (ctypes.c_size_t, [_i, _i, _i, _i, _i, _i, _i]),
     "bbp_info": (_i, [_vp, _ip, _ip, _ip]),
     "bbp_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _dp]),
@@ -285,6 +287,26 @@ def bbp_get_message(ctx, block: int, face: int, cap: int = 1 << 22):
     return out
 
 
+def bbp_core_pmps(ctx, block: int, core_sites, cap: int = 1 << 24, cap_len: int = 64):
+    """The pMPS around core sites (global ids) of a block: (tensors (l, p, r)
+    in cyclic order, [(position in core_sites, slot)] per tensor, logscale)."""
+    s = np.ascontiguousarray(core_sites, dtype=np.int32)
+    n = ctypes.c_int()
+    shapes = np.zeros(3 * cap_len, dtype=np.int32)
+    legs = np.zeros(2 * cap_len, dtype=np.int32)
+    data = np.zeros(cap, dtype=np.float64)
+    ls = ctypes.c_double()
+    _check(lib().bbp_core_pmps(ctx, block, _iptr(s), len(s), cap_len, ctypes.byref(n), _iptr(shapes), _iptr(legs),
+                               _dptr(data), cap, ctypes.byref(ls)), ctx)
+    out, off = [], 0
+    for q in range(n.value):
+        l, p, r = shapes[3 * q:3 * q + 3]
+        k = int(l * p * r)
+        out.append(data[off:off + 2 * k].view(np.complex128).reshape(l, p, r).copy())
+        off += 2 * k
+    return out, [(int(legs[2 * q]), int(legs[2 * q + 1])) for q in range(n.value)], ls.value
+
+
 def bbp_footprint_bytes(lattice, n_sites, D, chi, bx, by, precision=FP64) -> int:
     return int(lib().bbp_footprint_bytes(lattice, n_sites, D, chi, bx, by, precision))
 
@@ -464,6 +486,20 @@ def bbp_plan_debug(lattice, Lx, Ly, periodic, bx, by, block, face):
     _check(lib().bbp_plan_debug(lattice, Lx, Ly, int(periodic), bx, by, block, face, _iptr(out), out.size,
                                 ctypes.byref(n)))
     return out[:4 * n.value].reshape(-1, 4)
+
+def bbp_core_plan_debug(lattice, Lx, Ly, periodic, bx, by, block, core_sites):
+    """(bottom steps, top steps, (n, m, a, c, L), legs) of a core extraction's host plan."""
+    s = np.ascontiguousarray(core_sites, dtype=np.int32)
+    out = np.zeros(4 * 8192, dtype=np.int32)
+    info = np.zeros(7, dtype=np.int32)
+    legs = np.zeros(2 * 256, dtype=np.int32)
+    _check(lib().bbp_core_plan_debug(lattice, Lx, Ly, int(periodic), bx, by, block, _iptr(s), len(s), _iptr(out),
+                                     out.size, _iptr(info), _iptr(legs), 256))
+    nb, nt = int(info[0]), int(info[1])
+    steps = out[:4 * (nb + nt)].reshape(-1, 4)
+    L = int(info[6])
+    return (steps[:nb], steps[nb:], tuple(int(x) for x in info[2:7]),
+            [(int(legs[2 * q]), int(legs[2 * q + 1])) for q in range(L)])
 
 # ------------------------------------------------------- many problems
 

@@ -350,6 +350,46 @@ bbp_status bbp_get_message(bbp_ctx* ctx, int block, int face, int* k_out, int* s
   return guarded([&] { return from(ctx, ctx->eng.get_message(block, face, k_out, shapes_out, data_out, cap)); });
 }
 
+bbp_status bbp_core_pmps(bbp_ctx* ctx, int block, const int* core_sites, int ncore, int cap_len, int* len_out,
+                         int* shapes_out, int* legs_out, double* data_out, size_t cap, double* logscale_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!core_sites || ncore <= 0 || !len_out || !shapes_out || !legs_out || !data_out || !logscale_out)
+    return set_err(BBP_ERR_ARG, "bad arguments");
+  return guarded([&]() -> bbp_status {
+    bbp::Engine& e = ctx->eng;
+    if (!e.partitioned || !e.messages_ready) return set_err(BBP_ERR_STATE, "partition and messages are required first");
+    if (block < 0 || block >= e.geom.n_blocks()) return set_err(BBP_ERR_ARG, "block out of range");
+    const bbp::Block& b = e.geom.blocks[block];
+    std::vector<int> core;
+    for (int q = 0; q < ncore; ++q) {
+      auto it = std::find(b.gids.begin(), b.gids.end(), core_sites[q]);
+      if (it == b.gids.end()) return set_err(BBP_ERR_ARG, "site not in block");
+      core.push_back((int)(it - b.gids.begin()));
+    }
+    std::vector<bbp::TShape> shapes;
+    std::vector<std::array<int, 2>> legs;
+    std::vector<double2> data;
+    double ls = 0.0;
+    if (int rc = e.core_pmps(block, core, shapes, legs, data, &ls)) return from(ctx, rc);
+    if ((int)shapes.size() > cap_len) return set_err(BBP_ERR_ARG, "shapes buffer too small");
+    if (2 * data.size() > cap) return set_err(BBP_ERR_ARG, "output buffer too small");
+    *len_out = (int)shapes.size();
+    for (size_t q = 0; q < shapes.size(); ++q) {
+      shapes_out[3 * q] = shapes[q].l;
+      shapes_out[3 * q + 1] = shapes[q].p;
+      shapes_out[3 * q + 2] = shapes[q].r;
+      legs_out[2 * q] = legs[q][0];
+      legs_out[2 * q + 1] = legs[q][1];
+    }
+    for (size_t k = 0; k < data.size(); ++k) {
+      data_out[2 * k] = data[k].x;
+      data_out[2 * k + 1] = data[k].y;
+    }
+    *logscale_out = ls;
+    return BBP_OK;
+  });
+}
+
 size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int by, int precision) {
   (void)precision;
   const size_t z = 16;
@@ -586,6 +626,54 @@ bbp_status bbp_plan_debug(int lattice, int Lx, int Ly, int periodic, int bx, int
       out[4 * s + 3] = plan.steps[s].nout;
     }
     *n_steps_out = ns;
+    return BBP_OK;
+  });
+}
+
+bbp_status bbp_core_plan_debug(int lattice, int Lx, int Ly, int periodic, int bx, int by, int block,
+                               const int* core_sites, int ncore, int* steps_out, int cap, int* info_out, int* legs_out,
+                               int cap_len) {
+  return guarded([&]() -> bbp_status {
+    if (!core_sites || ncore <= 0 || !steps_out || !info_out || !legs_out) return set_err(BBP_ERR_ARG, "NULL argument");
+    bbp::Geometry g;
+    std::string err = g.build(lattice, Lx, Ly, periodic != 0, bx, by);
+    if (!err.empty()) return set_err(BBP_ERR_TILING, err);
+    if (block < 0 || block >= g.n_blocks()) return set_err(BBP_ERR_ARG, "block out of range");
+    const bbp::Block& b = g.blocks[block];
+    std::vector<int> core;
+    for (int q = 0; q < ncore; ++q) {
+      auto it = std::find(b.gids.begin(), b.gids.end(), core_sites[q]);
+      if (it == b.gids.end()) return set_err(BBP_ERR_ARG, "site not in block");
+      core.push_back((int)(it - b.gids.begin()));
+    }
+    bbp::Region R;
+    err = bbp::build_region(g, {{b.X, b.Y}}, R);
+    if (!err.empty()) return set_err(BBP_ERR_TILING, err);
+    bbp::CorePlan cp;
+    err = bbp::compile_core(g, R, core, cp);
+    if (!err.empty()) return set_err(BBP_ERR_ARG, err);
+    const int nb = (int)cp.bottom.steps.size(), nt = (int)cp.top.steps.size();
+    if (4 * (nb + nt) > cap || (int)cp.legs.size() > cap_len) return set_err(BBP_ERR_ARG, "output buffer too small");
+    int o = 0;
+    for (const bbp::SweepPlan* pl : {&cp.bottom, &cp.top})
+      for (size_t s = 0; s < pl->steps.size(); ++s) {
+        const bbp::SweepNode& nd = pl->nodes[s];
+        steps_out[o++] = nd.site ? 0 : 1;
+        steps_out[o++] = nd.site ? nd.gid : nd.msg_dir * 1024 + nd.msg_index;
+        steps_out[o++] = pl->steps[s].nin;
+        steps_out[o++] = pl->steps[s].nout;
+      }
+    info_out[0] = nb;
+    info_out[1] = nt;
+    info_out[2] = (int)cp.bottom.final_labels.size();
+    info_out[3] = (int)cp.top.final_labels.size();
+    info_out[4] = cp.a;
+    info_out[5] = cp.c;
+    info_out[6] = (int)cp.legs.size();
+    for (size_t q = 0; q < cp.legs.size(); ++q) {
+      legs_out[2 * q] = cp.legs[q][0];
+      legs_out[2 * q + 1] = cp.legs[q][1];
+    }
     return BBP_OK;
   });
 }

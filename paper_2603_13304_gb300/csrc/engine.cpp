@@ -1080,6 +1080,19 @@ int Engine::run_sweep(SweepJob& job, SweepWork& w) {
     if (int rc = normalise(c)) return rc;
   }
   const int n = (int)pos.size();
+  if (plan.raw) {                      // a bubble halted before a core: the boundary as it stands
+    if ((int)job.dest.size() != n || (int)tr.final_mps.size() != n)
+      return fail(this, 8, "sweep: raw boundary length mismatch");
+    for (int q = 0; q < n; ++q) {
+      const TShape t = sh[q];
+      const TShape f = tr.final_mps[q];
+      if (t.l != f.l || t.p != f.p || t.r != f.r) return fail(this, 8, "sweep: raw boundary shape mismatch");
+      CK(launch_copy_tensor(slot(pos[q]), (C*)job.dest[q], t.l, t.p, t.r, false, s));
+      ++launches;
+    }
+    sweep_launches += launches;
+    return 0;
+  }
   if (n < 3) return fail(this, 8, "sweep: final boundary too short");
   {
     const int t = take();
@@ -1690,6 +1703,214 @@ int Engine::get_message_t(int block, int face, int* k, int* shapes, double* data
     }
     off += 2 * (size_t)t.size();
   }
+  return 0;
+}
+
+// ------------------------------------------------------------ core (Sec. 2.3)
+//
+// Two bubbles approach the core from the bottom and top faces of the block:
+// the bottom-up bubble swallows every node before the core's last site (in
+// the bottom-up sweep order), the top-down bubble every node after it; both
+// skip the core, truncate like the message update, and return their
+// boundary as it stands (raw plans).  The bubbles share their two end bonds
+// and the legs of the two front lines; the zipper contracts each front line
+// into one matrix (E_L on the left, E_R on the right), which is folded into
+// the last tensor of the bottom bubble's core segment (E_R) and of the top
+// bubble's (E_L^T).  What is left is the periodic MPS around the core: the
+// bottom bubble's core legs left to right, then the top bubble's right to
+// left, the last tensor's right bond closing onto the first one's left bond.
+
+int Engine::core_pmps(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
+                      std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale) {
+  DeviceScope ds(device);
+  return precision == 0 ? core_pmps_t<double2>(block, core, shapes, legs, data, logscale)
+                        : core_pmps_t<float2>(block, core, shapes, legs, data, logscale);
+}
+
+template <typename C>
+int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
+                        std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale) {
+  if (!partitioned || !messages_ready) return fail(this, 8, "partition and messages are required first");
+  if (block < 0 || block >= (int)geom.blocks.size()) return fail(this, 1, "block out of range");
+  const Region& R = block_regions[block];
+  CorePlan cp;
+  const std::string err = compile_core(geom, R, core, cp);
+  if (!err.empty()) return fail(this, 1, "core: " + err);
+  const SweepPlan& pb = cp.bottom;
+  const SweepPlan& pt = cp.top;
+  const int n = (int)pb.final_labels.size(), m = (int)pt.final_labels.size();
+  const int a = cp.a, c = cp.c;
+
+  std::vector<DBuf*> tmp;
+  struct TmpGuard {
+    std::vector<DBuf*>& v;
+    ~TmpGuard() { for (DBuf* b : v) delete b; }
+  } guard{tmp};
+  DBuf outb[2], res, scratch, fold;    // res: [0..1] log scales, [2..3] status words of the bubbles
+  // every buffer above outlives the work queued on it, on every return path
+  struct SyncGuard {
+    Engine* e;
+    ~SyncGuard() {
+      if (e->stream) cudaStreamSynchronize(e->stream);
+      for (size_t i = 0; e->workers && i < 2 && i < e->workers->w.size(); ++i)
+        cudaStreamSynchronize(e->workers->w[i]->stream);
+    }
+  } sync_guard{this};
+  std::vector<SweepJob> jobs(2);
+  if (int rc = fill_job<C>(R, pb, jobs[0], {}, tmp)) return rc;
+  if (int rc = fill_job<C>(R, pt, jobs[1], {}, tmp)) return rc;
+  if ((int)jobs[0].tr.final_mps.size() != n || (int)jobs[1].tr.final_mps.size() != m)
+    return fail(this, 8, "core bubbles: boundary length disagrees with the plan");
+  for (int j = 0; j < 2; ++j) {
+    size_t tot = 0;
+    for (const TShape& t : jobs[j].tr.final_mps) tot += (size_t)t.size();
+    if (!outb[j].ensure(sizeof(C) * tot + 256, stream)) return fail(this, 2, "allocation failed");
+    size_t off = 0;
+    jobs[j].dest.clear();
+    for (const TShape& t : jobs[j].tr.final_mps) {
+      jobs[j].dest.push_back((C*)outb[j].p + off);
+      off += (size_t)t.size();
+    }
+  }
+  if (!res.ensure(4 * sizeof(double) + 256, stream)) return fail(this, 2, "allocation failed");
+  {
+    std::lock_guard<std::mutex> lk(pool_ref().mu);
+    for (int i = 0; i < 2; ++i)
+      if (!work(i)) return fail(this, 3, "stream creation failed");
+    CK(cudaStreamWaitEvent(stream, workers->last_done, 0));   // the pool's previous user
+    if (int rc = reserve_workers(jobs, 2)) return rc;
+    cudaEvent_t fork;
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    struct EvGuard {
+      cudaEvent_t e;
+      ~EvGuard() { cudaEventDestroy(e); }
+    } eg{fork};
+    CK(cudaEventRecord(fork, stream));
+    for (int i = 0; i < 2; ++i) {
+      SweepWork& w = *workers->w[i];
+      CK(cudaStreamWaitEvent(w.stream, fork, 0));
+      if (int rc = run_sweep<C>(jobs[i], w)) return rc;
+      double* rp = (double*)res.p;
+      CK(cudaMemcpyAsync(rp + i, w.logscale, sizeof(double), cudaMemcpyDeviceToDevice, w.stream));
+      CK(cudaMemcpyAsync(rp + 2 + i, w.status, 2 * sizeof(int), cudaMemcpyDeviceToDevice, w.stream));
+      CK(cudaEventRecord(w.done, w.stream));
+      CK(cudaStreamWaitEvent(stream, w.done, 0));
+    }
+    CK(cudaEventRecord(workers->last_done, stream));
+  }
+
+  // the zipper, on the context's stream (operands in outb and private scratch)
+  const std::vector<TShape>& SB = jobs[0].tr.final_mps;
+  const std::vector<TShape>& ST = jobs[1].tr.final_mps;
+  auto Bq = [&](int q) { return (const C*)jobs[0].dest[q]; };
+  auto Tq = [&](int q) { return (const C*)jobs[1].dest[q]; };
+  size_t mb = 1, mt = 1, mp = 1, mT = 1;
+  for (const TShape& t : SB) { mb = std::max<size_t>(mb, std::max(t.l, t.r)); mp = std::max<size_t>(mp, t.p); }
+  for (const TShape& t : ST) {
+    mt = std::max<size_t>(mt, std::max(t.l, t.r));
+    mp = std::max<size_t>(mp, t.p);
+    mT = std::max<size_t>(mT, (size_t)t.size());
+  }
+  const size_t capE = mb * mt, capF = mb * mp * mt;
+  if (!scratch.ensure(sizeof(C) * (4 * capE + capF + mT) + 256, stream)) return fail(this, 2, "allocation failed");
+  C* EL = (C*)scratch.p;
+  C* ER = EL + capE;
+  C* Ea = ER + capE;
+  C* Eb = Ea + capE;
+  C* F = Eb + capE;
+  C* Pm = F + capF;
+  const C one = one_of<C>(), zero = zero_of<C>();
+  // left front line: E[x, y] (x a bond of the bottom bubble, y of the top one)
+  int ex = 1, ey = 1;
+  CK(launch_fill(Ea, 1, 1.0, 0.0, stream));
+  for (int q = 0; q < a; ++q) {
+    const TShape b = SB[q], t = ST[m - 1 - q];
+    if (b.l != ex || t.r != ey || b.p != t.p) return fail(this, 8, "zipper: shapes do not match");
+    // F[y, (p z)] = sum_x E[x, y] B[x, (p z)]
+    CK(launch_zgemm('T', 'N', ey, b.p * b.r, ex, one, Ea, ey, 0, Bq(q), b.p * b.r, 0, zero, F, b.p * b.r, 0, 1, stream));
+    const int perm[3] = {2, 1, 0};   // T[w, p, y] -> [y, p, w]
+    CK(launch_permute3(Tq(m - 1 - q), t.l, t.p, t.r, perm, Pm, stream));
+    // E'[z, w] = sum_{(y p)} F[(y p), z] P[(y p), w]
+    CK(launch_zgemm('T', 'N', b.r, t.l, ey * b.p, one, F, b.r, 0, Pm, t.l, 0, zero, Eb, t.l, 0, 1, stream));
+    std::swap(Ea, Eb);
+    ex = b.r;
+    ey = t.l;
+  }
+  const int elx = ex, ely = ey;
+  CK(cudaMemcpyAsync(EL, Ea, sizeof(C) * (size_t)ex * ey, cudaMemcpyDeviceToDevice, stream));
+  // right front line: E[z, w] from the right ends inwards
+  ex = 1;
+  ey = 1;
+  CK(launch_fill(Ea, 1, 1.0, 0.0, stream));
+  for (int q = 0; q < c; ++q) {
+    const TShape b = SB[n - 1 - q], t = ST[q];
+    if (b.r != ex || t.l != ey || b.p != t.p) return fail(this, 8, "zipper: shapes do not match");
+    // G[(x p), w] = sum_z B[(x p), z] E[z, w]
+    CK(launch_zgemm('N', 'N', b.l * b.p, ey, ex, one, Bq(n - 1 - q), ex, 0, Ea, ey, 0, zero, F, ey, 0, 1, stream));
+    const int perm[3] = {1, 0, 2};   // T[w, p, y] -> [p, w, y]
+    CK(launch_permute3(Tq(q), t.l, t.p, t.r, perm, Pm, stream));
+    // E'[x, y] = sum_{(p w)} G[x, (p w)] P[(p w), y]
+    CK(launch_zgemm('N', 'N', b.l, t.r, b.p * ey, one, F, b.p * ey, 0, Pm, t.r, 0, zero, Eb, t.r, 0, 1, stream));
+    std::swap(Ea, Eb);
+    ex = b.l;
+    ey = t.r;
+  }
+  const int erx = ex, ery = ey;
+  CK(cudaMemcpyAsync(ER, Ea, sizeof(C) * (size_t)ex * ey, cudaMemcpyDeviceToDevice, stream));
+
+  // the pMPS: B[a .. n-c-1] (the last times E_R), then T[c .. m-a-1] (the last times E_L^T)
+  const int kb = n - c - 1, kt = m - a - 1;
+  if (SB[kb].r != erx || ST[c].l != ery || ST[kt].r != ely || SB[a].l != elx)
+    return fail(this, 8, "zipper: the ring does not close");
+  const size_t fb = (size_t)SB[kb].l * SB[kb].p * ery, ft = (size_t)ST[kt].l * ST[kt].p * elx;
+  if (!fold.ensure(sizeof(C) * (fb + ft) + 256, stream)) return fail(this, 2, "allocation failed");
+  C* FB = (C*)fold.p;
+  C* FT = FB + fb;
+  CK(launch_zgemm('N', 'N', SB[kb].l * SB[kb].p, ery, erx, one, Bq(kb), erx, 0, ER, ery, 0, zero, FB, ery, 0, 1,
+                  stream));
+  CK(launch_zgemm('N', 'T', ST[kt].l * ST[kt].p, elx, ely, one, Tq(kt), ely, 0, EL, ely, 0, zero, FT, elx, 0, 1,
+                  stream));
+  struct Piece { const C* p; TShape sh; };
+  std::vector<Piece> ring;
+  for (const auto& rq : cp.ring) {
+    const int q = rq[1];
+    if (rq[0] == 0) {
+      TShape t = SB[q];
+      if (q == kb) t.r = ery;
+      ring.push_back({q == kb ? FB : Bq(q), t});
+    } else {
+      TShape t = ST[q];
+      if (q == kt) t.r = elx;
+      ring.push_back({q == kt ? FT : Tq(q), t});
+    }
+  }
+  const int L = (int)ring.size();
+  for (int q = 0; q < L; ++q)
+    if (ring[q].sh.r != ring[(q + 1) % L].sh.l) return fail(this, 8, "zipper: pMPS bonds do not close");
+  shapes.clear();
+  legs = cp.legs;
+  size_t tot = 0;
+  for (const Piece& pc : ring) {
+    shapes.push_back(pc.sh);
+    tot += (size_t)pc.sh.size();
+  }
+  std::vector<C> host(tot);
+  size_t off = 0;
+  for (const Piece& pc : ring) {
+    CK(cudaMemcpyAsync(host.data() + off, pc.p, sizeof(C) * (size_t)pc.sh.size(), cudaMemcpyDeviceToHost, stream));
+    off += (size_t)pc.sh.size();
+  }
+  double hres[4];
+  CK(cudaMemcpyAsync(hres, res.p, sizeof(hres), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  int st[4];
+  std::memcpy(&st[0], &hres[2], 2 * sizeof(int));
+  std::memcpy(&st[2], &hres[3], 2 * sizeof(int));
+  if (st[1] || st[3]) return fail(this, 7, "a tensor-core wait timed out in a core bubble");
+  if (st[0] || st[2]) return fail(this, 5, "an SVD did not converge in a core bubble");
+  data.resize(tot);
+  for (size_t e = 0; e < tot; ++e) data[e] = make_double2((double)host[e].x, (double)host[e].y);
+  *logscale = hres[0] + hres[1];
   return 0;
 }
 

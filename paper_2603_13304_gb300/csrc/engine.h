@@ -158,6 +158,14 @@ class Engine {
   int bond_energies(const std::vector<std::array<int, 2>>& bonds, std::vector<double>& out);
   int log_norm(double* out);
   int get_message(int block, int face, int* k, int* shapes, double* data, size_t cap);
+  // Core extraction (Sec. 2.3, "Core"): two bubbles from the bottom and top
+  // faces of `block` that leave the sites `core` (local indices) open, joined
+  // by the zipper into a periodic MPS around the core.  Output on the host,
+  // complex128: the pMPS tensors in cyclic order (shapes l, p, r), the
+  // (position in `core`, slot) of each tensor's physical leg, and the log of
+  // the scale factored out of the two bubbles.
+  int core_pmps(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
+                std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale);
 
  private:
   SweepWork* work(size_t i);
@@ -178,6 +186,9 @@ class Engine {
                        std::vector<double>& logscale, std::vector<double>& re, std::vector<double>& im);
   template <typename C> int log_norm_t(double* out);
   template <typename C> int get_message_t(int block, int face, int* k, int* shapes, double* data, size_t cap);
+  template <typename C>
+  int core_pmps_t(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
+                  std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale);
   void job_needs(const SweepJob& job, size_t need[7]) const;
   // one captured iteration per message-buffer parity, valid while the
   // signature (shapes and device pointers of every job) is unchanged

@@ -36,9 +36,34 @@ void sweep_key(int out_dir, P4 p, long long& depth, long long& lat) {
   }
 }
 
+struct PartialSpec {
+  const std::vector<std::array<int, 2>>* skip = nullptr;
+  long long stop_depth = 0, stop_lat = 0;
+};
+
+std::string compile_impl(const Geometry& g, const Region& R, int out_dir, const PartialSpec* part, SweepPlan& plan);
+
 }  // namespace
 
+void plan_sweep_key(int out_dir, P4 p, long long& depth, long long& lat) { sweep_key(out_dir, p, depth, lat); }
+
 std::string compile_sweep(const Geometry& g, const Region& R, int out_dir, SweepPlan& plan) {
+  return compile_impl(g, R, out_dir, nullptr, plan);
+}
+
+std::string compile_partial_sweep(const Geometry& g, const Region& R, int out_dir,
+                                  const std::vector<std::array<int, 2>>& skip, long long stop_depth,
+                                  long long stop_lat, SweepPlan& plan) {
+  PartialSpec ps;
+  ps.skip = &skip;
+  ps.stop_depth = stop_depth;
+  ps.stop_lat = stop_lat;
+  return compile_impl(g, R, out_dir, &ps, plan);
+}
+
+namespace {
+
+std::string compile_impl(const Geometry& g, const Region& R, int out_dir, const PartialSpec* part, SweepPlan& plan) {
   const Lattice& lat = g.lat;
   plan = SweepPlan();
   plan.out_dir = out_dir;
@@ -51,6 +76,9 @@ std::string compile_sweep(const Geometry& g, const Region& R, int out_dir, Sweep
 
   std::vector<SweepNode> nodes;
   for (const RSite& rs : R.sites) {
+    if (part && std::find(part->skip->begin(), part->skip->end(), std::array<int, 2>{rs.inst, rs.local}) !=
+                    part->skip->end())
+      continue;
     SweepNode n;
     n.site = true; n.inst = rs.inst; n.local = rs.local; n.gid = rs.gid;
     n.nlegs = 4;
@@ -93,6 +121,13 @@ std::string compile_sweep(const Geometry& g, const Region& R, int out_dir, Sweep
     if (a.key_depth != b.key_depth) return a.key_depth < b.key_depth;
     return a.key_lat < b.key_lat;
   });
+  if (part) {   // the bubble halts before the first node at or after the stop key
+    size_t keep = 0;
+    while (keep < nodes.size() && (nodes[keep].key_depth < part->stop_depth ||
+                                   (nodes[keep].key_depth == part->stop_depth && nodes[keep].key_lat < part->stop_lat)))
+      ++keep;
+    nodes.resize(keep);
+  }
 
   auto end_label = [&](int d, bool at_start) {
     int K = (int)R.sides[d].size();
@@ -149,6 +184,12 @@ std::string compile_sweep(const Geometry& g, const Region& R, int out_dir, Sweep
     labels.insert(labels.begin() + i, newl.begin(), newl.end());
     plan.steps.push_back(st);
   }
+  if (part) {
+    plan.raw = true;
+    plan.final_labels = labels;
+    plan.nodes = std::move(nodes);
+    return "";
+  }
   // final boundary
   const auto& O = R.sides[out_dir];
   std::vector<int> want;
@@ -160,6 +201,73 @@ std::string compile_sweep(const Geometry& g, const Region& R, int out_dir, Sweep
   plan.out_reversed = !chain_forward;
   plan.out_len = (int)O.size();
   plan.nodes = std::move(nodes);
+  return "";
+}
+
+}  // namespace
+
+std::string compile_core(const Geometry& g, const Region& R, const std::vector<int>& core, CorePlan& cp) {
+  cp = CorePlan();
+  if (core.empty()) return "the core is empty";
+  std::vector<std::array<int, 2>> skip;
+  std::vector<const RSite*> cs;
+  for (int loc : core) {
+    for (const auto& sk : skip)
+      if (sk[1] == loc) return "core site repeated";
+    const RSite* rs = nullptr;
+    for (const RSite& x : R.sites)
+      if (x.inst == 0 && x.local == loc) rs = &x;
+    if (!rs) return "core site out of range";
+    skip.push_back({0, loc});
+    cs.push_back(rs);
+  }
+  long long bd = 0, bl = 0;
+  int last = -1;
+  for (int k = 0; k < (int)cs.size(); ++k) {
+    long long dd, ll;
+    sweep_key(TOP, cs[k]->pos, dd, ll);
+    if (last < 0 || dd > bd || (dd == bd && ll > bl)) { bd = dd; bl = ll; last = k; }
+  }
+  long long td, tl;
+  sweep_key(BOTTOM, cs[last]->pos, td, tl);
+  std::string err = compile_partial_sweep(g, R, TOP, skip, bd, bl, cp.bottom);
+  if (err.empty()) err = compile_partial_sweep(g, R, BOTTOM, skip, td, tl, cp.top);
+  if (!err.empty()) return err;
+  const std::vector<int>& LB = cp.bottom.final_labels;
+  const std::vector<int>& LT = cp.top.final_labels;
+  const int n = (int)LB.size(), m = (int)LT.size();
+  auto in_t = [&](int lab) { return std::find(LT.begin(), LT.end(), lab) != LT.end(); };
+  auto in_b = [&](int lab) { return std::find(LB.begin(), LB.end(), lab) != LB.end(); };
+  int a = 0;
+  while (a < n && in_t(LB[a])) ++a;
+  int c = 0;
+  while (c < n - a && in_t(LB[n - 1 - c])) ++c;
+  if (a == 0 || c == 0 || a + c > m) return "the bubbles do not share both end bonds";
+  for (int q = 0; q < a; ++q)
+    if (LB[q] != LT[m - 1 - q]) return "the front lines of the bubbles do not match";
+  for (int q = 0; q < c; ++q)
+    if (LB[n - 1 - q] != LT[q]) return "the front lines of the bubbles do not match";
+  for (int q = a; q < n - c; ++q)
+    if (in_t(LB[q])) return "a shared leg lies between the core legs";
+  for (int q = c; q < m - a; ++q)
+    if (in_b(LT[q])) return "a shared leg lies between the core legs";
+  if (a >= n - c || c >= m - a) return "the core needs open legs towards both faces";
+  cp.a = a;
+  cp.c = c;
+  auto add = [&](int side, int q, int lab) {
+    for (int k = 0; k < (int)cs.size(); ++k)
+      for (int sl = 0; sl < 4; ++sl)
+        if (cs[k]->label[sl] == lab) {
+          cp.ring.push_back({side, q});
+          cp.legs.push_back({k, sl});
+          return true;
+        }
+    return false;
+  };
+  for (int q = a; q < n - c; ++q)
+    if (!add(0, q, LB[q])) return "a pMPS leg is not a leg of the core";
+  for (int q = c; q < m - a; ++q)
+    if (!add(1, q, LT[q])) return "a pMPS leg is not a leg of the core";
   return "";
 }
 
@@ -243,6 +351,10 @@ std::string simulate_shapes(const SweepPlan& plan, const LegDims& dims, int chi,
     rec.split = nw;
     tr.max_len = std::max(tr.max_len, (int)A.size());
     tr.steps.push_back(rec);
+  }
+  if (plan.raw) {                      // the boundary as it stands, ends included
+    tr.final_mps = A;
+    return "";
   }
   // merge the two end tensors (both of leg dimension 1)
   if (A.size() < 3) return "final boundary too short";

@@ -49,9 +49,40 @@ struct SweepPlan {
   bool start_reversed = false;      // start tensors enter transposed (r, p, l)
   bool out_reversed = false;        // final MPS must be reversed into canonical order
   int out_len = 0;                  // number of out-face legs
+  // A bubble that halts before a core (Sec. 2.3, "Core"): the boundary is
+  // returned as it stands, end-bond tensors included, in boundary order.
+  bool raw = false;
+  std::vector<int> final_labels;    // leg label of every boundary position (raw plans)
 };
 
 std::string compile_sweep(const Geometry& g, const Region& R, int out_dir, SweepPlan& plan);
+
+// Sweep key of a position for a sweep towards out_dir.
+void plan_sweep_key(int out_dir, P4 p, long long& depth, long long& lat);
+
+// A raw plan: the sweep towards out_dir never swallows the sites in `skip`
+// (region instance, local index) and halts before the first node whose key
+// is (stop_depth, stop_lat) or later.
+std::string compile_partial_sweep(const Geometry& g, const Region& R, int out_dir,
+                                  const std::vector<std::array<int, 2>>& skip, long long stop_depth,
+                                  long long stop_lat, SweepPlan& plan);
+
+// Core extraction (Sec. 2.3, "Core"): the two bubbles around the core sites
+// `core` (local indices of the single-block region R) and the structure of
+// the zipper that joins them.  The bottom bubble (towards TOP) swallows every
+// node before the core's last site in the bottom-up order, the top bubble
+// (towards BOTTOM) every node after it; neither swallows the core.  Their
+// boundaries share the a leftmost legs of the bottom one (the a rightmost of
+// the top one, reversed) and the c rightmost (the c leftmost of the top one);
+// the legs between are the core's.  The pMPS takes, in cyclic order, the
+// bottom boundary's positions a .. n-c-1, then the top one's c .. m-a-1.
+struct CorePlan {
+  SweepPlan bottom, top;
+  int a = 0, c = 0;
+  std::vector<std::array<int, 2>> ring;   // per pMPS tensor: (0 bottom / 1 top, boundary position)
+  std::vector<std::array<int, 2>> legs;   // per pMPS tensor: (position in core, slot of that site)
+};
+std::string compile_core(const Geometry& g, const Region& R, const std::vector<int>& core, CorePlan& cp);
 
 // ---------------------------------------------------------- shape simulation
 

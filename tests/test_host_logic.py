@@ -91,3 +91,64 @@ def test_null_arguments_return_errors(L):
     assert L.bbp_partition_blocks(None, 3, 3) == 1
     assert L.bbp_iterate(None, 1e-8, 1, None, None) == 1
     assert P.bbp_footprint_bytes(1, 36, 4, 32, 2, 2) > 0
+
+
+CORES = [
+    ("square", (6, 6, 3, 3), 0, [4]),
+    ("square", (6, 6, 3, 3), 3, [3, 4]),
+    ("square", (6, 6, 3, 3), 0, [1, 4, 5]),
+    ("square", (4, 4, 2, 2), 0, [0, 1, 2, 3]),
+    ("kagome", (6, 2, 2), 0, "cell"),
+    ("kagome", (9, 3, 3), 1, "cell"),
+]
+
+
+def _steps(trace):
+    out = []
+    for rec in trace:
+        ident = rec[-1]
+        out.append((0, ident[1], rec[2], rec[3]) if ident[0] == "site" else (1, ident[1] * 1024 + ident[2], rec[2], rec[3]))
+    return out
+
+
+@pytest.mark.parametrize("kind,args,block,core", CORES)
+def test_core_plan_matches_oracle_bubbles(L, kind, args, block, core):
+    """The host plan of a core extraction (bbp_core_plan_debug) against the
+    oracle's two bubbles and zipper (Sec. 2.3): same swallow order and legs
+    per step in both bubbles, same boundary lengths, same shared end runs,
+    and the same core leg under every pMPS tensor."""
+    from oracle import core as C
+    if kind == "square":
+        geom = Geometry.square(*args)
+        lat, Lx, Ly, per, bx, by = 0, args[0], args[1], 0, args[2], args[3]
+    else:
+        geom = Geometry.kagome(*args)
+        lat, Lx, Ly, per, bx, by = 1, args[0], args[1], 1, args[2], args[2]
+    n = geom.n_sites
+    bb = BlockBP(geom, syn.gaussian_peps(n, 2, 1, seed=1), chi=4)
+    bb.init_messages(syn.initial_edge_matrices(n, 1, seed=2))
+    b = geom.blocks[block]
+    if core == "cell":    # the up-triangle of the block's second unit cell
+        i, j = b.sites[2][1:]
+        core = [b.sites.index((t, i, j)) for t in range(3)]
+    keys = [(0, q) for q in core]
+    traces = []
+    region, (B, LB, _), (Tt, LT, _) = C.bubbles(bb, [(b.X, b.Y)], set(keys), traces=traces)
+    ring = C.zipper(B, LB, Tt, LT)
+    a = 0
+    while LB[a] in set(LT):
+        a += 1
+    c = 0
+    while LB[len(LB) - 1 - c] in set(LT):
+        c += 1
+    sites = {(rs.inst, rs.local): rs for rs in region.sites}
+    want_legs = []
+    for _, lab in ring:
+        want_legs.append(next((k, sites[key].labels.index(lab)) for k, key in enumerate(keys)
+                              if lab in sites[key].labels))
+    got_b, got_t, (nb, mt, ga, gc, Lr), legs = P.bbp_core_plan_debug(lat, Lx, Ly, per, bx, by, block,
+                                                                     [b.gids[q] for q in core])
+    assert [tuple(int(x) for x in r) for r in got_b] == _steps(traces[0])
+    assert [tuple(int(x) for x in r) for r in got_t] == _steps(traces[1])
+    assert (nb, mt, ga, gc, Lr) == (len(LB), len(LT), a, c, len(ring))
+    assert legs == want_legs
