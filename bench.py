@@ -394,12 +394,38 @@ def run_core(workload: str, precision: int, reps: int = 3):
             ms.append(e0.elapsed_time(e1))
         ring_len = len(ring)
         bonds = max(bonds, max(x.shape[0] for x in ring))
+    # local quantities from the core: <S^z> of site A (one-site core) and
+    # <S_A . S_B> (the A-B bond's Edge TN, three product insertions)
+    import numpy as np
+    sz = np.diag([0.5, -0.5]).astype(np.complex128)
+    sx = np.array([[0, 0.5], [0.5, 0]], dtype=np.complex128)
+    sy = np.array([[0, -0.5j], [0.5j, 0]], dtype=np.complex128)
+    site_ms, bond_ms, bond_e = [], [], []
+    for b, c in enumerate(cells):
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a0 = time.perf_counter()
+            P.bbp_core_expect(ctx, b, c[:1], [[sz]])
+            torch.cuda.synchronize()
+            site_ms.append(1e3 * (time.perf_counter() - a0))
+            a0 = time.perf_counter()
+            e = P.bbp_core_expect(ctx, b, c[:2], [[s, s] for s in (sx, sy, sz)])
+            torch.cuda.synchronize()
+            bond_ms.append(1e3 * (time.perf_counter() - a0))
+        bond_e.append(float(np.sum(e).real))
     P.bbp_destroy(ctx)
     ms.sort()
+    site_ms.sort()
+    bond_ms.sort()
     return {"workload": workload, "core": "unit cell (up-triangle A, B, C) of each block",
             "cores_timed": len(cells), "calls": len(ms), "ms_per_core_median": ms[len(ms) // 2],
             "ms_per_core_min": ms[0], "pmps_tensors": ring_len, "pmps_bond_max": bonds,
-            "note": "two bubbles from the bottom and top faces, zipper into the pMPS, copy to host memory"}
+            "note": "two bubbles from the bottom and top faces, zipper into the pMPS, copy to host memory",
+            "site_expect_ms_median": site_ms[len(site_ms) // 2],
+            "bond_energy_ms_median": bond_ms[len(bond_ms) // 2],
+            "bond_energy_AB": bond_e,
+            "expect_note": "bbp_core_expect: pMPS of a one-site core or of the A-B bond (Edge TN) and its exact "
+                           "contraction with the fused core tensors, host time per call"}
 
 
 # -------------------------------------------------- many networks, serving

@@ -227,6 +227,18 @@ bbp_status bbp_get_message(bbp_ctx* ctx, int block, int face, int* k_out, int* s
 bbp_status bbp_core_pmps(bbp_ctx* ctx, int block, const int* core_sites, int ncore, int cap_len, int* len_out,
                          int* shapes_out, int* legs_out, double* data_out, size_t cap, double* logscale_out);
 
+/* Local quantities of a core (Sec. 2.3, "Core", "Edge"): the core is one
+ * site, or the two ends of a bond (its pMPS is then the bond's Edge TN).
+ * The core's fused tensors, with operators inserted, are contracted exactly
+ * with the pMPS of bbp_core_pmps on the device: <O_k> = Z(O_k) / Z(1).
+ * core_sites: ncore (1 or 2) global site ids of `block`; for 2 they must
+ * share exactly one bond.  ops: nops sets of ncore host d x d complex128
+ * operators O[s, s'] (interleaved), set k site q at ops + 2 d d (k ncore + q).
+ * re_out, im_out: nops doubles each.  Errors as bbp_core_pmps;
+ * BBP_ERR_NUMERIC also when Z(1) vanishes. */
+bbp_status bbp_core_expect(bbp_ctx* ctx, int block, const int* core_sites, int ncore, const double* ops, int nops,
+                           double* re_out, double* im_out);
+
 /* Device bytes the context would hold for the given problem (estimate). */
 size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int by, int precision);
 

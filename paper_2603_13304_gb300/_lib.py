@@ -25,7 +25,7 @@ BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
 
 EXPORTS = [
     "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
-    "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message", "bbp_core_pmps", "bbp_core_plan_debug",
+    "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message", "bbp_core_pmps", "bbp_core_plan_debug", "bbp_core_expect",
     "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
     "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_panel_cluster", "bbp_k_panel_qr", "bbp_k_svd_work_bytes_rand", "bbp_k_svd_trunc_rand", "bbp_k_fma_peak", "bbp_set_hermitise", "bbp_expect_product", "bbp_bond_energies", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
     "bbp_batch_iterate", "bbp_server_create", "bbp_job_footprint_bytes", "bbp_server_submit", "bbp_server_step",
@@ -67,6 +67,7 @@ _PROTOS = {
     "bbp_get_message": (_i, [_vp, _i, _i, _ip, _ip, _dp, ctypes.c_size_t]),
     "bbp_core_pmps": (_i, [_vp, _i, _ip, _i, _i, _ip, _ip, _ip, _dp, ctypes.c_size_t, _dp]),
     "bbp_core_plan_debug": (_i, [_i, _i, _i, _i, _i, _i, _i, _ip, _i, _ip, _i, _ip, _ip, _i]),
+    "bbp_core_expect": (_i, [_vp, _i, _ip, _i, _dp, _i, _dp, _dp]),
     "bbp_footprint_bytes": (ctypes.c_size_t, [_i, _i, _i, _i, _i, _i, _i]),
     "bbp_info": (_i, [_vp, _ip, _ip, _ip]),
     "bbp_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _dp]),
@@ -305,6 +306,18 @@ def bbp_core_pmps(ctx, block: int, core_sites, cap: int = 1 << 24, cap_len: int 
         out.append(data[off:off + 2 * k].view(np.complex128).reshape(l, p, r).copy())
         off += 2 * k
     return out, [(int(legs[2 * q]), int(legs[2 * q + 1])) for q in range(n.value)], ls.value
+
+
+def bbp_core_expect(ctx, block: int, core_sites, ops):
+    """<O_k> for operator sets ops[k] = [O_site0, (O_site1)] (d x d each) on a
+    core of one site or of a bond's two ends; returns a complex array."""
+    s = np.ascontiguousarray(core_sites, dtype=np.int32)
+    o = _c128(np.asarray(ops, dtype=np.complex128).reshape(len(ops), len(s), -1))
+    nops = len(ops)
+    re = np.zeros(max(nops, 1))
+    im = np.zeros(max(nops, 1))
+    _check(lib().bbp_core_expect(ctx, block, _iptr(s), len(s), _dptr(o), nops, _dptr(re), _dptr(im)), ctx)
+    return (re + 1j * im)[:nops]
 
 
 def bbp_footprint_bytes(lattice, n_sites, D, chi, bx, by, precision=FP64) -> int:

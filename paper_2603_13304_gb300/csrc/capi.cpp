@@ -390,6 +390,26 @@ bbp_status bbp_core_pmps(bbp_ctx* ctx, int block, const int* core_sites, int nco
   });
 }
 
+bbp_status bbp_core_expect(bbp_ctx* ctx, int block, const int* core_sites, int ncore, const double* ops, int nops,
+                           double* re_out, double* im_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!core_sites || ncore < 1 || ncore > 2 || nops < 0 || (nops > 0 && (!ops || !re_out || !im_out)))
+    return set_err(BBP_ERR_ARG, "bad arguments");
+  return guarded([&]() -> bbp_status {
+    bbp::Engine& e = ctx->eng;
+    if (!e.partitioned || !e.messages_ready) return set_err(BBP_ERR_STATE, "partition and messages are required first");
+    if (block < 0 || block >= e.geom.n_blocks()) return set_err(BBP_ERR_ARG, "block out of range");
+    const bbp::Block& b = e.geom.blocks[block];
+    std::vector<int> core;
+    for (int q = 0; q < ncore; ++q) {
+      auto it = std::find(b.gids.begin(), b.gids.end(), core_sites[q]);
+      if (it == b.gids.end()) return set_err(BBP_ERR_ARG, "site not in block");
+      core.push_back((int)(it - b.gids.begin()));
+    }
+    return from(ctx, e.core_expect(block, core, ops, nops, re_out, im_out));
+  });
+}
+
 size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int by, int precision) {
   (void)precision;
   const size_t z = 16;

@@ -1720,20 +1720,31 @@ int Engine::get_message_t(int block, int face, int* k, int* shapes, double* data
 // bottom bubble's core legs left to right, then the top bubble's right to
 // left, the last tensor's right bond closing onto the first one's left bond.
 
-int Engine::core_pmps(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
-                      std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale) {
-  DeviceScope ds(device);
-  return precision == 0 ? core_pmps_t<double2>(block, core, shapes, legs, data, logscale)
-                        : core_pmps_t<float2>(block, core, shapes, legs, data, logscale);
-}
+// The ring of one core on the device: the two bubbles' boundaries (outb),
+// the folded tensors (fold), and per pMPS tensor its device pointer and
+// shape.  The destructor waits for the work queued on the buffers.
+template <typename C>
+struct CoreRing {
+  Engine* e = nullptr;
+  DBuf outb[2], res, scratch, fold;    // res: [0..1] log scales, [2..3] status words of the bubbles
+  CorePlan cp;
+  std::vector<const C*> t;
+  std::vector<TShape> sh;
+  ~CoreRing() {
+    if (!e) return;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    for (size_t i = 0; e->workers && i < 2 && i < e->workers->w.size(); ++i)
+      cudaStreamSynchronize(e->workers->w[i]->stream);
+  }
+};
 
 template <typename C>
-int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
-                        std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale) {
+int Engine::core_ring(int block, const std::vector<int>& core, CoreRing<C>& ring) {
+  ring.e = this;
   if (!partitioned || !messages_ready) return fail(this, 8, "partition and messages are required first");
   if (block < 0 || block >= (int)geom.blocks.size()) return fail(this, 1, "block out of range");
   const Region& R = block_regions[block];
-  CorePlan cp;
+  CorePlan& cp = ring.cp;
   const std::string err = compile_core(geom, R, core, cp);
   if (!err.empty()) return fail(this, 1, "core: " + err);
   const SweepPlan& pb = cp.bottom;
@@ -1746,16 +1757,6 @@ int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TSh
     std::vector<DBuf*>& v;
     ~TmpGuard() { for (DBuf* b : v) delete b; }
   } guard{tmp};
-  DBuf outb[2], res, scratch, fold;    // res: [0..1] log scales, [2..3] status words of the bubbles
-  // every buffer above outlives the work queued on it, on every return path
-  struct SyncGuard {
-    Engine* e;
-    ~SyncGuard() {
-      if (e->stream) cudaStreamSynchronize(e->stream);
-      for (size_t i = 0; e->workers && i < 2 && i < e->workers->w.size(); ++i)
-        cudaStreamSynchronize(e->workers->w[i]->stream);
-    }
-  } sync_guard{this};
   std::vector<SweepJob> jobs(2);
   if (int rc = fill_job<C>(R, pb, jobs[0], {}, tmp)) return rc;
   if (int rc = fill_job<C>(R, pt, jobs[1], {}, tmp)) return rc;
@@ -1764,15 +1765,15 @@ int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TSh
   for (int j = 0; j < 2; ++j) {
     size_t tot = 0;
     for (const TShape& t : jobs[j].tr.final_mps) tot += (size_t)t.size();
-    if (!outb[j].ensure(sizeof(C) * tot + 256, stream)) return fail(this, 2, "allocation failed");
+    if (!ring.outb[j].ensure(sizeof(C) * tot + 256, stream)) return fail(this, 2, "allocation failed");
     size_t off = 0;
     jobs[j].dest.clear();
     for (const TShape& t : jobs[j].tr.final_mps) {
-      jobs[j].dest.push_back((C*)outb[j].p + off);
+      jobs[j].dest.push_back((C*)ring.outb[j].p + off);
       off += (size_t)t.size();
     }
   }
-  if (!res.ensure(4 * sizeof(double) + 256, stream)) return fail(this, 2, "allocation failed");
+  if (!ring.res.ensure(4 * sizeof(double) + 256, stream)) return fail(this, 2, "allocation failed");
   {
     std::lock_guard<std::mutex> lk(pool_ref().mu);
     for (int i = 0; i < 2; ++i)
@@ -1790,7 +1791,7 @@ int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TSh
       SweepWork& w = *workers->w[i];
       CK(cudaStreamWaitEvent(w.stream, fork, 0));
       if (int rc = run_sweep<C>(jobs[i], w)) return rc;
-      double* rp = (double*)res.p;
+      double* rp = (double*)ring.res.p;
       CK(cudaMemcpyAsync(rp + i, w.logscale, sizeof(double), cudaMemcpyDeviceToDevice, w.stream));
       CK(cudaMemcpyAsync(rp + 2 + i, w.status, 2 * sizeof(int), cudaMemcpyDeviceToDevice, w.stream));
       CK(cudaEventRecord(w.done, w.stream));
@@ -1802,8 +1803,9 @@ int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TSh
   // the zipper, on the context's stream (operands in outb and private scratch)
   const std::vector<TShape>& SB = jobs[0].tr.final_mps;
   const std::vector<TShape>& ST = jobs[1].tr.final_mps;
-  auto Bq = [&](int q) { return (const C*)jobs[0].dest[q]; };
-  auto Tq = [&](int q) { return (const C*)jobs[1].dest[q]; };
+  const std::vector<void*> dB = jobs[0].dest, dT = jobs[1].dest;
+  auto Bq = [&](int q) { return (const C*)dB[q]; };
+  auto Tq = [&](int q) { return (const C*)dT[q]; };
   size_t mb = 1, mt = 1, mp = 1, mT = 1;
   for (const TShape& t : SB) { mb = std::max<size_t>(mb, std::max(t.l, t.r)); mp = std::max<size_t>(mp, t.p); }
   for (const TShape& t : ST) {
@@ -1812,8 +1814,8 @@ int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TSh
     mT = std::max<size_t>(mT, (size_t)t.size());
   }
   const size_t capE = mb * mt, capF = mb * mp * mt;
-  if (!scratch.ensure(sizeof(C) * (4 * capE + capF + mT) + 256, stream)) return fail(this, 2, "allocation failed");
-  C* EL = (C*)scratch.p;
+  if (!ring.scratch.ensure(sizeof(C) * (4 * capE + capF + mT) + 256, stream)) return fail(this, 2, "allocation failed");
+  C* EL = (C*)ring.scratch.p;
   C* ER = EL + capE;
   C* Ea = ER + capE;
   C* Eb = Ea + capE;
@@ -1863,54 +1865,266 @@ int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TSh
   if (SB[kb].r != erx || ST[c].l != ery || ST[kt].r != ely || SB[a].l != elx)
     return fail(this, 8, "zipper: the ring does not close");
   const size_t fb = (size_t)SB[kb].l * SB[kb].p * ery, ft = (size_t)ST[kt].l * ST[kt].p * elx;
-  if (!fold.ensure(sizeof(C) * (fb + ft) + 256, stream)) return fail(this, 2, "allocation failed");
-  C* FB = (C*)fold.p;
+  if (!ring.fold.ensure(sizeof(C) * (fb + ft) + 256, stream)) return fail(this, 2, "allocation failed");
+  C* FB = (C*)ring.fold.p;
   C* FT = FB + fb;
   CK(launch_zgemm('N', 'N', SB[kb].l * SB[kb].p, ery, erx, one, Bq(kb), erx, 0, ER, ery, 0, zero, FB, ery, 0, 1,
                   stream));
   CK(launch_zgemm('N', 'T', ST[kt].l * ST[kt].p, elx, ely, one, Tq(kt), ely, 0, EL, ely, 0, zero, FT, elx, 0, 1,
                   stream));
-  struct Piece { const C* p; TShape sh; };
-  std::vector<Piece> ring;
+  ring.t.clear();
+  ring.sh.clear();
   for (const auto& rq : cp.ring) {
     const int q = rq[1];
     if (rq[0] == 0) {
       TShape t = SB[q];
       if (q == kb) t.r = ery;
-      ring.push_back({q == kb ? FB : Bq(q), t});
+      ring.t.push_back(q == kb ? FB : Bq(q));
+      ring.sh.push_back(t);
     } else {
       TShape t = ST[q];
       if (q == kt) t.r = elx;
-      ring.push_back({q == kt ? FT : Tq(q), t});
+      ring.t.push_back(q == kt ? FT : Tq(q));
+      ring.sh.push_back(t);
     }
   }
-  const int L = (int)ring.size();
+  const int L = (int)ring.sh.size();
   for (int q = 0; q < L; ++q)
-    if (ring[q].sh.r != ring[(q + 1) % L].sh.l) return fail(this, 8, "zipper: pMPS bonds do not close");
-  shapes.clear();
-  legs = cp.legs;
-  size_t tot = 0;
-  for (const Piece& pc : ring) {
-    shapes.push_back(pc.sh);
-    tot += (size_t)pc.sh.size();
-  }
-  std::vector<C> host(tot);
-  size_t off = 0;
-  for (const Piece& pc : ring) {
-    CK(cudaMemcpyAsync(host.data() + off, pc.p, sizeof(C) * (size_t)pc.sh.size(), cudaMemcpyDeviceToHost, stream));
-    off += (size_t)pc.sh.size();
-  }
+    if (ring.sh[q].r != ring.sh[(q + 1) % L].l) return fail(this, 8, "zipper: pMPS bonds do not close");
+  return 0;
+}
+
+// log scales and statuses of the two bubbles (synchronises the stream)
+template <typename C>
+int Engine::core_ring_result(CoreRing<C>& ring, double* logscale) {
   double hres[4];
-  CK(cudaMemcpyAsync(hres, res.p, sizeof(hres), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(hres, ring.res.p, sizeof(hres), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
   int st[4];
   std::memcpy(&st[0], &hres[2], 2 * sizeof(int));
   std::memcpy(&st[2], &hres[3], 2 * sizeof(int));
   if (st[1] || st[3]) return fail(this, 7, "a tensor-core wait timed out in a core bubble");
   if (st[0] || st[2]) return fail(this, 5, "an SVD did not converge in a core bubble");
+  *logscale = hres[0] + hres[1];
+  return 0;
+}
+
+int Engine::core_pmps(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
+                      std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale) {
+  DeviceScope ds(device);
+  return precision == 0 ? core_pmps_t<double2>(block, core, shapes, legs, data, logscale)
+                        : core_pmps_t<float2>(block, core, shapes, legs, data, logscale);
+}
+
+template <typename C>
+int Engine::core_pmps_t(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
+                        std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale) {
+  CoreRing<C> ring;
+  if (int rc = core_ring<C>(block, core, ring)) return rc;
+  shapes = ring.sh;
+  legs = ring.cp.legs;
+  size_t tot = 0;
+  for (const TShape& t : ring.sh) tot += (size_t)t.size();
+  std::vector<C> host(tot);
+  size_t off = 0;
+  for (size_t q = 0; q < ring.t.size(); ++q) {
+    CK(cudaMemcpyAsync(host.data() + off, ring.t[q], sizeof(C) * (size_t)ring.sh[q].size(), cudaMemcpyDeviceToHost,
+                       stream));
+    off += (size_t)ring.sh[q].size();
+  }
+  if (int rc = core_ring_result<C>(ring, logscale)) return rc;
   data.resize(tot);
   for (size_t e = 0; e < tot; ++e) data[e] = make_double2((double)host[e].x, (double)host[e].y);
-  *logscale = hres[0] + hres[1];
+  return 0;
+}
+
+// Local quantities of the core (Sec. 2.3, "Edge"): the ring is cut into two
+// runs, A (bonds l0 -> m, legs' product P1) and B (m -> l0, product P2).  A
+// bond core: A holds site 0's legs, B site 1's; with the fused site tensors
+// laid out as [outer legs in ring order, joint leg],
+// Z(O) = sum_{l0, m, j} (A T1(O1))[l0, m, j] (B T2(O2))[l0, m, j].
+// A one-site core: A and B each hold half of its legs, T1 = [first half,
+// second half], and Z(O) = sum_{l0, m, j} (A T1(O))[l0, m, j] B[l0, m, j].
+int Engine::core_expect(int block, const std::vector<int>& core, const double* ops, int nops, double* re, double* im) {
+  DeviceScope ds(device);
+  return precision == 0 ? core_expect_t<double2>(block, core, ops, nops, re, im)
+                        : core_expect_t<float2>(block, core, ops, nops, re, im);
+}
+
+template <typename C>
+int Engine::core_expect_t(int block, const std::vector<int>& core, const double* ops, int nops, double* re,
+                          double* im) {
+  const int nc = (int)core.size();
+  if (nc < 1 || nc > 2) return fail(this, 1, "core observables need one site or the two ends of a bond");
+  if (nops < 0 || (nops > 0 && !ops)) return fail(this, 1, "bad operator list");
+  CoreRing<C> ring;
+  if (int rc = core_ring<C>(block, core, ring)) return rc;
+  const Region& R = block_regions[block];
+  const RSite* rs[2] = {nullptr, nullptr};
+  for (int q = 0; q < nc; ++q)
+    for (const RSite& x : R.sites)
+      if (x.inst == 0 && x.local == core[q]) rs[q] = &x;
+  if (!rs[0] || (nc == 2 && !rs[1])) return fail(this, 8, "core site missing from the block region");
+  int js[2] = {-1, -1}, njoint = 0;
+  if (nc == 2)
+    for (int s1 = 0; s1 < 4; ++s1)
+      for (int s2 = 0; s2 < 4; ++s2)
+        if (rs[0]->label[s1] == rs[1]->label[s2]) { js[0] = s1; js[1] = s2; ++njoint; }
+  if (nc == 2 && njoint != 1) return fail(this, 1, "the two core sites must share exactly one bond");
+  // ring order starting at site 0's run of legs
+  const auto& legs = ring.cp.legs;
+  const int L = (int)legs.size();
+  int start = 0;
+  if (nc == 2) {
+    start = -1;
+    for (int q = 0; q < L && start < 0; ++q)
+      if (legs[q][0] == 0 && legs[(q + L - 1) % L][0] == 1) start = q;
+    if (start < 0) return fail(this, 8, "core legs are not in two runs");
+  }
+  std::vector<int> idx(L);
+  for (int i = 0; i < L; ++i) idx[i] = (start + i) % L;
+  int n0 = 0;
+  if (nc == 2) {
+    while (n0 < L && legs[idx[n0]][0] == 0) ++n0;
+    for (int i = n0; i < L; ++i)
+      if (legs[idx[i]][0] != 1) return fail(this, 8, "core legs are not in two runs");
+  } else {
+    n0 = L / 2;
+  }
+  if (n0 < 1 || n0 >= L) return fail(this, 8, "core legs are not in two runs");
+  int perm[2][4];
+  int cnt[2] = {0, 0};
+  for (int i = 0; i < L; ++i) {
+    const int k = legs[idx[i]][0];
+    if (cnt[k] >= 4) return fail(this, 8, "core leg list too long");
+    perm[k][cnt[k]++] = legs[idx[i]][1];
+  }
+  for (int k = 0; k < nc; ++k) {
+    if (nc == 2) perm[k][cnt[k]++] = js[k];
+    if (cnt[k] != 4) return fail(this, 8, "core site legs do not match the ring");
+    bool seen[4] = {false, false, false, false};
+    for (int q = 0; q < 4; ++q) {
+      if (perm[k][q] < 0 || perm[k][q] > 3 || seen[perm[k][q]]) return fail(this, 8, "core site legs repeated");
+      seen[perm[k][q]] = true;
+    }
+  }
+  // shapes: A (l0, P1, m), B (m, P2, l0), joint J
+  const int l0 = ring.sh[idx[0]].l;
+  const int m = ring.sh[idx[n0 - 1]].r;
+  long long P1 = 1, P2 = 1, capA = 1, capB = 1;
+  for (int i = 0; i < n0; ++i) {
+    P1 *= ring.sh[idx[i]].p;
+    capA = std::max(capA, (long long)l0 * P1 * ring.sh[idx[i]].r);
+  }
+  for (int i = n0; i < L; ++i) {
+    P2 *= ring.sh[idx[i]].p;
+    capB = std::max(capB, (long long)m * P2 * ring.sh[idx[i]].r);
+  }
+  if (ring.sh[idx[L - 1]].r != l0) return fail(this, 8, "the ring does not close");
+  const auto& n0d = site_n[rs[0]->gid];
+  long long f1 = 1;
+  for (int q = 0; q < (nc == 2 ? 3 : 4); ++q) f1 *= (long long)n0d[perm[0][q]] * n0d[perm[0][q]];
+  if (f1 != (nc == 2 ? P1 : P1 * P2)) return fail(this, 8, "core site 0 legs disagree with the ring");
+  const long long J = nc == 2 ? (long long)n0d[js[0]] * n0d[js[0]] : P2;
+  if (nc == 2) {
+    const auto& n1d = site_n[rs[1]->gid];
+    long long f2 = 1;
+    for (int q = 0; q < 3; ++q) f2 *= (long long)n1d[perm[1][q]] * n1d[perm[1][q]];
+    if (f2 != P2 || (long long)n1d[js[1]] * n1d[js[1]] != J) return fail(this, 8, "core site 1 legs disagree with the ring");
+  }
+  const long long LM = (long long)l0 * m;
+  const size_t nA = 2 * capA + LM * P1, nB = 2 * capB + LM * P2, nT = P1 * J + P2 * J, nX = 2 * LM * J;
+  const int nz = nops + 1;
+  DBuf wk, opd;
+  if (!wk.ensure(sizeof(C) * (nA + nB + nT + nX + 2 * LM + nz) + 1024, stream)) return fail(this, 2, "allocation failed");
+  C* A0 = (C*)wk.p;
+  C* A1 = A0 + capA;
+  C* Ap = A1 + capA;
+  C* B0 = Ap + LM * P1;
+  C* B1 = B0 + capB;
+  C* Bp = B1 + capB;
+  C* T1 = Bp + LM * P2;
+  C* T2 = T1 + P1 * J;
+  C* X1 = T2 + P2 * J;
+  C* X2 = X1 + LM * J;
+  C* Dp = X2 + LM * J;                 // per-row dots
+  C* ones = Dp + LM;
+  C* Zs = ones + LM;
+  CK(launch_fill(ones, LM, 1.0, 0.0, stream));
+  const size_t op_elems = (size_t)nops * nc * d * d;
+  if (nops > 0) {
+    if (!opd.ensure(sizeof(double2) * op_elems + 256, stream)) return fail(this, 2, "allocation failed");
+    CK(cudaMemcpyAsync(opd.p, ops, sizeof(double2) * op_elems, cudaMemcpyHostToDevice, stream));
+  }
+  const C one = one_of<C>(), zero = zero_of<C>();
+  // product of a run of ring tensors: (l, prod p, r); the rows of each
+  // product go in chunks (the GEMM grid's row count is bounded)
+  constexpr long long kRows = 1 << 20;
+  auto chain = [&](int i0, int i1, C* b0, C* b1) -> const C* {
+    const C* cur = ring.t[idx[i0]];
+    long long rows = (long long)ring.sh[idx[i0]].l * ring.sh[idx[i0]].p;
+    int cols = ring.sh[idx[i0]].r;
+    C* out = b0;
+    for (int i = i0 + 1; i < i1; ++i) {
+      const TShape t = ring.sh[idx[i]];
+      for (long long r0 = 0; r0 < rows; r0 += kRows)
+        if (launch_zgemm('N', 'N', (int)std::min(kRows, rows - r0), t.p * t.r, cols, one, cur + r0 * cols, cols, 0,
+                         ring.t[idx[i]], t.p * t.r, 0, zero, out + r0 * (long long)t.p * t.r, t.p * t.r, 0, 1,
+                         stream) != cudaSuccess)
+          return nullptr;
+      cur = out;
+      out = (out == b0) ? b1 : b0;
+      rows *= t.p;
+      cols = t.r;
+    }
+    return cur;
+  };
+  const C* A = chain(0, n0, A0, A1);
+  if (!A) return fail(this, 3, "core: ring product failed");
+  {
+    const int pa[3] = {0, 2, 1};   // (l0, P1, m) -> (l0, m, P1)
+    CK(launch_permute3(A, l0, (int)P1, m, pa, Ap, stream));
+  }
+  {
+    const C* B = chain(n0, L, B0, B1);
+    if (!B) return fail(this, 3, "core: ring product failed");
+    const int pb[3] = {2, 0, 1};   // (m, P2, l0) -> (l0, m, P2)
+    CK(launch_permute3(B, m, (int)P2, l0, pb, Bp, stream));
+  }
+  const double2* tbase = (const double2*)t_dev.p;
+  const size_t tsz = (size_t)d * D * D * D * D;
+  for (int k = 0; k <= nops; ++k) {          // k = nops: no operator, Z(1)
+    const double2* o0 = k < nops ? (const double2*)opd.p + ((size_t)k * nc) * d * d : nullptr;
+    CK(launch_fuse(tbase + (size_t)rs[0]->gid * tsz, d, D, n0d.data(), o0, perm[0], T1, stream));
+    CK(launch_zgemm('N', 'N', (int)LM, (int)J, (int)P1, one, Ap, (int)P1, 0, T1, (int)J, 0, zero, X1, (int)J, 0, 1,
+                    stream));
+    const C* Xb = Bp;
+    if (nc == 2) {
+      const double2* o1 = k < nops ? (const double2*)opd.p + ((size_t)k * nc + 1) * d * d : nullptr;
+      CK(launch_fuse(tbase + (size_t)rs[1]->gid * tsz, d, D, site_n[rs[1]->gid].data(), o1, perm[1], T2, stream));
+      CK(launch_zgemm('N', 'N', (int)LM, (int)J, (int)P2, one, Bp, (int)P2, 0, T2, (int)J, 0, zero, X2, (int)J, 0, 1,
+                      stream));
+      Xb = X2;
+    }
+    // Z = sum_rows sum_j X1[row, j] Xb[row, j]: one CTA per row (batched 1 x 1
+    // products), then the sum of the LM row dots
+    constexpr long long kBatch = 32768;
+    for (long long r0 = 0; r0 < LM; r0 += kBatch)
+      CK(launch_zgemm('N', 'T', 1, 1, (int)J, one, X1 + r0 * J, (int)J, J, Xb + r0 * J, (int)J, J, zero, Dp + r0, 1, 1,
+                      (int)std::min(kBatch, LM - r0), stream));
+    CK(launch_zgemm('N', 'N', 1, 1, (int)LM, one, ones, (int)LM, 0, Dp, 1, 0, zero, Zs + k, 1, 0, 1, stream));
+  }
+  std::vector<C> hz(nz);
+  CK(cudaMemcpyAsync(hz.data(), Zs, sizeof(C) * nz, cudaMemcpyDeviceToHost, stream));
+  double ls = 0.0;
+  if (int rc = core_ring_result<C>(ring, &ls)) return rc;   // (synchronises)
+  const double zr = hz[nops].x, zi = hz[nops].y, den = zr * zr + zi * zi;
+  if (!(den > 0.0)) return fail(this, 5, "the core's value vanishes");
+  for (int k = 0; k < nops; ++k) {
+    const double ar = hz[k].x, ai = hz[k].y;
+    re[k] = (ar * zr + ai * zi) / den;
+    im[k] = (ai * zr - ar * zi) / den;
+  }
   return 0;
 }
 

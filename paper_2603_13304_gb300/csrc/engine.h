@@ -106,6 +106,8 @@ struct SweepJob {
 
 using OpList = std::vector<std::pair<std::array<int, 2>, const double*>>;   // (instance, local) -> device d x d c128
 
+template <typename C> struct CoreRing;   // the pMPS of one core on the device (engine.cpp)
+
 class Engine {
  public:
   Geometry geom;
@@ -166,6 +168,11 @@ class Engine {
   // the scale factored out of the two bubbles.
   int core_pmps(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
                 std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale);
+  // Local quantities of a core of one site, or of the two ends of a bond
+  // (the Edge TN): for each of nops operator sets (ncore host d x d
+  // complex128 operators each, set k site q at ops + 2 d d (k ncore + q)),
+  // <O_k> = Z(O_k) / Z(1), the core contracted exactly with its pMPS.
+  int core_expect(int block, const std::vector<int>& core, const double* ops, int nops, double* re, double* im);
 
  private:
   SweepWork* work(size_t i);
@@ -189,6 +196,10 @@ class Engine {
   template <typename C>
   int core_pmps_t(int block, const std::vector<int>& core, std::vector<TShape>& shapes,
                   std::vector<std::array<int, 2>>& legs, std::vector<double2>& data, double* logscale);
+  template <typename C> int core_ring(int block, const std::vector<int>& core, CoreRing<C>& ring);
+  template <typename C> int core_ring_result(CoreRing<C>& ring, double* logscale);
+  template <typename C>
+  int core_expect_t(int block, const std::vector<int>& core, const double* ops, int nops, double* re, double* im);
   void job_needs(const SweepJob& job, size_t need[7]) const;
   // one captured iteration per message-buffer parity, valid while the
   // signature (shapes and device pointers of every job) is unchanged

@@ -153,3 +153,78 @@ def test_core_pmps_rejects_bad_cores():
         assert ei.value.status == 1
     finally:
         P.bbp_destroy(ctx)
+
+
+# ----------------------------------------------- local quantities of a core
+
+def _core_checks(geom, bb, ctx, block, cores, tol):
+    """bbp_core_expect against the oracle's core route: <S^z> on one-site
+    cores, <S^a S^a> (a = x, y, z) on bond cores."""
+    b = geom.blocks[block]
+    worst = 0.0
+    for core in cores:
+        keys = [(0, q) for q in core]
+        env = C.CoreEnv(bb, [(b.X, b.Y)], keys)
+        gids = [b.gids[q] for q in core]
+        if len(core) == 1:
+            sets = [[SZ], [SX]]
+        else:
+            sets = [[S, S] for S in (SX, SY, SZ)]
+        got = P.bbp_core_expect(ctx, block, gids, sets)
+        want = [env.expect({k: o for k, o in zip(keys, ops)}) for ops in sets]
+        worst = max(worst, float(np.max(np.abs(np.asarray(got) - np.asarray(want)))))
+    assert worst < tol, worst
+    return worst
+
+
+def test_core_expect_square_fp64():
+    """One-site cores (a corner, an edge and the centre of each 3 x 3 block)
+    and bond cores (horizontal and vertical) of the 6 x 6 square PEPS after
+    three iterations: every value equals the oracle's core route to 1e-10."""
+    geom, bb, ctx = _pair("square", (6, 6, 3, 3), 2, 8, 3, 1, P.FP64)
+    try:
+        w = 0.0
+        for block in range(len(geom.blocks)):
+            w = max(w, _core_checks(geom, bb, ctx, block, [[0], [1], [4], [3, 4], [4, 7], [0, 1]], 1e-10))
+        print(f"square core observables FP64: largest difference {w:.2e}")
+    finally:
+        P.bbp_destroy(ctx)
+
+
+def test_core_expect_kagome_fp64():
+    """Kagome D = 2, chi = 16: every site of each block's first unit cell and
+    its three bonds A-B, B-C, C-A (the Edge TN of each) against the oracle."""
+    geom, bb, ctx = _pair("kagome", (6, 2, 2), 2, 16, 2, 7, P.FP64)
+    try:
+        w = 0.0
+        for block in range(len(geom.blocks)):
+            b = geom.blocks[block]
+            i, j = b.sites[2][1:]
+            a_, b_, c_ = [b.sites.index((t, i, j)) for t in range(3)]
+            w = max(w, _core_checks(geom, bb, ctx, block, [[a_], [b_], [c_], [a_, b_], [b_, c_], [c_, a_]], 1e-10))
+        print(f"kagome core observables FP64: largest difference {w:.2e}")
+    finally:
+        P.bbp_destroy(ctx)
+
+
+def test_core_expect_tf32():
+    geom, bb, ctx = _pair("square", (6, 6, 3, 3), 2, 8, 3, 1, P.TF32)
+    try:
+        w = _core_checks(geom, bb, ctx, 0, [[4], [3, 4]], 1e-5)
+        print(f"square core observables TF32: largest difference {w:.2e}")
+    finally:
+        P.bbp_destroy(ctx)
+
+
+def test_core_expect_rejects_bad_cores():
+    geom, bb, ctx = _pair("square", (6, 6, 3, 3), 2, 8, 1, 1, P.FP64)
+    try:
+        b = geom.blocks[0]
+        with pytest.raises(P.BBPError) as ei:          # three sites
+            P.bbp_core_expect(ctx, 0, [b.gids[q] for q in (3, 4, 5)], [[SZ, SZ, SZ]])
+        assert ei.value.status == 1
+        with pytest.raises(P.BBPError) as ei:          # two sites that share no bond
+            P.bbp_core_expect(ctx, 0, [b.gids[0], b.gids[4]], [[SZ, SZ]])
+        assert ei.value.status == 1
+    finally:
+        P.bbp_destroy(ctx)
