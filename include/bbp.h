@@ -239,6 +239,30 @@ bbp_status bbp_core_pmps(bbp_ctx* ctx, int block, const int* core_sites, int nco
 bbp_status bbp_core_expect(bbp_ctx* ctx, int block, const int* core_sites, int ncore, const double* ops, int nops,
                            double* re_out, double* im_out);
 
+/* ITE update of one bond (Ch. 3, "ITE update step"), FP64 mode, both sites
+ * in one block, D at most 4: the bond leaving `site` through leg `slot`
+ * takes the two-site gate (host d^2 x d^2 complex128 over (s_site,
+ * s_neighbour), e.g. exp(-dt h)); then, with the bond's Edge TN from the
+ * current messages as the environment N, alternating least squares brings
+ * the bond back to D: from the truncated SVD of the evolved pair, each
+ * half-step minimises Phi = <psi - psi'| N |psi - psi'> over one tensor with
+ * the other fixed (least squares, rcond 1e-13), until a sweep lowers Phi by
+ * at most tol Phi_start or max_sweeps sweeps ran.  The two new tensors
+ * replace the old ones, each divided by its largest entry; the messages are
+ * kept.  phi_out (capacity phi_cap) receives Phi after the start and after
+ * every half-step, n_phi_out their number. */
+bbp_status bbp_ite_bond(bbp_ctx* ctx, int site, int slot, const double* gate, int max_sweeps, double tol,
+                        double* phi_out, int phi_cap, int* n_phi_out);
+
+/* Full ITE (Alg. 2): for each of ndt gates (host, d^2 x d^2 complex128 each,
+ * e.g. exp(-dt h / 2)), the nbonds bonds (site, slot pairs), then the same
+ * bonds backwards (second-order splitting), each updated as bbp_ite_bond
+ * (at most als_sweeps sweeps) after BlockBP runs to bp_tol (at most
+ * bp_max_iter iterations, from the current messages); energies_out (ndt
+ * doubles) receives the Heisenberg energy per site after each gate's pass. */
+bbp_status bbp_ite(bbp_ctx* ctx, const double* gates, int ndt, const int* bonds, int nbonds, double bp_tol,
+                   int bp_max_iter, int als_sweeps, double* energies_out);
+
 /* Device bytes the context would hold for the given problem (estimate). */
 size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int by, int precision);
 

@@ -7,7 +7,7 @@ CPU fallback: using the engine without the built library raises.
 from ._lib import (  # noqa: F401
     BBPError, BF16, BOTTOM, KT_ABSORB, KT_JACOBI, KT_ORTH, KT_QR, KT_TC, FP32, FP64, KAGOME, LEFT, RIGHT, SQUARE, TF32, TOP, EXPORTS, lib,
     bbp_block_rdm, bbp_create_peps, bbp_destroy, bbp_energy_per_site, bbp_expect_local, bbp_footprint_bytes,
-    bbp_get_message, bbp_core_pmps, bbp_core_plan_debug, bbp_core_expect, bbp_info, bbp_init_messages, bbp_iterate, bbp_k_fuse, bbp_k_qr, bbp_k_svd_trunc,
+    bbp_get_message, bbp_core_pmps, bbp_core_plan_debug, bbp_core_expect, bbp_ite_bond, bbp_ite, bbp_info, bbp_init_messages, bbp_iterate, bbp_k_fuse, bbp_k_qr, bbp_k_svd_trunc,
     bbp_k_panel_cluster, bbp_k_panel_qr, bbp_k_svd_work_bytes_rand, bbp_k_svd_trunc_rand, bbp_k_fma_peak, bbp_set_hermitise, bbp_expect_product, bbp_bond_energies,
     bbp_k_svd_stats, bbp_k_svd_trunc_noalloc, bbp_k_svd_work_bytes, bbp_k_tc_absorb, bbp_k_tc_absorb_bytes,
     bbp_k_tc_gemm, bbp_k_tc_gemm_tile, bbp_autotune_record, bbp_autotune_run, bbp_autotune_load, bbp_autotune_info,

@@ -25,7 +25,7 @@ BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
 
 EXPORTS = [
     "bbp_set_allocator", "bbp_create_peps", "bbp_partition_blocks", "bbp_set_options", "bbp_init_messages",
-    "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message", "bbp_core_pmps", "bbp_core_plan_debug", "bbp_core_expect",
+    "bbp_iterate", "bbp_expect_local", "bbp_block_rdm", "bbp_energy_per_site", "bbp_norm", "bbp_get_message", "bbp_core_pmps", "bbp_core_plan_debug", "bbp_core_expect", "bbp_ite_bond", "bbp_ite",
     "bbp_footprint_bytes", "bbp_info", "bbp_stats", "bbp_last_error", "bbp_destroy", "bbp_k_fuse",
     "bbp_k_svd_work_bytes", "bbp_k_svd_trunc", "bbp_k_svd_trunc_noalloc", "bbp_k_svd_stats", "bbp_k_qr", "bbp_k_panel_cluster", "bbp_k_panel_qr", "bbp_k_svd_work_bytes_rand", "bbp_k_svd_trunc_rand", "bbp_k_fma_peak", "bbp_set_hermitise", "bbp_expect_product", "bbp_bond_energies", "bbp_k_tc_gemm", "bbp_set_execution", "bbp_set_power_iters",
     "bbp_batch_iterate", "bbp_server_create", "bbp_job_footprint_bytes", "bbp_server_submit", "bbp_server_step",
@@ -68,6 +68,8 @@ _PROTOS = {
     "bbp_core_pmps": (_i, [_vp, _i, _ip, _i, _i, _ip, _ip, _ip, _dp, ctypes.c_size_t, _dp]),
     "bbp_core_plan_debug": (_i, [_i, _i, _i, _i, _i, _i, _i, _ip, _i, _ip, _i, _ip, _ip, _i]),
     "bbp_core_expect": (_i, [_vp, _i, _ip, _i, _dp, _i, _dp, _dp]),
+    "bbp_ite_bond": (_i, [_vp, _i, _i, _dp, _i, _d, _dp, _i, _ip]),
+    "bbp_ite": (_i, [_vp, _dp, _i, _ip, _i, _d, _i, _i, _dp]),
     "bbp_footprint_bytes": (ctypes.c_size_t, [_i, _i, _i, _i, _i, _i, _i]),
     "bbp_info": (_i, [_vp, _ip, _ip, _ip]),
     "bbp_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _dp]),
@@ -318,6 +320,26 @@ def bbp_core_expect(ctx, block: int, core_sites, ops):
     im = np.zeros(max(nops, 1))
     _check(lib().bbp_core_expect(ctx, block, _iptr(s), len(s), _dptr(o), nops, _dptr(re), _dptr(im)), ctx)
     return (re + 1j * im)[:nops]
+
+
+def bbp_ite_bond(ctx, site: int, slot: int, gate, max_sweeps: int = 50, tol: float = 1e-13):
+    """One ITE bond update; returns the Phi history (start, every half-step)."""
+    g = _c128(gate)
+    phi = np.zeros(2 * max_sweeps + 1)
+    n = ctypes.c_int()
+    _check(lib().bbp_ite_bond(ctx, site, slot, _dptr(g), max_sweeps, tol, _dptr(phi), phi.size, ctypes.byref(n)), ctx)
+    return phi[:n.value].copy()
+
+
+def bbp_ite(ctx, gates, bonds, bp_tol: float = 1e-10, bp_max_iter: int = 40, als_sweeps: int = 50):
+    """Full ITE over the gate list; bonds: (site, slot) pairs; returns the
+    energy per site after each gate."""
+    g = _c128(np.asarray(gates, dtype=np.complex128))
+    b = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1))
+    out = np.zeros(len(gates))
+    _check(lib().bbp_ite(ctx, _dptr(g), len(gates), _iptr(b), len(b) // 2, bp_tol, bp_max_iter, als_sweeps,
+                         _dptr(out)), ctx)
+    return out
 
 
 def bbp_footprint_bytes(lattice, n_sites, D, chi, bx, by, precision=FP64) -> int:

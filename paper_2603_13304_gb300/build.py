@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbbp.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["k_core.cu", "k_tc.cu", "k_panel.cu", "k_peak.cu", "k_noalloc.cu", "engine.cpp", "plan.cpp", "geom.cpp", "capi.cpp", "ktimer.cpp", "server.cpp"]
+SOURCES = ["k_core.cu", "k_tc.cu", "k_panel.cu", "k_peak.cu", "k_noalloc.cu", "k_ite.cu", "engine.cpp", "plan.cpp", "geom.cpp", "capi.cpp", "ktimer.cpp", "server.cpp"]
 
 
 def nvcc() -> str:

@@ -410,6 +410,32 @@ bbp_status bbp_core_expect(bbp_ctx* ctx, int block, const int* core_sites, int n
   });
 }
 
+bbp_status bbp_ite_bond(bbp_ctx* ctx, int site, int slot, const double* gate, int max_sweeps, double tol,
+                        double* phi_out, int phi_cap, int* n_phi_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!gate || !phi_out || !n_phi_out || phi_cap < 1 || max_sweeps < 0 || !(tol >= 0.0))
+    return set_err(BBP_ERR_ARG, "bad arguments");
+  return guarded([&]() -> bbp_status {
+    std::vector<double> phi;
+    if (int rc = ctx->eng.ite_bond(site, slot, gate, max_sweeps, tol, phi)) return from(ctx, rc);
+    const int n = (int)std::min<size_t>(phi.size(), (size_t)phi_cap);
+    for (int q = 0; q < n; ++q) phi_out[q] = phi[q];
+    *n_phi_out = n;
+    return BBP_OK;
+  });
+}
+
+bbp_status bbp_ite(bbp_ctx* ctx, const double* gates, int ndt, const int* bonds, int nbonds, double bp_tol,
+                   int bp_max_iter, int als_sweeps, double* energies_out) {
+  if (!ctx) return set_err(BBP_ERR_ARG, "ctx is NULL");
+  if (!gates || ndt < 0 || !bonds || nbonds <= 0 || !energies_out || bp_max_iter < 0 || als_sweeps < 0 ||
+      !(bp_tol >= 0.0))
+    return set_err(BBP_ERR_ARG, "bad arguments");
+  return guarded([&]() -> bbp_status {
+    return from(ctx, ctx->eng.ite(gates, ndt, bonds, nbonds, bp_tol, bp_max_iter, als_sweeps, energies_out));
+  });
+}
+
 size_t bbp_footprint_bytes(int lattice, int n_sites, int D, int chi, int bx, int by, int precision) {
   (void)precision;
   const size_t z = 16;

@@ -2128,4 +2128,353 @@ int Engine::core_expect_t(int block, const std::vector<int>& core, const double*
   return 0;
 }
 
+// ------------------------------------------------------------ ITE (Ch. 3)
+//
+// One bond update, every step on the device in complex128:
+//  * the bond's Edge TN (the pMPS around its two sites) contracted into the
+//    dense environment N[K1 K2, B1 B2] (ket legs, bra legs; site 1's three
+//    outer legs then site 2's, in ring order);
+//  * x = t1, y = t2 as [p, outer legs, bond]; Theta = gate (x y);
+//  * the ALS start: the truncated SVD of Theta across the bond, D kept;
+//  * ALS half-steps: the normal equations M v_p = c_p of Phi for one tensor
+//    with the other fixed (M from N and the fixed tensor, c from N, Theta
+//    and the fixed tensor), solved by the least-squares solution from the
+//    SVD of M (rcond 1e-13);
+//  * Phi = <psi - Theta| N |psi - Theta> after every half-step; the loop
+//    stops when a sweep lowers Phi by at most tol Phi_start.
+
+namespace {
+
+StridedView sview(std::initializer_list<long long> dims, std::initializer_list<long long> sstr) {
+  StridedView v;
+  v.rank = (int)dims.size();
+  int q = 0;
+  for (long long x : dims) v.dims[q++] = x;
+  q = 0;
+  for (long long x : sstr) v.sstr[q++] = x;
+  long long st = 1;
+  for (int k = v.rank - 1; k >= 0; --k) {
+    v.dstr[k] = st;
+    st *= v.dims[k];
+  }
+  v.total = st;
+  return v;
+}
+
+}  // namespace
+
+int Engine::ite_bond(int g1, int k1, const double* gate, int max_sweeps, double tol, std::vector<double>& phi) {
+  DeviceScope ds(device);
+  phi.clear();
+  if (precision != 0) return fail(this, 1, "the ITE update runs in the FP64 mode");
+  if (!partitioned || !messages_ready) return fail(this, 8, "partition and messages are required first");
+  if (!gate || k1 < 0 || k1 > 3 || max_sweeps < 0) return fail(this, 1, "bad arguments");
+  int loc1 = -1;
+  const int bid = geom.home_block(g1, &loc1);
+  if (bid < 0) return fail(this, 1, "site out of range");
+  const Block& blk = geom.blocks[bid];
+  const auto& st1 = blk.sites[loc1];
+  int t2, i2, j2, k2;
+  geom.lat.neighbour(st1[0], st1[1], st1[2], k1, t2, i2, j2, k2);
+  const int g2 = geom.lat.site_id(t2, i2, j2);
+  if (g2 < 0) return fail(this, 1, "the leg is open");
+  auto it2 = std::find(blk.gids.begin(), blk.gids.end(), g2);
+  if (it2 == blk.gids.end()) return fail(this, 1, "the ITE update needs both sites of the bond in one block");
+  const int loc2 = (int)(it2 - blk.gids.begin());
+  const std::vector<int> core = {loc1, loc2};
+
+  CoreRing<double2> ring;
+  if (int rc = core_ring<double2>(bid, core, ring)) return rc;
+  const Region& R = block_regions[bid];
+  const RSite* rs[2] = {nullptr, nullptr};
+  for (int q = 0; q < 2; ++q)
+    for (const RSite& x : R.sites)
+      if (x.inst == 0 && x.local == core[q]) rs[q] = &x;
+  if (!rs[0] || !rs[1]) return fail(this, 8, "core site missing from the block region");
+  int js[2] = {-1, -1}, njoint = 0;
+  for (int s1 = 0; s1 < 4; ++s1)
+    for (int s2 = 0; s2 < 4; ++s2)
+      if (rs[0]->label[s1] == rs[1]->label[s2]) { js[0] = s1; js[1] = s2; ++njoint; }
+  if (njoint != 1 || js[0] != k1) return fail(this, 1, "the two sites must share exactly this one bond");
+  const auto& legs = ring.cp.legs;
+  const int L = (int)legs.size();
+  int start = -1;
+  for (int q = 0; q < L && start < 0; ++q)
+    if (legs[q][0] == 0 && legs[(q + L - 1) % L][0] == 1) start = q;
+  if (start < 0) return fail(this, 8, "core legs are not in two runs");
+  std::vector<int> idx(L);
+  for (int i = 0; i < L; ++i) idx[i] = (start + i) % L;
+  int n0 = 0;
+  while (n0 < L && legs[idx[n0]][0] == 0) ++n0;
+  int outer[2][3], cnt[2] = {0, 0};
+  for (int i = 0; i < L; ++i) {
+    const int k = legs[idx[i]][0];
+    if ((k == 0) != (i < n0) || cnt[k] >= 3) return fail(this, 8, "core legs are not in two runs");
+    outer[k][cnt[k]++] = legs[idx[i]][1];
+  }
+  if (cnt[0] != 3 || cnt[1] != 3) return fail(this, 8, "a bond core has three outer legs a site");
+  const int gid[2] = {rs[0]->gid, rs[1]->gid};
+  const auto& na = site_n[gid[0]];
+  const auto& nb = site_n[gid[1]];
+  long long E1 = 1, E2 = 1;
+  for (int q = 0; q < 3; ++q) { E1 *= na[outer[0][q]]; E2 *= nb[outer[1][q]]; }
+  const int Db = na[js[0]];
+  if (nb[js[1]] != Db) return fail(this, 8, "bond extents differ");
+  const long long P1 = E1 * E1, P2 = E2 * E2;
+  long long rp1 = 1, rp2 = 1;
+  for (int i = 0; i < n0; ++i) rp1 *= ring.sh[idx[i]].p;
+  for (int i = n0; i < L; ++i) rp2 *= ring.sh[idx[i]].p;
+  if (rp1 != P1 || rp2 != P2) return fail(this, 8, "the Edge TN legs disagree with the sites");
+  if (P1 * P2 > (1LL << 26)) return fail(this, 1, "the bond's dense environment is too large (D at most 4)");
+  const int l0 = ring.sh[idx[0]].l, m = ring.sh[idx[n0 - 1]].r;
+  if (ring.sh[idx[L - 1]].r != l0) return fail(this, 8, "the ring does not close");
+  const long long LM = (long long)l0 * m;
+  long long capA = 1, capB = 1;
+  {
+    long long p = 1;
+    for (int i = 0; i < n0; ++i) { p *= ring.sh[idx[i]].p; capA = std::max(capA, (long long)l0 * p * ring.sh[idx[i]].r); }
+    p = 1;
+    for (int i = n0; i < L; ++i) { p *= ring.sh[idx[i]].p; capB = std::max(capB, (long long)m * p * ring.sh[idx[i]].r); }
+  }
+  const int dd = d;
+  const long long dE1 = dd * E1, dE2 = dd * E2, EE = E1 * E2, d2 = (long long)dd * dd;
+  const long long n1 = E1 * Db, n2 = E2 * Db, nmax = std::max(n1, n2);
+  // scratch layout
+  std::vector<std::pair<double2**, long long>> lay;
+  double2 *A0, *A1, *Ap, *B0, *B1, *Bp, *Nf, *Nkb, *Nr1, *Nr2, *X, *Y, *XT, *YT, *Gd, *psi1, *psi, *Th, *Thm, *TN, *TNp1,
+      *TNp2, *G, *Gr, *MM, *Mt, *cc, *cT, *W, *U, *Rm, *Xd, *Tq;
+  lay = {{&A0, capA}, {&A1, capA}, {&Ap, LM * P1}, {&B0, capB}, {&B1, capB}, {&Bp, LM * P2}, {&Nf, P1 * P2},
+         {&Nkb, P1 * P2}, {&Nr1, P1 * P2}, {&Nr2, P1 * P2}, {&X, dE1 * Db}, {&Y, dE2 * Db}, {&XT, dE1 * Db},
+         {&YT, dE2 * Db}, {&Gd, d2 * d2}, {&psi1, d2 * EE}, {&psi, d2 * EE}, {&Th, d2 * EE}, {&Thm, d2 * EE},
+         {&TN, d2 * EE}, {&TNp1, d2 * EE}, {&TNp2, d2 * EE}, {&G, nmax * nmax}, {&Gr, std::max(P1, P2) * Db * Db},
+         {&MM, std::max(P1, P2) * Db * Db}, {&Mt, nmax * nmax}, {&cc, nmax * dd}, {&cT, nmax * dd}, {&W, nmax * dd},
+         {&U, std::max(nmax * nmax, dE1 * dE2)}, {&Rm, std::max(nmax * nmax, dE1 * dE2)}, {&Xd, d2 * EE},
+         {&Tq, d2 * EE}};
+  size_t tot = 0;
+  for (auto& e : lay) tot += (size_t)((e.second + 31) / 32 * 32);
+  DBuf wk, svdw, sc;
+  if (!wk.ensure(sizeof(double2) * tot + 256, stream)) return fail(this, 2, "allocation failed");
+  {
+    size_t off = 0;
+    for (auto& e : lay) {
+      *e.first = (double2*)wk.p + off;
+      off += (size_t)((e.second + 31) / 32 * 32);
+    }
+  }
+  const size_t svd_bytes = std::max(svd_work_bytes((int)nmax, (int)nmax), svd_work_bytes((int)dE1, (int)dE2));
+  if (!svdw.ensure(svd_bytes + 256, stream) || !sc.ensure(64, stream)) return fail(this, 2, "allocation failed");
+  int* svd_status = (int*)sc.p;
+  double* phid = (double*)((char*)sc.p + 16);
+  CK(cudaMemsetAsync(svd_status, 0, sizeof(int), stream));
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  constexpr long long kRows = 1 << 20;
+  auto chain = [&](int i0, int i1, double2* b0, double2* b1) -> const double2* {
+    const double2* cur = ring.t[idx[i0]];
+    long long rows = (long long)ring.sh[idx[i0]].l * ring.sh[idx[i0]].p;
+    int cols = ring.sh[idx[i0]].r;
+    double2* out = b0;
+    for (int i = i0 + 1; i < i1; ++i) {
+      const TShape t = ring.sh[idx[i]];
+      for (long long r0 = 0; r0 < rows; r0 += kRows)
+        if (launch_zgemm('N', 'N', (int)std::min(kRows, rows - r0), t.p * t.r, cols, one, cur + r0 * cols, cols, 0,
+                         ring.t[idx[i]], t.p * t.r, 0, zero, out + r0 * (long long)t.p * t.r, t.p * t.r, 0, 1,
+                         stream) != cudaSuccess)
+          return nullptr;
+      cur = out;
+      out = (out == b0) ? b1 : b0;
+      rows *= t.p;
+      cols = t.r;
+    }
+    return cur;
+  };
+  auto copy = [&](const double2* src, double2* dst, const StridedView& v) { return launch_strided_copy(src, dst, v, stream); };
+
+  // dense environment: N[f1, f2] = sum_{l0, m} A[l0, f1, m] B[m, f2, l0]
+  const double2* A = chain(0, n0, A0, A1);
+  const double2* B = chain(n0, L, B0, B1);
+  if (!A || !B) return fail(this, 3, "ITE: ring product failed");
+  {
+    const int pa[3] = {1, 2, 0}, pb[3] = {0, 2, 1};
+    CK(launch_permute3(A, l0, (int)P1, m, pa, Ap, stream));   // (P1, m, l0)
+    CK(launch_permute3(B, m, (int)P2, l0, pb, Bp, stream));   // (m, l0, P2)
+  }
+  CK(launch_zgemm('N', 'N', (int)P1, (int)P2, (int)LM, one, Ap, (int)LM, 0, Bp, (int)P2, 0, zero, Nf, (int)P2, 0, 1,
+                  stream));
+  {   // unfuse: (k0 b0 k1 b1 ... k5 b5) -> (k0 .. k5, b0 .. b5)
+    long long dims12[12], str12[12];
+    for (int q = 0; q < 6; ++q) {
+      const int nq = q < 3 ? na[outer[0][q]] : nb[outer[1][q - 3]];
+      dims12[2 * q] = dims12[2 * q + 1] = nq;
+    }
+    long long stv = 1;
+    for (int a = 11; a >= 0; --a) { str12[a] = stv; stv *= dims12[a]; }
+    StridedView v;
+    v.rank = 12;
+    for (int q = 0; q < 6; ++q) {
+      v.dims[q] = dims12[2 * q];
+      v.sstr[q] = str12[2 * q];
+      v.dims[6 + q] = dims12[2 * q + 1];
+      v.sstr[6 + q] = str12[2 * q + 1];
+    }
+    long long st = 1;
+    for (int k = 11; k >= 0; --k) { v.dstr[k] = st; st *= v.dims[k]; }
+    v.total = st;
+    CK(copy(Nf, Nkb, v));
+  }
+  // x, y: [p, outer legs in ring order, bond] gathered from the site tensors
+  const long long sz = (long long)dd * D * D * D * D;
+  auto sstride = [&](int slot) { long long r = 1; for (int q = slot + 1; q < 4; ++q) r *= D; return r; };
+  const double2* tb = (const double2*)t_dev.p;
+  CK(copy(tb + gid[0] * sz, X, sview({dd, na[outer[0][0]], na[outer[0][1]], na[outer[0][2]], Db},
+                                     {(long long)D * D * D * D, sstride(outer[0][0]), sstride(outer[0][1]),
+                                      sstride(outer[0][2]), sstride(js[0])})));
+  CK(copy(tb + gid[1] * sz, Y, sview({dd, nb[outer[1][0]], nb[outer[1][1]], nb[outer[1][2]], Db},
+                                     {(long long)D * D * D * D, sstride(outer[1][0]), sstride(outer[1][1]),
+                                      sstride(outer[1][2]), sstride(js[1])})));
+  CK(cudaMemcpyAsync(Gd, gate, sizeof(double2) * d2 * d2, cudaMemcpyHostToDevice, stream));
+  // psi = x y over the bond, as [p1 p2, K1 K2]; Theta = gate psi
+  auto two_site = [&](const double2* x, const double2* y, double2* out) -> int {
+    CK(launch_zgemm('N', 'T', (int)dE1, (int)dE2, Db, one, x, Db, 0, y, Db, 0, zero, psi1, (int)dE2, 0, 1, stream));
+    CK(copy(psi1, out, sview({dd, dd, E1, E2}, {E1 * dE2, E2, dE2, 1})));
+    return 0;
+  };
+  if (int rc = two_site(X, Y, psi)) return rc;
+  CK(launch_zgemm('N', 'N', (int)d2, (int)EE, (int)d2, one, Gd, (int)d2, 0, psi, (int)EE, 0, zero, Th, (int)EE, 0, 1,
+                  stream));
+  // TN[p1 p2, B1 B2] = sum_K Theta[p, K] N[K, B]; its two groupings
+  CK(launch_zgemm('N', 'N', (int)d2, (int)EE, (int)EE, one, Th, (int)EE, 0, Nkb, (int)EE, 0, zero, TN, (int)EE, 0, 1,
+                  stream));
+  CK(copy(TN, TNp1, sview({dd, E1, dd, E2}, {dd * EE, E2, EE, 1})));     // [(p1 B1), (p2 B2)]
+  CK(copy(TN, TNp2, sview({dd, E2, dd, E1}, {EE, 1, dd * EE, E2})));     // [(p2 B2), (p1 B1)]
+  CK(copy(Nkb, Nr1, sview({E1, E1, E2, E2}, {E2 * EE, E2, EE, 1})));    // [K1, B1, K2, B2]
+  CK(copy(Nkb, Nr2, sview({E2, E2, E1, E1}, {EE, 1, E2 * EE, E2})));    // [K2, B2, K1, B1]
+  // the ALS start: truncated SVD of Theta as [(p1 K1), (p2 K2)]
+  CK(copy(Th, Thm, sview({dd, E1, dd, E2}, {dd * EE, E2, EE, 1})));
+  CK(launch_svd_trunc(Thm, (int)dE1, (int)dE2, Db, U, Rm, svdw.p, svd_status, stream));
+  const int k0 = (int)std::min<long long>(Db, std::min(dE1, dE2));
+  CK(cudaMemsetAsync(X, 0, sizeof(double2) * dE1 * Db, stream));
+  CK(cudaMemsetAsync(Y, 0, sizeof(double2) * dE2 * Db, stream));
+  {
+    StridedView v = sview({dE1, k0}, {k0, 1});
+    v.dstr[0] = Db;
+    v.dstr[1] = 1;
+    CK(copy(U, X, v));
+    StridedView w = sview({dE2, k0}, {1, dE2});                          // y[(p2 K2), b] = Rem[b, (p2 K2)]
+    w.dstr[0] = Db;
+    w.dstr[1] = 1;
+    CK(copy(Rm, Y, w));
+  }
+  auto phi_eval = [&](double* out) -> int {
+    if (int rc = two_site(X, Y, Xd)) return rc;
+    CK(launch_axpy(Th, Xd, d2 * EE, make_double2(-1, 0), stream));
+    CK(launch_zgemm('N', 'N', (int)d2, (int)EE, (int)EE, one, Xd, (int)EE, 0, Nkb, (int)EE, 0, zero, Tq, (int)EE, 0,
+                    1, stream));
+    CK(launch_quad_form(Tq, Xd, d2 * EE, phid, stream));
+    CK(cudaMemcpyAsync(out, phid, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return 0;
+  };
+  // least-squares solution of M v = c for the d columns of cT: out (n x d)
+  auto solve = [&](int n, double2* out) -> int {
+    CK(launch_svd_trunc(Mt, n, n, n, U, Rm, svdw.p, svd_status, stream));
+    CK(launch_zgemm('C', 'N', n, dd, n, one, U, n, 0, cT, dd, 0, zero, W, dd, 0, 1, stream));
+    CK(launch_pinv_rows(W, Rm, n, dd, 1e-13, stream));
+    CK(launch_zgemm('C', 'N', n, dd, n, one, Rm, n, 0, W, dd, 0, zero, out, dd, 0, 1, stream));
+    return 0;
+  };
+  // one half-step: the site tensor `var` (outer size Ev) with the other one,
+  // `fix` (outer size Ef), fixed
+  auto half = [&](bool first) -> int {
+    const long long Ev = first ? E1 : E2, Ef = first ? E2 : E1;
+    const long long nf = Ef * Db, nv = Ev * Db;
+    double2* fix = first ? Y : X;
+    double2* var = first ? X : Y;
+    // G[(Kf b), (Bf b')] = sum_p conj(fix[p, (Kf b)]) fix[p, (Bf b')]
+    CK(launch_zgemm('C', 'N', (int)nf, (int)nf, dd, one, fix, (int)nf, 0, fix, (int)nf, 0, zero, G, (int)nf, 0, 1,
+                    stream));
+    // Gr[(Kf Bf), (b b')] = G[(Bf b'), (Kf b)]
+    CK(copy(G, Gr, sview({Ef, Ef, Db, Db}, {Db, Db * nf, 1, nf})));
+    // MM[(Kv Bv), (b b')] = Nr[(Kv Bv), (Kf Bf)] Gr
+    CK(launch_zgemm('N', 'N', (int)(Ev * Ev), Db * Db, (int)(Ef * Ef), one, first ? Nr1 : Nr2, (int)(Ef * Ef), 0, Gr,
+                    Db * Db, 0, zero, MM, Db * Db, 0, 1, stream));
+    // M[(Bv b'), (Kv b)] = MM[Kv, Bv, b, b']
+    CK(copy(MM, Mt, sview({Ev, Db, Ev, Db}, {(long long)Db * Db, 1, Ev * Db * Db, Db})));
+    // fix^T: [b, (p Kf)]
+    CK(copy(fix, first ? YT : XT, sview({Db, dd * Ef}, {1, Db})));
+    // c[(p Bv), b'] = TNp[(p Bv), (p' Bf)] conj(fix[(p' Bf), b'])
+    CK(launch_zgemm('N', 'C', (int)(dd * Ev), Db, (int)(dd * Ef), one, first ? TNp1 : TNp2, (int)(dd * Ef), 0,
+                    first ? YT : XT, (int)(dd * Ef), 0, zero, cc, Db, 0, 1, stream));
+    // cT[(Bv b'), p] = c[p, Bv, b']
+    CK(copy(cc, cT, sview({Ev, Db, dd}, {Db, 1, Ev * Db})));
+    if (int rc = solve((int)nv, cc)) return rc;   // the solution, (Kv b) x p, replaces c
+    // var[p, Kv, b] = sol[(Kv b), p]
+    CK(copy(cc, var, sview({dd, Ev, Db}, {1, Db * dd, dd})));
+    return 0;
+  };
+  double ph = 0.0;
+  if (int rc = phi_eval(&ph)) return rc;
+  phi.push_back(ph);
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    if (int rc = half(true)) return rc;
+    if (int rc = phi_eval(&ph)) return rc;
+    phi.push_back(ph);
+    if (int rc = half(false)) return rc;
+    if (int rc = phi_eval(&ph)) return rc;
+    phi.push_back(ph);
+    const size_t q = phi.size();
+    if (phi[q - 3] - phi[q - 1] <= tol * std::max(std::fabs(phi[0]), 1e-300)) break;
+  }
+  int hst = 0;
+  CK(cudaMemcpyAsync(&hst, svd_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  if (hst) return fail(this, 5, "an SVD of the ITE update did not converge");
+  // the new tensors replace the old ones (open legs at index 0), each / max |entry|
+  drop_graphs();
+  for (int q = 0; q < 2; ++q) {
+    const auto& nn = q == 0 ? na : nb;
+    double2* dst = (double2*)t_dev.p + gid[q] * sz;
+    CK(cudaMemsetAsync(dst, 0, sizeof(double2) * sz, stream));
+    StridedView v = sview({dd, nn[outer[q][0]], nn[outer[q][1]], nn[outer[q][2]], Db}, {0, 0, 0, 0, 0});
+    long long st = 1;
+    for (int k = 4; k >= 0; --k) { v.sstr[k] = st; st *= v.dims[k]; }
+    v.dstr[0] = (long long)D * D * D * D;
+    v.dstr[1] = sstride(outer[q][0]);
+    v.dstr[2] = sstride(outer[q][1]);
+    v.dstr[3] = sstride(outer[q][2]);
+    v.dstr[4] = sstride(js[q]);
+    CK(copy(q == 0 ? X : Y, dst, v));
+    CK(launch_scale_absmax(dst, sz, stream));
+  }
+  for (auto itf = fused.begin(); itf != fused.end();) {
+    if (itf->first.first == gid[0] || itf->first.first == gid[1]) itf = fused.erase(itf);
+    else ++itf;
+  }
+  CK(cudaStreamSynchronize(stream));
+  return 0;
+}
+
+int Engine::ite(const double* gates, int ndt, const int* bonds, int nbonds, double bp_tol, int bp_iter,
+                int als_sweeps, double* energies) {
+  if (!gates || ndt < 0 || !bonds || nbonds <= 0 || !energies) return fail(this, 1, "bad arguments");
+  const size_t gsz = 2 * (size_t)d * d * d * d;
+  std::vector<double> phi;
+  for (int k = 0; k < ndt; ++k) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = 0; q < nbonds; ++q) {
+        const int b = pass == 0 ? q : nbonds - 1 - q;
+        int its = 0;
+        double err = 0.0;
+        const int rc = iterate(bp_tol, bp_iter, &its, &err);
+        if (rc && rc != 6) return rc;
+        if (int rc2 = ite_bond(bonds[2 * b], bonds[2 * b + 1], gates + gsz * k, als_sweeps, 1e-13, phi)) return rc2;
+      }
+    int its = 0;
+    double err = 0.0;
+    const int rc = iterate(bp_tol, bp_iter, &its, &err);
+    if (rc && rc != 6) return rc;
+    if (int rc2 = energy_per_site(&energies[k])) return rc2;
+  }
+  return 0;
+}
+
 }  // namespace bbp

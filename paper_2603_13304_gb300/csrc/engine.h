@@ -173,6 +173,18 @@ class Engine {
   // complex128 operators each, set k site q at ops + 2 d d (k ncore + q)),
   // <O_k> = Z(O_k) / Z(1), the core contracted exactly with its pMPS.
   int core_expect(int block, const std::vector<int>& core, const double* ops, int nops, double* re, double* im);
+  // ITE update of one bond (Ch. 3, "ITE update step"; FP64 mode, both ends in
+  // one block): the bond leaving site g1 through slot k1 takes the two-site
+  // gate (host d^2 x d^2 complex128 over (s1 s2)), then ALS on the bond's
+  // Edge TN brings it back to bond D; the new site tensors replace the old
+  // ones, each divided by its largest entry.  phi: Phi after the SVD start
+  // and after every ALS half-step.
+  int ite_bond(int g1, int k1, const double* gate, int max_sweeps, double tol, std::vector<double>& phi);
+  // Full ITE (Alg. 2): for each of ndt gates, every bond of the list, then
+  // the list backwards, is updated after BlockBP runs to bp_tol; energies
+  // receives the energy per site after each gate's pass.
+  int ite(const double* gates, int ndt, const int* bonds, int nbonds, double bp_tol, int bp_iter, int als_sweeps,
+          double* energies);
 
  private:
   SweepWork* work(size_t i);

@@ -95,6 +95,27 @@ cudaError_t launch_conj_transpose(const float2* src, int rows, int cols, float2*
 cudaError_t launch_permute3(const double2* src, int d0, int d1, int d2, const int perm[3], double2* dst, cudaStream_t s);
 cudaError_t launch_permute3(const float2* src, int d0, int d1, int d2, const int perm[3], float2* dst, cudaStream_t s);
 
+// ITE helpers (k_ite.cu, complex128).  A strided view: over the row-major
+// index space dims[0..rank), dst[sum c_q dstr[q]] = src[sum c_q sstr[q]]
+// (permutations, gathers and scatters of small tensors).
+constexpr int kStridedMaxRank = 12;
+struct StridedView {
+  int rank = 0;
+  long long total = 0;
+  long long dims[kStridedMaxRank], sstr[kStridedMaxRank], dstr[kStridedMaxRank];
+};
+cudaError_t launch_strided_copy(const double2* src, double2* dst, const StridedView& v, cudaStream_t s);
+// W (n x ncols) rows scaled by 1 / |Rem row|^2, zero below (rcond sigma_max)^2:
+// with M = U Rem the truncated SVD of a square M, Rem^H (this applied to
+// U^H c) is the least-squares solution of M x = c.
+cudaError_t launch_pinv_rows(double2* W, const double2* Rem, int n, int ncols, double rcond, cudaStream_t s);
+// *out = Re sum T[e] conj(X[e])
+cudaError_t launch_quad_form(const double2* T, const double2* X, long long n, double* out, cudaStream_t s);
+// A /= max |A|
+cudaError_t launch_scale_absmax(double2* A, long long n, cudaStream_t s);
+// y += a x
+cudaError_t launch_axpy(const double2* x, double2* y, long long n, double2 a, cudaStream_t s);
+
 // An MPS passed to a kernel by value (no device-side tables, no copies).
 constexpr int kMaxChain = 64;
 struct ChainDesc {
