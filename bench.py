@@ -428,6 +428,45 @@ def run_core(workload: str, precision: int, reps: int = 3):
                            "contraction with the fused core tensors, host time per call"}
 
 
+def run_ite(workload: str = "kagome-6x2-L2-D4-chi32", settle: int = 4, dt: float = 0.05, sweeps: int = 10):
+    """ITE with ALS (Ch. 3) at a Kagome workload in the FP64 mode: after
+    `settle` BlockBP iterations, one ITE update of the A-B bond of each
+    block's first unit cell (the bond's Edge TN, its dense environment, the
+    gate exp(-dt S.S), ALS of at most `sweeps` sweeps, the tensors replaced),
+    host time per update."""
+    import numpy as np
+    import torch
+    import paper_2603_13304_gb300 as P
+    w = WORKLOADS[workload]
+    t, em = make_inputs(w)
+    ctx = P.bbp_create_peps(P.KAGOME, w["Lx"], w["Ly"], 1, w["d"], w["D"], t)
+    P.bbp_partition_blocks(ctx, w["L"], w["L"])
+    P.bbp_set_options(ctx, w["chi"], P.FP64)
+    P.bbp_init_messages(ctx, em)
+    P.bbp_iterate(ctx, 0.0, settle)
+    s = [np.array([[0, 0.5], [0.5, 0]]), np.array([[0, -0.5j], [0.5j, 0]]), np.diag([0.5, -0.5])]
+    h = sum(np.kron(a, a) for a in s)
+    ev, V = np.linalg.eigh(h)
+    gate = (V * np.exp(-dt * ev)) @ V.conj().T          # the input gate exp(-dt h)
+    n_blocks = P.bbp_info(ctx)[0]
+    ms, phis = [], []
+    for b in range(n_blocks):
+        site = 3 * (b * w["L"])                          # A of cell (b L, 0); slot 0 joins B of the same cell
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        phi = P.bbp_ite_bond(ctx, site, 0, gate, max_sweeps=sweeps)
+        torch.cuda.synchronize()
+        ms.append(1e3 * (time.perf_counter() - a0))
+        phis.append([float(phi[0]), float(phi[-1]), len(phi)])
+    P.bbp_destroy(ctx)
+    ms.sort()
+    return {"workload": workload, "precision": "fp64", "settle_iterations": settle, "dt": dt,
+            "bond": "A-B of each block's first unit cell", "updates": len(ms), "ms_per_update_median": ms[len(ms) // 2],
+            "ms_per_update_min": ms[0], "phi_start_end_halfsteps": phis,
+            "note": "Edge TN (two bubbles + zipper), dense environment over the six outer legs (4^12 entries), "
+                    "gate, SVD start, ALS half-steps, tensors replaced; host time per bbp_ite_bond"}
+
+
 # -------------------------------------------------- many networks, serving
 
 def network_mix(n, seed):
@@ -958,8 +997,8 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=16, help="job templates of the serving stream")
     ap.add_argument("--serve-active", type=int, default=32, help="resident jobs at most (server slots)")
     ap.add_argument("--serve-no-fp64", action="store_true", help="skip the FP64 one-at-a-time baseline")
-    ap.add_argument("--only", choices=["batched", "serving", "core"],
-                    help="run only the batched, the serving or the core-extraction measurement and print it")
+    ap.add_argument("--only", choices=["batched", "serving", "core", "ite"],
+                    help="run only the batched, serving, core-extraction or ITE measurement and print it")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--peaks", action="store_true", help="measure the chip's ALU and tensor rates and exit")
     ap.add_argument("--kernel-case", choices=["fuse", "absorb", "panel", "panel_r", "svd"],
@@ -984,6 +1023,8 @@ def main():
             out = run_batched(args.batch, args.batch_rounds, 1, prec_code, groups=args.batch_pools)
         elif args.only == "core":
             out = run_core(args.workload, prec_code)
+        elif args.only == "ite":
+            out = run_ite()
         else:
             out = run_serving(args.serve, args.serve_rate, prec_code, warm_s=min(5.0, args.serve / 4),
                               pool_n=args.serve_pool, max_active=args.serve_active,
