@@ -20,6 +20,8 @@ core      core extraction: two opposing bubbles, the zipper into a pMPS, the
           Edge TN of a bond (Sec. 2.3, "Core", "Edge")
 ite       imaginary time evolution: two-site gate, ALS on the Edge TN, full
           ITE over a block (Ch. 3, Alg. 2)
+hexagonal hexagonal Kagome blocks of face-length N: geometry, the six
+          contraction orders, BlockBP on them (Sec. 2.3.1, Sec. 2.3)
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
 the loopy configurations themselves, which have no closed form: the BlockBP
