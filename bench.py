@@ -428,7 +428,8 @@ def run_core(workload: str, precision: int, reps: int = 3):
                            "contraction with the fused core tensors, host time per call"}
 
 
-def run_ite(workload: str = "kagome-6x2-L2-D4-chi32", settle: int = 4, dt: float = 0.05, sweeps: int = 10):
+def run_ite(workload: str = "kagome-6x2-L2-D4-chi32", settle: int = 4, dt: float = 0.05, sweeps: int = 10,
+            max_updates: int = 0):
     """ITE with ALS (Ch. 3) at a Kagome workload in the FP64 mode: after
     `settle` BlockBP iterations, one ITE update of the A-B bond of each
     block's first unit cell (the bond's Edge TN, its dense environment, the
@@ -449,6 +450,8 @@ def run_ite(workload: str = "kagome-6x2-L2-D4-chi32", settle: int = 4, dt: float
     ev, V = np.linalg.eigh(h)
     gate = (V * np.exp(-dt * ev)) @ V.conj().T          # the input gate exp(-dt h)
     n_blocks = P.bbp_info(ctx)[0]
+    if max_updates:
+        n_blocks = min(n_blocks, max_updates)
     ms, phis = [], []
     for b in range(n_blocks):
         site = 3 * (b * w["L"])                          # A of cell (b L, 0); slot 0 joins B of the same cell
@@ -1000,6 +1003,8 @@ def main():
     ap.add_argument("--only", choices=["batched", "serving", "core", "ite"],
                     help="run only the batched, serving, core-extraction or ITE measurement and print it")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the core-extraction and ITE legs of the default line")
     ap.add_argument("--peaks", action="store_true", help="measure the chip's ALU and tensor rates and exit")
     ap.add_argument("--kernel-case", choices=["fuse", "absorb", "panel", "panel_r", "svd"],
                     help="run one kernel alone and exit")
@@ -1088,6 +1093,18 @@ def main():
                            pool_n=args.serve_pool, max_active=args.serve_active,
                            fp64_baseline=not args.serve_no_fp64)
                if args.serve > 0 and world == 1 else None)
+    core = ite_leg = None
+    if world == 1 and not args.no_extras:
+        # the thesis' core extraction (Sec. 2.3) and ITE update (Ch. 3), each
+        # timed on its own; a failure is reported in the line, not raised
+        try:
+            core = run_core(args.workload, prec_code)
+        except Exception as e:                              # noqa: BLE001
+            core = {"error": str(e)[:300]}
+        try:
+            ite_leg = run_ite(max_updates=1)
+        except Exception as e:                              # noqa: BLE001
+            ite_leg = {"error": str(e)[:300]}
     line = {
         "metric": "BlockBP message updates/s", "value": res["value"], "unit": "message updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1102,7 +1119,7 @@ def main():
         "roofline": res["roofline"], "roofline_tensor_gemm": res["roofline_tc"], "cpu_baseline": cpu,
         "accuracy_vs_oracle": res["accuracy"],
         "energy_per_site": res["energy"], "absorb_tflop_per_step": res["flops_iter"] / 1e12,
-        "batched": batched, "serving": serving,
+        "batched": batched, "serving": serving, "core_extraction": core, "ite": ite_leg,
     }
     print(json.dumps(line))
     if world > 1:
