@@ -87,3 +87,33 @@ def test_zipper_front_line_transposed_is_caught(monkeypatch):
     except Exception:
         err = math.inf
     assert err > 1e-6
+
+
+def test_ite_gate_sign_flip_is_caught(monkeypatch):
+    """Plant exp(+dt h) for exp(-dt h) in the ITE oracle: the two-spin run
+    must then miss the singlet energy the pin fixes."""
+    from oracle import ite
+    real_gate = ite.gate
+    geom = Geometry.square(2, 1, 2, 1)
+    t = syn.gaussian_peps(2, 2, 2, seed=13)
+    em = syn.initial_edge_matrices(2, 2, seed=14)
+    _, E = ite.full_ite(geom, t, 16, [0.5] * 20, em)
+    assert abs(E[-1].real + 0.375) < 1e-6
+    monkeypatch.setattr(ite, "gate", lambda h, dt: real_gate(h, -dt))
+    _, E = ite.full_ite(geom, t, 16, [0.5] * 20, em)
+    assert abs(E[-1].real + 0.375) > 0.1
+
+
+def test_hexagonal_face_order_flip_is_caught(monkeypatch):
+    """Plant a reversed canonical edge order on one face of the hexagonal
+    blocks: the edge-for-edge pairing of opposite faces must then fail."""
+    from oracle import hexagonal as H
+    real = H._canon
+    monkeypatch.setattr(H, "_canon", lambda f, p4: -real(f, p4) if f == 1 else real(f, p4))
+    g = H.HexGeometry(2, 7, 7)
+    bad = 0
+    for b in g.blocks:
+        mine = b.faces[1].edges
+        other = g.blocks[b.faces[1].nbr].faces[4].edges
+        bad += sum(1 for e, o in zip(mine, other) if g.blocks[b.faces[1].nbr].gids[o.site] != e.gid)
+    assert bad > 0
