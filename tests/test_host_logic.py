@@ -100,6 +100,11 @@ CORES = [
     ("square", (4, 4, 2, 2), 0, [0, 1, 2, 3]),
     ("kagome", (6, 2, 2), 0, "cell"),
     ("kagome", (9, 3, 3), 1, "cell"),
+    ("kagome", (9, 3, 3), 0, ("cell", 4)),
+    ("kagome", (12, 4, 4), 0, ("cell", 7)),
+    ("kagome", (12, 4, 4), 2, ("cell", 12)),
+    ("square", (8, 8, 4, 4), 0, [5, 6]),
+    ("square", (8, 8, 4, 4), 3, [9, 10, 13]),
 ]
 
 
@@ -130,6 +135,10 @@ def test_core_plan_matches_oracle_bubbles(L, kind, args, block, core):
     b = geom.blocks[block]
     if core == "cell":    # the up-triangle of the block's second unit cell
         i, j = b.sites[2][1:]
+        core = [b.sites.index((t, i, j)) for t in range(3)]
+    elif isinstance(core, tuple):   # the k-th complete up-triangle of the block
+        cells = sorted({(i, j) for (t, i, j) in b.sites if all((u, i, j) in b.sites for u in range(3))})
+        i, j = cells[core[1]]
         core = [b.sites.index((t, i, j)) for t in range(3)]
     keys = [(0, q) for q in core]
     traces = []
