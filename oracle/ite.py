@@ -25,9 +25,10 @@ Readings:
 * each half-step solves the normal equations M x = c of the quadratic
   Phi with a least-squares routine (M may be singular); the environment
   enters through its Hermitian part;
-* the full environment is used: the thesis' reduced-environment variant
-  (QR of each site tensor, the Q part moved into the environment) is a
-  cost optimisation that it reports gives similar results;
+* als uses the full environment; als_reduced is the thesis' variant (QR of
+  each site tensor over its outer legs, the isometric Q moved into the
+  environment, ALS on the small R parts), which it reports gives similar
+  results at a lower cost;
 * after each update both tensors are divided by their largest entry (the
   state is defined up to normalisation; observables are ratios).
 """
@@ -177,7 +178,56 @@ def als(t1, t2, s1, s2, N, dims1, dims2, G, D, max_sweeps: int = 50, tol: float 
     return a, b, hist
 
 
-def bond_update(bbp: BlockBP, g1: int, k1: int, G, D: int, max_sweeps: int = 50):
+def reduce_site(t, s):
+    """The reduced-environment split of one site tensor (Sec. 3.2): a QR over
+    its outer legs, t[p, outer, bond] = sum_k Q[outer, k] r[p, k, bond], Q an
+    isometry that joins the environment and r (d x k x D) the part ALS
+    updates."""
+    x = _open(t, s)                                   # [p, E, bond]
+    d, E, Db = x.shape
+    Q, R = np.linalg.qr(np.transpose(x, (1, 0, 2)).reshape(E, d * Db))
+    k = Q.shape[1]
+    return Q, np.transpose(R.reshape(k, d, Db), (1, 0, 2))
+
+
+def reduced_env(N, dims1, dims2, Q1, Q2):
+    """The environment seen by the reduced tensors: N with site 1's outer
+    legs contracted with Q1 (ket) and conj(Q1) (bra), site 2's with Q2, as a
+    fused environment over the reduced legs (k1, 1, 1 | k2, 1, 1)."""
+    Nkb = env_matrix(N, dims1, dims2)
+    E1, E2 = Q1.shape[0], Q2.shape[0]
+    k1, k2 = Q1.shape[1], Q2.shape[1]
+    N4 = Nkb.reshape(E1, E2, E1, E2)
+    Nr = np.einsum("abcd,ak,bl,cm,dn->klmn", N4, Q1, Q2, Q1.conj(), Q2.conj())
+    return np.transpose(Nr, (0, 2, 1, 3)).reshape(k1 * k1, 1, 1, k2 * k2, 1, 1)
+
+
+def _as_site(r, s):
+    """r[p, k, bond] as a four-slot tensor: the bond at slot s, the other
+    slots (k, 1, 1) in slot order."""
+    d, k, Db = r.shape
+    return _insert(r.reshape(d, k, 1, 1, Db), s)
+
+
+def _restore(t_like, Q, a, s):
+    """t' = Q r' with the tensor laid out like t_like."""
+    ra = _open(a, s)                                  # [p, k, bond]
+    return _close(np.einsum("ek,pkb->peb", Q, ra), t_like, s)
+
+
+def als_reduced(t1, t2, s1, s2, N, dims1, dims2, G, D, max_sweeps: int = 50, tol: float = 1e-13):
+    """ALS on the reduced environment (the variant the thesis runs, Sec. 3.2):
+    both site tensors split by reduce_site, ALS (same steps as als) on the
+    reduced tensors r1, r2 with the projected environment, then t' = Q r'."""
+    Q1, r1 = reduce_site(t1, s1)
+    Q2, r2 = reduce_site(t2, s2)
+    Nf = reduced_env(N, dims1, dims2, Q1, Q2)
+    a, b, hist = als(_as_site(r1, s1), _as_site(r2, s2), s1, s2, Nf, [Q1.shape[1], 1, 1], [Q2.shape[1], 1, 1],
+                     G, D, max_sweeps, tol)
+    return _restore(t1, Q1, a, s1), _restore(t2, Q2, b, s2), hist
+
+
+def bond_update(bbp: BlockBP, g1: int, k1: int, G, D: int, max_sweeps: int = 50, reduced: bool = False):
     """One ITE update of the bond leaving site g1 through slot k1, with the Edge
     TN of the converged messages of ``bbp``.  Returns (g2, new t_g1, new t_g2,
     Phi history); the tensors have the open legs of the lattice cut to 1."""
@@ -191,7 +241,7 @@ def bond_update(bbp: BlockBP, g1: int, k1: int, G, D: int, max_sweeps: int = 50)
     t1, t2 = bbp.tc[rs1.gid], bbp.tc[rs2.gid]
     dims1 = [t1.shape[1 + s] for s in range(4) if s != s1]
     dims2 = [t2.shape[1 + s] for s in range(4) if s != s2]
-    a, b, hist = als(t1, t2, s1, s2, N, dims1, dims2, G, D, max_sweeps)
+    a, b, hist = (als_reduced if reduced else als)(t1, t2, s1, s2, N, dims1, dims2, G, D, max_sweeps)
     return rs2.gid, a, b, hist
 
 
@@ -202,7 +252,7 @@ def _put(t_full: np.ndarray, g: int, small: np.ndarray):
 
 
 def full_ite(geom, t: np.ndarray, chi: int, dts, edge_mats, h=None, bp_tol: float = 1e-10,
-             bp_iter: int = 40, als_sweeps: int = 50, on_step=None):
+             bp_iter: int = 40, als_sweeps: int = 50, on_step=None, reduced: bool = False):
     """Alg. 2 (Full ITE using BlockBP) on a finite or periodic network: for
     every dt, every bond is updated with exp(-dt/2 h), forwards through the
     bond list and then backwards (second-order splitting); BlockBP runs to
@@ -229,7 +279,7 @@ def full_ite(geom, t: np.ndarray, chi: int, dts, edge_mats, h=None, bp_tol: floa
         G = gate(h, 0.5 * dt)
         for (g1, k1, _, _) in bonds + bonds[::-1]:
             bbp = converged()
-            g2, a, b, _ = bond_update(bbp, g1, k1, G, D, als_sweeps)
+            g2, a, b, _ = bond_update(bbp, g1, k1, G, D, als_sweeps, reduced)
             _put(t, g1, a)
             _put(t, g2, b)
         e = converged().energy_per_site()

@@ -251,3 +251,68 @@ def test_ite_on_a_tree_of_blocks_matches_one_block():
     E0 = _ed_ground(bonds, 4) / 4
     assert all(e.real > E0 - 1e-12 for e in E1)
     assert E1[-1].real < E1[0].real < 0
+
+
+# ------------------------------------------- ITE on the reduced environment
+
+def test_reduced_environment_is_an_exact_projection():
+    """Sec. 3.2, reduced environment: for any reduced tensors r1, r2, Phi of
+    the reduced problem equals Phi of the full problem at t = Q r (the
+    projection of N onto the Q subspaces loses nothing for such t)."""
+    D = 2
+    t1, t2 = _random_bond(D, 21)
+    s1, s2 = 1, 3
+    dims = [D] * 3
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((D ** 6, D ** 6)) + 1j * rng.standard_normal((D ** 6, D ** 6))
+    Nkb = X @ X.conj().T / D ** 6
+    Nf = Nkb.reshape([D] * 12).transpose([q // 2 + 6 * (q % 2) for q in range(12)]).reshape([D * D] * 6)
+    G = ite.gate(ite.heisenberg_h(), 0.4)
+    Q1, r1 = ite.reduce_site(t1, s1)
+    Q2, r2 = ite.reduce_site(t2, s2)
+    assert np.abs(Q1.conj().T @ Q1 - np.eye(Q1.shape[1])).max() < 1e-13
+    assert np.abs(ite._restore(t1, Q1, ite._as_site(r1, s1), s1) - t1).max() < 1e-12
+    Nr = ite.reduced_env(Nf, dims, dims, Q1, Q2)
+    k1, k2 = Q1.shape[1], Q2.shape[1]
+    Theta_full = ite.evolve(t1, t2, s1, s2, G)
+    Theta_red = ite.evolve(ite._as_site(r1, s1), ite._as_site(r2, s2), s1, s2, G)
+    Nkb_red = ite.env_matrix(Nr, [k1, 1, 1], [k2, 1, 1])
+    for seed in (23, 24):
+        g = np.random.default_rng(seed)
+        a = g.standard_normal(r1.shape) + 1j * g.standard_normal(r1.shape)
+        b = g.standard_normal(r2.shape) + 1j * g.standard_normal(r2.shape)
+        red = ite.phi(ite._as_site(a, s1), ite._as_site(b, s2), s1, s2, Nkb_red, Theta_red)
+        full = ite.phi(ite._restore(t1, Q1, ite._as_site(a, s1), s1), ite._restore(t2, Q2, ite._as_site(b, s2), s2),
+                       s1, s2, ite.env_matrix(Nf, dims, dims), Theta_full)
+        assert abs(red - full) < 1e-11 * abs(full)
+
+
+def test_reduced_and_full_als_agree_when_the_split_is_square():
+    """When every site's outer legs are no wider than d D, Q is square and the
+    reduced ALS is the full ALS in another basis: the same Phi history and
+    the same full-ITE energies (2 x 2 plaquette)."""
+    geom = Geometry.square(2, 2, 2, 2)
+    t = syn.gaussian_peps(4, 2, 2, seed=3)
+    em = syn.initial_edge_matrices(4, 2, seed=4)
+    dts = [0.2] * 4
+    _, Ef = ite.full_ite(geom, t, 16, dts, em)
+    _, Er = ite.full_ite(geom, t, 16, dts, em, reduced=True)
+    assert max(abs(a - b) for a, b in zip(Ef, Er)) < 1e-12
+
+
+def test_reduced_ite_reaches_the_chain_ground_state():
+    geom = Geometry.square(3, 1, 3, 1)
+    t = syn.gaussian_peps(3, 2, 2, seed=3)
+    _, E = ite.full_ite(geom, t, 16, [0.2] * 20 + [0.05] * 20 + [0.01] * 20, syn.initial_edge_matrices(3, 2, seed=4),
+                        reduced=True)
+    assert abs(E[-1].real * 3 + 1.0) < 2e-4
+
+
+def test_reduced_als_phi_never_increases_on_an_interior_bond():
+    """An interior bond of a 3 x 3 block (outer legs 2^3 = 8 > d D = 4, so the
+    reduction is proper): every reduced half-step lowers Phi or keeps it."""
+    geom = Geometry.square(3, 3, 3, 3)
+    bb, _ = _bbp(geom, 2, 64, 5, 0)
+    G = ite.gate(ite.heisenberg_h(), 0.3)
+    _, a, b, hist = ite.bond_update(bb, 4, 1, G, 2, max_sweeps=8, reduced=True)
+    assert all(hist[q + 1] <= hist[q] * (1 + 1e-10) + 1e-14 for q in range(len(hist) - 1))
