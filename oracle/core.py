@@ -244,3 +244,33 @@ def two_site_spec(s1: int, s2: int) -> str:
     out = "xy" + "".join(a[q] for q in range(4) if q != s1) + "".join(b[q] for q in range(4) if q != s2)
     return "x" + "".join(a) + ",y" + "".join(b) + "->" + out
 
+
+
+# Down-triangle bonds of the Kagome lattice (Sec. 2.3.1): B(R)-A(R + a1),
+# C(R)-A(R + a2), B(R)-C(R + a1 - a2); through each vertex of the up-triangle
+# of cell R runs one down-triangle: its two other sites as (type, di, dj).
+_DOWN_THROUGH = {0: ((1, -1, 0), (2, 0, -1)),      # A(R): B(R - a1), C(R - a2)
+                 1: ((0, 1, 0), (2, 1, -1)),       # B(R): A(R + a1), C(R + a1 - a2)
+                 2: ((0, 0, 1), (1, -1, 1))}       # C(R): A(R + a2), B(R - a1 + a2)
+
+
+def kagome_mode(geom, bid: int, cell, vertex: int):
+    """A mode (Sec. 2.3, "Modes") of a parallelogram Kagome block: the
+    up-triangle A, B, C of unit cell `cell` and the down-triangle through
+    its `vertex` (0 A, 1 B, 2 C), five sites holding each of the six bond
+    types of the three-site unit cell once.  Returns the local indices
+    (up-triangle first), or None when a site lies outside the block."""
+    blk = geom.blocks[bid]
+    i, j = cell
+    sites = [(t, i, j) for t in range(3)]
+    for (t, di, dj) in _DOWN_THROUGH[vertex]:
+        sites.append((t, i + di, j + dj))
+    if any(s not in blk.sites for s in sites):
+        return None
+    return [blk.sites.index(s) for s in sites]
+
+
+def bond_type(lat, t: int, k: int):
+    """The bond type of leg k of a type-t site: its two (type, slot) ends."""
+    t2, _, _, k2 = lat.neighbour(t, 0, 0, k)
+    return tuple(sorted(((t, k), (t2, k2))))

@@ -103,6 +103,8 @@ CORES = [
     ("kagome", (9, 3, 3), 0, ("cell", 4)),
     ("kagome", (12, 4, 4), 0, ("cell", 7)),
     ("kagome", (12, 4, 4), 2, ("cell", 12)),
+    ("kagome", (6, 2, 2), 0, ("mode", 2)),
+    ("kagome", (9, 3, 3), 1, ("mode", 0)),
     ("square", (8, 8, 4, 4), 0, [5, 6]),
     ("square", (8, 8, 4, 4), 3, [9, 10, 13]),
 ]
@@ -136,6 +138,9 @@ def test_core_plan_matches_oracle_bubbles(L, kind, args, block, core):
     if core == "cell":    # the up-triangle of the block's second unit cell
         i, j = b.sites[2][1:]
         core = [b.sites.index((t, i, j)) for t in range(3)]
+    elif isinstance(core, tuple) and core[0] == "mode":   # the first mode through this vertex
+        core = next(m for (t, i, j) in b.sites
+                    for m in [C.kagome_mode(geom, block, (i, j), core[1])] if m is not None)
     elif isinstance(core, tuple):   # the k-th complete up-triangle of the block
         cells = sorted({(i, j) for (t, i, j) in b.sites if all((u, i, j) in b.sites for u in range(3))})
         i, j = cells[core[1]]

@@ -316,3 +316,46 @@ def test_reduced_als_phi_never_increases_on_an_interior_bond():
     G = ite.gate(ite.heisenberg_h(), 0.3)
     _, a, b, hist = ite.bond_update(bb, 4, 1, G, 2, max_sweeps=8, reduced=True)
     assert all(hist[q + 1] <= hist[q] * (1 + 1e-10) + 1e-14 for q in range(len(hist) - 1))
+
+
+def test_kagome_modes_hold_every_bond_type_once_and_give_the_edges():
+    """Sec. 2.3, Modes: a mode holds each of the six bond types of the
+    three-site unit cell exactly once; contracting its other three sites into
+    the pMPS gives the Edge TN of each of its bonds, whose RDM equals the
+    bond core's and the one-bubble route's when nothing is truncated."""
+    geom = Geometry.kagome(6, 2, 2)
+    bb, _ = _bbp(geom, 2, 16, 7, 2)
+    bb.chi = 256
+    lat = geom.lattice
+    b = geom.blocks[0]
+    found = 0
+    for (t0, i, j) in b.sites:
+        for v in range(3):
+            mode = C.kagome_mode(geom, 0, (i, j), v)
+            if mode is None:
+                continue
+            found += 1
+            keys = [(0, q) for q in mode]
+            env = C.CoreEnv(bb, [(b.X, b.Y)], keys)
+            bonds = []
+            for a in range(5):
+                for c in range(a + 1, 5):
+                    shared = set(env.sites[keys[a]].labels) & set(env.sites[keys[c]].labels)
+                    if shared:
+                        s = env.sites[keys[a]].labels.index(next(iter(shared)))
+                        bonds.append((a, c, C.bond_type(lat, b.sites[mode[a]][0], s)))
+            assert len(bonds) == 6 and len({x[2] for x in bonds}) == 6
+            for (a, c, _) in bonds[:2]:
+                k1, k2 = keys[a], keys[c]
+                N, _, slots = env.edge(k1, k2)
+                r1, r2 = env.sites[k1], env.sites[k2]
+                jt = next(iter(set(r1.labels) & set(r2.labels)))
+                rho = C.edge_rdm(N, slots, 2, 2, 2, bb.tc[r1.gid], bb.tc[r2.gid],
+                                 r1.labels.index(jt), r2.labels.index(jt))
+                direct = C.CoreEnv(bb, [(b.X, b.Y)], [k1, k2]).rdm([k1, k2])
+                assert np.abs(rho - direct).max() < 1e-11
+                assert np.abs(rho - bb.rdm([k1, k2], [(b.X, b.Y)])).max() < 1e-11
+            break
+        if found >= 2:
+            break
+    assert found >= 2
