@@ -148,3 +148,14 @@ def test_ite_rejects_cross_block_bonds_and_mixed_modes():
         assert ei.value.status == 1
     finally:
         P.bbp_destroy(ctx)
+    t = syn.gaussian_peps(36, 2, 2, seed=1)
+    ctx = P.bbp_create_peps(P.SQUARE, 6, 6, 0, 2, 2, t)
+    try:
+        P.bbp_partition_blocks(ctx, 3, 3)
+        P.bbp_set_options(ctx, 8, P.TF32)
+        P.bbp_init_messages(ctx, syn.initial_edge_matrices(36, 2, seed=2))
+        with pytest.raises(P.BBPError) as ei:       # the ITE update runs in the FP64 mode only
+            P.bbp_ite_bond(ctx, 7, 1, G)
+        assert ei.value.status == 1
+    finally:
+        P.bbp_destroy(ctx)
