@@ -314,8 +314,9 @@ def bbp_core_expect(ctx, block: int, core_sites, ops):
     """<O_k> for operator sets ops[k] = [O_site0, (O_site1)] (d x d each) on a
     core of one site or of a bond's two ends; returns a complex array."""
     s = np.ascontiguousarray(core_sites, dtype=np.int32)
-    o = _c128(np.asarray(ops, dtype=np.complex128).reshape(len(ops), len(s), -1))
     nops = len(ops)
+    o = _c128(np.asarray(ops, dtype=np.complex128).reshape(nops, len(s), -1) if nops
+              else np.zeros(1, dtype=np.complex128))
     re = np.zeros(max(nops, 1))
     im = np.zeros(max(nops, 1))
     _check(lib().bbp_core_expect(ctx, block, _iptr(s), len(s), _dptr(o), nops, _dptr(re), _dptr(im)), ctx)
