@@ -36,7 +36,6 @@ from __future__ import annotations
 import numpy as np
 
 from . import tn
-from .exact import contract_network
 from .geometry import BOTTOM, TOP
 from .region import build_region
 
@@ -152,7 +151,7 @@ class CoreEnv:
     def value(self, ops=None):
         """Step 3: (logscale, Z) of the core with operators ops[(inst, local)]
         inserted, contracted exactly with the pMPS."""
-        return self.logscale, contract_network(self.pmps_items() + self.core_items(ops))
+        return self.logscale, complex(contract_open(self.pmps_items() + self.core_items(ops), []))
 
     def expect(self, ops):
         _, z0 = self.value()
@@ -203,10 +202,28 @@ class CoreEnv:
 def contract_open(items, open_labels):
     """Dense contraction of labelled arrays, leaving ``open_labels`` (each on
     exactly one array) as the result's axes in that order; every other label
-    appears on exactly two arrays."""
+    appears on exactly two arrays.  The arrays are taken one at a time,
+    each time the one connected to what is already contracted that leaves
+    the smallest intermediate (an order only: the contraction is exact)."""
+    pending = list(items)
     Bt = np.ones((), dtype=np.complex128)
     labels: list = []
-    for X, lx in items:
+    while pending:
+        best, best_size = 0, None
+        for n, (X, lx) in enumerate(pending):
+            shared = [l for l in lx if l in labels]
+            if labels and not shared:
+                continue
+            size = 1
+            for q, l in enumerate(labels):
+                if l not in shared:
+                    size *= Bt.shape[q]
+            for q, l in enumerate(lx):
+                if l not in shared:
+                    size *= X.shape[q]
+            if best_size is None or size < best_size:
+                best, best_size = n, size
+        X, lx = pending.pop(best)
         shared = [l for l in lx if l in labels]
         Bt = np.tensordot(Bt, X, axes=([labels.index(l) for l in shared], [lx.index(l) for l in shared]))
         labels = [l for l in labels if l not in shared] + [l for l in lx if l not in shared]

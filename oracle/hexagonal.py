@@ -7,6 +7,8 @@ cells, N_T = 3(3N^2 - 3N + 1) sites (21 for N = 2, 57 for N = 3).  It has six
 faces, named counter-clockwise from the bottom: D, DR, UR, U, UL, DL; every
 edge leaving one face enters the opposite face of one neighbouring block.
 The block is contracted towards each of its six faces with its own order.
+HexCoreEnv extracts a core of the hexagonal block (Sec. 2.3, "Core"), e.g.
+the three unit cells around a down-triangle that hold the three "modes".
 
 Readings (the thesis draws the block and two of the six orders only):
 * cells (i, j) sit at i a1 + j a2; the hexagonal distance of (i, j) is
@@ -33,6 +35,7 @@ import numpy as np
 
 from . import tn
 from .blockbp import message_distance, normalise_message
+from .core import CoreEnv, zipper
 from .geometry import Edge, Lattice
 
 FACE_NAMES = ("D", "DR", "UR", "U", "UL", "DL")
@@ -228,22 +231,32 @@ def _angle(a4, b4) -> float:
     return math.atan2(by - ay, bx - ax) % (2.0 * math.pi)
 
 
-def hex_sweep(geom: HexGeometry, b: int, out: int, T: dict, msgs: dict, chi: int, trace: list | None = None):
+def hex_sweep(geom: HexGeometry, b: int, out: int, T: dict, msgs: dict, chi: int, trace: list | None = None,
+              skip=None, stop=None, raw: bool = False):
     """Contract block b with its incoming messages on every face but `out`
     towards face `out` (boundary MPS, truncation chi).  T[local] fused site
     tensors (slot order); msgs[f] the incoming MPS on face f, canonical
-    order.  Returns (mps over the out face in canonical order, logscale)."""
+    order.  Returns (mps over the out face in canonical order, logscale).
+
+    Side-chain bonds carry their physical names (("mb", f, q): the bond
+    before canonical tensor q of face f's message; ("mj", f, g): the joint
+    of two faces' messages), so that two sweeps of one block name shared
+    bonds alike.  skip / stop / raw as in tn.sweep: sites never swallowed,
+    the key at which the bubble halts, and the boundary returned as it
+    stands (tensors, labels, logscale)."""
     blk = geom.blocks[b]
     sites = _region(geom, b)
     start = (out + 3) % 6
     sides = {"lo": [(out + 2) % 6, (out + 1) % 6], "hi": [(out + 4) % 6, (out + 5) % 6]}
     nodes = []
     for rs in sites:
+        if skip and rs.local in skip:
+            continue
         legs = [(rs.labels[k], _angle(rs.pos4, rs.nbr_pos4[k])) for k in range(4)]
         nodes.append((_key(out, rs.pos4), "site", (rs, legs)))
-    kchain = {}
+    ends = {}
     for side, faces in sides.items():
-        chain = []                                    # (edge, tensor (prev, p, next)) from the start side
+        chain = []                 # (edge, tensor (prev, p, next), prev label, next label) from the start side
         for f in faces:
             edges = blk.faces[f].edges
             tens = msgs[f]
@@ -253,10 +266,16 @@ def hex_sweep(geom: HexGeometry, b: int, out: int, T: dict, msgs: dict, chi: int
                 order.reverse()
             for q in order:
                 a = np.asarray(tens[q])
-                chain.append((edges[q], a if forward else a.transpose(2, 1, 0)))
+                pl, nl = (("mb", f, q), ("mb", f, q + 1)) if forward else (("mb", f, q + 1), ("mb", f, q))
+                chain.append([edges[q], a if forward else a.transpose(2, 1, 0), pl, nl])
+        for m in range(len(chain) - 1):                # the joint of two faces' messages
+            if chain[m][3][1] != chain[m + 1][2][1]:
+                jl = ("mj",) + tuple(sorted((chain[m][3][1], chain[m + 1][2][1])))
+                chain[m][3] = jl
+                chain[m + 1][2] = jl
         K = len(chain)
-        kchain[side] = K
-        for m, (e, a) in enumerate(chain):
+        ends[side] = (chain[0][2], chain[-1][3])
+        for m, (e, a, pl, nl) in enumerate(chain):
             mid = e.mid4
             prv = chain[m - 1][0].mid4 if m > 0 else None
             nxt = chain[m + 1][0].mid4 if m < K - 1 else None
@@ -264,8 +283,7 @@ def hex_sweep(geom: HexGeometry, b: int, out: int, T: dict, msgs: dict, chi: int
                 prv = (2 * mid[0] - nxt[0], 2 * mid[1] - nxt[1]) if nxt is not None else (mid[0], mid[1] - 1)
             if nxt is None:
                 nxt = (2 * mid[0] - prv[0], 2 * mid[1] - prv[1])
-            legs = [(("b", side, m), _angle(mid, prv)), (("x", e.site, e.slot), _angle(mid, e.inner4)),
-                    (("b", side, m + 1), _angle(mid, nxt))]
+            legs = [(pl, _angle(mid, prv)), (("x", e.site, e.slot), _angle(mid, e.inner4)), (nl, _angle(mid, nxt))]
             nodes.append((_key(out, mid), "msg", (a, legs)))
     nodes.sort(key=lambda z: z[0])
 
@@ -279,7 +297,7 @@ def hex_sweep(geom: HexGeometry, b: int, out: int, T: dict, msgs: dict, chi: int
         lab = list(reversed(lab))
     one = np.ones((1, 1, 1), dtype=np.complex128)
     A = [one] + [np.array(a, dtype=np.complex128) for a in st] + [one]
-    labels = [("b", "lo", 0)] + lab + [("b", "hi", 0)]
+    labels = [ends["lo"][0]] + lab + [ends["hi"][0]]
     for p in range(len(A) - 1, 0, -1):
         A[p - 1], A[p] = tn.lq_left(A[p - 1], A[p])
     c = 0
@@ -296,6 +314,8 @@ def hex_sweep(geom: HexGeometry, b: int, out: int, T: dict, msgs: dict, chi: int
 
     normalise()
     for key, kind, payload in nodes:
+        if stop is not None and key >= stop:
+            break
         if kind == "site":
             rs, legs = payload
             X = T[rs.local]
@@ -361,12 +381,14 @@ def hex_sweep(geom: HexGeometry, b: int, out: int, T: dict, msgs: dict, chi: int
             labels[i:j + 1] = new_labels
             c = i + nout - 1
         normalise()
+    if raw:
+        return A, labels, logscale
     out_edges = blk.faces[out].edges
     want = [("x", e.site, e.slot) for e in out_edges]
     out_fwd = len(out_edges) < 2 or _key(out, out_edges[-1].mid4)[1] > _key(out, out_edges[0].mid4)[1]
     if not out_fwd:
         want = list(reversed(want))
-    if labels[0] != ("b", "lo", kchain["lo"]) or labels[-1] != ("b", "hi", kchain["hi"]) or labels[1:-1] != want:
+    if labels[0] != ends["lo"][1] or labels[-1] != ends["hi"][1] or labels[1:-1] != want:
         raise tn.SweepError("final boundary does not match the out face")
     first = A[0].reshape(1, -1)
     A[1] = np.tensordot(first, A[1], axes=(1, 0))
@@ -391,6 +413,7 @@ class HexBlockBP:
         self.chi = chi
         self.t = np.asarray(tensors, dtype=np.complex128)
         self.d, self.D = self.t.shape[1], self.t.shape[2]
+        self.tc = {g: self.t[g] for g in range(geom.n_sites)}     # (periodic: no open legs)
         self.T = {g: tn.fuse(self.t[g]) for g in range(geom.n_sites)}
         self.msgs = {}
 
@@ -442,3 +465,31 @@ class HexBlockBP:
         l0, z0 = self.contract(b)
         l1, z1 = self.contract(b, ops)
         return z1 / z0 * math.exp(l1 - l0)
+
+
+class HexCoreEnv(CoreEnv):
+    """The core of a hexagonal block with its pMPS (Sec. 2.3, "Core"): the
+    bubbles start from the bottom (D) and top (U) faces, the bottom one
+    swallowing every node before the core's last site in the bottom-up
+    order, the top one every node after it; the zipper joins them (see
+    core.zipper).  Values, RDMs and Edge TNs as for CoreEnv; sites are keyed
+    by their local index in the block."""
+
+    def __init__(self, bbp: HexBlockBP, b: int, core_locals):
+        self.bbp = bbp
+        self.core = list(core_locals)
+        geom = bbp.geom
+        blk = geom.blocks[b]
+        self.sites = {rs.local: rs for rs in _region(geom, b)}
+        if not self.core or any(q not in self.sites for q in self.core):
+            raise ValueError("core sites must be sites of the block")
+        last = max(self.core, key=lambda q: _key(3, blk.pos4[q]))
+        p4 = blk.pos4[last]
+        T = bbp.block_T(b)
+        msgs = {f: bbp.msgs[(b, f)] for f in range(6)}
+        skip = set(self.core)
+        B, LB, lsB = hex_sweep(geom, b, 3, T, msgs, bbp.chi, skip=skip, stop=_key(3, p4), raw=True)
+        Tt, LT, lsT = hex_sweep(geom, b, 0, T, msgs, bbp.chi, skip=skip, stop=_key(0, p4), raw=True)
+        self.pmps = zipper(B, LB, Tt, LT)
+        self.logscale = lsB + lsT
+        self.parts = (B, LB, Tt, LT)

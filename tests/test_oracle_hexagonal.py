@@ -161,3 +161,80 @@ def test_dimer_covering_hexagonal():
             else:
                 assert abs(e) < 1e-12
     assert n_dimer > 0
+
+
+def _hex_env(chi=4096):
+    from oracle.hexagonal import HexBlockBP
+    g = HexGeometry(2, 7, 7)
+    n = g.n_sites
+    bb = HexBlockBP(g, syn.gaussian_peps(n, 2, 2, seed=3), chi=chi)
+    bb.init_messages(syn.initial_edge_matrices(n, 2, seed=4))
+    bb.step()
+    return g, bb
+
+
+def test_hexagonal_core_route_is_exact():
+    """Sec. 2.3, Core, in the hexagonal block: two bubbles from the D and U
+    faces around a core, joined by the zipper, give exactly the block's value
+    with operators on the core (chi above every rank): one site, a bond, the
+    centre unit cell, three unit cells."""
+    from oracle.hexagonal import HexCoreEnv
+    g, bb = _hex_env()
+    b = g.blocks[0]
+    ci, cj = b.centre
+
+    def cell(i, j):
+        return [b.sites.index((t, ci + i, cj + j)) for t in (2, 0, 1)]
+
+    for core in (cell(0, 0)[:1], cell(0, 0)[:2], cell(0, 0), cell(0, 0) + cell(1, 0) + cell(1, -1)):
+        env = HexCoreEnv(bb, 0, core)
+        for q in core[:3]:
+            assert abs(env.expect({q: SZ}) - bb.expect(0, {q: SZ})) < 1e-12
+
+
+def test_hexagonal_core_of_three_cells_and_its_modes():
+    """The core of three unit cells around a down-triangle (Sec. 2.3, Core,
+    Modes): the three up-triangle bond types appear three times and the three
+    down-triangle types once; it holds three modes (an up-triangle and the
+    shared down-triangle), each holding every one of the six bond types
+    once; from a mode the Edge TN of each of its bonds follows by exact
+    contraction and gives the bond's RDM."""
+    from oracle import core as C
+    from oracle.hexagonal import HexCoreEnv
+    g, bb = _hex_env()
+    lat = g.lattice
+    b = g.blocks[0]
+    ci, cj = b.centre
+    cells = [(ci, cj), (ci + 1, cj), (ci + 1, cj - 1)]
+    core = [b.sites.index((t, i, j)) for (i, j) in cells for t in range(3)]
+    env = HexCoreEnv(bb, 0, core)
+    count = {}
+    for x in range(len(core)):
+        for y in range(x + 1, len(core)):
+            shared = set(env.sites[core[x]].labels) & set(env.sites[core[y]].labels)
+            for lab in shared:
+                s = env.sites[core[x]].labels.index(lab)
+                ty = C.bond_type(lat, b.sites[core[x]][0], s)
+                count[ty] = count.get(ty, 0) + 1
+    ref = GOLDEN["kagome_core_three_cells"]
+    assert sorted(count.values()) == ref["bond_multiplicities"]
+    modes = [C.kagome_mode(g, 0, cells[0], 1), C.kagome_mode(g, 0, cells[1], 0), C.kagome_mode(g, 0, cells[2], 2)]
+    assert len(modes) == ref["modes"]
+    for mode in modes:
+        assert mode is not None and set(mode) <= set(core)
+        types = set()
+        for x in range(5):
+            for y in range(x + 1, 5):
+                shared = set(env.sites[mode[x]].labels) & set(env.sites[mode[y]].labels)
+                for lab in shared:
+                    types.add(C.bond_type(lat, b.sites[mode[x]][0], env.sites[mode[x]].labels.index(lab)))
+        assert len(types) == ref["bond_types_per_mode"]
+    mode = modes[0]
+    menv = HexCoreEnv(bb, 0, mode)
+    k1, k2 = mode[0], mode[1]
+    N, _, slots = menv.edge(k1, k2)
+    r1, r2 = menv.sites[k1], menv.sites[k2]
+    jt = next(iter(set(r1.labels) & set(r2.labels)))
+    rho = C.edge_rdm(N, slots, 2, 2, 2, bb.tc[r1.gid], bb.tc[r2.gid], r1.labels.index(jt), r2.labels.index(jt))
+    direct = HexCoreEnv(bb, 0, [k1, k2]).rdm([k1, k2])
+    assert np.abs(rho - direct).max() < 1e-12
