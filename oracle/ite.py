@@ -15,7 +15,10 @@ Ch. 3.  One ITE step on a bond (i, j) (Sec. 3.2, "ITE update step"):
 Full ITE (Alg. 2): for every time step, for every bond of the block: run
 BlockBP, take the bond's Edge TN, update the two tensors by ALS, put them
 back; the bonds are visited forwards and then backwards with half steps
-(second-order Trotter splitting).
+(second-order Trotter splitting).  full_ite_unit_cell is the Kagome form of
+Sec. 3.3: one unit cell's three tensors repeated over the lattice, the six
+bonds of a mode updated, the new tensors copied to every site of their
+type (the thesis' random block rotations and mode shuffling are left out).
 
 Readings:
 * the start of ALS is the truncated SVD of the evolved two-site tensor
@@ -287,3 +290,59 @@ def full_ite(geom, t: np.ndarray, chi: int, dts, edge_mats, h=None, bp_tol: floa
         if on_step is not None:
             on_step(dt, e)
     return t, energies
+
+
+def full_ite_unit_cell(geom, t_cell: np.ndarray, chi: int, dts, edge_mats, h=None, bp_tol: float = 1e-10,
+                       bp_iter: int = 40, als_sweeps: int = 50, on_step=None, reduced: bool = False):
+    """Alg. 2 for a translation-invariant Kagome PEPS (Sec. 3.3): every site of
+    type t (A, B, C) carries the unit cell's tensor t_cell[t]; each time step
+    updates the six bonds of the unit cell (the up-triangle and the
+    down-triangle through it, a mode of block 0, forwards then backwards,
+    half steps), each on its bond inside the mode with the Edge TN of the
+    converged messages, and writes the two new tensors into every site of
+    their types.  Returns (t_cell, energy per site after each step)."""
+    from .core import kagome_mode
+    t_cell = np.array(t_cell, dtype=np.complex128)
+    D = t_cell.shape[2]
+    h = heisenberg_h() if h is None else h
+    lat = geom.lattice
+    b0 = geom.blocks[0]
+    mode = next(m for (t, i, j) in b0.sites for v in range(3)
+                for m in [kagome_mode(geom, 0, (i, j), v)] if m is not None)
+    bonds = []
+    for x in range(5):
+        for k in range(4):
+            t_, i, j = b0.sites[mode[x]]
+            t2, i2, j2, _ = lat.neighbour(t_, i, j, k)
+            if (t2, i2, j2) in [b0.sites[q] for q in mode[x + 1:]]:
+                bonds.append((b0.gids[mode[x]], k))
+    msgs = None
+    energies = []
+
+    def full():
+        return np.array([t_cell[g % 3] for g in range(geom.n_sites)])
+
+    def converged():
+        nonlocal msgs
+        bbp = BlockBP(geom, full(), chi)
+        bbp.init_messages(edge_mats)
+        if msgs is not None:
+            bbp.msgs = dict(msgs)
+        bbp.run(bp_tol, bp_iter)
+        msgs = dict(bbp.msgs)
+        return bbp
+
+    for dt in dts:
+        G = gate(h, 0.5 * dt)
+        for (g1, k1) in bonds + bonds[::-1]:
+            bbp = converged()
+            g2, a, b, _ = bond_update(bbp, g1, k1, G, D, als_sweeps, reduced)
+            for g, x in ((g1, a), (g2, b)):
+                tmp = np.zeros((1,) + t_cell.shape[1:], dtype=np.complex128)
+                _put(tmp, 0, x)
+                t_cell[g % 3] = tmp[0]
+        e = converged().energy_per_site()
+        energies.append(e)
+        if on_step is not None:
+            on_step(dt, e)
+    return t_cell, energies

@@ -359,3 +359,23 @@ def test_kagome_modes_hold_every_bond_type_once_and_give_the_edges():
         if found >= 2:
             break
     assert found >= 2
+
+
+def test_unit_cell_ite_lowers_the_kagome_energy():
+    """Alg. 2 with a translation-invariant unit cell (Sec. 3.3): the six bonds
+    of a mode are updated and their tensors copied to every site of their
+    type; imaginary time lowers the energy per site of the Kagome super-cell
+    (D = 2, from one cell of a dimer covering plus noise), and the energy
+    stays above the rigorous bound -1/2 (every triangle's energy is at least
+    -3/4, and there are two triangles per three sites)."""
+    geom = Geometry.kagome(6, 2, 2)
+    nb = syn.kagome_neighbours(6, 2)
+    t_cell = syn.dimer_singlet_peps(nb, 2, 2, seed=2, noise=1e-2, noise_seed=3)[:3]
+    em = syn.initial_edge_matrices(geom.n_sites, 2, seed=7)
+    bb = BlockBP(geom, np.array([t_cell[g % 3] for g in range(geom.n_sites)]), chi=8)
+    bb.init_messages(em)
+    bb.run(1e-8, 40)
+    e0 = bb.energy_per_site().real
+    tc, E = ite.full_ite_unit_cell(geom, t_cell, 8, [0.2, 0.2], em, bp_tol=1e-8, als_sweeps=10)
+    assert E[0].real < e0 and E[1].real < E[0].real
+    assert E[-1].real > -0.5
